@@ -1,0 +1,128 @@
+"""Pins for the ADMM / L-BFGS solver pieces (eq. 18-24) of the oracle."""
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import tlr_synth as synth
+from oracle import benchmark, layout, operator, solver
+from tests._cases import problem
+
+
+def _as_real(z):
+    return np.concatenate([z.real, z.imag])
+
+
+def _as_cplx(x):
+    n = x.size // 2
+    return x[:n] + 1j * x[n:]
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.1, 10.0])
+def test_prox_of_squared_frobenius_norm(lam):
+    # eq. (21)-(22): prox_{lam ||.||^2}(V) = V / (1 + 2 lam), checked by numeric argmin
+    V = synth.cn(synth.rng(1), 6)
+    obj = lambda x: lam * np.sum(x ** 2) + 0.5 * np.sum((x - _as_real(V)) ** 2)  # noqa: E731
+    num = _as_cplx(minimize(obj, np.zeros(12), tol=1e-14, method="BFGS").x)
+    np.testing.assert_allclose(num, V / (1 + 2 * lam), atol=1e-7)
+
+
+@pytest.mark.parametrize("lam,rho", [(0.1, 1.0), (10.0, 1.0), (1.0, 0.3)])
+def test_z_update(lam, rho):
+    # eq. (20) and (23): argmin_z lam||z||^2 + rho/2 ||x - z + u||^2 = (x + u)/(1 + 2 lam/rho)
+    x = synth.cn(synth.rng(2), 5)
+    u = synth.cn(synth.rng(3), 5)
+    obj = lambda zr: lam * np.sum(zr ** 2) + 0.5 * rho * np.sum((_as_real(x + u) - zr) ** 2)  # noqa: E731
+    num = _as_cplx(minimize(obj, np.zeros(10), tol=1e-14, method="BFGS").x)
+    np.testing.assert_allclose(num, (x + u) / (1 + 2 * lam / rho), atol=1e-7)
+
+
+def test_quartic_argmin_known_polynomial():
+    # phi(a) = (a-2)^2 (a+1)^2 = a^4 - 2a^3 - 3a^2 + 4a + 4: minimisers a=2 and a=-1, max at 0.5
+    c = [4.0, 4.0, -3.0, -2.0, 1.0]
+    assert abs(solver.quartic_argmin(c) - 2.0) < 1e-14
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_quartic_argmin_vs_grid(seed):
+    g = np.random.default_rng(seed)
+    c = g.standard_normal(5)
+    c[4] = abs(c[4]) + 0.1
+    c[1] = -abs(c[1]) - 0.05          # descent at 0
+    a = solver.quartic_argmin(c)
+    grid = np.linspace(1e-6, 20, 400001)
+    vals = c[0] + grid * (c[1] + grid * (c[2] + grid * (c[3] + grid * c[4])))
+    assert solver.quartic_eval(c, a) <= vals.min() + 1e-9
+
+
+def test_quadratic_case_is_a_line_minimum():
+    # c3 = c4 = 0 (all tiles dense): a* = -c1 / (2 c2)
+    c = [1.0, -3.0, 2.0, 0.0, 0.0]
+    assert abs(solver.quartic_argmin(c) - 0.75) < 1e-15
+
+
+def test_two_loop_secant_equation():
+    # the L-BFGS inverse-Hessian maps the newest y to the newest s
+    g = np.random.default_rng(0)
+    S = [synth.cn(synth.rng(s), 7) for s in range(3)]
+    A = g.standard_normal((14, 14))
+    A = A @ A.T + 14 * np.eye(14)
+    Y = [_as_cplx(A @ _as_real(s)) for s in S]
+    d = solver.two_loop(Y[-1], S, Y)
+    np.testing.assert_allclose(-d, S[-1], rtol=1e-12, atol=1e-12)
+
+
+def test_lbfgs_exact_line_search_is_finite_on_quadratic():
+    # one dense 4x4 tile and rho = 0: f is a convex quadratic in Z; the iterates
+    # stay symmetric (grad Z = W'/2), 20 real unknowns, so L-BFGS with the exact
+    # line search (CG-like on a quadratic) reaches the minimiser well within 40 steps
+    D, U, perm, lay, _ = problem(2, 2, 4, 0, "dense", ns=12, snr_db=0, planted=False)
+    Dh, Uh, _ = operator.normalise(D, U, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    th0 = np.zeros(lay.size, np.complex128)
+    th, f, gf = solver.lbfgs(prob, th0, np.zeros_like(th0), 0.0, 40, 50)
+    Zs = benchmark.solve_eq4(Dh, Uh, 0.0 + 1e-300)
+    Xs = 0.5 * (Zs + Zs.T)
+    Xh = operator.assemble_xh(th, lay)
+    assert np.linalg.norm(Xh - Xs) <= 1e-9 * np.linalg.norm(Xs)
+
+
+def test_admm_reaches_benchmark_minimiser_for_one_dense_tile():
+    # N = 1 dense diagonal: f + g of eq. (16) is exactly eq. (4); ADMM's fixed
+    # point is its minimiser, the solution of the normal equations (CG, 1e-14)
+    D, U, perm, lay, _ = problem(4, 2, 8, 0, "dense", ns=16, snr_db=10, planted=False)
+    Dh, Uh, _ = operator.normalise(D, U, perm)
+    lam = 0.1
+    Zs = benchmark.solve_eq4(Dh, Uh, lam)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    opts = solver.SolveOpts(lam0=lam, decay=1.0, stages=1, rho=1.0, admm_iters=400,
+                            lbfgs_iters=30, memory=20)
+    th, z, u, st = solver.admm(prob, np.zeros(lay.size, np.complex128), opts)
+    Z = th.reshape(8, 8)
+    assert np.linalg.norm(Z - Zs) <= 1e-6 * np.linalg.norm(Zs)
+    assert np.linalg.norm(th - z) <= 1e-6 * np.linalg.norm(z)
+
+
+def test_planted_recovery_noise_free():
+    # nr = 64 (8x8 grid), b = 16, k = 2, lambda = rho = 0: from the truth + 5%
+    # the solver recovers X to better than 1e-6 (the data are exact)
+    D, U, perm, lay, th_true = problem(8, 8, 16, 2, "lowrank", seed=4)
+    U = (D.astype(np.complex128) @ operator.unpermute(operator.assemble_xh(th_true, lay), perm))
+    Dh, Uh, _ = operator.normalise(D, U, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    th0 = th_true + 0.05 * np.abs(th_true).mean() * synth.cn(synth.rng(8), lay.size)
+    th, f, gf = solver.lbfgs(prob, th0, np.zeros_like(th0), 0.0, 400, 10)
+    X = operator.assemble_xh(th, lay)
+    Xt = operator.assemble_xh(th_true, lay)
+    assert np.linalg.norm(X - Xt) <= 1e-6 * np.linalg.norm(Xt)
+
+
+def test_config0_style_solve_runs_and_decreases():
+    D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
+    Dh, Uh, _ = operator.normalise(D, U, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    th0 = np.zeros(lay.size, np.complex128)
+    th0 += 0.01 * synth.cn(synth.rng(99), lay.size)
+    th, z, u, st = solver.admm(prob, th0)
+    assert st.iters == 30
+    f0 = operator.misfit(th0, lay, Dh, Uh)
+    assert st.f_hist[-1] < 0.5 * f0
