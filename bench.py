@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Frequency-solve throughput of reciprocity-aware TLR MDD on GB300.
+
+Workload (the plain-method batched-frequency configuration): nr = ns = 4096
+receivers / sources on a 64 x 64 grid (Hilbert-reordered), 64 frequencies,
+tile 256, off-diagonal rank rising linearly 4 -> 48 with frequency, low-rank
+diagonal tiles (rank < tile/4), D(w) = Q diag(sigma e^{i phi_w}) W^H with sigma
+decaying 1 -> 1e-3, U = D X + complex Gaussian noise at 10 dB SNR, X a planted
+symmetric TLR Green's function.  One step = one frequency solve (30 L-BFGS
+iterations: 3 lambda stages x 2 ADMM iterations x 5) for every frequency,
+inputs resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (the only place besides the cpu_baseline leg that runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NR = 4096
+GRID = (64, 64)
+NFREQ = 64
+TILE = 256
+RANK_LO, RANK_HI = 4, 48
+SNR_DB = 10.0
+ITERS_PER_SOLVE = 30
+FP32_LANES_PER_SM, SMS, SM_MAX_MHZ = 128, 152, 2070.0
+
+
+def rank_of(f, nfreq):
+    if nfreq == 1:
+        return RANK_LO
+    return RANK_LO + int(math.floor((RANK_HI - RANK_LO) * f / (nfreq - 1) + 0.5))
+
+
+def flops_per_iter(nr, ns, tile, k):
+    """Algorithmic flops of one L-BFGS iteration (8 real flops per complex MAC):
+    compress of the direction and of the residual (8 + 8), the two line-search
+    expands (16 + 8) and the gradient projection (16), all x ns x n_LR."""
+    n = nr // tile
+    n_lr = n * n * tile * k
+    return 56.0 * ns * n_lr
+
+
+def flops_per_solve(nr, ns, tile, k, iters=ITERS_PER_SOLVE):
+    n = nr // tile
+    n_lr = n * n * tile * k
+    return iters * flops_per_iter(nr, ns, tile, k) + 40.0 * ns * n_lr
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# synthetic workload on the device (input generation only)
+# ---------------------------------------------------------------------------
+def make_workload(T, torch, nfreq, seed, device):
+    """D, U stacks (paper layout, complex64) and start points theta0 per frequency."""
+    g = torch.Generator(device=device).manual_seed(seed)
+    n = NR
+
+    def cn(shape):
+        re = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+        im = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+        return torch.complex(re, im) * (1.0 / math.sqrt(2.0))
+
+    def haar(m):
+        q, r = torch.linalg.qr(cn((m, m)))
+        d = torch.diagonal(r)
+        return q * (d / d.abs())[None, :]
+
+    Q, W = haar(n), haar(n)
+    sig = torch.pow(10.0, -3.0 * torch.arange(n, device=device, dtype=torch.float32) / (n - 1))
+    perm = torch.empty(n, dtype=torch.int32, device=device)
+    T.tlr_mdd_hilbert_perm(GRID[0], GRID[1], perm)
+    inv = torch.empty_like(perm)
+    inv[perm.long()] = torch.arange(n, dtype=torch.int32, device=device)
+    D = torch.empty((nfreq, n, n), dtype=torch.complex64, device=device)
+    U = torch.empty_like(D)
+    thetas, descs, ranks = [], [], []
+    b = TILE
+    N = n // b
+    pairs = [(i, j) for j in range(N) for i in range(j + 1, N)]
+    for f in range(nfreq):
+        k = rank_of(f, nfreq)
+        ranks.append(k)
+        ph = torch.exp(2j * math.pi * torch.rand(n, generator=g, device=device)).to(torch.complex64)
+        D[f] = (Q * (sig * ph)[None, :]) @ W.conj().T
+        # planted X_h (Hilbert order) from random factors, then X = S X_h S^T
+        Xh = torch.zeros((n, n), dtype=torch.complex64, device=device)
+        for i in range(N):
+            Qi = cn((b, k)) / math.sqrt(b * k)
+            Xh[i * b:(i + 1) * b, i * b:(i + 1) * b] = Qi @ Qi.T
+        for (i, j) in pairs:
+            s = 1.0 / ((1 + abs(i - j)) * math.sqrt(b * k))
+            L, R = cn((b, k)) * s, cn((b, k)) * s
+            t = L @ R.T
+            Xh[i * b:(i + 1) * b, j * b:(j + 1) * b] = t
+            Xh[j * b:(j + 1) * b, i * b:(i + 1) * b] = t.T
+        X = Xh[inv.long()][:, inv.long()]
+        Y = D[f] @ X
+        nz = cn((n, n))
+        scale = Y.norm() / nz.norm() * 10 ** (-SNR_DB / 20)
+        U[f] = Y + scale * nz
+        d = T.desc(n, n, b, rank=k, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE)
+        descs.append(d)
+        nth = T.tlr_mdd_theta_size(d)
+        th0 = cn((nth,)) * (0.1 / math.sqrt(b * k))
+        thetas.append(th0)
+        del Xh, X, Y, nz
+    return D, U, thetas, descs, ranks
+
+
+def percentile(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))
+    return xs[i]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(D0, U0, k, lbfgs_iters):
+    """Time the FP64 oracle's TLR-structured solve on one frequency for a few
+    L-BFGS iterations; returns (seconds, iterations, theta, threads)."""
+    from oracle import hilbert, layout, operator, solver
+    perm = hilbert.perm(*GRID)
+    lay = layout.make_layout(NR, TILE, k, "rule")
+    Dh, Uh, alpha = operator.normalise(D0, U0, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    return prob, lay, perm, alpha
+
+
+def run_oracle(prob, th0, iters):
+    from oracle import solver
+    opts = solver.SolveOpts(stages=1, admm_iters=1, lbfgs_iters=iters)
+    t0 = time.perf_counter()
+    th, z, u, st = solver.admm(prob, th0, opts)
+    return time.perf_counter() - t0, th, st
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--freqs", type=int, default=NFREQ)
+    ap.add_argument("--seed", type=int, default=2412)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--oracle-iters", type=int, default=3)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    import paper_2412_14973_gb300 as T
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    nfreq = args.freqs
+    with torch.cuda.stream(stream):
+        D, U, th0, descs, ranks = make_workload(T, torch, nfreq, args.seed + 7919 * rank, dev)
+    torch.cuda.synchronize()
+    prec = T.TLR_PREC_FP32 if args.precision == "fp32" else T.TLR_PREC_BF16X3
+    for d in descs:
+        d.precision = prec
+    theta = [t.clone() for t in th0]
+    opts = T.solve_opts()
+    lat_ms = []
+
+    def step(record=False):
+        for f in range(nfreq):
+            h = T.tlr_mdd_create(descs[f], D[f], U[f], stream)
+            theta[f].copy_(th0[f])
+            st = T.tlr_mdd_solve(h, theta[f], opts)
+            if record:
+                lat_ms.append(st.gpu_ms)
+            T.tlr_mdd_destroy(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    T.tlr_mdd_timing_reset()
+    T.tlr_mdd_timing_enable(True)
+    n0 = T.tlr_mdd_launch_count()
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    T.tlr_mdd_timing_enable(False)
+    launches = T.tlr_mdd_launch_count() - n0
+    timing = T.tlr_mdd_timing_read()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    solves = nfreq * args.steps * world
+    value = solves / (ms / 1e3)
+    total_flops = sum(flops_per_solve(NR, NR, TILE, k) for k in ranks) * args.steps * world
+
+    # roofline of the dominant contraction kernel
+    names = ["cgemm_compress", "cgemm_expand", "cgemm_project"]
+    dom = max(range(len(timing)), key=lambda c: timing[c][0])
+    dms, dfl, dnl = timing[dom]
+    achieved = (dfl / max(1, dnl)) / (dms / max(1, dnl) / 1e3) / 1e12 if dnl else 0.0
+    peak_alu = FP32_LANES_PER_SM * SMS * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
+            "peak": round(peak_alu, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4),
+            "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
+            "per_class_ms": {names[c]: round(timing[c][0], 2) for c in range(len(timing))}}
+
+    # e2e through the C-ABI with host buffers (one timed step)
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.empty((nfreq, NR, NR), dtype=torch.complex64, pin_memory=True)
+        Uh = torch.empty_like(Dh, pin_memory=True)
+        Dh.copy_(D)
+        Uh.copy_(U)
+        th_h = [t.cpu().pin_memory() for t in th0]
+        out_h = [torch.empty_like(t) for t in th_h]
+        hd = []
+        for d in descs:
+            d2 = T.desc(d.nr, d.ns, d.tile, rank=d.rank, nx=d.nx, ny=d.ny, diag_mode=d.diag_mode,
+                        precision=d.precision, input_memory=T.TLR_MEM_HOST)
+            hd.append(d2)
+        hopts = T.solve_opts(theta_memory=T.TLR_MEM_HOST)
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            for f in range(nfreq):
+                h = T.tlr_mdd_create(hd[f], Dh[f], Uh[f], stream)
+                out_h[f].copy_(th_h[f])
+                T.tlr_mdd_solve(h, out_h[f], hopts)
+                T.tlr_mdd_destroy(h)
+                h2d += 2 * Dh[f].numel() * 8 + th_h[f].numel() * 8
+                d2h += out_h[f].numel() * 8
+
+        with torch.cuda.stream(stream):
+            e2e_step()  # warm
+            h2d = d2h = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
+        e2e = {"value": round(nfreq * world / te, 4), "unit": "freq-solves/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        f0 = 0
+        k0 = ranks[f0]
+        D0 = D[f0].cpu().numpy()
+        U0 = U[f0].cpu().numpy()
+        prob, lay, perm, alpha = oracle_sample(D0, U0, k0, args.oracle_iters)
+        th_start = th0[f0].cpu().numpy().astype(np.complex128)
+        secs, th_or, st_or = run_oracle(prob, th_start, args.oracle_iters)
+        # GPU with the same short schedule for the accuracy check
+        h = T.tlr_mdd_create(descs[f0], D[f0], U[f0], stream)
+        thg = th0[f0].clone()
+        T.tlr_mdd_solve(h, thg, T.solve_opts(stages=1, admm_iters=1, lbfgs_iters=args.oracle_iters))
+        T.tlr_mdd_destroy(h)
+        from oracle import operator
+        Xo = operator.assemble_xh(th_or, lay)
+        Xg = operator.assemble_xh(thg.cpu().numpy().astype(np.complex128), lay)
+        rel = float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo))
+        kmean = sum(ranks) / len(ranks)
+        per_solve = secs * (ITERS_PER_SOLVE / args.oracle_iters) * (kmean / k0)
+        cpu = {"value": round(1.0 / per_solve, 6), "unit": "freq-solves/s", "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": (f"frequency {f0} (rank {k0}), {args.oracle_iters} L-BFGS iterations of the FP64 "
+                          f"TLR-structured oracle in {secs:.1f} s, scaled to a {ITERS_PER_SOLVE}-iteration "
+                          f"solve at the mean rank {kmean:.1f} (work grows linearly with rank)")}
+        acc = {"frequency": f0, "iters": args.oracle_iters, "rel_err_X_vs_fp64_oracle": rel,
+               "within_1e-3": rel <= 1e-3}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "freq-solves/s", "value": round(value, 4), "unit": "freq-solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+        "data": "synthetic",
+        "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "
+                               "64 frequencies, tile 256, rank 4->48, low-rank diagonal, 10 dB SNR",
+                   "nr": NR, "ns": NR, "frequencies_per_gpu": nfreq, "tile": TILE,
+                   "ranks": f"{RANK_LO}->{RANK_HI} linear", "iters_per_solve": ITERS_PER_SOLVE,
+                   "precision": args.precision,
+                   "l2": "inputs larger than L2 (each 4096x4096 complex64 panel is 134 MB; 64 frequencies cycled)",
+                   "parallelism": f"frequency sharding x{world}"},
+        "gflops": round(total_flops / (ms / 1e3) / 1e9, 1),
+        "latency_ms": {"p50": percentile(lat_ms, 50), "p99": percentile(lat_ms, 99)},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches, "accuracy": acc,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, world, rank):
+    """The FP64 CPU oracle on this workload's config, a bounded sample per step."""
+    if rank != 0:
+        return
+    import tlr_synth as synth
+    from oracle import hilbert
+    k0 = rank_of(0, args.freqs)
+    # one frequency of the same recipe, generated on the host
+    D0 = synth.make_d(NR, NR, 1, args.seed, haar_max=1024)[0]
+    lay_perm = hilbert.perm(*GRID)
+    from oracle import layout, operator
+    lay = layout.make_layout(NR, TILE, k0, "rule")
+    th_true = synth.planted_theta(NR, TILE, k0, lay.dense, args.seed + 1)
+    X = operator.unpermute(operator.assemble_xh(th_true, lay), lay_perm)
+    Y = D0.astype(np.complex128) @ X
+    nz = synth.noise(Y.shape, args.seed + 2)
+    U0 = (Y + np.linalg.norm(Y) / np.linalg.norm(nz) * 10 ** (-SNR_DB / 20) * nz).astype(np.complex64)
+    prob, lay, perm, alpha = oracle_sample(D0, U0, k0, args.oracle_iters)
+    th0 = 0.1 * synth.planted_theta(NR, TILE, k0, lay.dense, args.seed + 3)
+    for _ in range(args.warmup):
+        run_oracle(prob, th0, args.oracle_iters)
+    t = 0.0
+    for _ in range(args.steps):
+        s, _, _ = run_oracle(prob, th0, args.oracle_iters)
+        t += s
+    ranks = [rank_of(f, args.freqs) for f in range(args.freqs)]
+    kmean = sum(ranks) / len(ranks)
+    per_solve = (t / args.steps) * (ITERS_PER_SOLVE / args.oracle_iters) * (kmean / k0)
+    v = 1.0 / per_solve
+    sample = (f"per step: frequency 0 (rank {k0}), {args.oracle_iters} L-BFGS iterations of the FP64 "
+              f"TLR-structured oracle, scaled to a {ITERS_PER_SOLVE}-iteration solve at mean rank {kmean:.1f}")
+    line = {"impl": "reference", "metric": "freq-solves/s", "value": round(v, 6), "unit": "freq-solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t / args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "
+                                   "64 frequencies, tile 256, rank 4->48, low-rank diagonal, 10 dB SNR",
+                       "nr": NR, "ns": NR, "frequencies_per_gpu": args.freqs, "tile": TILE},
+            "cpu_baseline": {"value": round(v, 6), "unit": "freq-solves/s", "cores": blas_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "freq-solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

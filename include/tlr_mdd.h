@@ -1,0 +1,208 @@
+/*
+ * tlr_mdd.h -- C ABI of the GB300 (sm_103a) library for reciprocity-aware
+ * tile low-rank (TLR) multidimensional deconvolution, arXiv 2412.14973.
+ *
+ * One handle holds one frequency's problem (eq. 2): D(w), U(w) in C^{ns x nr},
+ * unknown Green's function X = X^T in C^{nr x nr}.  The library reorders the
+ * receivers along a Hilbert curve (eq. 10-14), normalises by alpha
+ * (Hyper-parameter selection section), parametrises X_h by tiles (eq. 6-9) and
+ * evaluates the operator, its adjoint, the misfit (eq. 17a), the factor
+ * gradients (eq. 25-27) and the ADMM / L-BFGS solve (eq. 18-24) on the GPU.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (TLR_OK) on success, a negative TLR_ERR_* code otherwise; no
+ *     C++ exception crosses this boundary.  tlr_mdd_last_error() explains the
+ *     last failure on a handle (or the last handle-less failure with NULL).
+ *   - Complex numbers are complex64: interleaved (re, im) float pairs.
+ *   - All matrices are row-major.  "Receiver-major" matrices have one row per
+ *     receiver in Hilbert order (a = 0..nr-1) and one column per source.
+ *   - Buffers passed in are owned by the caller and are device pointers unless
+ *     a flag says host; the library never keeps a caller pointer past the call.
+ *     The library owns its reordered data panels and its workspace.
+ *   - Work is enqueued on the handle's stream; a call returns once its work is
+ *     enqueued, except where a result is written to host memory (then it
+ *     synchronises the stream first).
+ *   - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ */
+#ifndef TLR_MDD_H
+#define TLR_MDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TLR_OK               0
+#define TLR_ERR_ARG         -1  /* NULL or out-of-range argument */
+#define TLR_ERR_SHAPE       -2  /* nr % tile != 0, nx*ny != nr, rank outside [0, tile] */
+#define TLR_ERR_UNSUPPORTED -3  /* a valid option this build does not implement */
+#define TLR_ERR_NOMEM       -4  /* device allocation failed */
+#define TLR_ERR_CUDA        -5  /* a CUDA runtime call failed */
+#define TLR_ERR_NONFINITE   -6  /* NaN / Inf met in data or solver state */
+#define TLR_ERR_TIMEOUT     -7  /* a bounded device wait gave up */
+#define TLR_ERR_STATE       -8  /* call out of order (e.g. destroyed handle) */
+
+/* ---- precision of the complex contractions ---- */
+#define TLR_PREC_FP32   0  /* FP32 SIMT (CUDA cores), FP32 accumulation */
+#define TLR_PREC_BF16X3 1  /* tcgen05 tensor cores: BF16 hi/lo split (3 products), 3M complex, FP32 accumulation */
+
+/* ---- diagonal tile representation (eq. 6 / eq. 7) ---- */
+#define TLR_DIAG_RULE     0  /* dense iff k_ii >= tile/4 */
+#define TLR_DIAG_LOWRANK  1  /* every X_ii = Q_ii Q_ii^T */
+#define TLR_DIAG_DENSE    2  /* every X_ii = P Z_ii = (Z_ii + Z_ii^T)/2 */
+#define TLR_DIAG_PER_TILE 3  /* diag_dense[i] != 0 -> dense */
+
+/* ---- reciprocity constraint (Receivers re-ordering / eq. 9) ---- */
+#define TLR_RECIP_SYMMETRIC 0  /* X = X^T, super-diagonal tiles are plain transposes */
+#define TLR_RECIP_NONE      1  /* general TLR X: not implemented (TLR_ERR_UNSUPPORTED) */
+
+/* ---- where a buffer lives ---- */
+#define TLR_MEM_DEVICE 0
+#define TLR_MEM_HOST   1
+
+typedef struct tlr_mdd_s tlr_mdd_t;
+
+/* Problem description (Theory section, eq. 2; Tile Low-rank MDD section). */
+typedef struct {
+    int64_t nr;              /* receivers (= virtual sources); X is nr x nr */
+    int64_t ns;              /* sources (rows of D and U) */
+    int32_t nx, ny;          /* receiver grid, natural index r = y*nx + x; nx*ny == nr.
+                                Ignored when perm != NULL. */
+    const int32_t* perm;     /* optional HOST array [nr]: perm[a] = natural index of the
+                                receiver at position a (overrides the Hilbert order) */
+    int32_t tile;            /* tile size b; nr % b == 0 (uniform partition) */
+    int32_t rank;            /* uniform rank k of every tile, used when ranks == NULL */
+    const int32_t* ranks;    /* optional HOST array [N + N(N-1)/2], N = nr/b: the N
+                                diagonal ranks, then the sub-diagonal pair ranks in
+                                stacking order (column j ascending, row i > j ascending) */
+    int32_t diag_mode;       /* TLR_DIAG_* */
+    const uint8_t* diag_dense; /* HOST [N], used with TLR_DIAG_PER_TILE */
+    int32_t reciprocity;     /* TLR_RECIP_* */
+    int32_t precision;       /* TLR_PREC_* */
+    double alpha;            /* normalisation; 0 -> max_{s,r} |D[s,r]| of this D */
+    int32_t input_memory;    /* TLR_MEM_* for D and U passed to tlr_mdd_create */
+    int32_t reserved;
+} tlr_mdd_desc_t;
+
+/* Solver options (ADMM solver section; values the paper leaves open are
+ * defaults of this library: rho = 1, 2 ADMM iterations per lambda stage,
+ * 5 L-BFGS iterations per x-update, memory 10). */
+typedef struct {
+    double lam0;             /* first lambda (paper: 10) */
+    double decay;            /* lambda_{s+1} = decay * lambda_s (paper: 0.1) */
+    int32_t stages;          /* lambda stages (paper: 3) */
+    int32_t admm_iters;      /* ADMM iterations per stage */
+    int32_t lbfgs_iters;     /* L-BFGS iterations per x-update */
+    int32_t memory;          /* L-BFGS memory m (1..32) */
+    double rho;              /* ADMM penalty rho > 0 */
+    int32_t theta_memory;    /* TLR_MEM_* of theta_inout */
+    int32_t reserved;
+} tlr_mdd_solve_opts_t;
+
+#define TLR_MAX_HIST 1024
+typedef struct {
+    int32_t iters;           /* L-BFGS steps taken */
+    int32_t restarts;        /* steps where the memory was cleared (no descent) */
+    int32_t status;          /* TLR_OK or TLR_ERR_NONFINITE */
+    int32_t n_hist;
+    double f_hist[TLR_MAX_HIST]; /* data misfit f (eq. 17a) after each L-BFGS step */
+    double f0;               /* f at the starting point */
+    double gpu_ms;           /* device time of the solve (CUDA events) */
+} tlr_mdd_stats_t;
+
+/* Fill *d with defaults (SYMMETRIC, FP32, RULE, alpha = 0, device inputs). */
+void tlr_mdd_desc_init(tlr_mdd_desc_t* d);
+/* Fill *o with the paper's schedule (lam0 10, decay 0.1, 3 stages) and the
+ * library defaults above. */
+void tlr_mdd_solve_opts_init(tlr_mdd_solve_opts_t* o);
+
+/* Number of complex entries of the stacked unknown theta = (Z-bar, L-bar, R-bar)
+ * (Tile Low-rank MDD section) for this description. */
+int tlr_mdd_theta_size(const tlr_mdd_desc_t* d, int64_t* n_theta);
+
+/* Offsets (complex entries) of each block of theta, written to HOST arrays:
+ * off_diag[N] (Q_ii b x k_ii, or Z_ii b x b), off_l[P] and off_r[P] (b x k_ij,
+ * P = N(N-1)/2, pair order as for ranks).  Layout: all diagonal blocks in i
+ * order, then L-bar, then R-bar; every block row-major.  R_ij is stored as the
+ * b x k matrix whose transpose is the paper's k x b factor: X_ij = L_ij R_ij^T,
+ * X_ji = R_ij L_ij^T.  dense_out[N] (HOST, may be NULL) receives the resolved
+ * diagonal representation. */
+int tlr_mdd_theta_layout(const tlr_mdd_desc_t* d, int64_t* off_diag, int64_t* off_l,
+                         int64_t* off_r, uint8_t* dense_out);
+
+/* Device bytes the library allocates for a handle with this description
+ * (data panels + workspace), for admission control. */
+int64_t tlr_mdd_workspace_bytes(const tlr_mdd_desc_t* d);
+
+/* Hilbert order of an nx x ny receiver grid, computed on the GPU (eq. 10):
+ * perm_dev[a] = natural index (y*nx + x) of the a-th receiver along the curve
+ * drawn on the smallest power-of-two square holding the grid.  perm_dev is a
+ * DEVICE int32 array [nx*ny].  Bit-exact. */
+int tlr_mdd_hilbert_perm(int32_t nx, int32_t ny, int32_t* perm_dev, void* stream);
+
+/* Create a handle: validates *d, computes the receiver order, alpha, and the
+ * receiver-major panels Dfrak[a, s] = D[s, perm[a]] / alpha and
+ * Ufrak[a, s] = U[s, perm[a]] / alpha (eq. 14; normalisation), then allocates
+ * the workspace.  D, U: complex64 [ns x nr] row-major (the paper's layout),
+ * device or host per d->input_memory; they are not referenced after the call
+ * returns.  On failure *h is NULL. */
+int tlr_mdd_create(tlr_mdd_t** h, const tlr_mdd_desc_t* d, const void* D, const void* U,
+                   void* stream);
+
+/* Y = X_h Dfrak (receiver-major, Hilbert order), nr x ns complex64 DEVICE.
+ * X_h = C(theta) by eq. (6)-(9), (15); theta DEVICE complex64 [n_theta]. */
+int tlr_mdd_apply(tlr_mdd_t* h, const void* theta, void* Y);
+
+/* G = V Dfrak^H, nr x nr complex64 DEVICE, for V nr x ns complex64 DEVICE.
+ * With V = X_h Dfrak - Ufrak this is W^T, W = D^H (D X - U) (Derivatives
+ * paragraph); W' = G + G^T. */
+int tlr_mdd_adjoint(tlr_mdd_t* h, const void* V, void* G);
+
+/* f = 0.5 ||D-hat C(theta) - U-hat||_F^2 (eq. 17a) and its factor gradients
+ * (eq. 25-27) stacked like theta in grad (DEVICE complex64 [n_theta]); the
+ * convention is grad = df/dRe(theta) + i df/dIm(theta).  f: HOST double
+ * (the call synchronises the stream), or NULL. */
+int tlr_mdd_grad(tlr_mdd_t* h, const void* theta, void* grad, double* f);
+
+/* ADMM with an L-BFGS x-update and exact line search (eq. 18-24), lambda
+ * continuation (lam0, decay, stages).  theta_inout: complex64 [n_theta],
+ * device or host per opts->theta_memory; it is the start point on entry and
+ * the x-iterate on return.  stats: HOST, may be NULL.  Synchronises. */
+int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* opts,
+                  tlr_mdd_stats_t* stats);
+
+/* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
+int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);
+
+/* Copies of the handle's receiver order (HOST int32 [nr]), alpha (HOST) and,
+ * if Dt / Ut are non-NULL, its panels (DEVICE complex64 [nr x ns]). */
+int tlr_mdd_get_data(tlr_mdd_t* h, int32_t* perm_host, double* alpha, void* Dt, void* Ut);
+
+/* The handle's stream (as passed to create). */
+void* tlr_mdd_stream(const tlr_mdd_t* h);
+
+/* ---- diagnostics (process-wide, not part of the method) ----
+ * While enabled, every contraction kernel launch is bracketed by CUDA events
+ * on the stream it is launched on; tlr_mdd_timing_read() waits for those
+ * events and returns, per class, the summed device time (ms), the algorithmic
+ * flops (8 real flops per complex multiply-add) and the launch count.
+ * Classes: 0 compress (T = F^T Dfrak, V = F^H Rf), 1 expand (Y = F T~ + P Z
+ * Dfrak and the line-search products), 2 project (gradient split-K partials
+ * and the dense adjoint).  tlr_mdd_launch_count() is the number of kernels
+ * this library has launched since load (all classes and helpers). */
+#define TLR_NCLASS 3
+void tlr_mdd_timing_enable(int on);
+void tlr_mdd_timing_reset(void);
+int tlr_mdd_timing_read(double* ms, double* flops, int64_t* launches, int nclass);
+int64_t tlr_mdd_launch_count(void);
+
+const char* tlr_mdd_last_error(const tlr_mdd_t* h);
+int tlr_mdd_destroy(tlr_mdd_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLR_MDD_H */

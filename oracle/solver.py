@@ -20,6 +20,9 @@ Readings where the paper is silent (each is listed in the design notes):
 * the line search is exact: C is bilinear in the factors, so
   phi(a) = f(theta + a d) + rho/2 ||theta + a d - v||^2 is a quartic in a; its
   minimiser over a > 0 is taken among the real roots of phi'(a);
+* when d is not a descent direction (or phi has no minimiser on a > 0) the
+  iteration takes no step and clears the L-BFGS memory, so the next direction
+  is steepest descent; a pair (s, y) is kept only if <s,y> > 1e-12 |s||y|;
 * the returned iterate is theta (the x-block).
 """
 from __future__ import annotations
@@ -155,18 +158,16 @@ def lbfgs(prob: Problem, theta, v, rho: float, iters: int, memory: int,
     for _ in range(iters):
         d = two_loop(g, S, Y)
         c = prob.coefficients(theta, d, rho, v)
-        if not (c[1] < 0.0):
+        a = quartic_argmin(c) if c[1] < 0.0 else None
+        if a is None:
+            # no descent along d (or no minimiser on a > 0): take no step this
+            # iteration and clear the memory, so the next direction is -g
             S, Y = [], []
             stats.restarts += 1
-            d = -g
-            c = prob.coefficients(theta, d, rho, v)
-            if not (c[1] < 0.0):
-                stats.status = "stationary"
-                break
-        a = quartic_argmin(c)
-        if a is None:
-            stats.status = "line-search"
-            break
+            stats.f_hist.append(f)
+            stats.alphas.append(0.0)
+            stats.iters += 1
+            continue
         s = a * d
         theta = theta + s
         f, gf = prob.fgrad(theta)

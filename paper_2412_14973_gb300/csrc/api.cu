@@ -1,0 +1,1022 @@
+// C ABI of libtlr_mdd: handle life cycle, the tile layout of the stacked
+// unknown (Tile Low-rank MDD section), grouped-GEMM work tables and the
+// device-resident ADMM / L-BFGS solve (eq. 18-24).
+//
+// Internal representation.  Every factor of the TLR parametrisation acts on
+// exactly one block column of Dfrak in the forward product and on exactly one
+// block row of Y, and for a symmetric X both are the same block: block i holds
+//   F_i = [ Q_ii | L_ij (j < i) | R_ji (j > i) ]   (b x K_i, row-major panel)
+// so that, with T_i = F_i^T Dfrak_i (compress) and T~ the rows of T taken at
+// each column's partner factor (L_ij <-> R_ij, Q_ii <-> itself),
+//   Y_i = X_h Dfrak |_i = F_i T~_i + P(Z_ii) Dfrak_i            (eq. 6-9, 15)
+//   grad F_i = Rf_i T~_i^H + conj(Dfrak_i) V~_i^T,  V_i = F_i^H Rf_i (eq. 25-27)
+//   grad Z_ii = (G_ii + G_ii^T) / 2,  G_ii = Rf_i Dfrak_i^H       (eq. 26)
+// with Rf = Y - Ufrak the receiver-major residual.  The panel vector
+// [F_0 .. F_{N-1} | dense Z tiles] is a permutation of theta.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "solver_dev.h"
+
+#include <mutex>
+
+using namespace tlr;
+
+std::atomic<long long> tlr::g_launches{0};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// ---- diagnostics: CUDA-event timing of the contraction launches ----
+struct TimedLaunch {
+    int cls;
+    double flops;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<TimedLaunch> g_pending;
+std::vector<cudaEvent_t> g_evpool;
+double g_ms[TLR_NCLASS] = {0}, g_fl[TLR_NCLASS] = {0};
+long long g_nl[TLR_NCLASS] = {0};
+
+cudaEvent_t ev_get() {
+    if (!g_evpool.empty()) {
+        cudaEvent_t e = g_evpool.back();
+        g_evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// launch one grouped contraction, timed when diagnostics are on
+cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st) {
+    if (L.nprob == 0) return cudaSuccess;
+    if (!g_timing) return gemm_simt(L, st);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    TimedLaunch t{L.cls, L.flops, ev_get(), ev_get()};
+    cudaEventRecord(t.a, st);
+    cudaError_t e = gemm_simt(L, st);
+    cudaEventRecord(t.b, st);
+    g_pending.push_back(t);
+    return e;
+}
+
+struct Arena {
+    char* base = nullptr;
+    size_t used = 0;
+    size_t cap = 0;
+    template <class T>
+    T* take(size_t n) {
+        size_t bytes = (n * sizeof(T) + 255) & ~size_t(255);
+        if (base == nullptr) {  // sizing pass
+            used += bytes;
+            return nullptr;
+        }
+        T* p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+struct Layout {
+    int64_t nr = 0, ns = 0, b = 0;
+    int N = 0, P = 0;
+    std::vector<int> kd, kp;
+    std::vector<uint8_t> dense;
+    std::vector<int64_t> off_diag, off_l, off_r;
+    int64_t ntheta = 0;
+    // panel
+    std::vector<int> Kb;
+    std::vector<int64_t> Koff;
+    std::vector<int> dslot;   // dense slot of block i or -1
+    int64_t Ktot = 0, nlr = 0, ndense = 0, nth = 0;
+    // maps (host copies)
+    std::vector<int> partner, colstride, panstride;
+    std::vector<long long> colsrc, colpan, zsrc;
+};
+
+int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
+    if (!d) {
+        err = "desc is NULL";
+        return TLR_ERR_ARG;
+    }
+    if (d->nr <= 0 || d->ns <= 0 || d->tile <= 0) {
+        err = "nr, ns and tile must be positive";
+        return TLR_ERR_SHAPE;
+    }
+    if (d->nr % d->tile != 0) {
+        err = "tile must divide nr (uniform partition)";
+        return TLR_ERR_SHAPE;
+    }
+    if (d->nr > (int64_t)1 << 30 || d->ns > (int64_t)1 << 30) {
+        err = "nr and ns must be below 2^30";
+        return TLR_ERR_SHAPE;
+    }
+    if (d->reciprocity != TLR_RECIP_SYMMETRIC) {
+        err = "only the reciprocal (symmetric) parametrisation is implemented";
+        return TLR_ERR_UNSUPPORTED;
+    }
+    if (d->precision != TLR_PREC_FP32 && d->precision != TLR_PREC_BF16X3) {
+        err = "unknown precision mode";
+        return TLR_ERR_ARG;
+    }
+    L.nr = d->nr;
+    L.ns = d->ns;
+    L.b = d->tile;
+    L.N = (int)(d->nr / d->tile);
+    L.P = L.N * (L.N - 1) / 2;
+    const int N = L.N, P = L.P;
+    L.kd.assign(N, d->rank);
+    L.kp.assign(P, d->rank);
+    if (d->ranks) {
+        for (int i = 0; i < N; ++i) L.kd[i] = d->ranks[i];
+        for (int p = 0; p < P; ++p) L.kp[p] = d->ranks[N + p];
+    }
+    for (int k : L.kd)
+        if (k < 0 || k > L.b) {
+            err = "rank outside [0, tile]";
+            return TLR_ERR_SHAPE;
+        }
+    for (int k : L.kp)
+        if (k < 0 || k > L.b) {
+            err = "rank outside [0, tile]";
+            return TLR_ERR_SHAPE;
+        }
+    L.dense.assign(N, 0);
+    for (int i = 0; i < N; ++i) {
+        switch (d->diag_mode) {
+            case TLR_DIAG_RULE: L.dense[i] = (4LL * L.kd[i] >= L.b); break;
+            case TLR_DIAG_LOWRANK: L.dense[i] = 0; break;
+            case TLR_DIAG_DENSE: L.dense[i] = 1; break;
+            case TLR_DIAG_PER_TILE:
+                if (!d->diag_dense) {
+                    err = "diag_dense is NULL with TLR_DIAG_PER_TILE";
+                    return TLR_ERR_ARG;
+                }
+                L.dense[i] = d->diag_dense[i] != 0;
+                break;
+            default: err = "unknown diag_mode"; return TLR_ERR_ARG;
+        }
+    }
+    // theta (paper stacking): diagonal blocks, then L-bar, then R-bar
+    int64_t o = 0;
+    L.off_diag.resize(N);
+    for (int i = 0; i < N; ++i) {
+        L.off_diag[i] = o;
+        o += L.b * (L.dense[i] ? L.b : L.kd[i]);
+    }
+    L.off_l.resize(P);
+    L.off_r.resize(P);
+    for (int p = 0; p < P; ++p) {
+        L.off_l[p] = o;
+        o += L.b * L.kp[p];
+    }
+    for (int p = 0; p < P; ++p) {
+        L.off_r[p] = o;
+        o += L.b * L.kp[p];
+    }
+    L.ntheta = o;
+
+    // panels.  pair index p(i, j) = j N - j(j+1)/2 + (i - j - 1), i > j
+    auto pidx = [N](int i, int j) { return j * N - j * (j + 1) / 2 + (i - j - 1); };
+    // factor list per block: (theta offset, rank, partner factor id); factor ids:
+    // Q_i -> i ; L_p -> N + p ; R_p -> N + P + p
+    struct Fac {
+        int id;
+        int64_t off;
+        int k;
+        int partner;
+    };
+    std::vector<std::vector<Fac>> blk(N);
+    for (int i = 0; i < N; ++i) {
+        if (!L.dense[i] && L.kd[i] > 0) blk[i].push_back({i, L.off_diag[i], L.kd[i], i});
+        for (int j = 0; j < i; ++j) {
+            const int p = pidx(i, j);
+            if (L.kp[p] > 0) blk[i].push_back({N + p, L.off_l[p], L.kp[p], N + P + p});
+        }
+        for (int j = i + 1; j < N; ++j) {
+            const int p = pidx(j, i);
+            if (L.kp[p] > 0) blk[i].push_back({N + P + p, L.off_r[p], L.kp[p], N + p});
+        }
+    }
+    L.Kb.assign(N, 0);
+    L.Koff.assign(N, 0);
+    std::vector<int64_t> fac_col(N + 2 * P, -1);
+    int64_t K = 0;
+    for (int i = 0; i < N; ++i) {
+        L.Koff[i] = K;
+        for (auto& f : blk[i]) {
+            fac_col[f.id] = K + L.Kb[i];
+            L.Kb[i] += f.k;
+        }
+        K += L.Kb[i];
+    }
+    L.Ktot = K;
+    L.nlr = L.b * K;
+    L.partner.resize(K);
+    L.colsrc.resize(K);
+    L.colstride.resize(K);
+    L.colpan.resize(K);
+    L.panstride.resize(K);
+    for (int i = 0; i < N; ++i) {
+        int64_t c = 0;
+        for (auto& f : blk[i]) {
+            for (int q = 0; q < f.k; ++q) {
+                const int64_t g = L.Koff[i] + c + q;
+                L.partner[g] = (int)(fac_col[f.partner] + q);
+                L.colsrc[g] = f.off + q;
+                L.colstride[g] = f.k;
+                L.colpan[g] = L.b * L.Koff[i] + c + q;
+                L.panstride[g] = L.Kb[i];
+            }
+            c += f.k;
+        }
+    }
+    L.dslot.assign(N, -1);
+    for (int i = 0; i < N; ++i)
+        if (L.dense[i]) {
+            L.dslot[i] = (int)L.ndense++;
+            L.zsrc.push_back(L.off_diag[i]);
+        }
+    L.nth = L.nlr + L.ndense * L.b * L.b;
+    if (L.nth != L.ntheta) {
+        err = "internal: panel size differs from theta size";
+        return TLR_ERR_STATE;
+    }
+    return TLR_OK;
+}
+
+int choose_split(long long tiles, long long K) {
+    const long long target = 4LL * 152 * 2;
+    long long s = (target + tiles - 1) / std::max(1LL, tiles);
+    s = std::min(s, std::max(1LL, K / 256));
+    s = std::max(1LL, std::min(s, 64LL));
+    return (int)s;
+}
+
+}  // namespace
+
+struct tlr_mdd_s {
+    tlr_mdd_desc_t d{};
+    cudaStream_t st = nullptr;
+    Layout L;
+    std::string err;
+    // device arena
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    int32_t* perm = nullptr;   // 2 nr: perm, inverse
+    double* scal = nullptr;    // [0] alpha
+    double alpha = 0.0;
+    cf *Dt = nullptr, *Ut = nullptr, *R = nullptr, *A1 = nullptr, *A2 = nullptr;
+    cf *T = nullptr, *Tp = nullptr;   // Tp doubles as V
+    cf *Zs = nullptr, *Zsd = nullptr;
+    cf* part = nullptr;
+    int nsplit = 1;
+    int kchunk = 0;
+    double* dpart = nullptr;   // reduction partial slabs
+    int* d_partner = nullptr;
+    PanelMap pm{};
+    // theta-space vectors
+    cf *x = nullptr, *z = nullptr, *u = nullptr, *v = nullptr, *g = nullptr, *gf = nullptr, *dd = nullptr,
+       *q = nullptr;
+    // solver small state
+    double *rho_h = nullptr, *sy_h = nullptr, *yy_h = nullptr, *acoef = nullptr, *sc = nullptr, *fhist = nullptr;
+    int* ints = nullptr;
+    // ring (allocated on first solve)
+    float* ring = nullptr;
+    int ring_m = 0;
+    // GEMM tables
+    GemmLaunch Lc_x, Lc_d, Lc_v, Le_fwd, Le_apply, Le_a1, Le_a2, Lp;
+    char* tab_base = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+#define FAIL(h, code, msg)                  \
+    do {                                    \
+        if (h) (h)->err = (msg);            \
+        g_last_error = (msg);               \
+        return (code);                      \
+    } while (0)
+
+#define CK(h, expr)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            std::string m_ = std::string(#expr) + ": " + cudaGetErrorString(e_);           \
+            if (h) (h)->err = m_;                                                           \
+            g_last_error = m_;                                                              \
+            return e_ == cudaErrorMemoryAllocation ? TLR_ERR_NOMEM : TLR_ERR_CUDA;         \
+        }                                                                                   \
+    } while (0)
+
+namespace {
+
+// Lay out (or size, when a.base == nullptr) the handle's device arena.
+void carve(tlr_mdd_s* h, Arena& a) {
+    const Layout& L = h->L;
+    const size_t nrs = (size_t)L.nr * L.ns, kns = (size_t)std::max<int64_t>(1, L.Ktot) * L.ns;
+    h->perm = a.take<int32_t>(2 * L.nr);
+    h->scal = a.take<double>(16);
+    h->Dt = a.take<cf>(nrs);
+    h->Ut = a.take<cf>(nrs);
+    h->R = a.take<cf>(nrs);
+    h->A1 = a.take<cf>(nrs);
+    h->A2 = a.take<cf>(nrs);
+    h->T = a.take<cf>(kns);
+    h->Tp = a.take<cf>(kns);
+    const size_t nz = std::max<size_t>(1, (size_t)L.ndense * L.b * L.b);
+    h->Zs = a.take<cf>(nz);
+    h->Zsd = a.take<cf>(nz);
+    h->part = a.take<cf>((size_t)h->nsplit * L.nth);
+    h->dpart = a.take<double>(16 * kRedBlocks);
+    const size_t K = std::max<int64_t>(1, L.Ktot);
+    h->d_partner = a.take<int>(K);
+    long long* colsrc = a.take<long long>(K);
+    int* colstride = a.take<int>(K);
+    long long* colpan = a.take<long long>(K);
+    int* panstride = a.take<int>(K);
+    long long* zsrc = a.take<long long>(std::max<int64_t>(1, L.ndense));
+    h->pm = PanelMap{colsrc, colstride, colpan, panstride, zsrc, L.Ktot, L.b, L.ndense, L.nlr};
+    const size_t nth = std::max<int64_t>(1, L.nth);
+    h->x = a.take<cf>(nth);
+    h->z = a.take<cf>(nth);
+    h->u = a.take<cf>(nth);
+    h->v = a.take<cf>(nth);
+    h->g = a.take<cf>(nth);
+    h->gf = a.take<cf>(nth);
+    h->dd = a.take<cf>(nth);
+    h->q = a.take<cf>(nth);
+    h->rho_h = a.take<double>(64);
+    h->sy_h = a.take<double>(64);
+    h->yy_h = a.take<double>(64);
+    h->acoef = a.take<double>(64);
+    h->sc = a.take<double>(SC_COUNT + 8);
+    h->ints = a.take<int>(SI_COUNT + 8);
+    h->fhist = a.take<double>(TLR_MAX_HIST);
+    // GEMM tables: 8 slots of at most 2N problems each
+    h->tab_base = reinterpret_cast<char*>(a.take<GProb>(2 * (size_t)L.N + 1));
+    for (int t = 1; t < 8; ++t) a.take<GProb>(2 * (size_t)L.N + 1);
+}
+
+int split_for(const Layout& L) {
+    long long tiles = 0;
+    for (int i = 0; i < L.N; ++i) {
+        tiles += ((L.b + 63) / 64) * ((L.Kb[i] + 63) / 64);
+        if (L.dense[i]) tiles += ((L.b + 63) / 64) * ((L.b + 63) / 64);
+    }
+    return choose_split(std::max(1LL, tiles), L.ns);
+}
+
+GTerm term(const cf* A, long long lda, const cf* B, long long ldb, const int* g, int K, bool conjA, bool conjB) {
+    GTerm t;
+    t.A = A;
+    t.B = B;
+    t.g = g;
+    t.lda = lda;
+    t.ldb = ldb;
+    t.K = K;
+    t.sa = conjA ? -1.f : 1.f;
+    t.sb = conjB ? -1.f : 1.f;
+    return t;
+}
+
+// Build the grouped problems for every contraction of the handle and upload.
+int build_tables(tlr_mdd_s* h, char* tab_base) {
+    const Layout& L = h->L;
+    const long long ns = L.ns, b = L.b;
+    const size_t slot = ((sizeof(GProb) * (2 * (size_t)L.N + 1)) + 255) & ~size_t(255);
+    int ti = 0;
+    auto upload = [&](GemmLaunch& G, std::vector<GProb>& v, int am, int bm, int epi) -> int {
+        GProb* dst = reinterpret_cast<GProb*>(tab_base + slot * ti++);
+        G.d_probs = dst;
+        G.nprob = (int)v.size();
+        G.amode = am;
+        G.bmode = bm;
+        G.epi = epi;
+        G.maxM = G.maxN = G.maxK = 0;
+        G.flops = 0.0;
+        for (auto& p : v) {
+            G.maxM = std::max(G.maxM, p.M);
+            G.maxN = std::max(G.maxN, p.N);
+            for (int t = 0; t < p.nt; ++t) G.flops += 8.0 * p.M * (double)p.N * p.t[t].K;
+        }
+        G.cls = am == A_KM ? 0 : (bm == B_KN ? 1 : 2);
+        if (!v.empty()) {
+            cudaError_t e = cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(GProb), cudaMemcpyHostToDevice, h->st);
+            if (e != cudaSuccess) return -1;
+        }
+        return 0;
+    };
+    auto blank = []() {
+        GProb p;
+        memset(&p, 0, sizeof(p));
+        return p;
+    };
+    const cf* X = h->x;
+    const cf* Dd = h->dd;
+    // compress: T_i = F_i^T Dfrak_i (src x), Tp (src d), V = F_i^H Rf_i (into Tp)
+    for (int which = 0; which < 3; ++which) {
+        std::vector<GProb> v;
+        for (int i = 0; i < L.N; ++i) {
+            if (L.Kb[i] == 0) continue;
+            GProb p = blank();
+            const cf* src = which == 1 ? Dd : X;
+            const cf* data = which == 2 ? h->R : h->Dt;
+            cf* out = which == 0 ? h->T : h->Tp;
+            p.t[0] = term(src + b * L.Koff[i], L.Kb[i], data + (long long)i * b * ns, ns, nullptr, (int)b,
+                          which == 2, false);
+            p.nt = 1;
+            p.M = L.Kb[i];
+            p.N = (int)ns;
+            p.C = out + L.Koff[i] * ns;
+            p.ldc = ns;
+            v.push_back(p);
+        }
+        GemmLaunch& G = which == 0 ? h->Lc_x : (which == 1 ? h->Lc_d : h->Lc_v);
+        if (upload(G, v, A_KM, B_KN, EPI_STORE)) return -1;
+    }
+    // expand: forward residual (SUB Ufrak), plain apply (STORE), A1, A2
+    for (int which = 0; which < 4; ++which) {
+        std::vector<GProb> v;
+        for (int i = 0; i < L.N; ++i) {
+            GProb p = blank();
+            const int* gi = h->d_partner + L.Koff[i];
+            const int Ki = L.Kb[i];
+            const cf* Fi = X + b * L.Koff[i];
+            const cf* Fd = Dd + b * L.Koff[i];
+            const cf* Di = h->Dt + (long long)i * b * ns;
+            int nt = 0;
+            if (which <= 1) {
+                if (Ki > 0) p.t[nt++] = term(Fi, Ki, h->T, ns, gi, Ki, false, false);
+                if (L.dense[i]) p.t[nt++] = term(h->Zs + L.dslot[i] * b * b, b, Di, ns, nullptr, (int)b, false, false);
+            } else if (which == 2) {
+                if (Ki > 0) {
+                    p.t[nt++] = term(Fd, Ki, h->T, ns, gi, Ki, false, false);
+                    p.t[nt++] = term(Fi, Ki, h->Tp, ns, gi, Ki, false, false);
+                }
+                if (L.dense[i]) p.t[nt++] = term(h->Zsd + L.dslot[i] * b * b, b, Di, ns, nullptr, (int)b, false, false);
+            } else {
+                if (Ki > 0) p.t[nt++] = term(Fd, Ki, h->Tp, ns, gi, Ki, false, false);
+            }
+            p.nt = nt;
+            p.M = (int)b;
+            p.N = (int)ns;
+            cf* out = which <= 1 ? h->R : (which == 2 ? h->A1 : h->A2);
+            p.C = out + (long long)i * b * ns;
+            p.S = h->Ut + (long long)i * b * ns;
+            p.ldc = ns;
+            v.push_back(p);
+        }
+        GemmLaunch& G = which == 0 ? h->Le_fwd : which == 1 ? h->Le_apply : which == 2 ? h->Le_a1 : h->Le_a2;
+        if (upload(G, v, A_MK, B_KN, which == 0 ? EPI_SUB : EPI_STORE)) return -1;
+    }
+    // project: split-K partials of grad F_i and G_ii
+    {
+        std::vector<GProb> v;
+        for (int i = 0; i < L.N; ++i) {
+            const cf* Ri = h->R + (long long)i * b * ns;
+            const cf* Di = h->Dt + (long long)i * b * ns;
+            if (L.Kb[i] > 0) {
+                GProb p = blank();
+                const int* gi = h->d_partner + L.Koff[i];
+                p.t[0] = term(Ri, ns, h->T, ns, gi, (int)ns, false, true);
+                p.t[1] = term(Di, ns, h->Tp, ns, gi, (int)ns, true, false);
+                p.nt = 2;
+                p.M = (int)b;
+                p.N = L.Kb[i];
+                p.C = h->part + b * L.Koff[i];
+                p.ldc = L.Kb[i];
+                v.push_back(p);
+            }
+            if (L.dense[i]) {
+                GProb p = blank();
+                p.t[0] = term(Ri, ns, Di, ns, nullptr, (int)ns, false, true);
+                p.nt = 1;
+                p.M = (int)b;
+                p.N = (int)b;
+                p.C = h->part + L.nlr + L.dslot[i] * b * b;
+                p.ldc = b;
+                v.push_back(p);
+            }
+        }
+        if (upload(h->Lp, v, A_MK, B_NK, EPI_PARTIAL)) return -1;
+        h->Lp.nsplit = h->nsplit;
+        h->Lp.kchunk = h->kchunk;
+        h->Lp.part_stride = L.nth;
+    }
+    return 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// entry points
+// ===========================================================================
+extern "C" {
+
+void tlr_mdd_desc_init(tlr_mdd_desc_t* d) {
+    if (!d) return;
+    memset(d, 0, sizeof(*d));
+    d->diag_mode = TLR_DIAG_RULE;
+    d->reciprocity = TLR_RECIP_SYMMETRIC;
+    d->precision = TLR_PREC_FP32;
+    d->input_memory = TLR_MEM_DEVICE;
+}
+
+void tlr_mdd_solve_opts_init(tlr_mdd_solve_opts_t* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->lam0 = 10.0;
+    o->decay = 0.1;
+    o->stages = 3;
+    o->admm_iters = 2;
+    o->lbfgs_iters = 5;
+    o->memory = 10;
+    o->rho = 1.0;
+    o->theta_memory = TLR_MEM_DEVICE;
+}
+
+int tlr_mdd_theta_size(const tlr_mdd_desc_t* d, int64_t* n) {
+    Layout L;
+    std::string e;
+    int rc = build_layout(d, L, e);
+    if (rc) {
+        g_last_error = e;
+        return rc;
+    }
+    if (!n) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "n_theta is NULL");
+    *n = L.ntheta;
+    return TLR_OK;
+}
+
+int tlr_mdd_theta_layout(const tlr_mdd_desc_t* d, int64_t* off_diag, int64_t* off_l, int64_t* off_r,
+                         uint8_t* dense_out) {
+    Layout L;
+    std::string e;
+    int rc = build_layout(d, L, e);
+    if (rc) {
+        g_last_error = e;
+        return rc;
+    }
+    if (off_diag) std::copy(L.off_diag.begin(), L.off_diag.end(), off_diag);
+    if (off_l) std::copy(L.off_l.begin(), L.off_l.end(), off_l);
+    if (off_r) std::copy(L.off_r.begin(), L.off_r.end(), off_r);
+    if (dense_out) std::copy(L.dense.begin(), L.dense.end(), dense_out);
+    return TLR_OK;
+}
+
+int64_t tlr_mdd_workspace_bytes(const tlr_mdd_desc_t* d) {
+    tlr_mdd_s tmp;
+    std::string e;
+    if (build_layout(d, tmp.L, e)) return -1;
+    tmp.nsplit = split_for(tmp.L);
+    Arena a;
+    carve(&tmp, a);
+    // plus the L-BFGS ring for the default memory (m = 10: 11 slots of s and y)
+    return (int64_t)a.used + (int64_t)2 * 11 * tmp.L.nth * (int64_t)sizeof(cf);
+}
+
+int tlr_mdd_hilbert_perm(int32_t nx, int32_t ny, int32_t* perm_dev, void* stream) {
+    if (nx <= 0 || ny <= 0 || !perm_dev) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "bad grid or NULL perm");
+    if (nx > 32768 || ny > 32768) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_SHAPE, "grid side above 32768");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long n = 1;
+    while (n < nx || n < ny) n <<= 1;
+    int32_t* slot = nullptr;
+    tlr_mdd_s* h = nullptr;
+    CK(h, cudaMallocAsync((void**)&slot, (size_t)(n * n) * sizeof(int32_t), st));
+    cudaError_t e = hilbert_perm(nx, ny, perm_dev, slot, st);
+    cudaFreeAsync(slot, st);
+    CK(h, e);
+    return TLR_OK;
+}
+
+int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, const void* U, void* stream) {
+    if (!out) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "handle pointer is NULL");
+    *out = nullptr;
+    if (!d || !D || !U) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "desc, D or U is NULL");
+    tlr_mdd_s* h = new tlr_mdd_s();
+    h->d = *d;
+    h->d.perm = nullptr;
+    h->d.ranks = nullptr;
+    h->d.diag_dense = nullptr;
+    h->st = (cudaStream_t)stream;
+    int rc = build_layout(d, h->L, h->err);
+    if (rc) {
+        g_last_error = h->err;
+        delete h;
+        return rc;
+    }
+    const Layout& L = h->L;
+    if (!d->perm && ((int64_t)d->nx * d->ny != d->nr || d->nx <= 0 || d->ny <= 0)) {
+        g_last_error = "nx * ny must equal nr (or pass perm)";
+        delete h;
+        return TLR_ERR_SHAPE;
+    }
+    if (d->precision != TLR_PREC_FP32) {
+        g_last_error = "precision mode not available in this build";
+        delete h;
+        return TLR_ERR_UNSUPPORTED;
+    }
+    h->nsplit = split_for(L);
+    h->kchunk = (int)(((L.ns + h->nsplit - 1) / h->nsplit + 15) / 16 * 16);
+    Arena a;
+    carve(h, a);
+    h->arena_bytes = a.used;
+    auto fail = [&](int code) {
+        g_last_error = h->err;
+        if (h->arena) cudaFreeAsync(h->arena, h->st);
+        delete h;
+        return code;
+    };
+    {
+        cudaError_t e = cudaMallocAsync((void**)&h->arena, h->arena_bytes, h->st);
+        if (e != cudaSuccess) {
+            h->arena = nullptr;
+            h->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+            return fail(TLR_ERR_NOMEM);
+        }
+    }
+    Arena b2;
+    b2.base = h->arena;
+    carve(h, b2);
+#define CKF(expr)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            h->err = std::string(#expr) + ": " + cudaGetErrorString(e_);           \
+            return fail(e_ == cudaErrorMemoryAllocation ? TLR_ERR_NOMEM : TLR_ERR_CUDA); \
+        }                                                                          \
+    } while (0)
+    // receiver order
+    if (d->perm) {
+        std::vector<char> seen(L.nr, 0);
+        for (int64_t a2 = 0; a2 < L.nr; ++a2) {
+            const int32_t r = d->perm[a2];
+            if (r < 0 || r >= L.nr || seen[r]) {
+                h->err = "perm is not a permutation of 0..nr-1";
+                return fail(TLR_ERR_ARG);
+            }
+            seen[r] = 1;
+        }
+        CKF(cudaMemcpyAsync(h->perm, d->perm, L.nr * sizeof(int32_t), cudaMemcpyHostToDevice, h->st));
+    } else {
+        long long n = 1;
+        while (n < d->nx || n < d->ny) n <<= 1;
+        int32_t* slot = nullptr;
+        CKF(cudaMallocAsync((void**)&slot, (size_t)(n * n) * sizeof(int32_t), h->st));
+        cudaError_t e = hilbert_perm(d->nx, d->ny, h->perm, slot, h->st);
+        cudaFreeAsync(slot, h->st);
+        CKF(e);
+    }
+    // inputs (host inputs are staged through the residual / A1 buffers)
+    const cf* Dsrc = (const cf*)D;
+    const cf* Usrc = (const cf*)U;
+    const size_t nrs = (size_t)L.nr * L.ns;
+    if (d->input_memory == TLR_MEM_HOST) {
+        CKF(cudaMemcpyAsync(h->R, D, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync(h->A1, U, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
+        Dsrc = h->R;
+        Usrc = h->A1;
+    }
+    if (d->alpha > 0.0) {
+        const double al = d->alpha;
+        CKF(cudaMemcpyAsync(h->scal, &al, sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaStreamSynchronize(h->st));
+    } else {
+        CKF(max_abs2(Dsrc, (long long)nrs, h->dpart, kRedBlocks, h->scal, h->st));
+    }
+    CKF(permute_normalise(Dsrc, L.ns, L.nr, h->perm, h->scal, h->Dt, h->st));
+    CKF(permute_normalise(Usrc, L.ns, L.nr, h->perm, h->scal, h->Ut, h->st));
+    // maps
+    if (L.Ktot > 0) {
+        CKF(cudaMemcpyAsync(h->d_partner, L.partner.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colsrc, L.colsrc.data(), L.Ktot * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colstride, L.colstride.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colpan, L.colpan.data(), L.Ktot * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.panstride, L.panstride.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    }
+    if (L.ndense > 0)
+        CKF(cudaMemcpyAsync((void*)h->pm.zsrc, L.zsrc.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+    if (build_tables(h, h->tab_base)) {
+        h->err = "uploading GEMM tables failed";
+        return fail(TLR_ERR_CUDA);
+    }
+    CKF(cudaEventCreate(&h->ev0));
+    CKF(cudaEventCreate(&h->ev1));
+    CKF(cudaStreamSynchronize(h->st));
+    CKF(cudaMemcpy(&h->alpha, h->scal, sizeof(double), cudaMemcpyDeviceToHost));
+#undef CKF
+    *out = h;
+    return TLR_OK;
+}
+
+static int forward(tlr_mdd_s* h, bool plain_apply) {
+    const Layout& L = h->L;
+    CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st));
+    CK(h, run_gemm(h->Lc_x, h->st));
+    CK(h, gemm_simt(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
+    return TLR_OK;
+}
+
+static int gradient(tlr_mdd_s* h) {
+    const Layout& L = h->L;
+    CK(h, run_gemm(h->Lc_v, h->st));
+    CK(h, run_gemm(h->Lp, h->st));
+    CK(h, reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.b, h->gf, h->st));
+    return TLR_OK;
+}
+
+int tlr_mdd_apply(tlr_mdd_t* h, const void* theta, void* Y) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!theta || !Y) FAIL(h, TLR_ERR_ARG, "theta or Y is NULL");
+    const Layout& L = h->L;
+    CK(h, theta_to_panel(h->pm, (const cf*)theta, h->x, h->st));
+    int rc = forward(h, true);
+    if (rc) return rc;
+    CK(h, cudaMemcpyAsync(Y, h->R, (size_t)L.nr * L.ns * sizeof(cf), cudaMemcpyDeviceToDevice, h->st));
+    return TLR_OK;
+}
+
+int tlr_mdd_grad(tlr_mdd_t* h, const void* theta, void* grad, double* f) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!theta || !grad) FAIL(h, TLR_ERR_ARG, "theta or grad is NULL");
+    const Layout& L = h->L;
+    CK(h, theta_to_panel(h->pm, (const cf*)theta, h->x, h->st));
+    int rc = forward(h, false);
+    if (rc) return rc;
+    rc = gradient(h);
+    if (rc) return rc;
+    CK(h, panel_to_theta(h->pm, h->gf, (cf*)grad, h->st));
+    if (f) {
+        CK(h, sv_norm_part(h->R, (long long)L.nr * L.ns, h->dpart, h->st));
+        CK(h, finalize(h->dpart, kRedBlocks, 1, 1, h->scal + 1, h->st));
+        double rr = 0;
+        CK(h, cudaMemcpyAsync(&rr, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        *f = 0.5 * rr;
+    }
+    return TLR_OK;
+}
+
+int tlr_mdd_adjoint(tlr_mdd_t* h, const void* V, void* G) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!V || !G) FAIL(h, TLR_ERR_ARG, "V or G is NULL");
+    const Layout& L = h->L;
+    const long long nr = L.nr, ns = L.ns;
+    const long long tiles = ((nr + 63) / 64) * ((nr + 63) / 64);
+    const int ns_split = choose_split(tiles, ns);
+    GProb p;
+    memset(&p, 0, sizeof(p));
+    p.t[0] = term((const cf*)V, ns, h->Dt, ns, nullptr, (int)ns, false, true);
+    p.nt = 1;
+    p.M = (int)nr;
+    p.N = (int)nr;
+    p.ldc = nr;
+    GProb* dp = nullptr;
+    cf* part = nullptr;
+    CK(h, cudaMallocAsync((void**)&dp, sizeof(GProb), h->st));
+    if (ns_split > 1) {
+        cudaError_t e = cudaMallocAsync((void**)&part, (size_t)ns_split * nr * nr * sizeof(cf), h->st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dp, h->st);
+            CK(h, e);
+        }
+        p.C = part;
+    } else {
+        p.C = (cf*)G;
+    }
+    GemmLaunch G1;
+    G1.d_probs = dp;
+    G1.nprob = 1;
+    G1.maxM = G1.maxN = (int)nr;
+    G1.amode = A_MK;
+    G1.bmode = B_NK;
+    G1.nsplit = ns_split;
+    G1.kchunk = (int)(((ns + ns_split - 1) / ns_split + 15) / 16 * 16);
+    G1.part_stride = nr * nr;
+    G1.epi = ns_split > 1 ? EPI_PARTIAL : EPI_STORE;
+    cudaError_t e = cudaMemcpyAsync(dp, &p, sizeof(GProb), cudaMemcpyHostToDevice, h->st);
+    G1.flops = 8.0 * nr * (double)nr * ns;
+    G1.cls = 2;
+    if (e == cudaSuccess) e = run_gemm(G1, h->st);
+    if (e == cudaSuccess && ns_split > 1) e = reduce_grad(part, ns_split, nr * nr, nr * nr, 0, 1, (cf*)G, h->st);
+    if (part) cudaFreeAsync(part, h->st);
+    cudaFreeAsync(dp, h->st);
+    CK(h, e);
+    CK(h, cudaStreamSynchronize(h->st));  // p lives on this stack frame
+    return TLR_OK;
+}
+
+int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");
+    const Layout& L = h->L;
+    const long long nr = L.nr;
+    std::vector<AsmTile> tiles(L.N + L.P);
+    for (int i = 0; i < L.N; ++i)
+        tiles[i] = AsmTile{L.off_diag[i], L.off_diag[i], L.dense[i] ? (int)L.b : L.kd[i], (int)L.dense[i]};
+    for (int p = 0; p < L.P; ++p) tiles[L.N + p] = AsmTile{L.off_l[p], L.off_r[p], L.kp[p], 0};
+    cf* Xh = nullptr;
+    AsmTile* dt = nullptr;
+    CK(h, cudaMallocAsync((void**)&Xh, (size_t)nr * nr * sizeof(cf), h->st));
+    cudaError_t e = cudaMallocAsync((void**)&dt, tiles.size() * sizeof(AsmTile), h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(AsmTile), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = assemble_dense((const cf*)theta, nr, L.b, L.N, dt, Xh, h->st);
+    if (e == cudaSuccess) e = unpermute_dense(Xh, nr, h->perm, (cf*)X, h->st);
+    if (dt) cudaFreeAsync(dt, h->st);
+    cudaFreeAsync(Xh, h->st);
+    CK(h, e);
+    CK(h, cudaStreamSynchronize(h->st));
+    return TLR_OK;
+}
+
+int tlr_mdd_get_data(tlr_mdd_t* h, int32_t* perm_host, double* alpha, void* Dt, void* Ut) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    const Layout& L = h->L;
+    if (perm_host) CK(h, cudaMemcpyAsync(perm_host, h->perm, L.nr * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+    if (Dt) CK(h, cudaMemcpyAsync(Dt, h->Dt, (size_t)L.nr * L.ns * sizeof(cf), cudaMemcpyDeviceToDevice, h->st));
+    if (Ut) CK(h, cudaMemcpyAsync(Ut, h->Ut, (size_t)L.nr * L.ns * sizeof(cf), cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (alpha) *alpha = h->alpha;
+    return TLR_OK;
+}
+
+void tlr_mdd_timing_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing = on != 0;
+}
+
+void tlr_mdd_timing_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (auto& t : g_pending) {
+        cudaEventSynchronize(t.b);
+        g_evpool.push_back(t.a);
+        g_evpool.push_back(t.b);
+    }
+    g_pending.clear();
+    for (int c = 0; c < TLR_NCLASS; ++c) g_ms[c] = g_fl[c] = 0.0, g_nl[c] = 0;
+}
+
+int tlr_mdd_timing_read(double* ms, double* flops, int64_t* launches, int nclass) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (auto& t : g_pending) {
+        if (cudaEventSynchronize(t.b) != cudaSuccess) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_CUDA, "timing event failed");
+        float m = 0.f;
+        cudaEventElapsedTime(&m, t.a, t.b);
+        g_ms[t.cls] += m;
+        g_fl[t.cls] += t.flops;
+        g_nl[t.cls] += 1;
+        g_evpool.push_back(t.a);
+        g_evpool.push_back(t.b);
+    }
+    g_pending.clear();
+    for (int c = 0; c < nclass && c < TLR_NCLASS; ++c) {
+        if (ms) ms[c] = g_ms[c];
+        if (flops) flops[c] = g_fl[c];
+        if (launches) launches[c] = g_nl[c];
+    }
+    return TLR_OK;
+}
+
+int64_t tlr_mdd_launch_count(void) { return g_launches.load(); }
+
+void* tlr_mdd_stream(const tlr_mdd_t* h) { return h ? (void*)h->st : nullptr; }
+
+const char* tlr_mdd_last_error(const tlr_mdd_t* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+int tlr_mdd_destroy(tlr_mdd_t* h) {
+    if (!h) return TLR_ERR_ARG;
+    if (h->ring) cudaFreeAsync(h->ring, h->st);
+    if (h->arena) cudaFreeAsync(h->arena, h->st);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    delete h;
+    return e == cudaSuccess ? TLR_OK : TLR_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o, tlr_mdd_stats_t* stats) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!theta_inout || !o) FAIL(h, TLR_ERR_ARG, "theta or opts is NULL");
+    if (o->memory < 1 || o->memory > 32) FAIL(h, TLR_ERR_ARG, "memory must lie in [1, 32]");
+    if (!(o->rho > 0.0) || o->stages < 0 || o->admm_iters < 0 || o->lbfgs_iters < 0 || !(o->lam0 >= 0.0))
+        FAIL(h, TLR_ERR_ARG, "invalid solver options");
+    const Layout& L = h->L;
+    const long long n2 = 2 * L.nth;
+    const long long nrs = (long long)L.nr * L.ns;
+    // ring of s / y vectors, m + 1 slots each
+    if (h->ring_m < o->memory) {
+        if (h->ring) cudaFreeAsync(h->ring, h->st);
+        h->ring = nullptr;
+        h->ring_m = 0;
+        CK(h, cudaMallocAsync((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), h->st));
+        h->ring_m = o->memory;
+    }
+    SolverDev S;
+    S.n2 = n2;
+    S.m = o->memory;
+    S.ring = o->memory + 1;
+    S.x = (float*)h->x;
+    S.z = (float*)h->z;
+    S.u = (float*)h->u;
+    S.v = (float*)h->v;
+    S.g = (float*)h->g;
+    S.gf = (float*)h->gf;
+    S.d = (float*)h->dd;
+    S.q = (float*)h->q;
+    S.sh = h->ring;
+    S.yh = h->ring + (size_t)S.ring * n2;
+    S.rho_h = h->rho_h;
+    S.sy_h = h->sy_h;
+    S.yy_h = h->yy_h;
+    S.acoef = h->acoef;
+    S.sc = h->sc;
+    S.ints = h->ints;
+    S.fhist = h->fhist;
+    S.part = h->dpart;                       // 2 slabs
+    double* part6 = h->dpart + 2 * kRedBlocks;   // 6 slabs
+    double* part3 = h->dpart + 8 * kRedBlocks;   // 3 slabs
+    double* part3b = h->dpart + 11 * kRedBlocks; // 3 slabs
+    double* partf = h->dpart + 14 * kRedBlocks;  // 1 slab
+    const double rho = o->rho;
+
+    CK(h, cudaEventRecord(h->ev0, h->st));
+    if (o->theta_memory == TLR_MEM_HOST) {
+        CK(h, cudaMemcpyAsync(h->q, theta_inout, L.nth * sizeof(cf), cudaMemcpyHostToDevice, h->st));
+        CK(h, theta_to_panel(h->pm, h->q, h->x, h->st));
+    } else {
+        CK(h, theta_to_panel(h->pm, (const cf*)theta_inout, h->x, h->st));
+    }
+    CK(h, sv_admm_init(S, h->st));
+    int rc = forward(h, false);
+    if (rc) return rc;
+    CK(h, sv_norm_part(h->R, nrs, partf, h->st));
+    CK(h, sv_record_f0(S, partf, h->st));
+    rc = gradient(h);
+    if (rc) return rc;
+    for (int s = 0; s < o->stages; ++s) {
+        const double lam = o->lam0 * std::pow(o->decay, (double)s);
+        for (int it = 0; it < o->admm_iters; ++it) {
+            CK(h, sv_xupdate_start(S, rho, h->st));
+            for (int t = 0; t < o->lbfgs_iters; ++t) {
+                CK(h, sv_two_loop(S, h->st));
+                CK(h, run_gemm(h->Lc_d, h->st));
+                CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.b, h->Zsd, h->st));
+                CK(h, run_gemm(h->Le_a1, h->st));
+                CK(h, run_gemm(h->Le_a2, h->st));
+                CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));
+                CK(h, sv_dots3(S, part3, h->st));
+                CK(h, sv_line_search(S, part6, part3, rho, h->st));
+                CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
+                if (L.Ktot > 0)
+                    CK(h, axpy_dev((float*)h->T, (const float*)h->Tp, 2LL * L.Ktot * L.ns, h->sc + SC_ALPHA, h->st));
+                CK(h, sv_step_theta(S, h->st));
+                rc = gradient(h);
+                if (rc) return rc;
+                CK(h, sv_pair_prep(S, rho, part3b, h->st));
+                CK(h, sv_pair_accept(S, part3b, partf, h->st));
+            }
+            CK(h, sv_admm_zu(S, lam, rho, h->st));
+        }
+    }
+    if (o->theta_memory == TLR_MEM_HOST) {
+        CK(h, panel_to_theta(h->pm, h->x, h->q, h->st));
+        CK(h, cudaMemcpyAsync(theta_inout, h->q, L.nth * sizeof(cf), cudaMemcpyDeviceToHost, h->st));
+    } else {
+        CK(h, panel_to_theta(h->pm, h->x, (cf*)theta_inout, h->st));
+    }
+    CK(h, cudaEventRecord(h->ev1, h->st));
+    int ints[SI_COUNT];
+    double sc[SC_COUNT];
+    CK(h, cudaMemcpyAsync(ints, h->ints, sizeof(ints), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->st));
+    if (stats) CK(h, cudaMemcpyAsync(stats->f_hist, h->fhist, sizeof(double) * TLR_MAX_HIST, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (stats) {
+        stats->iters = ints[SI_ITERS];
+        stats->restarts = ints[SI_RESTARTS];
+        stats->status = ints[SI_STATUS];
+        stats->n_hist = std::min(ints[SI_ITERS], TLR_MAX_HIST);
+        stats->f0 = sc[SC_F0];
+        stats->gpu_ms = ms;
+    }
+    if (ints[SI_STATUS] != 0) FAIL(h, TLR_ERR_NONFINITE, "non-finite value met during the solve");
+    return TLR_OK;
+}
+
+}  // extern "C"

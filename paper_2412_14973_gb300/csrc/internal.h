@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of libtlr_mdd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/tlr_mdd.h"
+
+namespace tlr {
+
+typedef float2 cf;  // complex64, interleaved
+
+// number of kernels this library has launched (diagnostics)
+extern std::atomic<long long> g_launches;
+inline void counted(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Grouped complex GEMM descriptors (FP32 SIMT and tensor-core paths).
+//
+// One problem computes C[m, n] (M x N) = sum over terms t of
+//   sum_k opA_t[m, k] * opB_t[k, n]
+// with, per term,
+//   A element (m, k) at A[k * lda + m]  (KM mode) or A[m * lda + k] (MK mode),
+//   B element (k, n) at B[row(k) * ldb + n] (KN mode) or B[row(n) * ldb + k]
+//   (NK mode), row(r) = g ? g[r] : r  (a row gather),
+//   and the imaginary parts of A / B multiplied by sa / sb (+1 or -1: conj).
+// ---------------------------------------------------------------------------
+struct GTerm {
+    const cf* A;
+    const cf* B;
+    const int* g;
+    long long lda, ldb;
+    int K;
+    float sa, sb;
+};
+
+constexpr int kMaxTerms = 3;
+
+struct GProb {
+    GTerm t[kMaxTerms];
+    int nt;
+    int M, N;
+    cf* C;          // output (or partial buffer base for split-K)
+    const cf* S;    // subtrahend for EPI_SUB (same indexing as C)
+    long long ldc;
+};
+
+enum Epi { EPI_STORE = 0, EPI_SUB = 1, EPI_ACCUM = 2, EPI_PARTIAL = 3 };
+enum AMode { A_KM = 0, A_MK = 1 };
+enum BMode { B_KN = 0, B_NK = 1 };
+
+struct GemmLaunch {
+    GProb* d_probs = nullptr;   // device copy
+    int nprob = 0;
+    int maxM = 0, maxN = 0, maxK = 0;
+    int nsplit = 1;
+    int kchunk = 0;             // per-split K range (multiple of the K tile)
+    long long part_stride = 0;  // elements between split-K partial slabs
+    int amode = 0, bmode = 0, epi = 0;
+    double flops = 0.0;         // algorithmic flops of one launch (8 per complex MAC)
+    int cls = 0;                // diagnostics class (0 compress, 1 expand, 2 project)
+};
+
+// SIMT path (k_gemm_simt.cu)
+cudaError_t gemm_simt(const GemmLaunch& L, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// data kernels (k_data.cu)
+// ---------------------------------------------------------------------------
+cudaError_t hilbert_perm(int nx, int ny, int32_t* perm, int32_t* scratch_keys, cudaStream_t st);
+// max |D|^2 over n complex entries -> *out (device double), deterministic
+cudaError_t max_abs2(const cf* D, long long n, double* partial, int nblk, double* out, cudaStream_t st);
+// Dt[a, s] = D[s, perm[a]] / alpha for D ns x nr row-major; alpha read from device
+cudaError_t permute_normalise(const cf* D, long long ns, long long nr, const int32_t* perm,
+                              const double* alpha_dev, cf* Dt, cudaStream_t st);
+// Per-tile description for dense assembly: tiles 0..N-1 are the diagonal
+// (off_l = theta offset of Q_ii or Z_ii, off_r = off_l for Q), then the
+// sub-diagonal pairs in stacking order (off_l = L_ij, off_r = R_ij).
+struct AsmTile {
+    long long off_l, off_r;
+    int k;
+    int dense;
+};
+cudaError_t assemble_dense(const cf* theta, long long nr, long long b, int N, const AsmTile* tiles, cf* Xh,
+                           cudaStream_t st);
+// X[perm[a], perm[c]] = Xh[a, c]
+cudaError_t unpermute_dense(const cf* Xh, long long nr, const int32_t* perm, cf* X, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// theta-space and reduction kernels (k_vec.cu)
+// ---------------------------------------------------------------------------
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs: fixed grid -> fixed summation order
+constexpr int kRedThreads = 256;
+
+// theta (paper stacking) <-> panel vector (block-major factor panels + dense tiles)
+struct PanelMap {
+    const long long* colsrc;   // [Ktot] theta offset of row 0 of this panel column
+    const int* colstride;      // [Ktot] row stride in theta (rank of the factor)
+    const long long* colpan;   // [Ktot] panel offset of row 0 of this column
+    const int* panstride;      // [Ktot] row stride in the panel (K of its block)
+    const long long* zsrc;     // [ndense] theta offset of each dense tile
+    long long Ktot, b, ndense, zbase;  // zbase = b * Ktot
+};
+cudaError_t theta_to_panel(const PanelMap& m, const cf* theta, cf* pan, cudaStream_t st);
+cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStream_t st);
+// Zs = (Z + Z^T)/2 for every dense tile of a panel vector
+cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st);
+// grad[e] = sum_c part[c * stride + e] (LR part), dense tiles symmetrised: (G + G^T)/2;
+// then, if rho != 0: grad += rho (x - v)   (x, v may be null when rho == 0)
+cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
+                        long long b, cf* grad, cudaStream_t st);
+
+// partial FP64 real dot sums over float arrays (2 per complex) -> part[kRedBlocks]
+cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st);
+// out[k] = sum_{blk} part[blk * stride + k], k < cnt, one block, fixed order
+cudaError_t finalize(const double* part, int nblk, int stride, int cnt, double* out, cudaStream_t st);
+// six partials of the line-search inner products over Rf, A1, A2 (n complex)
+cudaError_t dots6_part(const cf* R, const cf* A1, const cf* A2, long long n, double* part, cudaStream_t st);
+// elementwise step: R += a A1 + a^2 A2 (n complex); alpha read from device
+cudaError_t step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha, cudaStream_t st);
+// x += a * y over n2 floats, a = alpha[0] (device)
+cudaError_t axpy_dev(float* x, const float* y, long long n2, const double* alpha, cudaStream_t st);
+
+
+}  // namespace tlr

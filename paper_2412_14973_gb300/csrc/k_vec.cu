@@ -1,0 +1,677 @@
+// theta-space and reduction kernels: the layout maps between the stacked
+// unknown (Z-bar, L-bar, R-bar) and the block panels, the gradient split-K
+// reduction with the dense-tile symmetrisation (eq. 26), FP64 inner products,
+// the exact line search on the quartic phi(alpha), and the L-BFGS two-loop
+// recursion / ADMM updates (eq. 19-24) with every scalar kept on the device.
+//
+// All reductions run on a fixed grid (kRedBlocks x kRedThreads) and sum their
+// per-block partials in a fixed order, so results are bitwise reproducible.
+#include "internal.h"
+#include "solver_dev.h"
+
+namespace tlr {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of v (blockDim.x == kRedThreads); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Sum of part[i * stride + k] over i < nblk by warp 0 in a fixed order; every
+// block that calls this obtains the same value.  Result broadcast via shared.
+__device__ __forceinline__ double sum_partials(const double* part, int nblk, int stride, int k, double* sh1) {
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nblk; i += 32) v += part[(long long)i * stride + k];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) sh1[0] = v;
+    }
+    __syncthreads();
+    const double r = sh1[0];
+    __syncthreads();
+    return r;
+}
+
+#define GRID_STRIDE(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// layout maps
+// ---------------------------------------------------------------------------
+__global__ void k_theta_to_panel(PanelMap m, const cf* __restrict__ th, cf* __restrict__ pan) {
+    const long long nlr = m.Ktot * m.b;
+    GRID_STRIDE(e, nlr) {
+        const long long g = e % m.Ktot, a = e / m.Ktot;
+        pan[m.colpan[g] + a * m.panstride[g]] = th[m.colsrc[g] + a * m.colstride[g]];
+    }
+    const long long nz = m.ndense * m.b * m.b;
+    GRID_STRIDE(e, nz) {
+        const long long t = e / (m.b * m.b), r = e % (m.b * m.b);
+        pan[m.zbase + e] = th[m.zsrc[t] + r];
+    }
+}
+
+__global__ void k_panel_to_theta(PanelMap m, const cf* __restrict__ pan, cf* __restrict__ th) {
+    const long long nlr = m.Ktot * m.b;
+    GRID_STRIDE(e, nlr) {
+        const long long g = e % m.Ktot, a = e / m.Ktot;
+        th[m.colsrc[g] + a * m.colstride[g]] = pan[m.colpan[g] + a * m.panstride[g]];
+    }
+    const long long nz = m.ndense * m.b * m.b;
+    GRID_STRIDE(e, nz) {
+        const long long t = e / (m.b * m.b), r = e % (m.b * m.b);
+        th[m.zsrc[t] + r] = pan[m.zbase + e];
+    }
+}
+
+cudaError_t theta_to_panel(const PanelMap& m, const cf* theta, cf* pan, cudaStream_t st) {
+    k_theta_to_panel<<<1024, 256, 0, st>>>(m, theta, pan);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStream_t st) {
+    k_panel_to_theta<<<1024, 256, 0, st>>>(m, pan, theta);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// Zs = (Z + Z^T)/2 (the symmetrisation preconditioner P of eq. 7)
+__global__ void k_sym_dense(const cf* __restrict__ pan, long long zbase, long long ndense, long long b,
+                            cf* __restrict__ Zs) {
+    const long long bb = b * b;
+    GRID_STRIDE(e, ndense * bb) {
+        const long long t = e / bb, r = (e % bb) / b, c = e % b;
+        const cf u = pan[zbase + t * bb + r * b + c];
+        const cf v = pan[zbase + t * bb + c * b + r];
+        Zs[e] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y + v.y));
+    }
+}
+
+cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st) {
+    if (ndense == 0) return cudaSuccess;
+    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// grad = sum of split-K partials (FP64, fixed order); dense tiles: (G + G^T)/2
+__global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long stride, long long nlr,
+                              long long ndense, long long b, cf* __restrict__ grad) {
+    GRID_STRIDE(e, nlr) {
+        double x = 0.0, y = 0.0;
+        for (int c = 0; c < nsplit; ++c) {
+            const cf v = part[c * stride + e];
+            x += v.x;
+            y += v.y;
+        }
+        grad[e] = make_float2((float)x, (float)y);
+    }
+    const long long bb = b * b;
+    GRID_STRIDE(e, ndense * bb) {
+        const long long t = e / bb, r = (e % bb) / b, q = e % b;
+        const long long e1 = nlr + t * bb + r * b + q, e2 = nlr + t * bb + q * b + r;
+        double x = 0.0, y = 0.0;
+        for (int c = 0; c < nsplit; ++c) {
+            const cf u = part[c * stride + e1];
+            const cf v = part[c * stride + e2];
+            x += (double)u.x + v.x;
+            y += (double)u.y + v.y;
+        }
+        grad[nlr + e] = make_float2((float)(0.5 * x), (float)(0.5 * y));
+    }
+}
+
+cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
+                        long long b, cf* grad, cudaStream_t st) {
+    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 inner products
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads) k_dot_part(const float* __restrict__ a, const float* __restrict__ b,
+                                                         long long n2, double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    GRID_STRIDE(i, n2) s += (double)a[i] * b[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st) {
+    k_dot_part<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n2, part);
+    counted(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_finalize(const double* part, int nblk, int stride, int cnt, double* out) {
+    __shared__ double sh1[1];
+    for (int k = 0; k < cnt; ++k) {
+        const double v = sum_partials(part, nblk, stride, k, sh1);
+        if (threadIdx.x == 0) out[k] = v;
+    }
+}
+
+cudaError_t finalize(const double* part, int nblk, int stride, int cnt, double* out, cudaStream_t st) {
+    k_finalize<<<1, 32, 0, st>>>(part, nblk, stride, cnt, out);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// Re<R,R>, Re<R,A1>, Re<R,A2>, Re<A1,A1>, Re<A1,A2>, Re<A2,A2>  -> part[blk*6 + k]
+__global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R, const cf* __restrict__ A1,
+                                                      const cf* __restrict__ A2, long long n, double* part) {
+    __shared__ double sh[32];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    GRID_STRIDE(i, n) {
+        const cf r = R[i], a = A1[i], c = A2[i];
+        s[0] += (double)r.x * r.x + (double)r.y * r.y;
+        s[1] += (double)r.x * a.x + (double)r.y * a.y;
+        s[2] += (double)r.x * c.x + (double)r.y * c.y;
+        s[3] += (double)a.x * a.x + (double)a.y * a.y;
+        s[4] += (double)a.x * c.x + (double)a.y * c.y;
+        s[5] += (double)c.x * c.x + (double)c.y * c.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = block_sum(s[k], sh);
+        if (threadIdx.x == 0) part[blockIdx.x * 6 + k] = v;
+    }
+}
+
+cudaError_t dots6_part(const cf* R, const cf* A1, const cf* A2, long long n, double* part, cudaStream_t st) {
+    k_dots6<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, part);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// R += a A1 + a^2 A2 ; partial of ||R_new||^2 -> part[blk]
+__global__ void __launch_bounds__(kRedThreads) k_step_residual(cf* __restrict__ R, const cf* __restrict__ A1,
+                                                              const cf* __restrict__ A2, long long n,
+                                                              const double* __restrict__ alpha, double* part) {
+    __shared__ double sh[32];
+    const float a = (float)alpha[0];
+    const float a2 = (float)(alpha[0] * alpha[0]);
+    double s = 0.0;
+    GRID_STRIDE(i, n) {
+        cf r = R[i];
+        if (a != 0.f) {
+            const cf u = A1[i], w = A2[i];
+            r.x = fmaf(a2, w.x, fmaf(a, u.x, r.x));
+            r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
+            R[i] = r;
+        }
+        s += (double)r.x * r.x + (double)r.y * r.y;
+    }
+    s = block_sum(s, sh);
+    if (part && threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+cudaError_t step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha, cudaStream_t st) {
+    k_step_residual<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, alpha, nullptr);
+    counted(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_axpy_dev(float* __restrict__ x, const float* __restrict__ y, long long n2,
+                           const double* __restrict__ alpha) {
+    const float a = (float)alpha[0];
+    if (a == 0.f) return;
+    GRID_STRIDE(i, n2) x[i] = fmaf(a, y[i], x[i]);
+}
+
+cudaError_t axpy_dev(float* x, const float* y, long long n2, const double* alpha, cudaStream_t st) {
+    k_axpy_dev<<<1024, 256, 0, st>>>(x, y, n2, alpha);
+    counted(1);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Solver kernels (L-BFGS two-loop recursion, exact line search, ADMM).
+// ===========================================================================
+
+// f = 0.5 ||R||^2 from a fresh norm pass: part[blk] -> sc[SC_F]
+__global__ void __launch_bounds__(kRedThreads) k_norm_part(const cf* __restrict__ R, long long n, double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    GRID_STRIDE(i, n) {
+        const cf r = R[i];
+        s += (double)r.x * r.x + (double)r.y * r.y;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// g = gf + rho (x - v); history cleared (start of an x-update)
+__global__ void k_xupdate_start(SolverDev S, double rho) {
+    const float r = (float)rho;
+    GRID_STRIDE(i, S.n2) S.g[i] = S.gf[i] + r * (S.x[i] - S.v[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.ints[SI_CNT] = 0;
+}
+
+__device__ __forceinline__ int ring_idx(const SolverDev& S, int j) {
+    // j-th newest pair (0 = newest)
+    const int R = S.ring;
+    return ((S.ints[SI_NEWEST] - j) % R + R) % R;
+}
+
+// The two-loop kernels pass partial sums along the chain in two ping-pong
+// slabs: kernel t reads slab pin (written by kernel t-1) in every block and
+// writes its own partials to pout, so no block overwrites what another reads.
+
+// first pass, initial kernel: q = g; partial <s_0, q> if cnt > 0
+__global__ void __launch_bounds__(kRedThreads) k_tl1_init(SolverDev S, double* pout) {
+    __shared__ double sh[32];
+    const int cnt = S.ints[SI_CNT];
+    const float* s0 = cnt > 0 ? S.sh + (long long)ring_idx(S, 0) * S.n2 : nullptr;
+    double acc = 0.0;
+    GRID_STRIDE(i, S.n2) {
+        const float q = S.g[i];
+        S.q[i] = q;
+        if (s0) acc += (double)s0[i] * q;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+}
+
+// first pass, step j (j-th newest pair): a_j = rho_j <s_j, q>; q -= a_j y_j;
+// partial <s_{j+1}, q> for the next step
+__global__ void __launch_bounds__(kRedThreads) k_tl1_step(SolverDev S, int j, const double* pin, double* pout) {
+    __shared__ double sh[32];
+    __shared__ double sh1[1];
+    const int cnt = S.ints[SI_CNT];
+    if (j >= cnt) return;
+    const int idx = ring_idx(S, j);
+    const double dot = sum_partials(pin, kRedBlocks, 1, 0, sh1);
+    const double a = S.rho_h[idx] * dot;
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.acoef[j] = a;
+    const float af = (float)a;
+    const float* y = S.yh + (long long)idx * S.n2;
+    const float* sn = (j + 1 < cnt) ? S.sh + (long long)ring_idx(S, j + 1) * S.n2 : nullptr;
+    double acc = 0.0;
+    GRID_STRIDE(i, S.n2) {
+        const float q = fmaf(-af, y[i], S.q[i]);
+        S.q[i] = q;
+        if (sn) acc += (double)sn[i] * q;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+}
+
+// second pass, initial kernel: r = gamma q with gamma = <s,y>/<y,y> of the
+// newest pair (1 without pairs); partial <y_jstart, r> if jstart < cnt
+__global__ void __launch_bounds__(kRedThreads) k_tl2_init(SolverDev S, int jstart, double* pout) {
+    __shared__ double sh[32];
+    const int cnt = S.ints[SI_CNT];
+    double gamma = 1.0;
+    if (cnt > 0) {
+        const int nw = ring_idx(S, 0);
+        gamma = S.sy_h[nw] / S.yy_h[nw];
+    }
+    const float gf = (float)gamma;
+    const float* yn = (jstart < cnt) ? S.yh + (long long)ring_idx(S, jstart) * S.n2 : nullptr;
+    double acc = 0.0;
+    GRID_STRIDE(i, S.n2) {
+        const float r = gf * S.q[i];
+        S.q[i] = r;
+        if (yn) acc += (double)yn[i] * r;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+}
+
+// second pass, step j (j descending, oldest first): b = rho_j <y_j, r>;
+// r += (a_j - b) s_j; partial <y_{j-1}, r>; the last step (j == 0) writes d = -r.
+__global__ void __launch_bounds__(kRedThreads) k_tl2_step(SolverDev S, int j, const double* pin, double* pout) {
+    __shared__ double sh[32];
+    __shared__ double sh1[1];
+    const int cnt = S.ints[SI_CNT];
+    const bool active = j < cnt;
+    const bool need_next = (j - 1 >= 0) && (j - 1 < cnt);
+    if (!active && !need_next && j != 0) return;
+    float coef = 0.f;
+    const float* s = nullptr;
+    if (active) {
+        const int idx = ring_idx(S, j);
+        const double dot = sum_partials(pin, kRedBlocks, 1, 0, sh1);
+        coef = (float)(S.acoef[j] - S.rho_h[idx] * dot);
+        s = S.sh + (long long)idx * S.n2;
+    }
+    const float* yn = need_next ? S.yh + (long long)ring_idx(S, j - 1) * S.n2 : nullptr;
+    double acc = 0.0;
+    GRID_STRIDE(i, S.n2) {
+        float r = S.q[i];
+        if (s) {
+            r = fmaf(coef, s[i], r);
+            S.q[i] = r;
+        }
+        if (yn) acc += (double)yn[i] * r;
+        if (j == 0) S.d[i] = -r;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+}
+
+// theta-space line-search inner products: <x - v, x - v>, <x - v, d>, <d, d>
+__global__ void __launch_bounds__(kRedThreads) k_dots3(SolverDev S, double* part) {
+    __shared__ double sh[32];
+    double s0 = 0, s1 = 0, s2 = 0;
+    GRID_STRIDE(i, S.n2) {
+        const double w = (double)S.x[i] - S.v[i];
+        const double d = S.d[i];
+        s0 += w * w;
+        s1 += w * d;
+        s2 += d * d;
+    }
+    double r;
+    r = block_sum(s0, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 0] = r;
+    r = block_sum(s1, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 1] = r;
+    r = block_sum(s2, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 2] = r;
+}
+
+__device__ double quartic_val(const double* c, double a) {
+    return c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * c[4])));
+}
+
+__device__ void consider(const double* c, double a, double& best_a, double& best_v, bool& have) {
+    // two Newton polishes on phi'
+    for (int it = 0; it < 2; ++it) {
+        const double d1 = c[1] + a * (2 * c[2] + a * (3 * c[3] + a * 4 * c[4]));
+        const double d2 = 2 * c[2] + a * (6 * c[3] + a * 12 * c[4]);
+        if (d2 != 0.0) a -= d1 / d2;
+    }
+    if (!(a > 0.0) || !isfinite(a)) return;
+    const double v = quartic_val(c, a);
+    if (!have || v < best_v || (v == best_v && a < best_a)) {
+        have = true;
+        best_a = a;
+        best_v = v;
+    }
+}
+
+// Minimiser over a > 0 of the quartic: real roots of phi'(a) =
+// 4 c4 a^3 + 3 c3 a^2 + 2 c2 a + c1 in closed form (depressed cubic:
+// trigonometric form for three real roots, Cardano otherwise), polished.
+__device__ bool quartic_argmin(const double* c, double* out) {
+    double best_a = 0.0, best_v = 0.0;
+    bool have = false;
+    const double A = 4 * c[4], B = 3 * c[3], C = 2 * c[2], D = c[1];
+    if (A != 0.0) {
+        const double p = B / A, q = C / A, r = D / A;
+        const double P = q - p * p / 3.0;
+        const double Q = 2.0 * p * p * p / 27.0 - p * q / 3.0 + r;
+        const double disc = 0.25 * Q * Q + P * P * P / 27.0;
+        const double sh = -p / 3.0;
+        if (disc > 0.0) {
+            const double sq = sqrt(disc);
+            const double t = cbrt(-0.5 * Q + sq) + cbrt(-0.5 * Q - sq);
+            consider(c, t + sh, best_a, best_v, have);
+        } else if (P == 0.0) {
+            consider(c, cbrt(-Q) + sh, best_a, best_v, have);
+        } else {
+            const double m = 2.0 * sqrt(-P / 3.0);
+            double arg = 3.0 * Q / (P * m);
+            arg = fmin(1.0, fmax(-1.0, arg));
+            const double th = acos(arg) / 3.0;
+            const double tpi = 2.0943951023931954923;  // 2 pi / 3
+            for (int k = 0; k < 3; ++k) consider(c, m * cos(th - tpi * k) + sh, best_a, best_v, have);
+        }
+    } else if (B != 0.0) {
+        const double dsc = C * C - 4 * B * D;
+        if (dsc >= 0.0) {
+            const double s = sqrt(dsc);
+            consider(c, (-C + s) / (2 * B), best_a, best_v, have);
+            consider(c, (-C - s) / (2 * B), best_a, best_v, have);
+        }
+    } else if (C != 0.0) {
+        consider(c, -D / C, best_a, best_v, have);
+    }
+    *out = best_a;
+    return have;
+}
+
+// One thread: finalise the 6 + 3 inner products, form phi's coefficients,
+// check descent, pick alpha; alpha = 0 and a memory reset when no step.
+__global__ void k_line_search(SolverDev S, const double* part6, const double* part3, double rho) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double d6[6] = {0, 0, 0, 0, 0, 0}, d3[3] = {0, 0, 0};
+    for (int i = 0; i < kRedBlocks; ++i) {
+        for (int k = 0; k < 6; ++k) d6[k] += part6[i * 6 + k];
+        for (int k = 0; k < 3; ++k) d3[k] += part3[i * 3 + k];
+    }
+    double c[5];
+    c[0] = 0.5 * d6[0] + 0.5 * rho * d3[0];
+    c[1] = d6[1] + rho * d3[1];
+    c[2] = 0.5 * d6[3] + d6[2] + 0.5 * rho * d3[2];
+    c[3] = d6[4];
+    c[4] = 0.5 * d6[5];
+    for (int k = 0; k < 5; ++k) S.sc[SC_C0 + k] = c[k];
+    double a = 0.0;
+    bool ok = false;
+    if (c[1] < 0.0) ok = quartic_argmin(c, &a);
+    if (!ok) {
+        a = 0.0;
+        S.ints[SI_CNT] = 0;
+        S.ints[SI_RESTARTS] += 1;
+    }
+    bool finite = isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(c[3]) && isfinite(c[4]);
+    if (!finite) {
+        a = 0.0;
+        S.ints[SI_STATUS] = TLR_ERR_NONFINITE;
+    }
+    S.sc[SC_ALPHA] = a;
+}
+
+// x += a d ; s_free = a d
+__global__ void k_step_theta(SolverDev S) {
+    const double ad = S.sc[SC_ALPHA];
+    const float a = (float)ad;
+    const int R = S.ring;
+    const int fr = (S.ints[SI_NEWEST] + 1) % R;
+    float* s = S.sh + (long long)fr * S.n2;
+    GRID_STRIDE(i, S.n2) {
+        const float st = a * S.d[i];
+        s[i] = st;
+        S.x[i] += st;
+    }
+}
+
+// y_free = (gf + rho (x - v)) - g ; g <- gf + rho (x - v); partials ss, sy, yy
+__global__ void __launch_bounds__(kRedThreads) k_pair_prep(SolverDev S, double rho, double* part) {
+    __shared__ double sh[32];
+    const float r = (float)rho;
+    const int R = S.ring;
+    const int fr = (S.ints[SI_NEWEST] + 1) % R;
+    const float* s = S.sh + (long long)fr * S.n2;
+    float* y = S.yh + (long long)fr * S.n2;
+    double ss = 0, sy = 0, yy = 0;
+    GRID_STRIDE(i, S.n2) {
+        const float gn = S.gf[i] + r * (S.x[i] - S.v[i]);
+        const float yi = gn - S.g[i];
+        y[i] = yi;
+        S.g[i] = gn;
+        const double si = s[i];
+        ss += si * si;
+        sy += si * yi;
+        yy += (double)yi * yi;
+    }
+    double t;
+    t = block_sum(ss, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 0] = t;
+    t = block_sum(sy, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 1] = t;
+    t = block_sum(yy, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 3 + 2] = t;
+}
+
+// one thread: accept the pair (s, y) when alpha > 0 and <s,y> > 1e-12 |s||y|;
+// record f = 0.5 ||R||^2 from the residual-norm partials.
+__global__ void k_pair_accept(SolverDev S, const double* part3, const double* partf) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double ss = 0, sy = 0, yy = 0, rr = 0;
+    for (int i = 0; i < kRedBlocks; ++i) {
+        ss += part3[i * 3 + 0];
+        sy += part3[i * 3 + 1];
+        yy += part3[i * 3 + 2];
+        rr += partf[i];
+    }
+    const double f = 0.5 * rr;
+    S.sc[SC_F] = f;
+    const int it = S.ints[SI_ITERS];
+    if (it < TLR_MAX_HIST) S.fhist[it] = f;
+    S.ints[SI_ITERS] = it + 1;
+    if (!isfinite(f)) S.ints[SI_STATUS] = TLR_ERR_NONFINITE;
+    if (S.sc[SC_ALPHA] > 0.0 && sy > 1e-12 * sqrt(ss * yy)) {
+        const int R = S.ring;
+        const int fr = (S.ints[SI_NEWEST] + 1) % R;
+        S.ints[SI_NEWEST] = fr;
+        S.ints[SI_CNT] = min(S.ints[SI_CNT] + 1, S.m);
+        S.rho_h[fr] = 1.0 / sy;
+        S.sy_h[fr] = sy;
+        S.yy_h[fr] = yy;
+    }
+}
+
+// ADMM z- and dual updates (eq. 23, 24 in scaled form) and v = z - u
+__global__ void k_admm_zu(SolverDev S, double lam, double rho) {
+    const float den = (float)(1.0 / (1.0 + 2.0 * lam / rho));
+    GRID_STRIDE(i, S.n2) {
+        const float x = S.x[i], u = S.u[i];
+        const float z = (x + u) * den;
+        const float un = u + x - z;
+        S.z[i] = z;
+        S.u[i] = un;
+        S.v[i] = z - un;
+    }
+}
+
+// start of the solve: z = x, u = 0, v = x, counters cleared
+__global__ void k_admm_init(SolverDev S) {
+    GRID_STRIDE(i, S.n2) {
+        const float x = S.x[i];
+        S.z[i] = x;
+        S.u[i] = 0.f;
+        S.v[i] = x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.ints[SI_CNT] = 0;
+        S.ints[SI_NEWEST] = 0;
+        S.ints[SI_ITERS] = 0;
+        S.ints[SI_RESTARTS] = 0;
+        S.ints[SI_STATUS] = 0;
+    }
+}
+
+// record f0 = 0.5 ||R||^2
+__global__ void k_record_f0(SolverDev S, const double* partf) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double rr = 0;
+    for (int i = 0; i < kRedBlocks; ++i) rr += partf[i];
+    S.sc[SC_F0] = 0.5 * rr;
+    S.sc[SC_F] = 0.5 * rr;
+}
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+cudaError_t sv_norm_part(const cf* R, long long n, double* part, cudaStream_t st) {
+    k_norm_part<<<kRedBlocks, kRedThreads, 0, st>>>(R, n, part);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t st) {
+    k_record_f0<<<1, 32, 0, st>>>(S, partf);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st) {
+    k_admm_init<<<1024, 256, 0, st>>>(S);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st) {
+    k_xupdate_start<<<1024, 256, 0, st>>>(S, rho);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_two_loop(const SolverDev& S, cudaStream_t st) {
+    double* slab[2] = {S.part, S.part + kRedBlocks};
+    // first pass: newest -> oldest
+    k_tl1_init<<<kRedBlocks, kRedThreads, 0, st>>>(S, slab[0]);
+    counted(1);
+    for (int j = 0; j < S.m; ++j) {
+        k_tl1_step<<<kRedBlocks, kRedThreads, 0, st>>>(S, j, slab[j & 1], slab[(j + 1) & 1]);
+        counted(1);
+    }
+    // second pass: oldest -> newest (j descending)
+    k_tl2_init<<<kRedBlocks, kRedThreads, 0, st>>>(S, S.m - 1, slab[0]);
+    counted(1);
+    for (int t = 0; t < S.m; ++t) {
+        const int j = S.m - 1 - t;
+        k_tl2_step<<<kRedBlocks, kRedThreads, 0, st>>>(S, j, slab[t & 1], slab[(t + 1) & 1]);
+        counted(1);
+    }
+    return cudaGetLastError();
+}
+cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {
+    k_dots3<<<kRedBlocks, kRedThreads, 0, st>>>(S, part);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
+                           cudaStream_t st) {
+    k_line_search<<<1, 32, 0, st>>>(S, part6, part3, rho);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha,
+                             double* partf, cudaStream_t st) {
+    k_step_residual<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, alpha, partf);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_step_theta(const SolverDev& S, cudaStream_t st) {
+    k_step_theta<<<1024, 256, 0, st>>>(S);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStream_t st) {
+    k_pair_prep<<<kRedBlocks, kRedThreads, 0, st>>>(S, rho, part);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, cudaStream_t st) {
+    k_pair_accept<<<1, 32, 0, st>>>(S, part3, partf);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_admm_zu(const SolverDev& S, double lam, double rho, cudaStream_t st) {
+    k_admm_zu<<<1024, 256, 0, st>>>(S, lam, rho);
+    counted(1);
+    return cudaGetLastError();
+}
+
+}  // namespace tlr

@@ -1,0 +1,45 @@
+// Device-side state of the ADMM / L-BFGS solver: every vector lives in the
+// panel layout of the stacked unknown (2 * n floats), every scalar decision
+// (step length, pair acceptance, memory reset) stays in device memory so the
+// whole solve is a fixed sequence of launches with no host round trip.
+#pragma once
+
+#include "internal.h"
+
+namespace tlr {
+
+enum ScalarSlot { SC_ALPHA = 0, SC_F, SC_F0, SC_C0, SC_C1, SC_C2, SC_C3, SC_C4, SC_COUNT };
+enum IntSlot { SI_CNT = 0, SI_NEWEST, SI_ITERS, SI_RESTARTS, SI_STATUS, SI_COUNT };
+
+struct SolverDev {
+    long long n2;        // floats per theta-space vector (2 * n_theta)
+    int m;               // L-BFGS memory
+    int ring;            // m + 1 slots: the slot after the newest is always free
+    float *x, *z, *u, *v, *g, *gf, *d, *q;
+    float *sh, *yh;      // ring of s and y vectors, ring * n2 floats each
+    double* rho_h;       // [ring] 1 / <s, y>
+    double* sy_h;        // [ring] <s, y>
+    double* yy_h;        // [ring] <y, y>
+    double* acoef;       // [m] first-pass coefficients
+    double* sc;          // ScalarSlot values
+    int* ints;           // IntSlot values
+    double* fhist;       // [TLR_MAX_HIST]
+    double* part;        // 2 * kRedBlocks partial slabs for the two-loop chain
+};
+
+cudaError_t sv_norm_part(const cf* R, long long n, double* part, cudaStream_t st);
+cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t st);
+cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st);
+cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st);
+cudaError_t sv_two_loop(const SolverDev& S, cudaStream_t st);
+cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st);
+cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
+                           cudaStream_t st);
+cudaError_t sv_step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha,
+                             double* partf, cudaStream_t st);
+cudaError_t sv_step_theta(const SolverDev& S, cudaStream_t st);
+cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStream_t st);
+cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, cudaStream_t st);
+cudaError_t sv_admm_zu(const SolverDev& S, double lam, double rho, cudaStream_t st);
+
+}  // namespace tlr

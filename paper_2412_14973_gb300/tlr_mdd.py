@@ -1,0 +1,285 @@
+"""ctypes binding of ``include/tlr_mdd.h`` -- argument marshalling only.
+
+Every function mirrors the C entry point of the same name; tensors are passed
+as raw device pointers (``tensor.data_ptr()``) and streams as
+``torch.cuda.Stream.cuda_stream``.  Errors raise ``TLRError`` carrying the C
+status code and the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+__all__ = [
+    "TLRError", "Desc", "SolveOpts", "Stats", "lib", "lib_path",
+    "TLR_PREC_FP32", "TLR_PREC_BF16X3", "TLR_DIAG_RULE", "TLR_DIAG_LOWRANK", "TLR_DIAG_DENSE",
+    "TLR_DIAG_PER_TILE", "TLR_MEM_DEVICE", "TLR_MEM_HOST", "TLR_RECIP_SYMMETRIC", "TLR_RECIP_NONE",
+    "ERR", "desc", "solve_opts", "tlr_mdd_theta_size", "tlr_mdd_theta_layout",
+    "tlr_mdd_workspace_bytes", "tlr_mdd_hilbert_perm", "tlr_mdd_create", "tlr_mdd_apply",
+    "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
+    "tlr_mdd_get_data", "tlr_mdd_destroy", "tlr_mdd_last_error", "EXPORTED",
+    "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
+]
+
+TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
+TLR_DIAG_RULE, TLR_DIAG_LOWRANK, TLR_DIAG_DENSE, TLR_DIAG_PER_TILE = 0, 1, 2, 3
+TLR_RECIP_SYMMETRIC, TLR_RECIP_NONE = 0, 1
+TLR_MEM_DEVICE, TLR_MEM_HOST = 0, 1
+ERR = {0: "OK", -1: "ARG", -2: "SHAPE", -3: "UNSUPPORTED", -4: "NOMEM", -5: "CUDA",
+       -6: "NONFINITE", -7: "TIMEOUT", -8: "STATE"}
+TLR_MAX_HIST = 1024
+
+EXPORTED = [
+    "tlr_mdd_desc_init", "tlr_mdd_solve_opts_init", "tlr_mdd_theta_size", "tlr_mdd_theta_layout",
+    "tlr_mdd_workspace_bytes", "tlr_mdd_hilbert_perm", "tlr_mdd_create", "tlr_mdd_apply",
+    "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
+    "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
+    "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
+]
+TLR_NCLASS = 3
+
+
+class TLRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"TLR_ERR_{ERR.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int64), ("ns", C.c_int64), ("nx", C.c_int32), ("ny", C.c_int32),
+        ("perm", C.POINTER(C.c_int32)), ("tile", C.c_int32), ("rank", C.c_int32),
+        ("ranks", C.POINTER(C.c_int32)), ("diag_mode", C.c_int32),
+        ("diag_dense", C.POINTER(C.c_uint8)), ("reciprocity", C.c_int32),
+        ("precision", C.c_int32), ("alpha", C.c_double), ("input_memory", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [
+        ("lam0", C.c_double), ("decay", C.c_double), ("stages", C.c_int32),
+        ("admm_iters", C.c_int32), ("lbfgs_iters", C.c_int32), ("memory", C.c_int32),
+        ("rho", C.c_double), ("theta_memory", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32), ("n_hist", C.c_int32),
+        ("f_hist", C.c_double * TLR_MAX_HIST), ("f0", C.c_double), ("gpu_ms", C.c_double),
+    ]
+
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "lib", "libtlr_mdd.so")
+
+
+def lib():
+    """The loaded library; raises if it was not built (there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        p = lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                               "(python paper_2412_14973_gb300/build.py)")
+        L = C.CDLL(p)
+        vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+        L.tlr_mdd_desc_init.argtypes = [C.POINTER(Desc)]
+        L.tlr_mdd_desc_init.restype = None
+        L.tlr_mdd_solve_opts_init.argtypes = [C.POINTER(SolveOpts)]
+        L.tlr_mdd_solve_opts_init.restype = None
+        L.tlr_mdd_theta_size.argtypes = [C.POINTER(Desc), C.POINTER(C.c_int64)]
+        L.tlr_mdd_theta_layout.argtypes = [C.POINTER(Desc), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_int64), C.POINTER(C.c_uint8)]
+        L.tlr_mdd_workspace_bytes.argtypes = [C.POINTER(Desc)]
+        L.tlr_mdd_workspace_bytes.restype = i64
+        L.tlr_mdd_hilbert_perm.argtypes = [C.c_int32, C.c_int32, vp, vp]
+        L.tlr_mdd_create.argtypes = [C.POINTER(vp), C.POINTER(Desc), vp, vp, vp]
+        L.tlr_mdd_apply.argtypes = [vp, vp, vp]
+        L.tlr_mdd_adjoint.argtypes = [vp, vp, vp]
+        L.tlr_mdd_grad.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.tlr_mdd_solve.argtypes = [vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)]
+        L.tlr_mdd_unpermute_dense.argtypes = [vp, vp, vp]
+        L.tlr_mdd_get_data.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp, vp]
+        L.tlr_mdd_stream.argtypes = [vp]
+        L.tlr_mdd_stream.restype = vp
+        L.tlr_mdd_last_error.argtypes = [vp]
+        L.tlr_mdd_last_error.restype = C.c_char_p
+        L.tlr_mdd_destroy.argtypes = [vp]
+        L.tlr_mdd_timing_enable.argtypes = [C.c_int]
+        L.tlr_mdd_timing_enable.restype = None
+        L.tlr_mdd_timing_reset.argtypes = []
+        L.tlr_mdd_timing_reset.restype = None
+        L.tlr_mdd_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int64), C.c_int]
+        L.tlr_mdd_timing_read.restype = i32
+        L.tlr_mdd_launch_count.argtypes = []
+        L.tlr_mdd_launch_count.restype = i64
+        for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
+                     "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
+                     "tlr_mdd_solve", "tlr_mdd_unpermute_dense", "tlr_mdd_get_data",
+                     "tlr_mdd_destroy"):
+            getattr(L, name).restype = i32
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, h=None):
+    if rc != 0:
+        msg = lib().tlr_mdd_last_error(h)
+        raise TLRError(rc, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array (host)
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class _Keep:
+    """Keeps the host arrays referenced by a Desc alive."""
+
+
+def desc(nr, ns, tile, rank=0, nx=0, ny=0, perm=None, ranks=None, diag_mode=TLR_DIAG_RULE,
+         diag_dense=None, precision=TLR_PREC_FP32, alpha=0.0, input_memory=TLR_MEM_DEVICE,
+         reciprocity=TLR_RECIP_SYMMETRIC) -> Desc:
+    d = Desc()
+    lib().tlr_mdd_desc_init(C.byref(d))
+    d.nr, d.ns, d.tile, d.rank, d.nx, d.ny = nr, ns, tile, rank, nx, ny
+    d.diag_mode, d.precision, d.alpha, d.input_memory = diag_mode, precision, float(alpha), input_memory
+    d.reciprocity = reciprocity
+    keep = []
+    if perm is not None:
+        a = (C.c_int32 * len(perm))(*[int(v) for v in perm])
+        keep.append(a)
+        d.perm = C.cast(a, C.POINTER(C.c_int32))
+    if ranks is not None:
+        a = (C.c_int32 * len(ranks))(*[int(v) for v in ranks])
+        keep.append(a)
+        d.ranks = C.cast(a, C.POINTER(C.c_int32))
+    if diag_dense is not None:
+        a = (C.c_uint8 * len(diag_dense))(*[1 if v else 0 for v in diag_dense])
+        keep.append(a)
+        d.diag_dense = C.cast(a, C.POINTER(C.c_uint8))
+    d._keep = keep
+    return d
+
+
+def solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().tlr_mdd_solve_opts_init(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tlr_mdd_theta_size(d: Desc) -> int:
+    n = C.c_int64()
+    _check(lib().tlr_mdd_theta_size(C.byref(d), C.byref(n)))
+    return n.value
+
+
+def tlr_mdd_theta_layout(d: Desc):
+    N = d.nr // d.tile
+    P = N * (N - 1) // 2
+    od = (C.c_int64 * max(N, 1))()
+    ol = (C.c_int64 * max(P, 1))()
+    orr = (C.c_int64 * max(P, 1))()
+    dn = (C.c_uint8 * max(N, 1))()
+    _check(lib().tlr_mdd_theta_layout(C.byref(d), od, ol, orr, dn))
+    return list(od)[:N], list(ol)[:P], list(orr)[:P], [bool(x) for x in list(dn)[:N]]
+
+
+def tlr_mdd_workspace_bytes(d: Desc) -> int:
+    return lib().tlr_mdd_workspace_bytes(C.byref(d))
+
+
+def tlr_mdd_hilbert_perm(nx, ny, perm_dev, stream=None):
+    _check(lib().tlr_mdd_hilbert_perm(nx, ny, _ptr(perm_dev), _stream(stream)))
+
+
+def tlr_mdd_create(d: Desc, D, U, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().tlr_mdd_create(C.byref(h), C.byref(d), _ptr(D), _ptr(U), _stream(stream)))
+    return h.value
+
+
+def tlr_mdd_apply(h, theta, Y):
+    _check(lib().tlr_mdd_apply(h, _ptr(theta), _ptr(Y)), h)
+
+
+def tlr_mdd_adjoint(h, V, G):
+    _check(lib().tlr_mdd_adjoint(h, _ptr(V), _ptr(G)), h)
+
+
+def tlr_mdd_grad(h, theta, grad, want_f=True):
+    f = C.c_double()
+    _check(lib().tlr_mdd_grad(h, _ptr(theta), _ptr(grad), C.byref(f) if want_f else None), h)
+    return f.value if want_f else None
+
+
+def tlr_mdd_solve(h, theta, opts: SolveOpts | None = None) -> Stats:
+    st = Stats()
+    opts = opts if opts is not None else solve_opts()
+    _check(lib().tlr_mdd_solve(h, _ptr(theta), C.byref(opts), C.byref(st)), h)
+    return st
+
+
+def tlr_mdd_unpermute_dense(h, theta, X):
+    _check(lib().tlr_mdd_unpermute_dense(h, _ptr(theta), _ptr(X)), h)
+
+
+def tlr_mdd_get_data(h, nr, Dt=None, Ut=None):
+    perm = (C.c_int32 * nr)()
+    alpha = C.c_double()
+    _check(lib().tlr_mdd_get_data(h, perm, C.byref(alpha), _ptr(Dt), _ptr(Ut)), h)
+    return list(perm), alpha.value
+
+
+def tlr_mdd_destroy(h):
+    _check(lib().tlr_mdd_destroy(h))
+
+
+def tlr_mdd_last_error(h=None) -> str:
+    m = lib().tlr_mdd_last_error(h)
+    return m.decode() if m else ""
+
+
+def tlr_mdd_timing_enable(on: bool):
+    lib().tlr_mdd_timing_enable(1 if on else 0)
+
+
+def tlr_mdd_timing_reset():
+    lib().tlr_mdd_timing_reset()
+
+
+def tlr_mdd_timing_read():
+    """[(ms, flops, launches)] per class: 0 compress, 1 expand, 2 project."""
+    ms = (C.c_double * TLR_NCLASS)()
+    fl = (C.c_double * TLR_NCLASS)()
+    nl = (C.c_int64 * TLR_NCLASS)()
+    _check(lib().tlr_mdd_timing_read(ms, fl, nl, TLR_NCLASS))
+    return [(ms[c], fl[c], nl[c]) for c in range(TLR_NCLASS)]
+
+
+def tlr_mdd_launch_count() -> int:
+    return lib().tlr_mdd_launch_count()

@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every declared entry point; host-only
+calls (layout, sizes, validation) agree with the oracle.  No GPU needed."""
+import os
+import re
+
+import pytest
+
+from oracle import layout
+
+pt = pytest.importorskip("paper_2412_14973_gb300")
+T = pt
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "tlr_mdd.h")
+
+
+def _lib():
+    try:
+        return T.lib()
+    except RuntimeError as e:  # not built in this checkout
+        pytest.skip(str(e))
+
+
+def test_exports_every_declared_symbol():
+    L = _lib()
+    src = open(HDR).read()
+    declared = sorted(set(re.findall(r"\b(tlr_mdd_\w+)\s*\(", src)))
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(declared) == set(T.EXPORTED)
+
+
+@pytest.mark.parametrize("nr,b,ranks,mode,abimode", [
+    (256, 64, 8, "dense", T.TLR_DIAG_DENSE),
+    (4096, 256, 26, "rule", T.TLR_DIAG_RULE),
+    (96, 16, [1, 0, 16, 2, 0, 3] + list(range(15)), "rule", T.TLR_DIAG_RULE),
+    (64, 16, 2, "lowrank", T.TLR_DIAG_LOWRANK),
+])
+def test_theta_layout_bit_exact(nr, b, ranks, mode, abimode):
+    _lib()
+    lay = layout.make_layout(nr, b, ranks, mode)
+    kw = dict(ranks=ranks) if isinstance(ranks, list) else dict(rank=ranks)
+    d = T.desc(nr, nr, b, nx=nr, ny=1, diag_mode=abimode, **kw)
+    od, ol, orr, dn = T.tlr_mdd_theta_layout(d)
+    assert od == lay.off_diag
+    assert ol == lay.off_l
+    assert orr == lay.off_r
+    assert dn == lay.dense
+    assert T.tlr_mdd_theta_size(d) == lay.size
+    assert T.tlr_mdd_workspace_bytes(d) > 8 * 5 * nr * nr
+
+
+def test_per_tile_diag_mode():
+    _lib()
+    d = T.desc(48, 48, 16, rank=2, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=[True, False, True])
+    lay = layout.make_layout(48, 16, 2, [True, False, True])
+    assert T.tlr_mdd_theta_layout(d)[0] == lay.off_diag
+    assert T.tlr_mdd_theta_size(d) == lay.size
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nr=100, ns=10, tile=64, rank=4), -2),          # tile does not divide nr
+    (dict(nr=128, ns=10, tile=64, rank=65), -2),         # rank above tile
+    (dict(nr=128, ns=10, tile=64, rank=-1), -2),
+    (dict(nr=128, ns=0, tile=64, rank=4), -2),
+    (dict(nr=128, ns=10, tile=64, rank=4, reciprocity=1), -3),  # general TLR not implemented
+    (dict(nr=128, ns=10, tile=64, rank=4, precision=7), -1),
+    (dict(nr=128, ns=10, tile=64, rank=4, diag_mode=9), -1),
+])
+def test_invalid_descriptions_rejected(kw, code):
+    _lib()
+    d = T.desc(**kw)
+    with pytest.raises(T.TLRError) as ei:
+        T.tlr_mdd_theta_size(d)
+    assert ei.value.code == code
+    assert T.tlr_mdd_workspace_bytes(d) == -1
+    assert T.tlr_mdd_last_error()

@@ -1,0 +1,66 @@
+"""Hilbert order, alpha and the reordered panels on the GPU vs the oracle (bit-exact)."""
+import numpy as np
+import pytest
+import torch
+
+import tlr_synth as synth
+from oracle import hilbert, layout, operator
+from tests._cases import problem
+
+pytestmark = pytest.mark.gpu
+T = pytest.importorskip("paper_2412_14973_gb300")
+from tests._gpu import Gpu  # noqa: E402
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (16, 16), (64, 32), (5, 3), (177, 90), (96, 96), (128, 64), (7, 33)])
+def test_hilbert_perm_bit_exact(nx, ny):
+    p = torch.empty(nx * ny, dtype=torch.int32, device="cuda")
+    T.tlr_mdd_hilbert_perm(nx, ny, p)
+    torch.cuda.synchronize()
+    assert np.array_equal(p.cpu().numpy(), hilbert.perm(nx, ny))
+
+
+@pytest.mark.parametrize("host_inputs", [False, True])
+def test_panels_bit_exact(host_inputs):
+    D, U, perm, lay, _ = problem(8, 8, 16, 3, "rule", ns=45, snr_db=10)
+    a_or = float(np.max(np.abs(D.astype(np.complex128))))
+    # explicit alpha: Dfrak = (complex64)(D[:, perm]^T / alpha), each part divided in FP64
+    g = Gpu(D, U, lay, nx=8, ny=8, alpha=a_or, host_inputs=host_inputs)
+    p, alpha, Dt, Ut = g.data()
+    assert np.array_equal(p, perm)
+    assert alpha == a_or
+    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=a_or)
+    assert np.array_equal(Dt, Dh.T.astype(np.complex64))
+    assert np.array_equal(Ut, Uh.T.astype(np.complex64))
+    g.close()
+    # alpha computed on the device: max |D| (FP64 from the complex64 entries)
+    g2 = Gpu(D, U, lay, nx=8, ny=8)
+    _, alpha2, _, _ = g2.data()
+    assert abs(alpha2 - a_or) <= 1e-15 * a_or
+    g2.close()
+
+
+def test_explicit_perm_and_ragged_sizes():
+    rng = np.random.default_rng(3)
+    nr, ns = 48, 37
+    lay = layout.make_layout(nr, 16, 2, "lowrank")
+    D = synth.cn(synth.rng(1), (ns, nr)).astype(np.complex64)
+    U = synth.cn(synth.rng(2), (ns, nr)).astype(np.complex64)
+    perm = rng.permutation(nr).astype(np.int32)
+    g = Gpu(D, U, lay, perm=perm, alpha=2.0)
+    p, alpha, Dt, Ut = g.data()
+    assert np.array_equal(p, perm)
+    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=2.0)
+    assert np.array_equal(Dt, Dh.T.astype(np.complex64))
+    g.close()
+
+
+def test_invalid_inputs_are_errors_not_faults():
+    D = np.zeros((4, 16), np.complex64)
+    lay = layout.make_layout(16, 4, 1, "lowrank")
+    with pytest.raises(T.TLRError) as ei:
+        Gpu(D, D, lay, nx=3, ny=5)            # nx*ny != nr
+    assert ei.value.code == -2
+    with pytest.raises(T.TLRError) as ei:
+        Gpu(D, D, lay, perm=[0] * 16)         # not a permutation
+    assert ei.value.code == -1

@@ -1,0 +1,88 @@
+"""Device-resident ADMM / L-BFGS solve vs the FP64 oracle (eq. 18-24)."""
+import numpy as np
+import pytest
+
+import tlr_synth as synth
+from oracle import operator, solver
+from tests._cases import problem
+
+pytestmark = pytest.mark.gpu
+T = pytest.importorskip("paper_2412_14973_gb300")
+from tests._gpu import Gpu, rel  # noqa: E402
+
+
+def _start(lay, seed=77, scale=0.1):
+    th = scale * synth.planted_theta(lay.nr, lay.b, list(lay.k_diag) + list(lay.k_pair), lay.dense, seed)
+    return th.astype(np.complex64).astype(np.complex128)
+
+
+def _oracle_solve(D, U, perm, lay, th0, **kw):
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    th, z, u, st = solver.admm(prob, th0, solver.SolveOpts(**kw))
+    return th, st, alpha
+
+
+def test_config0_final_x_within_1e_3():
+    # nr = ns = 256 (16 x 16 grid), tile 64, rank 8, dense diagonal, 20 dB, 30 iterations
+    D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
+    th0 = _start(lay)
+    tho, sto, alpha = _oracle_solve(D, U, perm, lay, th0)
+    g = Gpu(D, U, lay, nx=16, ny=16, alpha=alpha)
+    th, st = g.solve(th0)
+    g.close()
+    assert st.iters == 30 and st.status == 0
+    Xo = operator.unpermute(operator.assemble_xh(tho, lay), perm)
+    X = operator.unpermute(operator.assemble_xh(th, lay), perm)
+    assert rel(X, Xo) <= 1e-3
+    fh = np.array(st.f_hist[:st.n_hist])
+    np.testing.assert_allclose(fh, sto.f_hist, rtol=1e-3)
+    assert st.restarts == sto.restarts
+
+
+@pytest.mark.parametrize("mode,ranks", [("lowrank", 3), ("rule", [5, 9, 1, 2, 3, 4])])
+def test_small_solves_match_oracle(mode, ranks):
+    D, U, perm, lay, _ = problem(8, 6, 16, ranks, mode, ns=60, seed=5, snr_db=10)
+    th0 = _start(lay, seed=3, scale=0.3)
+    kw = dict(stages=2, admm_iters=2, lbfgs_iters=4, memory=3)
+    tho, sto, alpha = _oracle_solve(D, U, perm, lay, th0, **kw)
+    g = Gpu(D, U, lay, nx=8, ny=6, alpha=alpha)
+    th, st = g.solve(th0, **kw)
+    g.close()
+    Xo = operator.assemble_xh(tho, lay)
+    X = operator.assemble_xh(th, lay)
+    assert rel(X, Xo) <= 1e-3
+    np.testing.assert_allclose(np.array(st.f_hist[:st.n_hist]), sto.f_hist, rtol=1e-3)
+
+
+def test_solve_host_theta_matches_device_theta():
+    D, U, perm, lay, _ = problem(8, 8, 16, 2, "lowrank", seed=2, snr_db=10)
+    th0 = _start(lay, scale=0.3)
+    g = Gpu(D, U, lay, nx=8, ny=8)
+    th_d, st_d = g.solve(th0, lbfgs_iters=3, stages=1)
+    th_h = np.ascontiguousarray(th0.astype(np.complex64))
+    st_h = T.tlr_mdd_solve(g.h, th_h, T.solve_opts(lbfgs_iters=3, stages=1, theta_memory=T.TLR_MEM_HOST))
+    g.close()
+    assert np.array_equal(th_h.astype(np.complex128), th_d)
+    assert st_h.iters == st_d.iters
+
+
+def test_nonfinite_data_reported():
+    D, U, perm, lay, _ = problem(4, 4, 8, 2, "lowrank", seed=1)
+    D = D.copy()
+    D[1, 3] = np.nan
+    g = Gpu(D, U, lay, nx=4, ny=4, alpha=1.0)
+    with pytest.raises(T.TLRError) as ei:
+        g.solve(_start(lay), stages=1, admm_iters=1, lbfgs_iters=2)
+    assert ei.value.code == -6
+    g.close()
+
+
+def test_invalid_solver_options():
+    D, U, perm, lay, _ = problem(4, 4, 8, 2, "lowrank", seed=1)
+    g = Gpu(D, U, lay, nx=4, ny=4)
+    for kw in (dict(memory=0), dict(memory=33), dict(rho=0.0), dict(stages=-1)):
+        with pytest.raises(T.TLRError) as ei:
+            g.solve(_start(lay), **kw)
+        assert ei.value.code == -1
+    g.close()
