@@ -122,12 +122,11 @@ def make_workload(T, torch, nfreq, seed, device):
         im = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
         return torch.complex(re, im) * (1.0 / math.sqrt(2.0))
 
-    def haar(m):
-        q, r = torch.linalg.qr(cn((m, m)))
-        d = torch.diagonal(r)
-        return q * (d / d.abs())[None, :]
-
-    Q, W = haar(n), haar(n)
+    # exactly unitary random-phase DFT products (tlr_synth recipe), built on the host
+    import tlr_synth as synth
+    hg = synth.rng(seed)
+    Q = torch.from_numpy(synth.phase_dft_unitary(n, hg).astype(np.complex64)).to(device)
+    W = torch.from_numpy(synth.phase_dft_unitary(n, hg).astype(np.complex64)).to(device)
     sig = torch.pow(10.0, -3.0 * torch.arange(n, device=device, dtype=torch.float32) / (n - 1))
     perm = torch.empty(n, dtype=torch.int32, device=device)
     T.tlr_mdd_hilbert_perm(GRID[0], GRID[1], perm)

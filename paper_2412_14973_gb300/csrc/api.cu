@@ -60,11 +60,11 @@ cudaEvent_t ev_get() {
 // launch one grouped contraction, timed when diagnostics are on
 cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st) {
     if (L.nprob == 0) return cudaSuccess;
-    if (!g_timing) return gemm_simt(L, st);
+    if (!g_timing) return gemm_any(L, st);
     std::lock_guard<std::mutex> lk(g_tmu);
     TimedLaunch t{L.cls, L.flops, ev_get(), ev_get()};
     cudaEventRecord(t.a, st);
-    cudaError_t e = gemm_simt(L, st);
+    cudaError_t e = gemm_any(L, st);
     cudaEventRecord(t.b, st);
     g_pending.push_back(t);
     return e;
@@ -410,6 +410,8 @@ int build_tables(tlr_mdd_s* h, char* tab_base) {
             for (int t = 0; t < p.nt; ++t) G.flops += 8.0 * p.M * (double)p.N * p.t[t].K;
         }
         G.cls = am == A_KM ? 0 : (bm == B_KN ? 1 : 2);
+        G.prec = h->d.precision;
+        G.err = h->ints + SI_COUNT + 1;
         if (!v.empty()) {
             cudaError_t e = cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(GProb), cudaMemcpyHostToDevice, h->st);
             if (e != cudaSuccess) return -1;
@@ -622,11 +624,6 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         delete h;
         return TLR_ERR_SHAPE;
     }
-    if (d->precision != TLR_PREC_FP32) {
-        g_last_error = "precision mode not available in this build";
-        delete h;
-        return TLR_ERR_UNSUPPORTED;
-    }
     h->nsplit = split_for(L);
     h->kchunk = (int)(((L.ns + h->nsplit - 1) / h->nsplit + 15) / 16 * 16);
     Arena a;
@@ -808,6 +805,8 @@ int tlr_mdd_adjoint(tlr_mdd_t* h, const void* V, void* G) {
     cudaError_t e = cudaMemcpyAsync(dp, &p, sizeof(GProb), cudaMemcpyHostToDevice, h->st);
     G1.flops = 8.0 * nr * (double)nr * ns;
     G1.cls = 2;
+    G1.prec = h->d.precision;
+    G1.err = h->ints + SI_COUNT + 1;
     if (e == cudaSuccess) e = run_gemm(G1, h->st);
     if (e == cudaSuccess && ns_split > 1) e = reduce_grad(part, ns_split, nr * nr, nr * nr, 0, 1, (cf*)G, h->st);
     if (part) cudaFreeAsync(part, h->st);

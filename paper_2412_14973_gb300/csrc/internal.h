@@ -63,10 +63,17 @@ struct GemmLaunch {
     int amode = 0, bmode = 0, epi = 0;
     double flops = 0.0;         // algorithmic flops of one launch (8 per complex MAC)
     int cls = 0;                // diagnostics class (0 compress, 1 expand, 2 project)
+    int prec = 0;               // TLR_PREC_FP32 (SIMT) or TLR_PREC_BF16X3 (tcgen05)
+    int* err = nullptr;         // device error word (tensor-core path: bounded-wait timeouts)
 };
 
 // SIMT path (k_gemm_simt.cu)
 cudaError_t gemm_simt(const GemmLaunch& L, cudaStream_t st);
+// tcgen05 path (k_gemm_tc.cu): BF16x3 split, 3M complex, FP32 accumulation in TMEM
+cudaError_t gemm_tc(const GemmLaunch& L, cudaStream_t st);
+inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
+    return L.prec == TLR_PREC_BF16X3 ? gemm_tc(L, st) : gemm_simt(L, st);
+}
 
 // ---------------------------------------------------------------------------
 // data kernels (k_data.cu)

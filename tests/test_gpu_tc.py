@@ -1,0 +1,81 @@
+"""tcgen05 BF16x3 / 3M path vs the FP64 oracle.
+
+Tolerance for the tensor-core path: relative Frobenius error <= 1e-3 per
+operator application (BF16x3 keeps about 16 significant bits of each operand;
+the measured error is printed with -s)."""
+import numpy as np
+import pytest
+
+import tlr_synth as synth
+from oracle import operator, solver
+from tests._cases import problem
+from tests.test_gpu_operator import CASES
+
+pytestmark = pytest.mark.gpu
+T = pytest.importorskip("paper_2412_14973_gb300")
+from tests._gpu import Gpu, elem, rel  # noqa: E402
+
+TC_TOL = 1e-3
+
+
+def _setup(name):
+    nx, ny, b, ranks, mode, ns = CASES[name]
+    D, U, perm, lay, _ = problem(nx, ny, b, ranks, mode, ns=ns, snr_db=10, planted=False)
+    th = synth.cn(synth.rng(sorted(CASES).index(name)), lay.size) * 0.2
+    th = th.astype(np.complex64).astype(np.complex128)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, precision=T.TLR_PREC_BF16X3)
+    _, alpha, _, _ = g.data()
+    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    return g, lay, th, Dh, Uh
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tc_apply(name):
+    g, lay, th, Dh, Uh = _setup(name)
+    Y = g.apply(th)
+    Yo = operator.apply_y(th, lay, Dh)
+    e = rel(Y, Yo)
+    print(f"tc apply {name}: rel {e:.2e} elem {elem(Y, Yo):.2e}")
+    assert e <= TC_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tc_grad(name):
+    g, lay, th, Dh, Uh = _setup(name)
+    f, gr = g.grad(th)
+    fo = operator.misfit(th, lay, Dh, Uh)
+    go = operator.gradient(th, lay, Dh, Uh)
+    e = rel(gr, go)
+    print(f"tc grad {name}: rel {e:.2e} f {abs(f - fo) / fo:.2e}")
+    assert abs(f - fo) <= TC_TOL * fo
+    assert e <= TC_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["config0", "ragged"])
+def test_tc_adjoint(name):
+    g, lay, th, Dh, Uh = _setup(name)
+    V = synth.cn(synth.rng(17), (lay.nr, Dh.shape[0])).astype(np.complex64).astype(np.complex128)
+    G = g.adjoint(V)
+    Go = operator.adjoint_g(V, Dh)
+    e = rel(G, Go)
+    print(f"tc adjoint {name}: rel {e:.2e}")
+    assert e <= TC_TOL
+    g.close()
+
+
+def test_tc_config0_solve():
+    D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
+    th0 = (0.1 * synth.planted_theta(256, 64, 8, lay.dense, 77)).astype(np.complex64).astype(np.complex128)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dh.T, Uh.T), th0)
+    g = Gpu(D, U, lay, nx=16, ny=16, alpha=alpha, precision=T.TLR_PREC_BF16X3)
+    th, st = g.solve(th0)
+    g.close()
+    Xo = operator.unpermute(operator.assemble_xh(tho, lay), perm)
+    X = operator.unpermute(operator.assemble_xh(th, lay), perm)
+    e = rel(X, Xo)
+    print(f"tc config0 solve: rel X {e:.2e}")
+    assert st.iters == 30 and st.status == 0
+    assert e <= 1e-2
