@@ -184,6 +184,28 @@ int tlr_mdd_get_data(tlr_mdd_t* h, int32_t* perm_host, double* alpha, void* Dt, 
 /* The handle's stream (as passed to create). */
 void* tlr_mdd_stream(const tlr_mdd_t* h);
 
+/* ---- allocation-free dense adjoint ----
+ * G = V Dt^H (nr x nr) for receiver-major V and Dt (nr x ns), all complex64
+ * DEVICE buffers owned by the caller; FP32 CUDA-core arithmetic, the same
+ * kernels as tlr_mdd_adjoint.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- a process that
+ * hands all device memory to its own pool allocator (an allocation from this
+ * library would fail or fragment that pool), or a latency-critical path on
+ * which an allocation call may synchronise the device.  It allocates nothing
+ * and needs no handle: its split-K scratch is one fixed device array of
+ * TLR_NOALLOC_SCRATCH_BYTES inside the library, held on every GPU that loads
+ * the library until the process exits.  Sizes: nr * nr * 8 bytes must fit in
+ * TLR_NOALLOC_SCRATCH_BYTES - 256 (nr <= 1448); larger nr returns
+ * TLR_ERR_SHAPE before any work is enqueued.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and it keeps the last call's contents (each call
+ * overwrites all it reads): calls that overlap on the GPU -- other streams,
+ * other host threads -- race on it.  Synchronises the stream before
+ * returning. */
+#define TLR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int tlr_mdd_adjoint_noalloc(const void* V, const void* Dt, int64_t nr, int64_t ns, void* G, void* stream);
+
 /* ---- diagnostics (process-wide, not part of the method) ----
  * While enabled, every contraction kernel launch is bracketed by CUDA events
  * on the stream it is launched on; tlr_mdd_timing_read() waits for those

@@ -19,6 +19,7 @@ __all__ = [
     "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
     "tlr_mdd_get_data", "tlr_mdd_destroy", "tlr_mdd_last_error", "EXPORTED",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
+    "tlr_mdd_adjoint_noalloc", "TLR_NOALLOC_SCRATCH_BYTES",
 ]
 
 TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
@@ -35,8 +36,10 @@ EXPORTED = [
     "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
     "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
+    "tlr_mdd_adjoint_noalloc",
 ]
 TLR_NCLASS = 3
+TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class TLRError(RuntimeError):
@@ -120,6 +123,8 @@ def lib():
         L.tlr_mdd_timing_read.restype = i32
         L.tlr_mdd_launch_count.argtypes = []
         L.tlr_mdd_launch_count.restype = i64
+        L.tlr_mdd_adjoint_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, vp]
+        L.tlr_mdd_adjoint_noalloc.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
                      "tlr_mdd_solve", "tlr_mdd_unpermute_dense", "tlr_mdd_get_data",
@@ -283,3 +288,8 @@ def tlr_mdd_timing_read():
 
 def tlr_mdd_launch_count() -> int:
     return lib().tlr_mdd_launch_count()
+
+
+def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
+    """G = V Dt^H without any device allocation (fixed in-library scratch)."""
+    _check(lib().tlr_mdd_adjoint_noalloc(_ptr(V), _ptr(Dt), nr, ns, _ptr(G), _stream(stream)))
