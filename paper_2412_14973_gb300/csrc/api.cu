@@ -721,7 +721,7 @@ static int forward(tlr_mdd_s* h, bool plain_apply) {
     const Layout& L = h->L;
     CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st));
     CK(h, run_gemm(h->Lc_x, h->st));
-    CK(h, gemm_simt(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
+    CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
     return TLR_OK;
 }
 

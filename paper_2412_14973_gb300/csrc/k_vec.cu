@@ -50,6 +50,22 @@ __device__ __forceinline__ double sum_partials(const double* part, int nblk, int
     return r;
 }
 
+// Per-thread partial sum: FP32 terms accumulated with Knuth's two-sum
+// compensation (error-free transformation), so a thread's partial is as good
+// as an FP64 sum of its FP32 terms while costing FP32 adds only; partials are
+// then combined in FP64.  Elementwise FP64 multiply-adds would cost far more on
+// this part than the memory traffic they sit on.
+struct Acc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ double val() const { return (double)s + (double)c; }
+};
+
 #define GRID_STRIDE(i, n) \
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
@@ -116,26 +132,28 @@ cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long lon
 __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long stride, long long nlr,
                               long long ndense, long long b, cf* __restrict__ grad) {
     GRID_STRIDE(e, nlr) {
-        double x = 0.0, y = 0.0;
+        Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
             const cf v = part[c * stride + e];
-            x += v.x;
-            y += v.y;
+            x.add(v.x);
+            y.add(v.y);
         }
-        grad[e] = make_float2((float)x, (float)y);
+        grad[e] = make_float2((float)x.val(), (float)y.val());
     }
     const long long bb = b * b;
     GRID_STRIDE(e, ndense * bb) {
         const long long t = e / bb, r = (e % bb) / b, q = e % b;
         const long long e1 = nlr + t * bb + r * b + q, e2 = nlr + t * bb + q * b + r;
-        double x = 0.0, y = 0.0;
+        Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
             const cf u = part[c * stride + e1];
             const cf v = part[c * stride + e2];
-            x += (double)u.x + v.x;
-            y += (double)u.y + v.y;
+            x.add(u.x);
+            x.add(v.x);
+            y.add(u.y);
+            y.add(v.y);
         }
-        grad[nlr + e] = make_float2((float)(0.5 * x), (float)(0.5 * y));
+        grad[nlr + e] = make_float2((float)(0.5 * x.val()), (float)(0.5 * y.val()));
     }
 }
 
@@ -152,10 +170,10 @@ cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long 
 __global__ void __launch_bounds__(kRedThreads) k_dot_part(const float* __restrict__ a, const float* __restrict__ b,
                                                          long long n2, double* part) {
     __shared__ double sh[32];
-    double s = 0.0;
-    GRID_STRIDE(i, n2) s += (double)a[i] * b[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    Acc s;
+    GRID_STRIDE(i, n2) s.add(a[i] * b[i]);
+    const double r = block_sum(s.val(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
 cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st) {
@@ -182,19 +200,19 @@ cudaError_t finalize(const double* part, int nblk, int stride, int cnt, double* 
 __global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R, const cf* __restrict__ A1,
                                                       const cf* __restrict__ A2, long long n, double* part) {
     __shared__ double sh[32];
-    double s[6] = {0, 0, 0, 0, 0, 0};
+    Acc s[6];
     GRID_STRIDE(i, n) {
         const cf r = R[i], a = A1[i], c = A2[i];
-        s[0] += (double)r.x * r.x + (double)r.y * r.y;
-        s[1] += (double)r.x * a.x + (double)r.y * a.y;
-        s[2] += (double)r.x * c.x + (double)r.y * c.y;
-        s[3] += (double)a.x * a.x + (double)a.y * a.y;
-        s[4] += (double)a.x * c.x + (double)a.y * c.y;
-        s[5] += (double)c.x * c.x + (double)c.y * c.y;
+        s[0].add(fmaf(r.x, r.x, r.y * r.y));
+        s[1].add(fmaf(r.x, a.x, r.y * a.y));
+        s[2].add(fmaf(r.x, c.x, r.y * c.y));
+        s[3].add(fmaf(a.x, a.x, a.y * a.y));
+        s[4].add(fmaf(a.x, c.x, a.y * c.y));
+        s[5].add(fmaf(c.x, c.x, c.y * c.y));
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double v = block_sum(s[k], sh);
+        const double v = block_sum(s[k].val(), sh);
         if (threadIdx.x == 0) part[blockIdx.x * 6 + k] = v;
     }
 }
@@ -212,7 +230,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step_residual(cf* __restrict__ 
     __shared__ double sh[32];
     const float a = (float)alpha[0];
     const float a2 = (float)(alpha[0] * alpha[0]);
-    double s = 0.0;
+    Acc s;
     GRID_STRIDE(i, n) {
         cf r = R[i];
         if (a != 0.f) {
@@ -221,10 +239,10 @@ __global__ void __launch_bounds__(kRedThreads) k_step_residual(cf* __restrict__ 
             r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
             R[i] = r;
         }
-        s += (double)r.x * r.x + (double)r.y * r.y;
+        s.add(fmaf(r.x, r.x, r.y * r.y));
     }
-    s = block_sum(s, sh);
-    if (part && threadIdx.x == 0) part[blockIdx.x] = s;
+    const double t = block_sum(s.val(), sh);
+    if (part && threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 cudaError_t step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha, cudaStream_t st) {
@@ -253,13 +271,13 @@ cudaError_t axpy_dev(float* x, const float* y, long long n2, const double* alpha
 // f = 0.5 ||R||^2 from a fresh norm pass: part[blk] -> sc[SC_F]
 __global__ void __launch_bounds__(kRedThreads) k_norm_part(const cf* __restrict__ R, long long n, double* part) {
     __shared__ double sh[32];
-    double s = 0.0;
+    Acc s;
     GRID_STRIDE(i, n) {
         const cf r = R[i];
-        s += (double)r.x * r.x + (double)r.y * r.y;
+        s.add(fmaf(r.x, r.x, r.y * r.y));
     }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    const double t = block_sum(s.val(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // g = gf + rho (x - v); history cleared (start of an x-update)
@@ -284,14 +302,14 @@ __global__ void __launch_bounds__(kRedThreads) k_tl1_init(SolverDev S, double* p
     __shared__ double sh[32];
     const int cnt = S.ints[SI_CNT];
     const float* s0 = cnt > 0 ? S.sh + (long long)ring_idx(S, 0) * S.n2 : nullptr;
-    double acc = 0.0;
+    Acc acc;
     GRID_STRIDE(i, S.n2) {
         const float q = S.g[i];
         S.q[i] = q;
-        if (s0) acc += (double)s0[i] * q;
+        if (s0) acc.add(s0[i] * q);
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+    const double t = block_sum(acc.val(), sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
 }
 
 // first pass, step j (j-th newest pair): a_j = rho_j <s_j, q>; q -= a_j y_j;
@@ -308,14 +326,14 @@ __global__ void __launch_bounds__(kRedThreads) k_tl1_step(SolverDev S, int j, co
     const float af = (float)a;
     const float* y = S.yh + (long long)idx * S.n2;
     const float* sn = (j + 1 < cnt) ? S.sh + (long long)ring_idx(S, j + 1) * S.n2 : nullptr;
-    double acc = 0.0;
+    Acc acc;
     GRID_STRIDE(i, S.n2) {
         const float q = fmaf(-af, y[i], S.q[i]);
         S.q[i] = q;
-        if (sn) acc += (double)sn[i] * q;
+        if (sn) acc.add(sn[i] * q);
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+    const double t = block_sum(acc.val(), sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
 }
 
 // second pass, initial kernel: r = gamma q with gamma = <s,y>/<y,y> of the
@@ -330,14 +348,14 @@ __global__ void __launch_bounds__(kRedThreads) k_tl2_init(SolverDev S, int jstar
     }
     const float gf = (float)gamma;
     const float* yn = (jstart < cnt) ? S.yh + (long long)ring_idx(S, jstart) * S.n2 : nullptr;
-    double acc = 0.0;
+    Acc acc;
     GRID_STRIDE(i, S.n2) {
         const float r = gf * S.q[i];
         S.q[i] = r;
-        if (yn) acc += (double)yn[i] * r;
+        if (yn) acc.add(yn[i] * r);
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+    const double t = block_sum(acc.val(), sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
 }
 
 // second pass, step j (j descending, oldest first): b = rho_j <y_j, r>;
@@ -358,37 +376,37 @@ __global__ void __launch_bounds__(kRedThreads) k_tl2_step(SolverDev S, int j, co
         s = S.sh + (long long)idx * S.n2;
     }
     const float* yn = need_next ? S.yh + (long long)ring_idx(S, j - 1) * S.n2 : nullptr;
-    double acc = 0.0;
+    Acc acc;
     GRID_STRIDE(i, S.n2) {
         float r = S.q[i];
         if (s) {
             r = fmaf(coef, s[i], r);
             S.q[i] = r;
         }
-        if (yn) acc += (double)yn[i] * r;
+        if (yn) acc.add(yn[i] * r);
         if (j == 0) S.d[i] = -r;
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+    const double t = block_sum(acc.val(), sh);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
 }
 
 // theta-space line-search inner products: <x - v, x - v>, <x - v, d>, <d, d>
 __global__ void __launch_bounds__(kRedThreads) k_dots3(SolverDev S, double* part) {
     __shared__ double sh[32];
-    double s0 = 0, s1 = 0, s2 = 0;
+    Acc s0, s1, s2;
     GRID_STRIDE(i, S.n2) {
-        const double w = (double)S.x[i] - S.v[i];
-        const double d = S.d[i];
-        s0 += w * w;
-        s1 += w * d;
-        s2 += d * d;
+        const float w = S.x[i] - S.v[i];
+        const float d = S.d[i];
+        s0.add(w * w);
+        s1.add(w * d);
+        s2.add(d * d);
     }
     double r;
-    r = block_sum(s0, sh);
+    r = block_sum(s0.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 0] = r;
-    r = block_sum(s1, sh);
+    r = block_sum(s1.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 1] = r;
-    r = block_sum(s2, sh);
+    r = block_sum(s2.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 2] = r;
 }
 
@@ -455,13 +473,21 @@ __device__ bool quartic_argmin(const double* c, double* out) {
 
 // One thread: finalise the 6 + 3 inner products, form phi's coefficients,
 // check descent, pick alpha; alpha = 0 and a memory reset when no step.
-__global__ void k_line_search(SolverDev S, const double* part6, const double* part3, double rho) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double d6[6] = {0, 0, 0, 0, 0, 0}, d3[3] = {0, 0, 0};
-    for (int i = 0; i < kRedBlocks; ++i) {
-        for (int k = 0; k < 6; ++k) d6[k] += part6[i * 6 + k];
-        for (int k = 0; k < 3; ++k) d3[k] += part3[i * 3 + k];
+__global__ void __launch_bounds__(kRedThreads) k_line_search(SolverDev S, const double* part6, const double* part3,
+                                                             double rho) {
+    __shared__ double sh[32];
+    double d6[6], d3[3];
+    for (int k = 0; k < 6; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += part6[i * 6 + k];
+        d6[k] = block_sum(v, sh);
     }
+    for (int k = 0; k < 3; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += part3[i * 3 + k];
+        d3[k] = block_sum(v, sh);
+    }
+    if (threadIdx.x != 0) return;
     double c[5];
     c[0] = 0.5 * d6[0] + 0.5 * rho * d3[0];
     c[1] = d6[1] + rho * d3[1];
@@ -507,37 +533,38 @@ __global__ void __launch_bounds__(kRedThreads) k_pair_prep(SolverDev S, double r
     const int fr = (S.ints[SI_NEWEST] + 1) % R;
     const float* s = S.sh + (long long)fr * S.n2;
     float* y = S.yh + (long long)fr * S.n2;
-    double ss = 0, sy = 0, yy = 0;
+    Acc ss, sy, yy;
     GRID_STRIDE(i, S.n2) {
         const float gn = S.gf[i] + r * (S.x[i] - S.v[i]);
         const float yi = gn - S.g[i];
         y[i] = yi;
         S.g[i] = gn;
-        const double si = s[i];
-        ss += si * si;
-        sy += si * yi;
-        yy += (double)yi * yi;
+        const float si = s[i];
+        ss.add(si * si);
+        sy.add(si * yi);
+        yy.add(yi * yi);
     }
     double t;
-    t = block_sum(ss, sh);
+    t = block_sum(ss.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 0] = t;
-    t = block_sum(sy, sh);
+    t = block_sum(sy.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 1] = t;
-    t = block_sum(yy, sh);
+    t = block_sum(yy.val(), sh);
     if (threadIdx.x == 0) part[blockIdx.x * 3 + 2] = t;
 }
 
 // one thread: accept the pair (s, y) when alpha > 0 and <s,y> > 1e-12 |s||y|;
 // record f = 0.5 ||R||^2 from the residual-norm partials.
-__global__ void k_pair_accept(SolverDev S, const double* part3, const double* partf) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double ss = 0, sy = 0, yy = 0, rr = 0;
-    for (int i = 0; i < kRedBlocks; ++i) {
-        ss += part3[i * 3 + 0];
-        sy += part3[i * 3 + 1];
-        yy += part3[i * 3 + 2];
-        rr += partf[i];
+__global__ void __launch_bounds__(kRedThreads) k_pair_accept(SolverDev S, const double* part3, const double* partf) {
+    __shared__ double sh[32];
+    double v[4];
+    for (int k = 0; k < 4; ++k) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) a += k < 3 ? part3[i * 3 + k] : partf[i];
+        v[k] = block_sum(a, sh);
     }
+    if (threadIdx.x != 0) return;
+    const double ss = v[0], sy = v[1], yy = v[2], rr = v[3];
     const double f = 0.5 * rr;
     S.sc[SC_F] = f;
     const int it = S.ints[SI_ITERS];
@@ -643,7 +670,7 @@ cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {
 }
 cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
                            cudaStream_t st) {
-    k_line_search<<<1, 32, 0, st>>>(S, part6, part3, rho);
+    k_line_search<<<1, kRedThreads, 0, st>>>(S, part6, part3, rho);
     counted(1);
     return cudaGetLastError();
 }
@@ -664,7 +691,7 @@ cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStrea
     return cudaGetLastError();
 }
 cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, cudaStream_t st) {
-    k_pair_accept<<<1, 32, 0, st>>>(S, part3, partf);
+    k_pair_accept<<<1, kRedThreads, 0, st>>>(S, part3, partf);
     counted(1);
     return cudaGetLastError();
 }
