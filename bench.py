@@ -228,6 +228,7 @@ def main():
     ap.add_argument("--freqs", type=int, default=NFREQ)
     ap.add_argument("--seed", type=int, default=2412)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the frequencies are spread over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=3)
     args = ap.parse_args()
@@ -259,35 +260,62 @@ def main():
     theta = [t.clone() for t in th0]
     opts = T.solve_opts()
     lat_ms = []
+    # one handle per frequency, kept across steps (workspace and recorded
+    # solve); each step re-runs the data step (alpha, reorder, normalise)
+    nstream = max(1, min(args.streams, nfreq))
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstream)]
+    handles = [T.tlr_mdd_create(descs[f], D[f], U[f], streams[f % nstream]) for f in range(nfreq)]
+    main_stream = torch.cuda.current_stream(dev)
 
-    def step(record=False):
+    def step(record=False, host=None):
+        """One pass over every frequency; returns the device ms between the
+        start event (main stream) and the join of all worker streams."""
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main_stream)
+        for s_ in streams:
+            s_.wait_event(e0)
         for f in range(nfreq):
-            h = T.tlr_mdd_create(descs[f], D[f], U[f], stream)
-            theta[f].copy_(th0[f])
-            st = T.tlr_mdd_solve(h, theta[f], opts)
+            st_ = streams[f % nstream]
+            if host is None:
+                T.tlr_mdd_set_data(handles[f], D[f], U[f], T.TLR_MEM_DEVICE)
+                with torch.cuda.stream(st_):
+                    theta[f].copy_(th0[f])
+                T.tlr_mdd_solve_async(handles[f], theta[f], opts)
+            else:
+                Dh_, Uh_, th_h_, out_h_, hopts_ = host
+                T.tlr_mdd_set_data(handles[f], Dh_[f], Uh_[f], T.TLR_MEM_HOST)
+                out_h_[f].copy_(th_h_[f])
+                T.tlr_mdd_solve_async(handles[f], out_h_[f], hopts_)
+        for f in range(nfreq):
+            st = T.tlr_mdd_solve_wait(handles[f])
             if record:
                 lat_ms.append(st.gpu_ms)
-            T.tlr_mdd_destroy(h)
+        for s_ in streams:
+            ev = torch.cuda.Event()
+            ev.record(s_)
+            main_stream.wait_event(ev)
+        e1.record(main_stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     T.tlr_mdd_timing_reset()
     T.tlr_mdd_timing_enable(True)
+    step()   # records the solve graphs with the timing events (not timed)
+    T.tlr_mdd_timing_reset()
+    torch.cuda.synchronize()
     n0 = T.tlr_mdd_launch_count()
     clk = ClockSampler(local)
     clk.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(args.steps):
-            step(record=True)
-        e1.record(stream)
+    ms = 0.0
+    for _ in range(args.steps):
+        ms += step(record=True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -295,7 +323,6 @@ def main():
     T.tlr_mdd_timing_enable(False)
     launches = T.tlr_mdd_launch_count() - n0
     timing = T.tlr_mdd_timing_read()
-    ms = e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -323,8 +350,15 @@ def main():
                 "bf16_issued_tflops": round(achieved * 24.0 / 8.0, 2),
                 "peak_source": f"{src} bf16 {bf16} TFLOP/s x 8/24 (complex flops per issued BF16 flop, 4M x BF16x3)"}
     roof["per_class_ms"] = {names[c]: round(timing[c][0], 2) for c in range(len(timing))}
+    # launches of different frequencies overlap on the 4 streams, so a launch's
+    # event-timed duration includes time shared with other launches; the
+    # device-wide rate below is all contraction flops over the timed wall time
+    roof["aggregate_contraction_tflops"] = round(sum(t[1] for t in timing) / (ms / 1e3) / 1e12, 2)
+    roof["aggregate_frac"] = round(roof["aggregate_contraction_tflops"] / peak, 4)
 
-    # e2e through the C-ABI with host buffers (one timed step)
+    # e2e through the C-ABI with HOST buffers: every step copies each
+    # frequency's D, U and start point from pinned host memory inside the
+    # timed region and reads the solved factors back
     e2e = None
     if not args.no_e2e:
         Dh = torch.empty((nfreq, NR, NR), dtype=torch.complex64, pin_memory=True)
@@ -332,35 +366,20 @@ def main():
         Dh.copy_(D)
         Uh.copy_(U)
         th_h = [t.cpu().pin_memory() for t in th0]
-        out_h = [torch.empty_like(t) for t in th_h]
-        hd = []
-        for d in descs:
-            d2 = T.desc(d.nr, d.ns, d.tile, rank=d.rank, nx=d.nx, ny=d.ny, diag_mode=d.diag_mode,
-                        precision=d.precision, input_memory=T.TLR_MEM_HOST)
-            hd.append(d2)
+        out_h = [torch.empty_like(t).pin_memory() for t in th_h]
         hopts = T.solve_opts(theta_memory=T.TLR_MEM_HOST)
-        h2d = d2h = 0
-
-        def e2e_step():
-            nonlocal h2d, d2h
-            for f in range(nfreq):
-                h = T.tlr_mdd_create(hd[f], Dh[f], Uh[f], stream)
-                out_h[f].copy_(th_h[f])
-                T.tlr_mdd_solve(h, out_h[f], hopts)
-                T.tlr_mdd_destroy(h)
-                h2d += 2 * Dh[f].numel() * 8 + th_h[f].numel() * 8
-                d2h += out_h[f].numel() * 8
-
-        with torch.cuda.stream(stream):
-            e2e_step()  # warm
-            h2d = d2h = 0
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2e_step()
-            torch.cuda.synchronize()
-            te = time.perf_counter() - t0
+        host = (Dh, Uh, th_h, out_h, hopts)
+        step(host=host)  # records the host-theta graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(host=host)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = sum(2 * Dh[f].numel() * 8 + th_h[f].numel() * 8 for f in range(nfreq))
+        d2h = sum(out_h[f].numel() * 8 for f in range(nfreq))
         e2e = {"value": round(nfreq * world / te, 4), "unit": "freq-solves/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del Dh, Uh
 
     # the plain FP32 SIMT form on an evenly spaced subset, same subset on tensor cores
     cmp = None
@@ -368,31 +387,32 @@ def main():
         sub = sorted(set(int(round(i * (nfreq - 1) / max(1, args.compare_fp32 - 1)))
                          for i in range(min(args.compare_fp32, nfreq))))
 
-        def run_subset(prec):
-            ms_tot = 0.0
-            with torch.cuda.stream(stream):
-                for rep in range(2):          # first pass warms up
-                    t0 = torch.cuda.Event(enable_timing=True)
-                    t1 = torch.cuda.Event(enable_timing=True)
-                    t0.record(stream)
-                    for f in sub:
-                        d = descs[f]
-                        d.precision = prec
-                        h = T.tlr_mdd_create(d, D[f], U[f], stream)
-                        theta[f].copy_(th0[f])
-                        T.tlr_mdd_solve(h, theta[f], opts)
-                        T.tlr_mdd_destroy(h)
-                    t1.record(stream)
-                    torch.cuda.synchronize()
-                    if rep == 1:
-                        ms_tot = t0.elapsed_time(t1)
+        def run_subset(prec_):
+            hs = []
             for f in sub:
-                descs[f].precision = prec_main
+                d = T.desc(NR, NR, TILE, rank=ranks[f], nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
+                           precision=prec_)
+                hs.append(T.tlr_mdd_create(d, D[f], U[f], streams[0]))
+            ms_tot = 0.0
+            for rep in range(2):          # first pass records the graphs
+                t0_ = torch.cuda.Event(enable_timing=True)
+                t1_ = torch.cuda.Event(enable_timing=True)
+                t0_.record(streams[0])
+                for h_, f in zip(hs, sub):
+                    T.tlr_mdd_set_data(h_, D[f], U[f], T.TLR_MEM_DEVICE)
+                    with torch.cuda.stream(streams[0]):
+                        theta[f].copy_(th0[f])
+                    T.tlr_mdd_solve(h_, theta[f], opts)
+                t1_.record(streams[0])
+                torch.cuda.synchronize()
+                if rep == 1:
+                    ms_tot = t0_.elapsed_time(t1_)
+            for h_ in hs:
+                T.tlr_mdd_destroy(h_)
             return ms_tot
 
-        prec_main = prec
         t_fp32 = run_subset(T.TLR_PREC_FP32)
-        t_tc = run_subset(prec_main)
+        t_tc = run_subset(prec)
         cmp = {"frequencies": sub, "fp32_simt_freq_solves_per_s": round(len(sub) / (t_fp32 / 1e3), 4),
                "tensor_core_freq_solves_per_s": round(len(sub) / (t_tc / 1e3), 4),
                "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
@@ -428,12 +448,15 @@ def main():
         acc = {"frequency": f0, "iters": args.oracle_iters, "rel_err_X_vs_fp64_oracle": rel,
                "within_1e-3": rel <= 1e-3}
 
+    for h_ in handles:
+        T.tlr_mdd_destroy(h_)
     if rank != 0:
         return
     line = {
         "metric": "freq-solves/s", "value": round(value, 4), "unit": "freq-solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+        "streams": nstream,
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
         "data": "synthetic",
         "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "

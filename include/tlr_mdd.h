@@ -152,6 +152,14 @@ int tlr_mdd_hilbert_perm(int32_t nx, int32_t ny, int32_t* perm_dev, void* stream
 int tlr_mdd_create(tlr_mdd_t** h, const tlr_mdd_desc_t* d, const void* D, const void* U,
                    void* stream);
 
+/* New data for an existing handle (same shapes): recomputes alpha (when
+ * desc.alpha == 0) and the panels Dfrak, Ufrak from D, U exactly as
+ * tlr_mdd_create does, reusing the handle's workspace and its recorded solve.
+ * D, U: complex64 ns x nr row-major, device or host per input_memory
+ * (TLR_MEM_*); host inputs are copied on the handle's stream.  Synchronises
+ * only when alpha is computed. */
+int tlr_mdd_set_data(tlr_mdd_t* h, const void* D, const void* U, int32_t input_memory);
+
 /* Y = X_h Dfrak (receiver-major, Hilbert order), nr x ns complex64 DEVICE.
  * X_h = C(theta) by eq. (6)-(9), (15); theta DEVICE complex64 [n_theta]. */
 int tlr_mdd_apply(tlr_mdd_t* h, const void* theta, void* Y);
@@ -173,6 +181,22 @@ int tlr_mdd_grad(tlr_mdd_t* h, const void* theta, void* grad, double* f);
  * the x-iterate on return.  stats: HOST, may be NULL.  Synchronises. */
 int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* opts,
                   tlr_mdd_stats_t* stats);
+
+/* Asynchronous form of tlr_mdd_solve: enqueues the whole solve on the
+ * handle's stream and returns.  theta_inout (device or host per
+ * opts->theta_memory) must stay valid and untouched until the solve has
+ * finished.  The launch sequence is recorded once into a CUDA graph per
+ * handle and solver options and replayed afterwards (set the environment
+ * variable TLR_MDD_GRAPHS=0, or use the NULL stream, for plain launches).
+ * One solve may be pending per handle; handles on different streams run
+ * concurrently. */
+int tlr_mdd_solve_async(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* opts);
+/* 1 if the handle's pending solve (if any) has finished, 0 if it is still
+ * running, a negative code on error.  Never blocks. */
+int tlr_mdd_solve_query(tlr_mdd_t* h);
+/* Waits for the pending solve, fills stats (HOST, may be NULL) and returns its
+ * status (TLR_ERR_NONFINITE, TLR_ERR_TIMEOUT, ...). */
+int tlr_mdd_solve_wait(tlr_mdd_t* h, tlr_mdd_stats_t* stats);
 
 /* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);

@@ -57,18 +57,59 @@ cudaEvent_t ev_get() {
     return e;
 }
 
+// While a solve is being captured into a CUDA graph, timed launches are
+// collected here (per handle) instead of in g_pending: their events are
+// re-recorded at every replay and read after each one.
+thread_local std::vector<TimedLaunch>* g_capture_sink = nullptr;
+
 // launch one grouped contraction, timed when diagnostics are on
 cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st) {
     if (L.nprob == 0) return cudaSuccess;
     if (!g_timing) return gemm_any(L, st);
     std::lock_guard<std::mutex> lk(g_tmu);
     TimedLaunch t{L.cls, L.flops, ev_get(), ev_get()};
-    cudaEventRecord(t.a, st);
-    cudaError_t e = gemm_any(L, st);
-    cudaEventRecord(t.b, st);
-    g_pending.push_back(t);
+    // inside a stream capture the events must become real event-record
+    // nodes of the graph (external), so every replay records them
+    const unsigned fl = g_capture_sink ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaError_t e = cudaEventRecordWithFlags(t.a, st, fl);
+    if (e == cudaSuccess) e = gemm_any(L, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(t.b, st, fl);
+    if (g_capture_sink)
+        g_capture_sink->push_back(t);
+    else
+        g_pending.push_back(t);
     return e;
 }
+
+// add the device times of a replayed graph's timed launches to the totals
+void account_replay(const std::vector<TimedLaunch>& v) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (const auto& t : v) {
+        float m = 0.f;
+        if (cudaEventElapsedTime(&m, t.a, t.b) == cudaSuccess) {
+            g_ms[t.cls] += m;
+            g_fl[t.cls] += t.flops;
+            g_nl[t.cls] += 1;
+        } else {
+            (void)cudaGetLastError();  // a diagnostic read never poisons later calls
+        }
+    }
+}
+
+struct HostStats {
+    int ints[SI_COUNT + 2];
+    double sc[SC_COUNT];
+    double fhist[TLR_MAX_HIST];
+};
+
+struct GraphKey {
+    double lam0 = -1, decay = 0, rho = 0;
+    int stages = -1, admm = -1, lbfgs = -1, mem = -1, timing = -1;
+    bool operator==(const GraphKey& o) const {
+        return lam0 == o.lam0 && decay == o.decay && rho == o.rho && stages == o.stages && admm == o.admm &&
+               lbfgs == o.lbfgs && mem == o.mem && timing == o.timing;
+    }
+};
 
 struct Arena {
     char* base = nullptr;
@@ -298,6 +339,16 @@ struct tlr_mdd_s {
     GemmLaunch Lc_x, Lc_d, Lc_v, Le_fwd, Le_apply, Le_a1, Le_a2, Lp;
     char* tab_base = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // asynchronous solve and its CUDA graph
+    cf* th_io = nullptr;               // theta staging (stable address for the graph)
+    HostStats* hstats = nullptr;       // pinned
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;       // kernel launches recorded in gexec
+    GraphKey gkey;
+    std::vector<TimedLaunch> gtimed;
+    bool pending = false;
+    bool pending_graph = false;
+    void* pending_host_theta = nullptr;
 };
 
 #define FAIL(h, code, msg)                  \
@@ -355,6 +406,7 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->gf = a.take<cf>(nth);
     h->dd = a.take<cf>(nth);
     h->q = a.take<cf>(nth);
+    h->th_io = a.take<cf>(nth);
     h->rho_h = a.take<double>(64);
     h->sy_h = a.take<double>(64);
     h->yy_h = a.take<double>(64);
@@ -520,6 +572,31 @@ int build_tables(tlr_mdd_s* h, char* tab_base) {
 
 }  // namespace
 
+// The data step of a request (eq. 14 and the normalisation): alpha, then the
+// receiver-major panels Dfrak = D[:, perm]^T / alpha and Ufrak likewise.
+static int load_data(tlr_mdd_s* h, const void* D, const void* U, int memory) {
+    const Layout& L = h->L;
+    const tlr_mdd_desc_t* d = &h->d;
+    const cf* Dsrc = (const cf*)D;
+    const cf* Usrc = (const cf*)U;
+    const size_t nrs = (size_t)L.nr * L.ns;
+    if (memory == TLR_MEM_HOST) {  // host inputs are staged through the residual / A1 buffers
+        CK(h, cudaMemcpyAsync(h->R, D, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
+        CK(h, cudaMemcpyAsync(h->A1, U, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
+        Dsrc = h->R;
+        Usrc = h->A1;
+    }
+    if (d->alpha > 0.0) {
+        const double al = d->alpha;
+        CK(h, cudaMemcpyAsync(h->scal, &al, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    } else {
+        CK(h, max_abs2(Dsrc, (long long)nrs, h->dpart, kRedBlocks, h->scal, h->st));
+    }
+    CK(h, permute_normalise(Dsrc, L.ns, L.nr, h->perm, h->scal, h->Dt, h->st));
+    CK(h, permute_normalise(Usrc, L.ns, L.nr, h->perm, h->scal, h->Ut, h->st));
+    return TLR_OK;
+}
+
 // ===========================================================================
 // entry points
 // ===========================================================================
@@ -675,25 +752,13 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         cudaFreeAsync(slot, h->st);
         CKF(e);
     }
-    // inputs (host inputs are staged through the residual / A1 buffers)
-    const cf* Dsrc = (const cf*)D;
-    const cf* Usrc = (const cf*)U;
-    const size_t nrs = (size_t)L.nr * L.ns;
-    if (d->input_memory == TLR_MEM_HOST) {
-        CKF(cudaMemcpyAsync(h->R, D, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaMemcpyAsync(h->A1, U, nrs * sizeof(cf), cudaMemcpyHostToDevice, h->st));
-        Dsrc = h->R;
-        Usrc = h->A1;
+    {
+        int rc = load_data(h, D, U, d->input_memory);
+        if (rc) {
+            h->err = g_last_error;
+            return fail(rc);
+        }
     }
-    if (d->alpha > 0.0) {
-        const double al = d->alpha;
-        CKF(cudaMemcpyAsync(h->scal, &al, sizeof(double), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaStreamSynchronize(h->st));
-    } else {
-        CKF(max_abs2(Dsrc, (long long)nrs, h->dpart, kRedBlocks, h->scal, h->st));
-    }
-    CKF(permute_normalise(Dsrc, L.ns, L.nr, h->perm, h->scal, h->Dt, h->st));
-    CKF(permute_normalise(Usrc, L.ns, L.nr, h->perm, h->scal, h->Ut, h->st));
     // maps
     if (L.Ktot > 0) {
         CKF(cudaMemcpyAsync(h->d_partner, L.partner.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -704,16 +769,34 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
     }
     if (L.ndense > 0)
         CKF(cudaMemcpyAsync((void*)h->pm.zsrc, L.zsrc.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+    // solver counters and the contraction kernels' error word start at zero
+    CKF(cudaMemsetAsync(h->ints, 0, (SI_COUNT + 8) * sizeof(int), h->st));
     if (build_tables(h, h->tab_base)) {
         h->err = "uploading GEMM tables failed";
         return fail(TLR_ERR_CUDA);
     }
     CKF(cudaEventCreate(&h->ev0));
     CKF(cudaEventCreate(&h->ev1));
+    CKF(cudaMallocHost((void**)&h->hstats, sizeof(HostStats)));
+    if (d->precision == TLR_PREC_BF16X3) CKF(gemm_tc_prepare());
     CKF(cudaStreamSynchronize(h->st));
     CKF(cudaMemcpy(&h->alpha, h->scal, sizeof(double), cudaMemcpyDeviceToHost));
 #undef CKF
     *out = h;
+    return TLR_OK;
+}
+
+int tlr_mdd_set_data(tlr_mdd_t* h, const void* D, const void* U, int32_t input_memory) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!D || !U) FAIL(h, TLR_ERR_ARG, "D or U is NULL");
+    if (input_memory != TLR_MEM_DEVICE && input_memory != TLR_MEM_HOST) FAIL(h, TLR_ERR_ARG, "bad input_memory");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
+    int rc = load_data(h, D, U, input_memory);
+    if (rc) return rc;
+    if (h->d.alpha <= 0.0) {
+        CK(h, cudaMemcpyAsync(&h->alpha, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+    }
     return TLR_OK;
 }
 
@@ -758,8 +841,15 @@ int tlr_mdd_grad(tlr_mdd_t* h, const void* theta, void* grad, double* f) {
         CK(h, sv_norm_part(h->R, (long long)L.nr * L.ns, h->dpart, h->st));
         CK(h, finalize(h->dpart, kRedBlocks, 1, 1, h->scal + 1, h->st));
         double rr = 0;
+        int werr = 0;
         CK(h, cudaMemcpyAsync(&rr, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaMemcpyAsync(&werr, h->ints + SI_COUNT + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
         CK(h, cudaStreamSynchronize(h->st));
+        if (werr != 0) {
+            CK(h, cudaMemsetAsync(h->ints + SI_COUNT + 1, 0, sizeof(int), h->st));
+            CK(h, cudaStreamSynchronize(h->st));
+            FAIL(h, TLR_ERR_TIMEOUT, "a tensor-core contraction timed out on a barrier wait");
+        }
         *f = 0.5 * rr;
     }
     return TLR_OK;
@@ -871,7 +961,7 @@ int tlr_mdd_timing_read(double* ms, double* flops, int64_t* launches, int nclass
     for (auto& t : g_pending) {
         if (cudaEventSynchronize(t.b) != cudaSuccess) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_CUDA, "timing event failed");
         float m = 0.f;
-        cudaEventElapsedTime(&m, t.a, t.b);
+        if (cudaEventElapsedTime(&m, t.a, t.b) != cudaSuccess) (void)cudaGetLastError();
         g_ms[t.cls] += m;
         g_fl[t.cls] += t.flops;
         g_nl[t.cls] += 1;
@@ -895,6 +985,13 @@ const char* tlr_mdd_last_error(const tlr_mdd_t* h) { return h ? h->err.c_str() :
 
 int tlr_mdd_destroy(tlr_mdd_t* h) {
     if (!h) return TLR_ERR_ARG;
+    if (h->pending) cudaEventSynchronize(h->ev1);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto& t : h->gtimed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    if (h->hstats) cudaFreeHost(h->hstats);
     if (h->ring) cudaFreeAsync(h->ring, h->st);
     if (h->arena) cudaFreeAsync(h->arena, h->st);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -907,23 +1004,19 @@ int tlr_mdd_destroy(tlr_mdd_t* h) {
 // ---------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------
-int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o, tlr_mdd_stats_t* stats) {
-    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
-    if (!theta_inout || !o) FAIL(h, TLR_ERR_ARG, "theta or opts is NULL");
+static int check_opts(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     if (o->memory < 1 || o->memory > 32) FAIL(h, TLR_ERR_ARG, "memory must lie in [1, 32]");
     if (!(o->rho > 0.0) || o->stages < 0 || o->admm_iters < 0 || o->lbfgs_iters < 0 || !(o->lam0 >= 0.0))
         FAIL(h, TLR_ERR_ARG, "invalid solver options");
+    return TLR_OK;
+}
+
+// The whole solve as a fixed sequence of launches on h->st: theta is read from
+// and written back to h->th_io; every decision lives in device memory.
+static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     const Layout& L = h->L;
     const long long n2 = 2 * L.nth;
     const long long nrs = (long long)L.nr * L.ns;
-    // ring of s / y vectors, m + 1 slots each
-    if (h->ring_m < o->memory) {
-        if (h->ring) cudaFreeAsync(h->ring, h->st);
-        h->ring = nullptr;
-        h->ring_m = 0;
-        CK(h, cudaMallocAsync((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), h->st));
-        h->ring_m = o->memory;
-    }
     SolverDev S;
     S.n2 = n2;
     S.m = o->memory;
@@ -945,20 +1038,14 @@ int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o
     S.sc = h->sc;
     S.ints = h->ints;
     S.fhist = h->fhist;
-    S.part = h->dpart;                       // 2 slabs
-    double* part6 = h->dpart + 2 * kRedBlocks;   // 6 slabs
-    double* part3 = h->dpart + 8 * kRedBlocks;   // 3 slabs
-    double* part3b = h->dpart + 11 * kRedBlocks; // 3 slabs
-    double* partf = h->dpart + 14 * kRedBlocks;  // 1 slab
+    S.part = h->dpart;                            // 2 slabs
+    double* part6 = h->dpart + 2 * kRedBlocks;    // 6 slabs
+    double* part3 = h->dpart + 8 * kRedBlocks;    // 3 slabs
+    double* part3b = h->dpart + 11 * kRedBlocks;  // 3 slabs
+    double* partf = h->dpart + 14 * kRedBlocks;   // 1 slab
     const double rho = o->rho;
 
-    CK(h, cudaEventRecord(h->ev0, h->st));
-    if (o->theta_memory == TLR_MEM_HOST) {
-        CK(h, cudaMemcpyAsync(h->q, theta_inout, L.nth * sizeof(cf), cudaMemcpyHostToDevice, h->st));
-        CK(h, theta_to_panel(h->pm, h->q, h->x, h->st));
-    } else {
-        CK(h, theta_to_panel(h->pm, (const cf*)theta_inout, h->x, h->st));
-    }
+    CK(h, theta_to_panel(h->pm, h->th_io, h->x, h->st));
     CK(h, sv_admm_init(S, h->st));
     int rc = forward(h, false);
     if (rc) return rc;
@@ -991,31 +1078,145 @@ int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o
             CK(h, sv_admm_zu(S, lam, rho, h->st));
         }
     }
-    if (o->theta_memory == TLR_MEM_HOST) {
-        CK(h, panel_to_theta(h->pm, h->x, h->q, h->st));
-        CK(h, cudaMemcpyAsync(theta_inout, h->q, L.nth * sizeof(cf), cudaMemcpyDeviceToHost, h->st));
-    } else {
-        CK(h, panel_to_theta(h->pm, h->x, (cf*)theta_inout, h->st));
+    CK(h, panel_to_theta(h->pm, h->x, h->th_io, h->st));
+    return TLR_OK;
+}
+
+static bool graphs_enabled(const tlr_mdd_s* h) {
+    if (h->st == nullptr) return false;  // the legacy default stream cannot be captured
+    const char* e = getenv("TLR_MDD_GRAPHS");
+    return !(e && e[0] == '0');
+}
+
+// Everything between the staging copies; a CUDA graph replay when possible.
+static int enqueue_body(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
+    const Layout& L = h->L;
+    const long long n2 = 2 * L.nth;
+    if (h->ring_m < o->memory) {  // ring of s / y vectors, m + 1 slots each
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        if (h->ring) cudaFreeAsync(h->ring, h->st);
+        h->ring = nullptr;
+        h->ring_m = 0;
+        CK(h, cudaMallocAsync((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), h->st));
+        h->ring_m = o->memory;
     }
+    h->pending_graph = false;
+    if (!graphs_enabled(h)) return enqueue_solve(h, o);
+    GraphKey k;
+    k.lam0 = o->lam0;
+    k.decay = o->decay;
+    k.rho = o->rho;
+    k.stages = o->stages;
+    k.admm = o->admm_iters;
+    k.lbfgs = o->lbfgs_iters;
+    k.mem = o->memory;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        k.timing = g_timing ? 1 : 0;
+    }
+    if (!h->gexec || !(k == h->gkey)) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        for (auto& t : h->gtimed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        h->gtimed.clear();
+        cudaGraph_t g = nullptr;
+        CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+        g_capture_sink = &h->gtimed;
+        const long long n_before = g_launches.load();
+        int rc = enqueue_solve(h, o);
+        h->graph_kernels = g_launches.load() - n_before;
+        g_launches.fetch_sub(h->graph_kernels);   // recorded, not launched: counted at each replay
+        g_capture_sink = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(h, e);
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(h, e);
+        h->gkey = k;
+    }
+    CK(h, cudaGraphLaunch(h->gexec, h->st));
+    counted((int)h->graph_kernels);
+    h->pending_graph = true;
+    return TLR_OK;
+}
+
+int tlr_mdd_solve_async(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!theta_inout || !o) FAIL(h, TLR_ERR_ARG, "theta or opts is NULL");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is already pending on this handle");
+    int rc = check_opts(h, o);
+    if (rc) return rc;
+    const size_t bytes = h->L.nth * sizeof(cf);
+    const bool host = o->theta_memory == TLR_MEM_HOST;
+    CK(h, cudaEventRecord(h->ev0, h->st));
+    CK(h, cudaMemcpyAsync(h->th_io, theta_inout, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          h->st));
+    rc = enqueue_body(h, o);
+    if (rc) return rc;
+    CK(h, cudaMemcpyAsync(theta_inout, h->th_io, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          h->st));
+    CK(h, cudaMemcpyAsync(h->hstats->ints, h->ints, sizeof(h->hstats->ints), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(h->hstats->sc, h->sc, sizeof(h->hstats->sc), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(h->hstats->fhist, h->fhist, sizeof(h->hstats->fhist), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaEventRecord(h->ev1, h->st));
-    int ints[SI_COUNT];
-    double sc[SC_COUNT];
-    CK(h, cudaMemcpyAsync(ints, h->ints, sizeof(ints), cudaMemcpyDeviceToHost, h->st));
-    CK(h, cudaMemcpyAsync(sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->st));
-    if (stats) CK(h, cudaMemcpyAsync(stats->f_hist, h->fhist, sizeof(double) * TLR_MAX_HIST, cudaMemcpyDeviceToHost, h->st));
-    CK(h, cudaStreamSynchronize(h->st));
+    h->pending = true;
+    return TLR_OK;
+}
+
+int tlr_mdd_solve_query(tlr_mdd_t* h) {
+    if (!h) return TLR_ERR_STATE;
+    if (!h->pending) return 1;
+    cudaError_t e = cudaEventQuery(h->ev1);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    h->err = cudaGetErrorString(e);
+    return TLR_ERR_CUDA;
+}
+
+int tlr_mdd_solve_wait(tlr_mdd_t* h, tlr_mdd_stats_t* stats) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!h->pending) FAIL(h, TLR_ERR_STATE, "no solve is pending on this handle");
+    h->pending = false;
+    CK(h, cudaEventSynchronize(h->ev1));
+    if (h->pending_graph && !h->gtimed.empty()) account_replay(h->gtimed);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess) (void)cudaGetLastError();
+    const HostStats& hs = *h->hstats;
     if (stats) {
-        stats->iters = ints[SI_ITERS];
-        stats->restarts = ints[SI_RESTARTS];
-        stats->status = ints[SI_STATUS];
-        stats->n_hist = std::min(ints[SI_ITERS], TLR_MAX_HIST);
-        stats->f0 = sc[SC_F0];
+        stats->iters = hs.ints[SI_ITERS];
+        stats->restarts = hs.ints[SI_RESTARTS];
+        stats->status = hs.ints[SI_STATUS];
+        stats->n_hist = std::min(hs.ints[SI_ITERS], TLR_MAX_HIST);
+        memcpy(stats->f_hist, hs.fhist, sizeof(stats->f_hist));
+        stats->f0 = hs.sc[SC_F0];
         stats->gpu_ms = ms;
     }
-    if (ints[SI_STATUS] != 0) FAIL(h, TLR_ERR_NONFINITE, "non-finite value met during the solve");
+    if (hs.ints[SI_COUNT + 1] != 0) {
+        // a tensor-core contraction gave up on a bounded wait: report and re-arm
+        CK(h, cudaMemsetAsync(h->ints + SI_COUNT + 1, 0, sizeof(int), h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        FAIL(h, TLR_ERR_TIMEOUT, "a tensor-core contraction timed out on a barrier wait");
+    }
+    if (hs.ints[SI_STATUS] != 0) FAIL(h, TLR_ERR_NONFINITE, "non-finite value met during the solve");
     return TLR_OK;
+}
+
+int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o, tlr_mdd_stats_t* stats) {
+    int rc = tlr_mdd_solve_async(h, theta_inout, o);
+    if (rc) return rc;
+    return tlr_mdd_solve_wait(h, stats);
 }
 
 }  // extern "C"

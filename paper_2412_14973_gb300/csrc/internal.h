@@ -71,6 +71,8 @@ struct GemmLaunch {
 cudaError_t gemm_simt(const GemmLaunch& L, cudaStream_t st);
 // tcgen05 path (k_gemm_tc.cu): BF16x3 split, 3M complex, FP32 accumulation in TMEM
 cudaError_t gemm_tc(const GemmLaunch& L, cudaStream_t st);
+// one-time kernel attributes (shared-memory size), outside any stream capture
+cudaError_t gemm_tc_prepare();
 inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
     return L.prec == TLR_PREC_BF16X3 ? gemm_tc(L, st) : gemm_simt(L, st);
 }

@@ -56,7 +56,7 @@ constexpr int PROB_OFF = CTRL_OFF + CTRL;           // problem descriptor copy
 constexpr int IDX_OFF = PROB_OFF + 256;
 constexpr int SMEM_BYTES = IDX_OFF + IDX_CAP * 4;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long WAIT_LIMIT = 1LL << 22;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // a barrier wait gives up after 2 s
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 
 // instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 256, M = 128
@@ -79,8 +79,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the given phase parity of an mbarrier: gives up after
+// WAIT_NS of wall time, or at once when another CTA has already recorded an
+// error in the launch's error word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err) {
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -90,8 +100,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 255u && (*err != 0 || now_ns() - t0 > WAIT_NS)) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -278,6 +288,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tc(const GProb* __restrict__ 
     {
         const GProb& Pg = probs[prob];
         if (m0 >= Pg.M || n0 >= Pg.N) return;
+        if (*(volatile int*)err != 0) return;   // an earlier CTA gave up: do no more work
     }
     // descriptor and gather indices go to shared memory once, so the
     // producers' per-chunk loads are single, independent global loads
@@ -383,7 +394,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tc(const GProb* __restrict__ 
             asm volatile("cp.async.wait_group %0;" ::"n"(RSTAGE - 1) : "memory");  // chunk c has landed
             const int s = c % NSTAGE;
             if (c >= NSTAGE) {
-                if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)(((c / NSTAGE) - 1) & 1))) *abort_flag = 1;
+                if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)(((c / NSTAGE) - 1) & 1), err)) *abort_flag = 1;
             }
             if (*abort_flag) break;
             const GTerm& t = P.t[cur.ti];
@@ -408,7 +419,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tc(const GProb* __restrict__ 
         // ---------------- MMA issuer ----------------
         for (int c = 0; c < C; ++c) {
             const int s = c % NSTAGE;
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((c / NSTAGE) & 1))) {
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((c / NSTAGE) & 1), err)) {
                 *abort_flag = 1;
                 break;
             }
@@ -443,7 +454,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tc(const GProb* __restrict__ 
 
     // ---------------- epilogue (producer warps) ----------------
     bool ok = true;
-    if (warp < 8 && C > 0) ok = mbar_wait(smem_u32(done), 0u);
+    if (warp < 8 && C > 0) ok = mbar_wait(smem_u32(done), 0u, err);
     if (!ok || *abort_flag) {
         if (threadIdx.x == 0 || !ok) atomicExch(err, TLR_ERR_TIMEOUT);
     }
@@ -508,6 +519,15 @@ cudaError_t launch_tc(const GemmLaunch& L, dim3 grid, int kchunk, cudaStream_t s
 }
 
 }  // namespace
+
+cudaError_t gemm_tc_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<A_KM, B_KN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cgemm_tc<A_MK, B_KN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cgemm_tc<A_MK, B_NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return e;
+}
 
 cudaError_t gemm_tc(const GemmLaunch& L, cudaStream_t st) {
     if (L.nprob == 0 || L.maxM == 0 || L.maxN == 0) return cudaSuccess;

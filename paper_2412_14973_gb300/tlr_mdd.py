@@ -20,6 +20,7 @@ __all__ = [
     "tlr_mdd_get_data", "tlr_mdd_destroy", "tlr_mdd_last_error", "EXPORTED",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "TLR_NOALLOC_SCRATCH_BYTES",
+    "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
 ]
 
 TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
@@ -36,7 +37,8 @@ EXPORTED = [
     "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
     "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
-    "tlr_mdd_adjoint_noalloc",
+    "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
+    "tlr_mdd_set_data",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -125,6 +127,14 @@ def lib():
         L.tlr_mdd_launch_count.restype = i64
         L.tlr_mdd_adjoint_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, vp]
         L.tlr_mdd_adjoint_noalloc.restype = i32
+        L.tlr_mdd_solve_async.argtypes = [vp, vp, C.POINTER(SolveOpts)]
+        L.tlr_mdd_solve_async.restype = i32
+        L.tlr_mdd_solve_query.argtypes = [vp]
+        L.tlr_mdd_solve_query.restype = i32
+        L.tlr_mdd_solve_wait.argtypes = [vp, C.POINTER(Stats)]
+        L.tlr_mdd_solve_wait.restype = i32
+        L.tlr_mdd_set_data.argtypes = [vp, vp, vp, C.c_int32]
+        L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
                      "tlr_mdd_solve", "tlr_mdd_unpermute_dense", "tlr_mdd_get_data",
@@ -293,3 +303,26 @@ def tlr_mdd_launch_count() -> int:
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
     """G = V Dt^H without any device allocation (fixed in-library scratch)."""
     _check(lib().tlr_mdd_adjoint_noalloc(_ptr(V), _ptr(Dt), nr, ns, _ptr(G), _stream(stream)))
+
+
+def tlr_mdd_solve_async(h, theta, opts: SolveOpts | None = None):
+    """Enqueue a solve; keep ``theta`` (and ``opts``) alive until it finishes."""
+    opts = opts if opts is not None else solve_opts()
+    _check(lib().tlr_mdd_solve_async(h, _ptr(theta), C.byref(opts)), h)
+
+
+def tlr_mdd_solve_query(h) -> bool:
+    rc = lib().tlr_mdd_solve_query(h)
+    if rc < 0:
+        _check(rc, h)
+    return rc == 1
+
+
+def tlr_mdd_solve_wait(h) -> Stats:
+    st = Stats()
+    _check(lib().tlr_mdd_solve_wait(h, C.byref(st)), h)
+    return st
+
+
+def tlr_mdd_set_data(h, D, U, input_memory=TLR_MEM_DEVICE):
+    _check(lib().tlr_mdd_set_data(h, _ptr(D), _ptr(U), input_memory), h)

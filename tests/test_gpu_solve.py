@@ -8,7 +8,7 @@ from tests._cases import problem
 
 pytestmark = pytest.mark.gpu
 T = pytest.importorskip("paper_2412_14973_gb300")
-from tests._gpu import Gpu, rel  # noqa: E402
+from tests._gpu import Gpu, dev, rel  # noqa: E402
 
 
 def _start(lay, seed=77, scale=0.1):
@@ -86,3 +86,36 @@ def test_invalid_solver_options():
             g.solve(_start(lay), **kw)
         assert ei.value.code == -1
     g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_async_graph_solves_on_two_streams_match_plain_solves(prec, monkeypatch):
+    """Concurrent solves (graph replay, two streams) give bit-identical results
+    to one-at-a-time solves without graphs: every reduction has a fixed order."""
+    import torch
+    probs = [problem(8, 8, 16, 3, "lowrank", seed=40 + i, snr_db=10) for i in range(2)]
+    th0 = [_start(p[3], seed=50 + i, scale=0.3) for i, p in enumerate(probs)]
+    kw = dict(stages=1, admm_iters=2, lbfgs_iters=4)
+    # reference: plain launches, one at a time
+    monkeypatch.setenv("TLR_MDD_GRAPHS", "0")
+    ref = []
+    for p, t in zip(probs, th0):
+        g = Gpu(p[0], p[1], p[3], nx=8, ny=8, precision=prec)
+        th, st = g.solve(t, **kw)
+        ref.append(th)
+        g.close()
+    monkeypatch.setenv("TLR_MDD_GRAPHS", "1")
+    streams = [torch.cuda.Stream() for _ in probs]
+    gs = [Gpu(p[0], p[1], p[3], nx=8, ny=8, precision=prec, stream=s) for p, s in zip(probs, streams)]
+    for rep in range(2):   # the second round replays the recorded graphs
+        ths = [dev(t) for t in th0]
+        opts = T.solve_opts(**kw)
+        for g, th in zip(gs, ths):
+            T.tlr_mdd_solve_async(g.h, th, opts)
+        for g in gs:
+            st = T.tlr_mdd_solve_wait(g.h)
+            assert st.iters == 8 and st.status == 0
+        for th, r in zip(ths, ref):
+            assert np.array_equal(th.cpu().numpy().astype(np.complex128), r)
+    for g in gs:
+        g.close()
