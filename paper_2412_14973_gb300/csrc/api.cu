@@ -23,7 +23,10 @@
 #include "internal.h"
 #include "solver_dev.h"
 
+#include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
 
 using namespace tlr;
 
@@ -32,6 +35,12 @@ std::atomic<long long> tlr::g_launches{0};
 namespace {
 
 thread_local std::string g_last_error;
+
+// environment switch set to "0"
+bool getenv_off(const char* name) {
+    const char* e = getenv(name);
+    return e && e[0] == '0';
+}
 
 // ---- diagnostics: CUDA-event timing of the contraction launches ----
 struct TimedLaunch {
@@ -339,6 +348,13 @@ struct tlr_mdd_s {
     GemmLaunch Lc_x, Lc_d, Lc_v, Le_fwd, Le_apply, Le_a1, Le_a2, Lp;
     char* tab_base = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // packed tensor-core path: packed operand storage, tables, static packs
+    char* packed = nullptr;
+    size_t packed_size = 0;
+    char* tcp_tables = nullptr;
+    PackJob* d_static_jobs = nullptr;
+    int n_static_jobs = 0;
+    long long static_items = 0;
     // asynchronous solve and its CUDA graph
     cf* th_io = nullptr;               // theta staging (stable address for the graph)
     HostStats* hstats = nullptr;       // pinned
@@ -419,6 +435,25 @@ void carve(tlr_mdd_s* h, Arena& a) {
     for (int t = 1; t < 8; ++t) a.take<GProb>(2 * (size_t)L.N + 1);
 }
 
+// Upper bound of the packed-operand storage of the tensor-core path (the
+// distinct operands listed in build_tc; 1 KB alignment per operand).
+long long packed_estimate(const Layout& L) {
+    auto pb = [](long long R, long long K, int TR) { return (packed_bytes(R, K, TR) + 1023) & ~1023LL; };
+    const long long b = L.b, ns = L.ns;
+    long long t = 0;
+    for (int i = 0; i < L.N; ++i) {
+        const long long Ki = L.Kb[i];
+        if (Ki > 0) {
+            t += 3 * pb(Ki, b, 128) + 2 * pb(b, Ki, 128);     // F, conj F, F_d (KM); F, F_d (MK)
+            t += 2 * pb(ns, Ki, 256) + 2 * pb(Ki, ns, 256);   // T~, T~_p (KN); conj T~, V~ (NK)
+            t += pb(ns, b, 256);                              // Rf_i (KN)
+        }
+        if (Ki > 0 || L.dense[i]) t += pb(ns, b, 256) + 2 * pb(b, ns, 128);   // Dfrak_i (KN); Rf_i, conj Dfrak_i (MK)
+        if (L.dense[i]) t += 2 * pb(b, b, 128) + pb(b, ns, 256);              // Zs, Zs_d; conj Dfrak_i (NK)
+    }
+    return t;
+}
+
 int split_for(const Layout& L) {
     long long tiles = 0;
     for (int i = 0; i < L.N; ++i) {
@@ -441,8 +476,13 @@ GTerm term(const cf* A, long long lda, const cf* B, long long ldb, const int* g,
     return t;
 }
 
+struct HostTable {
+    GemmLaunch* G;
+    std::vector<GProb> v;
+};
+
 // Build the grouped problems for every contraction of the handle and upload.
-int build_tables(tlr_mdd_s* h, char* tab_base) {
+int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
     const Layout& L = h->L;
     const long long ns = L.ns, b = L.b;
     const size_t slot = ((sizeof(GProb) * (2 * (size_t)L.N + 1)) + 255) & ~size_t(255);
@@ -468,6 +508,7 @@ int build_tables(tlr_mdd_s* h, char* tab_base) {
             cudaError_t e = cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(GProb), cudaMemcpyHostToDevice, h->st);
             if (e != cudaSuccess) return -1;
         }
+        if (keep) keep->push_back(HostTable{&G, v});
         return 0;
     };
     auto blank = []() {
@@ -570,6 +611,176 @@ int build_tables(tlr_mdd_s* h, char* tab_base) {
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Packed tensor-core plan.  Every operand of every tensor-core contraction is
+// written once per use into the packed BF16-plane tile format by a pack job
+// that runs just before the contraction; identical operands (same source,
+// layout, gather, conjugation and shape) share one packed buffer.  Operands
+// read from the data panel Dfrak never change during a solve: they are packed
+// once when the data are loaded.  The line-search pair A1 / A2 shares its
+// packs (A2 packs nothing).
+// ---------------------------------------------------------------------------
+struct PackKey {
+    const void* src;
+    long long ld;
+    const void* gr;
+    const void* gk;
+    int kcontig, R, K, TR;
+    float sgn;
+    bool operator<(const PackKey& o) const {
+        return std::tie(src, ld, gr, gk, kcontig, R, K, TR, sgn) <
+               std::tie(o.src, o.ld, o.gr, o.gk, o.kcontig, o.R, o.K, o.TR, o.sgn);
+    }
+};
+
+int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
+    const Layout& L = h->L;
+    const char* dlo = reinterpret_cast<const char*>(h->Dt);
+    const char* dhi = dlo + (size_t)L.nr * L.ns * sizeof(cf);
+    std::map<PackKey, size_t> offs;   // key -> byte offset in the packed arena
+    std::vector<std::pair<PackKey, size_t>> order;
+    size_t total = 0;
+    auto key_of = [](const GTerm& t, bool isA, int amode, int bmode, int R) {
+        PackKey k{};
+        if (isA) {
+            k.src = t.A;
+            k.ld = t.lda;
+            k.kcontig = amode == A_MK;
+            k.sgn = t.sa;
+            k.TR = 128;
+        } else {
+            k.src = t.B;
+            k.ld = t.ldb;
+            k.kcontig = bmode == B_NK;
+            if (k.kcontig)
+                k.gr = t.g;
+            else
+                k.gk = t.g;
+            k.sgn = t.sb;
+            k.TR = 256;
+        }
+        k.R = R;
+        k.K = t.K;
+        return k;
+    };
+    auto place = [&](const PackKey& k) -> size_t {
+        auto it = offs.find(k);
+        if (it != offs.end()) return it->second;
+        const size_t o = total;
+        offs[k] = o;
+        order.push_back({k, o});
+        total += (size_t)((packed_bytes(k.R, k.K, k.TR) + 1023) & ~1023LL);
+        return o;
+    };
+    // pass 1: storage
+    for (auto& T : tabs)
+        for (auto& p : T.v)
+            for (int t = 0; t < p.nt; ++t) {
+                place(key_of(p.t[t], true, T.G->amode, T.G->bmode, p.M));
+                place(key_of(p.t[t], false, T.G->amode, T.G->bmode, p.N));
+            }
+    h->packed_size = total;
+    CK(h, cudaMallocAsync((void**)&h->packed, std::max<size_t>(total, 256), h->st));
+    auto job_of = [&](const PackKey& k, size_t off) {
+        PackJob j;
+        j.src = (const cf*)k.src;
+        j.ld = k.ld;
+        j.g_row = (const int*)k.gr;
+        j.g_k = (const int*)k.gk;
+        j.kcontig = k.kcontig;
+        j.sgn = k.sgn;
+        j.R = k.R;
+        j.K = k.K;
+        j.TR = k.TR;
+        j.dst = h->packed + off;
+        return j;
+    };
+    auto items_of = [](const PackKey& k) {
+        const long long nkc = (k.K + 15) / 16, nrb = (k.R + k.TR - 1) / k.TR;
+        return nrb * k.TR * nkc * 2;
+    };
+    auto is_static = [&](const PackKey& k) {
+        const char* c = reinterpret_cast<const char*>(k.src);
+        return c >= dlo && c < dhi;
+    };
+    // pass 2: problems on packed operands and per-launch pack jobs
+    std::vector<std::vector<PProb>> pp(tabs.size());
+    std::vector<std::vector<PackJob>> jobs(tabs.size());
+    std::vector<long long> maxit(tabs.size(), 0);
+    std::vector<PackJob> sjobs;
+    long long smax = 0;
+    std::set<PackKey> static_done;
+    std::set<PackKey> a1_keys;
+    for (size_t ti = 0; ti < tabs.size(); ++ti) {
+        auto& T = tabs[ti];
+        std::set<PackKey> here;
+        for (auto& p : T.v) {
+            PProb q;
+            memset(&q, 0, sizeof(q));
+            q.nt = p.nt;
+            q.M = p.M;
+            q.N = p.N;
+            q.C = p.C;
+            q.S = p.S;
+            q.ldc = p.ldc;
+            for (int t = 0; t < p.nt; ++t) {
+                const PackKey ka = key_of(p.t[t], true, T.G->amode, T.G->bmode, p.M);
+                const PackKey kb = key_of(p.t[t], false, T.G->amode, T.G->bmode, p.N);
+                q.t[t].A = h->packed + offs[ka];
+                q.t[t].B = h->packed + offs[kb];
+                q.t[t].K = p.t[t].K;
+                for (const PackKey* k : {&ka, &kb}) {
+                    if (is_static(*k)) {
+                        if (static_done.insert(*k).second) {
+                            sjobs.push_back(job_of(*k, offs[*k]));
+                            smax = std::max(smax, items_of(*k));
+                        }
+                    } else if (here.insert(*k).second) {
+                        if (T.G == &h->Le_a2 && a1_keys.count(*k)) continue;   // packed for A1 already
+                        jobs[ti].push_back(job_of(*k, offs[*k]));
+                        maxit[ti] = std::max(maxit[ti], items_of(*k));
+                    }
+                }
+            }
+            pp[ti].push_back(q);
+        }
+        if (T.G == &h->Le_a1) a1_keys = here;
+    }
+    // upload: one allocation for all tables
+    size_t bytes = 0;
+    std::vector<size_t> po(tabs.size()), jo(tabs.size());
+    for (size_t ti = 0; ti < tabs.size(); ++ti) {
+        po[ti] = bytes;
+        bytes += (pp[ti].size() * sizeof(PProb) + 255) & ~size_t(255);
+        jo[ti] = bytes;
+        bytes += (jobs[ti].size() * sizeof(PackJob) + 255) & ~size_t(255);
+    }
+    const size_t so = bytes;
+    bytes += (sjobs.size() * sizeof(PackJob) + 255) & ~size_t(255);
+    CK(h, cudaMallocAsync((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
+    for (size_t ti = 0; ti < tabs.size(); ++ti) {
+        GemmLaunch& G = *tabs[ti].G;
+        G.d_pprobs = reinterpret_cast<PProb*>(h->tcp_tables + po[ti]);
+        G.d_jobs = reinterpret_cast<PackJob*>(h->tcp_tables + jo[ti]);
+        G.njobs = (int)jobs[ti].size();
+        G.max_items = maxit[ti];
+        if (!pp[ti].empty())
+            CK(h, cudaMemcpyAsync(G.d_pprobs, pp[ti].data(), pp[ti].size() * sizeof(PProb), cudaMemcpyHostToDevice,
+                                  h->st));
+        if (!jobs[ti].empty())
+            CK(h, cudaMemcpyAsync(G.d_jobs, jobs[ti].data(), jobs[ti].size() * sizeof(PackJob),
+                                  cudaMemcpyHostToDevice, h->st));
+    }
+    h->d_static_jobs = reinterpret_cast<PackJob*>(h->tcp_tables + so);
+    h->n_static_jobs = (int)sjobs.size();
+    h->static_items = smax;
+    if (!sjobs.empty())
+        CK(h, cudaMemcpyAsync(h->d_static_jobs, sjobs.data(), sjobs.size() * sizeof(PackJob), cudaMemcpyHostToDevice,
+                              h->st));
+    CK(h, cudaStreamSynchronize(h->st));   // host vectors go out of scope
+    return TLR_OK;
+}
+
 }  // namespace
 
 // The data step of a request (eq. 14 and the normalisation): alpha, then the
@@ -661,7 +872,9 @@ int64_t tlr_mdd_workspace_bytes(const tlr_mdd_desc_t* d) {
     Arena a;
     carve(&tmp, a);
     // plus the L-BFGS ring for the default memory (m = 10: 11 slots of s and y)
-    return (int64_t)a.used + (int64_t)2 * 11 * tmp.L.nth * (int64_t)sizeof(cf);
+    int64_t total = (int64_t)a.used + (int64_t)2 * 11 * tmp.L.nth * (int64_t)sizeof(cf);
+    if (d->precision == TLR_PREC_BF16X3) total += packed_estimate(tmp.L);
+    return total;
 }
 
 int tlr_mdd_hilbert_perm(int32_t nx, int32_t ny, int32_t* perm_dev, void* stream) {
@@ -708,6 +921,8 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
     h->arena_bytes = a.used;
     auto fail = [&](int code) {
         g_last_error = h->err;
+        if (h->packed) cudaFreeAsync(h->packed, h->st);
+        if (h->tcp_tables) cudaFreeAsync(h->tcp_tables, h->st);
         if (h->arena) cudaFreeAsync(h->arena, h->st);
         delete h;
         return code;
@@ -771,9 +986,17 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         CKF(cudaMemcpyAsync((void*)h->pm.zsrc, L.zsrc.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
     // solver counters and the contraction kernels' error word start at zero
     CKF(cudaMemsetAsync(h->ints, 0, (SI_COUNT + 8) * sizeof(int), h->st));
-    if (build_tables(h, h->tab_base)) {
+    std::vector<HostTable> tabs;
+    if (build_tables(h, h->tab_base, &tabs)) {
         h->err = "uploading GEMM tables failed";
         return fail(TLR_ERR_CUDA);
+    }
+    if (d->precision == TLR_PREC_BF16X3 && !getenv_off("TLR_MDD_PACKED")) {
+        // every tensor-core contraction except the dense adjoint (allocated per call)
+        int rc = build_tc(h, tabs);
+        if (rc) return fail(rc);
+        CKF(gemm_tcp_prepare());
+        CKF(pack_operands(h->d_static_jobs, h->n_static_jobs, h->static_items, h->st));
     }
     CKF(cudaEventCreate(&h->ev0));
     CKF(cudaEventCreate(&h->ev1));
@@ -793,6 +1016,7 @@ int tlr_mdd_set_data(tlr_mdd_t* h, const void* D, const void* U, int32_t input_m
     if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
     int rc = load_data(h, D, U, input_memory);
     if (rc) return rc;
+    if (h->n_static_jobs) CK(h, pack_operands(h->d_static_jobs, h->n_static_jobs, h->static_items, h->st));
     if (h->d.alpha <= 0.0) {
         CK(h, cudaMemcpyAsync(&h->alpha, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
         CK(h, cudaStreamSynchronize(h->st));
@@ -993,6 +1217,8 @@ int tlr_mdd_destroy(tlr_mdd_t* h) {
     }
     if (h->hstats) cudaFreeHost(h->hstats);
     if (h->ring) cudaFreeAsync(h->ring, h->st);
+    if (h->packed) cudaFreeAsync(h->packed, h->st);
+    if (h->tcp_tables) cudaFreeAsync(h->tcp_tables, h->st);
     if (h->arena) cudaFreeAsync(h->arena, h->st);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

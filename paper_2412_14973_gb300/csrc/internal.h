@@ -53,6 +53,36 @@ enum Epi { EPI_STORE = 0, EPI_SUB = 1, EPI_ACCUM = 2, EPI_PARTIAL = 3 };
 enum AMode { A_KM = 0, A_MK = 1 };
 enum BMode { B_KN = 0, B_NK = 1 };
 
+// ---------------------------------------------------------------------------
+// Packed-operand tensor-core path (k_gemm_tcp.cu).
+// One pack job writes one operand in the BF16-plane tile format; element
+// (r, k) of the logical operand is src[row(r) * ld + k] when kcontig, else
+// src[krow(k) * ld + r]; row(r) = g_row ? g_row[r] : r, krow likewise with g_k;
+// the imaginary part is multiplied by sgn.
+struct PackJob {
+    const cf* src;
+    long long ld;
+    const int* g_row;
+    const int* g_k;
+    int kcontig;
+    float sgn;
+    int R, K, TR;
+    void* dst;
+};
+struct PTerm {
+    const void* A;   // packed A of this problem (TR = 128), all row blocks
+    const void* B;   // packed B of this problem (TR = 256)
+    int K;
+};
+struct PProb {
+    PTerm t[kMaxTerms];
+    int nt;
+    int M, N;
+    cf* C;
+    const cf* S;
+    long long ldc;
+};
+
 struct GemmLaunch {
     GProb* d_probs = nullptr;   // device copy
     int nprob = 0;
@@ -65,7 +95,17 @@ struct GemmLaunch {
     int cls = 0;                // diagnostics class (0 compress, 1 expand, 2 project)
     int prec = 0;               // TLR_PREC_FP32 (SIMT) or TLR_PREC_BF16X3 (tcgen05)
     int* err = nullptr;         // device error word (tensor-core path: bounded-wait timeouts)
+    // packed tensor-core path: problems on packed operands and the packs to run first
+    PProb* d_pprobs = nullptr;
+    PackJob* d_jobs = nullptr;
+    int njobs = 0;
+    long long max_items = 0;
 };
+// bytes of one operand (R rows x K) in the packed tile format with TR-row tiles
+long long packed_bytes(long long R, long long K, int TR);
+cudaError_t pack_operands(const PackJob* d_jobs, int njobs, long long max_items, cudaStream_t st);
+cudaError_t gemm_tcp_prepare();
+cudaError_t gemm_tcp(const GemmLaunch& L, cudaStream_t st);
 
 // SIMT path (k_gemm_simt.cu)
 cudaError_t gemm_simt(const GemmLaunch& L, cudaStream_t st);
@@ -74,7 +114,10 @@ cudaError_t gemm_tc(const GemmLaunch& L, cudaStream_t st);
 // one-time kernel attributes (shared-memory size), outside any stream capture
 cudaError_t gemm_tc_prepare();
 inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
-    return L.prec == TLR_PREC_BF16X3 ? gemm_tc(L, st) : gemm_simt(L, st);
+    if (L.prec != TLR_PREC_BF16X3) return gemm_simt(L, st);
+    if (!L.d_pprobs) return gemm_tc(L, st);
+    cudaError_t e = pack_operands(L.d_jobs, L.njobs, L.max_items, st);
+    return e == cudaSuccess ? gemm_tcp(L, st) : e;
 }
 
 // ---------------------------------------------------------------------------

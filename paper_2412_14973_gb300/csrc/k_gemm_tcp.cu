@@ -1,0 +1,368 @@
+// Tensor-core GEMM on pre-packed operands, and the pack kernel that makes them.
+//
+// Packed format ("P-format") of an operand with R rows (the M or N index) and
+// K columns (the contraction index): tiles of TR rows x 16 k, TR = 128 for an
+// A operand and 256 for a B operand; tile (rb, kc) starts at byte
+// (rb * nkc + kc) * 4 * TR * 32 and holds four BF16 planes (Re hi, Re lo,
+// Im hi, Im lo; x = hi + lo with hi = RN_bf16(x), lo = RN_bf16(x - hi)), each
+// in the tensor core's canonical K-major, no-swizzle layout (8-row x 16-byte
+// core matrices, 128 B apart along K, 256 B apart along rows).  Elements
+// outside R x K are zero.  The pack applies the row gather and the
+// conjugation of the operand, so a tile is exactly what a stage of the GEMM
+// needs and is moved with one cp.async.bulk copy.
+//
+// The GEMM (4M complex products, 128 x 256 tile, 12 MMAs per 16-deep chunk as
+// in k_gemm_tc.cu) has one thread issuing the bulk copies of the A and B
+// tiles of each chunk into a 4-stage ring with a transaction-count mbarrier,
+// one thread issuing the MMAs, and four warps for the epilogue.  Every wait
+// is bounded (2 s of %globaltimer, grid-wide abort word).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace tlr {
+
+namespace {
+
+constexpr int TM = 128, TN = 256, KC = 16;
+constexpr int NSTAGE = 4;
+constexpr int TILE_A = 4 * TM * KC * 2;             // 16 KB
+constexpr int TILE_B = 4 * TN * KC * 2;             // 32 KB
+constexpr int STAGE = TILE_A + TILE_B;              // 48 KB
+constexpr int CTRL_OFF = NSTAGE * STAGE;
+constexpr int SMEM_BYTES = CTRL_OFF + 256 + 256;    // barriers etc. + problem descriptor
+constexpr int NTHR = 192;                           // warps 0-3 epilogue, 4 copies, 5 MMAs
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(256u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err) {
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 255u && (*err != 0 || now_ns() - t0 > WAIT_NS)) return false;
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int core_off(int r, int kg) { return ((r >> 3) * 2 + kg) * 128 + (r & 7) * 16; }
+
+// ---------------------------------------------------------------------------
+// pack
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs, int njobs) {
+    const PackJob& J = jobs[blockIdx.y];
+    const int nkc = (J.K + KC - 1) / KC;
+    const int nrb = (J.R + J.TR - 1) / J.TR;
+    const long long items = (long long)nrb * J.TR * nkc * 2;   // (row, k-group of 8)
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
+         e += (long long)gridDim.x * blockDim.x) {
+        // consecutive threads take consecutive rows of one k-group
+        const long long rowsP = (long long)nrb * J.TR;
+        const int r = (int)(e % rowsP);
+        const int kg2 = (int)(e / rowsP);        // global k-group index (8 k each)
+        const int kc = kg2 >> 1, kg = kg2 & 1;
+        const int rb = r / J.TR, rr = r % J.TR;
+        float2 v[8];
+        const bool rv = r < J.R;
+        long long rowoff = 0;
+        if (rv && J.kcontig) rowoff = (long long)(J.g_row ? J.g_row[r] : r) * J.ld;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = kc * KC + kg * 8 + j;
+            float2 x = make_float2(0.f, 0.f);
+            if (rv && k < J.K) {
+                if (J.kcontig) {
+                    x = J.src[rowoff + k];
+                } else {
+                    const long long kr = J.g_k ? J.g_k[k] : k;
+                    x = J.src[kr * J.ld + r];
+                }
+                x.y *= J.sgn;
+            }
+            v[j] = x;
+        }
+        uint32_t w[4][4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const float x[2][2] = {{v[j].x, v[j + 1].x}, {v[j].y, v[j + 1].y}};
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(x[p][0], x[p][1]);
+                const float2 hf = __bfloat1622float2(hi);
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(x[p][0] - hf.x, x[p][1] - hf.y);
+                w[2 * p][j >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
+                w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
+            }
+        }
+        const long long plane = (long long)J.TR * KC * 2;
+        char* tile = reinterpret_cast<char*>(J.dst) + ((long long)rb * nkc + kc) * 4 * plane;
+        const int off = core_off(rr, kg);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(tile + q * plane + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM on packed operands
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
+                                                       int epi, long long part_stride, int* err) {
+    extern __shared__ __align__(1024) char smem[];
+    const int prob = blockIdx.z / nsplit, chunk = blockIdx.z % nsplit;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    {
+        const PProb& Pg = probs[prob];
+        if (m0 >= Pg.M || n0 >= Pg.N) return;
+        if (*(volatile int*)err != 0) return;
+    }
+    PProb& P = *reinterpret_cast<PProb*>(smem + CTRL_OFF + 256);
+    static_assert(sizeof(PProb) <= 256, "descriptor slot");
+    {
+        const int* src = reinterpret_cast<const int*>(&probs[prob]);
+        int* dst = reinterpret_cast<int*>(&P);
+        for (int i = threadIdx.x; i < (int)(sizeof(PProb) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + CTRL_OFF);
+    uint64_t* empty = full + NSTAGE;
+    uint64_t* done = empty + NSTAGE;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    // the chunk list: per term, K chunks [kb, ke) of 16 (kb a multiple of 16)
+    int C = 0;
+    for (int ti = 0; ti < P.nt; ++ti) {
+        int kb = 0, ke = P.t[ti].K;
+        if (nsplit > 1) {
+            kb = chunk * kchunk;
+            ke = min(P.t[ti].K, kb + kchunk);
+        }
+        if (ke > kb) C += (ke - kb + KC - 1) / KC;
+    }
+
+    if (warp == 4 && lane == 0) {
+        // ---------------- bulk copies ----------------
+        int c = 0;
+        for (int ti = 0; ti < P.nt && !*abort_flag; ++ti) {
+            const PTerm& t = P.t[ti];
+            int kb = 0, ke = t.K;
+            if (nsplit > 1) {
+                kb = chunk * kchunk;
+                ke = min(t.K, kb + kchunk);
+            }
+            const int nkcA = (t.K + KC - 1) / KC, nkcB = nkcA;
+            const char* abase = reinterpret_cast<const char*>(t.A) + (long long)(m0 / TM) * nkcA * TILE_A;
+            const char* bbase = reinterpret_cast<const char*>(t.B) + (long long)(n0 / TN) * nkcB * TILE_B;
+            for (int k0 = kb; k0 < ke; k0 += KC, ++c) {
+                const int s = c % NSTAGE;
+                if (c >= NSTAGE) {
+                    if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)(((c / NSTAGE) - 1) & 1), err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                }
+                const uint32_t fb = smem_u32(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE)
+                             : "memory");
+                const int kc = k0 / KC;
+                const uint32_t dst = smem_u32(smem + s * STAGE);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                    "l"(abase + (long long)kc * TILE_A), "r"(TILE_A), "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        dst + TILE_A),
+                    "l"(bbase + (long long)kc * TILE_B), "r"(TILE_B), "r"(fb)
+                    : "memory");
+            }
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        for (int c = 0; c < C; ++c) {
+            const int s = c % NSTAGE;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((c / NSTAGE) & 1), err)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + TILE_A;
+            constexpr int PA = TILE_A / 4, PB = TILE_B / 4;
+            const uint64_t arh = sdesc(a0), arl = sdesc(a0 + PA), aih = sdesc(a0 + 2 * PA), ail = sdesc(a0 + 3 * PA);
+            const uint64_t brh = sdesc(b0), brl = sdesc(b0 + PB), bih = sdesc(b0 + 2 * PB), bil = sdesc(b0 + 3 * PB);
+            const uint32_t dr = tmem, di = tmem + 256;
+            const uint32_t first = c > 0 ? 1u : 0u;
+            mma_bf16(dr, arh, brh, IDESC, first);
+            mma_bf16(dr, arh, brl, IDESC, 1u);
+            mma_bf16(dr, arl, brh, IDESC, 1u);
+            mma_bf16(dr, aih, bih, IDESC_NEG_A, 1u);
+            mma_bf16(dr, aih, bil, IDESC_NEG_A, 1u);
+            mma_bf16(dr, ail, bih, IDESC_NEG_A, 1u);
+            mma_bf16(di, arh, bih, IDESC, first);
+            mma_bf16(di, arh, bil, IDESC, 1u);
+            mma_bf16(di, arl, bih, IDESC, 1u);
+            mma_bf16(di, aih, brh, IDESC, 1u);
+            mma_bf16(di, aih, brl, IDESC, 1u);
+            mma_bf16(di, ail, brh, IDESC, 1u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(done))
+                     : "memory");
+    }
+
+    // ---------------- epilogue (warps 0-3) ----------------
+    bool ok = true;
+    if (warp < 4 && C > 0) ok = mbar_wait(smem_u32(done), 0u, err);
+    if (!ok || *abort_flag) {
+        if (threadIdx.x == 0 || !ok) atomicExch(err, TLR_ERR_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp < 4 && ok && !*abort_flag) {
+        const int m = m0 + warp * 32 + lane;
+        cf* Cp = P.C + (epi == EPI_PARTIAL ? chunk * part_stride : 0);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int cb = 0; cb < TN / 16; ++cb) {
+            const int col = cb * 16;
+            if (n0 + col >= P.N) break;
+            float pr[16], pi[16];
+            if (C > 0) {
+                tmem_ld16(lane_addr + col, pr);
+                tmem_ld16(lane_addr + 256 + col, pi);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
+            }
+            if (m < P.M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + col + j;
+                    if (n >= P.N) break;
+                    const long long o = (long long)m * P.ldc + n;
+                    cf v = make_float2(pr[j], pi[j]);
+                    if (epi == EPI_SUB) {
+                        const cf sv = P.S[o];
+                        v.x -= sv.x;
+                        v.y -= sv.y;
+                    } else if (epi == EPI_ACCUM) {
+                        const cf cv = Cp[o];
+                        v.x += cv.x;
+                        v.y += cv.y;
+                    }
+                    Cp[o] = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace
+
+long long packed_bytes(long long R, long long K, int TR) {
+    const long long nkc = (K + KC - 1) / KC, nrb = (R + TR - 1) / TR;
+    return nrb * nkc * 4LL * TR * KC * 2;
+}
+
+cudaError_t pack_operands(const PackJob* jobs, int njobs, long long max_items, cudaStream_t st) {
+    if (njobs == 0 || max_items == 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((max_items + 255) / 256, 2048);
+    dim3 grid((unsigned)blocks, (unsigned)njobs);
+    k_pack<<<grid, 256, 0, st>>>(jobs, njobs);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_tcp_prepare() {
+    return cudaFuncSetAttribute(k_cgemm_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+cudaError_t gemm_tcp(const GemmLaunch& L, cudaStream_t st) {
+    if (L.nprob == 0 || L.maxM == 0 || L.maxN == 0) return cudaSuccess;
+    if (!L.err || !L.d_pprobs) return cudaErrorInvalidValue;
+    dim3 grid((L.maxN + TN - 1) / TN, (L.maxM + TM - 1) / TM, L.nprob * L.nsplit);
+    const int kchunk = L.nsplit > 1 ? L.kchunk : 0;
+    k_cgemm_tcp<<<grid, NTHR, SMEM_BYTES, st>>>(L.d_pprobs, L.nsplit, kchunk, L.epi, L.part_stride, L.err);
+    counted(1);
+    return cudaGetLastError();
+}
+
+}  // namespace tlr
