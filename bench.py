@@ -231,6 +231,8 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the frequencies are spread over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=3)
+    ap.add_argument("--serving", type=int, default=0,
+                    help="also serve this many per-frequency requests of the serving mix (nr 1024-8192)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -450,6 +452,11 @@ def main():
 
     for h_ in handles:
         T.tlr_mdd_destroy(h_)
+    serve = None
+    if args.serving > 0 and rank == 0:
+        del D, U
+        torch.cuda.empty_cache()
+        serve = serving_leg(T, torch, args.serving, args.seed, dev)
     if rank != 0:
         return
     line = {
@@ -471,9 +478,75 @@ def main():
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "accuracy": acc, "fp32_comparison": cmp,
     }
+    if serve is not None:
+        line["serving"] = serve
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serving_leg(T, torch, n, seed, dev):
+    """The serving mix: per-frequency solve requests with nr = ns uniform over
+    {1024, 2048, 4096, 8192}, tile over {128, 256, 512}, rank log-uniform 2-64,
+    Poisson arrivals.  Measures one-at-a-time throughput on the FP32 and the
+    tensor-core paths, then serves the stream with continuous batching (4
+    slots, HBM budget 200 GB) at 90% of the tensor-core one-at-a-time capacity
+    and reports p50 / p99 latency.  One seeded D, U per problem size is shared
+    by the requests of that size (work does not depend on the values)."""
+    import tlr_synth as synth
+    from paper_2412_14973_gb300 import serving
+    reqs = synth.request_stream(n, 1.0, seed + 17)
+    g = torch.Generator(device=dev).manual_seed(seed + 18)
+    pool = {}
+    for r in reqs:
+        if r.nr not in pool:
+            re = torch.randn((r.nr, r.nr), generator=g, device=dev)
+            im = torch.randn((r.nr, r.nr), generator=g, device=dev)
+            Dm = (torch.complex(re, im) / math.sqrt(2 * r.nr)).to(torch.complex64)
+            re = torch.randn((r.nr, r.nr), generator=g, device=dev)
+            im = torch.randn((r.nr, r.nr), generator=g, device=dev)
+            Um = (torch.complex(re, im) / math.sqrt(2 * r.nr)).to(torch.complex64)
+            pool[r.nr] = (Dm, Um)
+
+    def make(prec, arrivals):
+        out = []
+        for r, t in zip(reqs, arrivals):
+            d = T.desc(r.nr, r.nr, r.tile, rank=r.rank, nx=r.nx, ny=r.ny, diag_mode=T.TLR_DIAG_RULE,
+                       precision=prec)
+            nth = T.tlr_mdd_theta_size(d)
+            gg = torch.Generator(device=dev).manual_seed(r.seed)
+            th = (torch.randn(nth, generator=gg, device=dev) + 1j * torch.randn(nth, generator=gg, device=dev))
+            th = (th * (0.1 / math.sqrt(r.tile * max(1, r.rank)))).to(torch.complex64)
+            out.append(serving.SolveRequest(r.rid, t, d, pool[r.nr][0], pool[r.nr][1], th, T.solve_opts()))
+        return out
+
+    budget = 200 << 30
+    zero = [0.0] * n
+    t0 = time.perf_counter()
+    res_fp32 = serving.Server(budget, max_active=1).run(make(T.TLR_PREC_FP32, zero), realtime=False)
+    t_fp32 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_tc1 = serving.Server(budget, max_active=1).run(make(T.TLR_PREC_BF16X3, zero), realtime=False)
+    t_tc1 = time.perf_counter() - t0
+    rate = 0.9 * n / t_tc1
+    gg = np.random.default_rng(seed + 19)
+    arrivals = list(np.cumsum(gg.exponential(1.0 / rate, n)))
+    srv = serving.Server(budget, max_active=4)
+    t0 = time.perf_counter()
+    res = srv.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
+    t_srv = time.perf_counter() - t0
+    ok = [r for r in res if r.status == 0]
+    pc = serving.percentiles(res)
+    same = all(torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, res) if a.status == 0 and b.status == 0)
+    return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
+            "fp32_one_at_a_time_solves_per_s": round(n / t_fp32, 3),
+            "tc_one_at_a_time_solves_per_s": round(n / t_tc1, 3),
+            "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
+            "p50_ms": round(1e3 * pc[50], 1) if pc[50] else None,
+            "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,
+            "peak_active": srv.peak_active, "peak_budget_gb": round(srv.peak_used / 2**30, 1),
+            "results_identical_alone_and_in_mix": bool(same),
+            "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson"}
 
 
 def reference_arm(args, world, rank):

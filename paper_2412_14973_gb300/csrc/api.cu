@@ -695,9 +695,13 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         j.dst = h->packed + off;
         return j;
     };
+    // (padded rows << 32) | k-groups of 8; the launch grid covers the maximum of each
     auto items_of = [](const PackKey& k) {
         const long long nkc = (k.K + 15) / 16, nrb = (k.R + k.TR - 1) / k.TR;
-        return nrb * k.TR * nkc * 2;
+        return ((nrb * k.TR) << 32) | (nkc * 2);
+    };
+    auto merge = [](long long a, long long b) {
+        return (std::max(a >> 32, b >> 32) << 32) | std::max(a & 0xffffffffLL, b & 0xffffffffLL);
     };
     auto is_static = [&](const PackKey& k) {
         const char* c = reinterpret_cast<const char*>(k.src);
@@ -733,12 +737,12 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                     if (is_static(*k)) {
                         if (static_done.insert(*k).second) {
                             sjobs.push_back(job_of(*k, offs[*k]));
-                            smax = std::max(smax, items_of(*k));
+                            smax = merge(smax, items_of(*k));
                         }
                     } else if (here.insert(*k).second) {
                         if (T.G == &h->Le_a2 && a1_keys.count(*k)) continue;   // packed for A1 already
                         jobs[ti].push_back(job_of(*k, offs[*k]));
-                        maxit[ti] = std::max(maxit[ti], items_of(*k));
+                        maxit[ti] = merge(maxit[ti], items_of(*k));
                     }
                 }
             }

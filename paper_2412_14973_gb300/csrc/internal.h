@@ -101,7 +101,8 @@ struct GemmLaunch {
     int njobs = 0;
     long long max_items = 0;
 };
-// bytes of one operand (R rows x K) in the packed tile format with TR-row tiles
+// bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
+// pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);
 cudaError_t pack_operands(const PackJob* d_jobs, int njobs, long long max_items, cudaStream_t st);
 cudaError_t gemm_tcp_prepare();

@@ -100,37 +100,60 @@ __device__ __forceinline__ int core_off(int r, int kg) { return ((r >> 3) * 2 + 
 // ---------------------------------------------------------------------------
 // pack
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs, int njobs) {
+// One CTA packs 256 consecutive (padded) rows of one job over PACK_KG k-groups
+// of 8: thread = row, so the strided source reads (k-major sources) and the
+// 16-byte tile writes are both coalesced across a warp; row-contiguous
+// sources are read 16 bytes at a time.  All index arithmetic is 32-bit and
+// TR is a power of two.
+constexpr int PACK_KG = 8;
+
+__global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) {
     const PackJob& J = jobs[blockIdx.y];
     const int nkc = (J.K + KC - 1) / KC;
     const int nrb = (J.R + J.TR - 1) / J.TR;
-    const long long items = (long long)nrb * J.TR * nkc * 2;   // (row, k-group of 8)
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < items;
-         e += (long long)gridDim.x * blockDim.x) {
-        // consecutive threads take consecutive rows of one k-group
-        const long long rowsP = (long long)nrb * J.TR;
-        const int r = (int)(e % rowsP);
-        const int kg2 = (int)(e / rowsP);        // global k-group index (8 k each)
+    const int r = blockIdx.x * 256 + threadIdx.x;
+    if (r >= nrb * J.TR) return;
+    const int kg_end = min(2 * nkc, (int)(blockIdx.z + 1) * PACK_KG);
+    const int trs = J.TR == 256 ? 8 : 7;           // log2(TR)
+    const int rb = r >> trs, rr = r & (J.TR - 1);
+    const bool rv = r < J.R;
+    const cf* rowp = nullptr;
+    bool vec = false;
+    if (rv && J.kcontig) {
+        const long long row = J.g_row ? J.g_row[r] : r;
+        rowp = J.src + row * J.ld;
+        vec = ((reinterpret_cast<uintptr_t>(rowp) & 15) == 0);
+    }
+    const int plane = J.TR * KC * 2;
+    char* const base = reinterpret_cast<char*>(J.dst) + (size_t)rb * nkc * 4 * plane;
+    for (int kg2 = blockIdx.z * PACK_KG; kg2 < kg_end; ++kg2) {
         const int kc = kg2 >> 1, kg = kg2 & 1;
-        const int rb = r / J.TR, rr = r % J.TR;
+        const int k0 = kc * KC + kg * 8;
         float2 v[8];
-        const bool rv = r < J.R;
-        long long rowoff = 0;
-        if (rv && J.kcontig) rowoff = (long long)(J.g_row ? J.g_row[r] : r) * J.ld;
+        if (rv && J.kcontig && vec && k0 + 8 <= J.K) {
+            const float4* q = reinterpret_cast<const float4*>(rowp + k0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int k = kc * KC + kg * 8 + j;
-            float2 x = make_float2(0.f, 0.f);
-            if (rv && k < J.K) {
-                if (J.kcontig) {
-                    x = J.src[rowoff + k];
-                } else {
-                    const long long kr = J.g_k ? J.g_k[k] : k;
-                    x = J.src[kr * J.ld + r];
-                }
-                x.y *= J.sgn;
+            for (int j = 0; j < 4; ++j) {
+                const float4 t = q[j];
+                v[2 * j] = make_float2(t.x, t.y * J.sgn);
+                v[2 * j + 1] = make_float2(t.z, t.w * J.sgn);
             }
-            v[j] = x;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = k0 + j;
+                float2 x = make_float2(0.f, 0.f);
+                if (rv && k < J.K) {
+                    if (J.kcontig) {
+                        x = rowp[k];
+                    } else {
+                        const long long kr = J.g_k ? J.g_k[k] : k;
+                        x = J.src[kr * J.ld + r];
+                    }
+                    x.y *= J.sgn;
+                }
+                v[j] = x;
+            }
         }
         uint32_t w[4][4];
 #pragma unroll
@@ -145,12 +168,10 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs, 
                 w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
             }
         }
-        const long long plane = (long long)J.TR * KC * 2;
-        char* tile = reinterpret_cast<char*>(J.dst) + ((long long)rb * nkc + kc) * 4 * plane;
-        const int off = core_off(rr, kg);
+        char* tile = base + (size_t)kc * 4 * plane + core_off(rr, kg);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(tile + q * plane + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            *reinterpret_cast<uint4*>(tile + q * plane) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
     }
 }
 
@@ -342,11 +363,12 @@ long long packed_bytes(long long R, long long K, int TR) {
     return nrb * nkc * 4LL * TR * KC * 2;
 }
 
+// max_items encodes the largest job: (padded rows << 32) | k-groups
 cudaError_t pack_operands(const PackJob* jobs, int njobs, long long max_items, cudaStream_t st) {
     if (njobs == 0 || max_items == 0) return cudaSuccess;
-    const long long blocks = std::min<long long>((max_items + 255) / 256, 2048);
-    dim3 grid((unsigned)blocks, (unsigned)njobs);
-    k_pack<<<grid, 256, 0, st>>>(jobs, njobs);
+    const long long rows = max_items >> 32, kgs = max_items & 0xffffffffLL;
+    dim3 grid((unsigned)((rows + 255) / 256), (unsigned)njobs, (unsigned)((kgs + PACK_KG - 1) / PACK_KG));
+    k_pack<<<grid, 256, 0, st>>>(jobs);
     counted(1);
     return cudaGetLastError();
 }
