@@ -145,7 +145,8 @@ int tlr_mdd_hilbert_perm(int32_t nx, int32_t ny, int32_t* perm_dev, void* stream
 
 /* Create a handle: validates *d, computes the receiver order, alpha, and the
  * receiver-major panels Dfrak[a, s] = D[s, perm[a]] / alpha and
- * Ufrak[a, s] = U[s, perm[a]] / alpha (eq. 14; normalisation), then allocates
+ * Ufrak[a, s] = U[s, perm[a]] / alpha (eq. 14; normalisation; each part is one
+ * IEEE FP32 division by alpha rounded to FP32), then allocates
  * the workspace.  D, U: complex64 [ns x nr] row-major (the paper's layout),
  * device or host per d->input_memory; they are not referenced after the call
  * returns.  On failure *h is NULL. */

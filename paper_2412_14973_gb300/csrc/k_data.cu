@@ -123,7 +123,7 @@ cudaError_t max_abs2(const cf* D, long long n, double* part, int nblk, double* o
 }
 
 // ---------------------------------------------------------------------------
-// Dt[a, s] = D[s, perm[a]] / alpha.  Walks D in natural receiver order so both
+// Dt[a, s] = RN32(D[s, perm[a]] / RN32(alpha)).  Walks D in natural receiver order so both
 // the read (a row segment of D) and the write (a row segment of Dt, at row
 // inv[r]) are 256-byte contiguous; a 32 x 32 tile is transposed in shared memory.
 // ---------------------------------------------------------------------------
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256) k_permute_normalise(const cf* __restrict_
     __shared__ cf tile[32][33];
     const long long r0 = (long long)blockIdx.x * 32, s0 = (long long)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const double alpha = alpha_dev[0];
+    // one IEEE FP32 division by alpha rounded to FP32: Dt = RN(D / RN(alpha))
+    const float alpha = (float)alpha_dev[0];
 #pragma unroll
     for (int j = 0; j < 32; j += 8) {
         const long long s = s0 + ty + j, r = r0 + tx;
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(256) k_permute_normalise(const cf* __restrict_
         if (r < nr && s < ns) {
             const cf v = tile[tx][ty + j];
             cf o;
-            o.x = (float)((double)v.x / alpha);
-            o.y = (float)((double)v.y / alpha);
+            o.x = __fdiv_rn(v.x, alpha);
+            o.y = __fdiv_rn(v.y, alpha);
             Dt[(long long)inv[r] * ns + s] = o;
         }
     }

@@ -14,7 +14,7 @@
 // The GEMM (4M complex products, 128 x 256 tile, 12 MMAs per 16-deep chunk as
 // in k_gemm_tc.cu) has one thread issuing the bulk copies of the A and B
 // tiles of each chunk into a 4-stage ring with a transaction-count mbarrier,
-// one thread issuing the MMAs, and four warps for the epilogue.  Every wait
+// one thread issuing the MMAs, and eight warps for the epilogue.  Every wait
 // is bounded (2 s of %globaltimer, grid-wide abort word).
 #include <cuda_bf16.h>
 
@@ -33,7 +33,8 @@ constexpr int TILE_B = 4 * TN * KC * 2;             // 32 KB
 constexpr int STAGE = TILE_A + TILE_B;              // 48 KB
 constexpr int CTRL_OFF = NSTAGE * STAGE;
 constexpr int SMEM_BYTES = CTRL_OFF + 256 + 256;    // barriers etc. + problem descriptor
-constexpr int NTHR = 192;                           // warps 0-3 epilogue, 4 copies, 5 MMAs
+constexpr int NTHR = 320;                           // warps 0-7 epilogue, 8 copies, 9 MMAs
+constexpr int WCOPY = 8, WMMA = 9;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
-    if (warp == 5) {
+    if (warp == WMMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(TMEM_COLS)
                      : "memory");
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
         if (ke > kb) C += (ke - kb + KC - 1) / KC;
     }
 
-    if (warp == 4 && lane == 0) {
+    if (warp == WCOPY && lane == 0) {
         // ---------------- bulk copies ----------------
         int c = 0;
         for (int ti = 0; ti < P.nt && !*abort_flag; ++ti) {
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
                     : "memory");
             }
         }
-    } else if (warp == 5 && lane == 0) {
+    } else if (warp == WMMA && lane == 0) {
         // ---------------- MMA issuer ----------------
         for (int c = 0; c < C; ++c) {
             const int s = c % NSTAGE;
@@ -305,20 +306,27 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
                      : "memory");
     }
 
-    // ---------------- epilogue (warps 0-3) ----------------
+    // ---------------- epilogue (warps 0-7) ----------------
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 and columns [128 (w / 4), +128)
     bool ok = true;
-    if (warp < 4 && C > 0) ok = mbar_wait(smem_u32(done), 0u, err);
+    if (warp < 8 && C > 0) ok = mbar_wait(smem_u32(done), 0u, err);
     if (!ok || *abort_flag) {
         if (threadIdx.x == 0 || !ok) atomicExch(err, TLR_ERR_TIMEOUT);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 4 && ok && !*abort_flag) {
-        const int m = m0 + warp * 32 + lane;
+    if (warp < 8 && ok && !*abort_flag) {
+        // Each warp drains 32 rows x 16 columns at a time: tcgen05.ld gives a
+        // thread one row; the block is transposed through shared memory (the
+        // operand ring is idle once the last MMA has completed) so that each
+        // store instruction writes four full 128-byte row segments.
+        const int lg = warp & 3, ch = warp >> 2;
         cf* Cp = P.C + (epi == EPI_PARTIAL ? chunk * part_stride : 0);
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
+        cf* stg = reinterpret_cast<cf*>(smem) + warp * (32 * 17);   // 32 rows x 16 (+1 pad)
+        const int rsub = lane >> 3, q = lane & 7;                   // write phase: row group, 16-B chunk
 #pragma unroll 1
-        for (int cb = 0; cb < TN / 16; ++cb) {
-            const int col = cb * 16;
+        for (int cb = 0; cb < TN / 32; ++cb) {
+            const int col = ch * (TN / 2) + cb * 16;
             if (n0 + col >= P.N) break;
             float pr[16], pi[16];
             if (C > 0) {
@@ -328,30 +336,51 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
 #pragma unroll
                 for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
             }
-            if (m < P.M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + col + j;
-                    if (n >= P.N) break;
+            for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = make_float2(pr[j], pi[j]);
+            __syncwarp();
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                const int r = j2 * 4 + rsub;
+                const int m = m0 + lg * 32 + r;
+                const int n = n0 + col + 2 * q;
+                if (m < P.M && n < P.N) {
                     const long long o = (long long)m * P.ldc + n;
-                    cf v = make_float2(pr[j], pi[j]);
+                    cf v0 = stg[r * 17 + 2 * q], v1 = stg[r * 17 + 2 * q + 1];
+                    const bool two = n + 1 < P.N;
                     if (epi == EPI_SUB) {
-                        const cf sv = P.S[o];
-                        v.x -= sv.x;
-                        v.y -= sv.y;
+                        const cf s0 = P.S[o];
+                        v0.x -= s0.x;
+                        v0.y -= s0.y;
+                        if (two) {
+                            const cf s1 = P.S[o + 1];
+                            v1.x -= s1.x;
+                            v1.y -= s1.y;
+                        }
                     } else if (epi == EPI_ACCUM) {
-                        const cf cv = Cp[o];
-                        v.x += cv.x;
-                        v.y += cv.y;
+                        const cf c0 = Cp[o];
+                        v0.x += c0.x;
+                        v0.y += c0.y;
+                        if (two) {
+                            const cf c1 = Cp[o + 1];
+                            v1.x += c1.x;
+                            v1.y += c1.y;
+                        }
                     }
-                    Cp[o] = v;
+                    if (two && ((reinterpret_cast<uintptr_t>(Cp + o) & 15) == 0)) {
+                        *reinterpret_cast<float4*>(Cp + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                    } else {
+                        Cp[o] = v0;
+                        if (two) Cp[o + 1] = v1;
+                    }
                 }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 5) {
+    if (warp == WMMA) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
