@@ -397,6 +397,9 @@ def main():
                 hs.append(T.tlr_mdd_create(d, D[f], U[f], streams[0]))
             ms_tot = 0.0
             for rep in range(2):          # first pass records the graphs
+                if rep == 1 and prec_ == prec and prec != T.TLR_PREC_FP32:
+                    T.tlr_mdd_timing_reset()
+                    T.tlr_mdd_timing_enable(True)
                 t0_ = torch.cuda.Event(enable_timing=True)
                 t1_ = torch.cuda.Event(enable_timing=True)
                 t0_.record(streams[0])
@@ -409,12 +412,23 @@ def main():
                 torch.cuda.synchronize()
                 if rep == 1:
                     ms_tot = t0_.elapsed_time(t1_)
+                    if T.tlr_mdd_timing_read and prec_ == prec and prec != T.TLR_PREC_FP32:
+                        single[:] = T.tlr_mdd_timing_read()
+                        T.tlr_mdd_timing_enable(False)
             for h_ in hs:
                 T.tlr_mdd_destroy(h_)
             return ms_tot
 
+        single = []
         t_fp32 = run_subset(T.TLR_PREC_FP32)
         t_tc = run_subset(prec)
+        if single:
+            # one stream, no overlap between launches: per-launch rates of each class
+            roof["single_stream_tflops_per_class"] = {
+                names[c]: round(single[c][1] / (single[c][0] / 1e3) / 1e12, 1) for c in range(len(single))
+                if single[c][0] > 0}
+            roof["single_stream_frac_per_class"] = {
+                k: round(v / roof["peak"], 4) for k, v in roof["single_stream_tflops_per_class"].items()}
         cmp = {"frequencies": sub, "fp32_simt_freq_solves_per_s": round(len(sub) / (t_fp32 / 1e3), 4),
                "tensor_core_freq_solves_per_s": round(len(sub) / (t_tc / 1e3), 4),
                "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),

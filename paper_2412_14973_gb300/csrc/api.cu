@@ -444,12 +444,12 @@ long long packed_estimate(const Layout& L) {
     for (int i = 0; i < L.N; ++i) {
         const long long Ki = L.Kb[i];
         if (Ki > 0) {
-            t += 3 * pb(Ki, b, 128) + 2 * pb(b, Ki, 128);     // F, conj F, F_d (KM); F, F_d (MK)
-            t += 2 * pb(ns, Ki, 256) + 2 * pb(Ki, ns, 256);   // T~, T~_p (KN); conj T~, V~ (NK)
-            t += pb(ns, b, 256);                              // Rf_i (KN)
+            t += 3 * pb(Ki, b, kPackTRA) + 2 * pb(b, Ki, kPackTRA);     // F, conj F, F_d (KM); F, F_d (MK)
+            t += 2 * pb(ns, Ki, kPackTRB) + 2 * pb(Ki, ns, kPackTRB);   // T~, T~_p (KN); conj T~, V~ (NK)
+            t += pb(ns, b, kPackTRB);                              // Rf_i (KN)
         }
-        if (Ki > 0 || L.dense[i]) t += pb(ns, b, 256) + 2 * pb(b, ns, 128);   // Dfrak_i (KN); Rf_i, conj Dfrak_i (MK)
-        if (L.dense[i]) t += 2 * pb(b, b, 128) + pb(b, ns, 256);              // Zs, Zs_d; conj Dfrak_i (NK)
+        if (Ki > 0 || L.dense[i]) t += pb(ns, b, kPackTRB) + 2 * pb(b, ns, kPackTRA);   // Dfrak_i (KN); Rf_i, conj Dfrak_i (MK)
+        if (L.dense[i]) t += 2 * pb(b, b, kPackTRA) + pb(b, ns, kPackTRB);              // Zs, Zs_d; conj Dfrak_i (NK)
     }
     return t;
 }
@@ -647,7 +647,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             k.ld = t.lda;
             k.kcontig = amode == A_MK;
             k.sgn = t.sa;
-            k.TR = 128;
+            k.TR = kPackTRA;
         } else {
             k.src = t.B;
             k.ld = t.ldb;
@@ -657,7 +657,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             else
                 k.gk = t.g;
             k.sgn = t.sb;
-            k.TR = 256;
+            k.TR = kPackTRB;
         }
         k.R = R;
         k.K = t.K;

@@ -69,9 +69,11 @@ struct PackJob {
     int R, K, TR;
     void* dst;
 };
+// row-tile heights of packed A (M) and B (N) operands: the GEMM tile's M and N
+constexpr int kPackTRA = 128, kPackTRB = 128;
 struct PTerm {
-    const void* A;   // packed A of this problem (TR = 128), all row blocks
-    const void* B;   // packed B of this problem (TR = 256)
+    const void* A;   // packed A of this problem (TR = kPackTRA), all row blocks
+    const void* B;   // packed B of this problem (TR = kPackTRB)
     int K;
 };
 struct PProb {

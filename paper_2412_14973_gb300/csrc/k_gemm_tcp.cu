@@ -1,8 +1,8 @@
 // Tensor-core GEMM on pre-packed operands, and the pack kernel that makes them.
 //
 // Packed format ("P-format") of an operand with R rows (the M or N index) and
-// K columns (the contraction index): tiles of TR rows x 16 k, TR = 128 for an
-// A operand and 256 for a B operand; tile (rb, kc) starts at byte
+// K columns (the contraction index): tiles of TR = 128 rows x 16 k; tile
+// (rb, kc) starts at byte
 // (rb * nkc + kc) * 4 * TR * 32 and holds four BF16 planes (Re hi, Re lo,
 // Im hi, Im lo; x = hi + lo with hi = RN_bf16(x), lo = RN_bf16(x - hi)), each
 // in the tensor core's canonical K-major, no-swizzle layout (8-row x 16-byte
@@ -11,9 +11,9 @@
 // conjugation of the operand, so a tile is exactly what a stage of the GEMM
 // needs and is moved with one cp.async.bulk copy.
 //
-// The GEMM (4M complex products, 128 x 256 tile, 12 MMAs per 16-deep chunk as
-// in k_gemm_tc.cu) has one thread issuing the bulk copies of the A and B
-// tiles of each chunk into a 4-stage ring with a transaction-count mbarrier,
+// The GEMM (4M complex products, 128 x 128 tile, 12 MMAs per 16-deep chunk)
+// has one thread issuing the bulk copies of the A and B tiles of each chunk
+// into a 3-stage ring with a transaction-count mbarrier,
 // one thread issuing the MMAs, and eight warps for the epilogue.  Every wait
 // is bounded (2 s of %globaltimer, grid-wide abort word).
 #include <cuda_bf16.h>
@@ -26,16 +26,23 @@ namespace tlr {
 
 namespace {
 
-constexpr int TM = 128, TN = 256, KC = 16;
-constexpr int NSTAGE = 4;
+// 128 x 128 tiles, 3 stages: about 97 KB of shared memory and 256 TMEM columns
+// per CTA, so two CTAs share an SM and one's epilogue and set-up run while the
+// other's MMAs keep the tensor core busy.
+constexpr int TM = kPackTRA, TN = kPackTRB, KC = 16;
+static_assert(TM == 128 && (TN == 128 || TN == 256), "tile shapes of the MMA and epilogue");
+constexpr int NSTAGE = TN == 128 ? 3 : 4;
+constexpr int CTAS_PER_SM = TN == 128 ? 2 : 1;
 constexpr int TILE_A = 4 * TM * KC * 2;             // 16 KB
-constexpr int TILE_B = 4 * TN * KC * 2;             // 32 KB
-constexpr int STAGE = TILE_A + TILE_B;              // 48 KB
+constexpr int TILE_B = 4 * TN * KC * 2;             // 16 KB (TN 128)
+constexpr int STAGE = TILE_A + TILE_B;              // 32 KB (TN 128)
 constexpr int CTRL_OFF = NSTAGE * STAGE;
 constexpr int SMEM_BYTES = CTRL_OFF + 256 + 256;    // barriers etc. + problem descriptor
 constexpr int NTHR = 320;                           // warps 0-7 epilogue, 8 copies, 9 MMAs
 constexpr int WCOPY = 8, WMMA = 9;
-constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_COLS = 2 * TN;              // Cr at column 0, Ci at column TN
+static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "TMEM columns of the CTAs sharing an SM");
+static_assert(8 * 32 * 17 * 8 <= NSTAGE * STAGE, "epilogue staging fits in the operand ring");
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
     const int r = blockIdx.x * 256 + threadIdx.x;
     if (r >= nrb * J.TR) return;
     const int kg_end = min(2 * nkc, (int)(blockIdx.z + 1) * PACK_KG);
-    const int trs = J.TR == 256 ? 8 : 7;           // log2(TR)
+    const int trs = 31 - __clz(J.TR);              // log2(TR)
     const int rb = r >> trs, rr = r & (J.TR - 1);
     const bool rv = r < J.R;
     const cf* rowp = nullptr;
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 // ---------------------------------------------------------------------------
 // GEMM on packed operands
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
+__global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
                                                        int epi, long long part_stride, int* err) {
     extern __shared__ __align__(1024) char smem[];
     const int prob = blockIdx.z / nsplit, chunk = blockIdx.z % nsplit;
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
             constexpr int PA = TILE_A / 4, PB = TILE_B / 4;
             const uint64_t arh = sdesc(a0), arl = sdesc(a0 + PA), aih = sdesc(a0 + 2 * PA), ail = sdesc(a0 + 3 * PA);
             const uint64_t brh = sdesc(b0), brl = sdesc(b0 + PB), bih = sdesc(b0 + 2 * PB), bil = sdesc(b0 + 3 * PB);
-            const uint32_t dr = tmem, di = tmem + 256;
+            const uint32_t dr = tmem, di = tmem + TN;
             const uint32_t first = c > 0 ? 1u : 0u;
             mma_bf16(dr, arh, brh, IDESC, first);
             mma_bf16(dr, arh, brl, IDESC, 1u);
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
     }
 
     // ---------------- epilogue (warps 0-7) ----------------
-    // warp w reads TMEM lanes 32 (w % 4) .. +31 and columns [128 (w / 4), +128)
+    // warp w reads TMEM lanes 32 (w % 4) .. +31 and columns [TN/2 (w / 4), +TN/2)
     bool ok = true;
     if (warp < 8 && C > 0) ok = mbar_wait(smem_u32(done), 0u, err);
     if (!ok || *abort_flag) {
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp(const PProb* __restrict__
             float pr[16], pi[16];
             if (C > 0) {
                 tmem_ld16(lane_addr + col, pr);
-                tmem_ld16(lane_addr + 256 + col, pi);
+                tmem_ld16(lane_addr + TN + col, pi);
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
