@@ -355,6 +355,8 @@ struct tlr_mdd_s {
     PackJob* d_static_jobs = nullptr;
     int n_static_jobs = 0;
     long long static_items = 0;
+    TPackTile* d_tpack = nullptr;      // fused update + packing of T (packs of T are not per-launch jobs)
+    int n_tpack = 0;
     // asynchronous solve and its CUDA graph
     cf* th_io = nullptr;               // theta staging (stable address for the graph)
     HostStats* hstats = nullptr;       // pinned
@@ -454,7 +456,44 @@ long long packed_estimate(const Layout& L) {
     return t;
 }
 
-int split_for(const Layout& L) {
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;
+    }
+    return n;
+}
+
+// Split of the contraction over ns in the gradient projection.  SIMT path:
+// enough 64 x 64 tiles for a few waves.  Tensor-core path: the split s that
+// minimises the modelled time ceil(tiles s / SMs) (ns / s + c0) of 128 x 128
+// tiles, c0 = 128 standing for a tile's fixed cost (set-up, pipeline fill,
+// epilogue) in units of contraction depth; this avoids a short last wave.
+int split_for(const Layout& L, int prec) {
+    if (prec == TLR_PREC_BF16X3) {
+        long long tiles = 0;
+        for (int i = 0; i < L.N; ++i) {
+            tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.Kb[i] + kPackTRB - 1) / kPackTRB);
+            if (L.dense[i]) tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.b + kPackTRB - 1) / kPackTRB);
+        }
+        tiles = std::max(1LL, tiles);
+        const long long sms = sm_count(), smax = std::max(1LL, std::min(16LL, (long long)L.ns / 256));
+        long long best = 1;
+        double tbest = 1e300;
+        for (long long sp = 1; sp <= smax; ++sp) {
+            const double t = (double)((tiles * sp + sms - 1) / sms) * ((double)L.ns / sp + 128.0);
+            if (t < tbest * 0.999) {
+                tbest = t;
+                best = sp;
+            }
+        }
+        return (int)best;
+    }
     long long tiles = 0;
     for (int i = 0; i < L.N; ++i) {
         tiles += ((L.b + 63) / 64) * ((L.Kb[i] + 63) / 64);
@@ -618,7 +657,9 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
 // layout, gather, conjugation and shape) share one packed buffer.  Operands
 // read from the data panel Dfrak never change during a solve: they are packed
 // once when the data are loaded.  The line-search pair A1 / A2 shares its
-// packs (A2 packs nothing).
+// packs (A2 packs nothing).  The two packings of the factor products T (KN for
+// the expansions, conjugated NK for the projection) are written by tpack right
+// after T is formed or updated, so no contraction packs them.
 // ---------------------------------------------------------------------------
 struct PackKey {
     const void* src;
@@ -681,6 +722,8 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             }
     h->packed_size = total;
     CK(h, cudaMallocAsync((void**)&h->packed, std::max<size_t>(total, 256), h->st));
+    // padding rows and k-slots of every packed operand stay zero from here on
+    CK(h, cudaMemsetAsync(h->packed, 0, std::max<size_t>(total, 256), h->st));
     auto job_of = [&](const PackKey& k, size_t off) {
         PackJob j;
         j.src = (const cf*)k.src;
@@ -715,6 +758,8 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     long long smax = 0;
     std::set<PackKey> static_done;
     std::set<PackKey> a1_keys;
+    std::map<const void*, size_t> t_kn, t_nk;   // gather of block i -> packed T~_i (KN), conj T~_i (NK)
+    auto is_T = [&](const PackKey& k) { return k.src == (const void*)h->T; };
     for (size_t ti = 0; ti < tabs.size(); ++ti) {
         auto& T = tabs[ti];
         std::set<PackKey> here;
@@ -734,6 +779,15 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                 q.t[t].B = h->packed + offs[kb];
                 q.t[t].K = p.t[t].K;
                 for (const PackKey* k : {&ka, &kb}) {
+                    if (is_T(*k)) {
+                        if (k->kcontig == 0 && k->sgn > 0)
+                            t_kn[k->gk] = offs[*k];
+                        else if (k->kcontig == 1 && k->sgn < 0)
+                            t_nk[k->gr] = offs[*k];
+                        else
+                            FAIL(h, TLR_ERR_STATE, "internal: unexpected packing of T");
+                        continue;
+                    }
                     if (is_static(*k)) {
                         if (static_done.insert(*k).second) {
                             sjobs.push_back(job_of(*k, offs[*k]));
@@ -759,8 +813,28 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         jo[ti] = bytes;
         bytes += (jobs[ti].size() * sizeof(PackJob) + 255) & ~size_t(255);
     }
+    std::vector<TPackTile> tt;
+    for (int i = 0; i < L.N; ++i) {
+        const int Ki = L.Kb[i];
+        if (Ki == 0) continue;
+        const int* gi = h->d_partner + L.Koff[i];
+        auto a = t_kn.find(gi), c = t_nk.find(gi);
+        if (a == t_kn.end() || c == t_nk.end()) FAIL(h, TLR_ERR_STATE, "internal: T packing not planned");
+        for (int k0 = 0; k0 < Ki; k0 += 32) {
+            TPackTile t;
+            t.g = gi;
+            t.k0 = k0;
+            t.nk = std::min(32, Ki - k0);
+            t.Ki = Ki;
+            t.kn = h->packed + a->second;
+            t.nk_dst = h->packed + c->second;
+            tt.push_back(t);
+        }
+    }
     const size_t so = bytes;
     bytes += (sjobs.size() * sizeof(PackJob) + 255) & ~size_t(255);
+    const size_t to = bytes;
+    bytes += (tt.size() * sizeof(TPackTile) + 255) & ~size_t(255);
     CK(h, cudaMallocAsync((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
     for (size_t ti = 0; ti < tabs.size(); ++ti) {
         GemmLaunch& G = *tabs[ti].G;
@@ -775,6 +849,10 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             CK(h, cudaMemcpyAsync(G.d_jobs, jobs[ti].data(), jobs[ti].size() * sizeof(PackJob),
                                   cudaMemcpyHostToDevice, h->st));
     }
+    h->d_tpack = reinterpret_cast<TPackTile*>(h->tcp_tables + to);
+    h->n_tpack = (int)tt.size();
+    if (!tt.empty())
+        CK(h, cudaMemcpyAsync(h->d_tpack, tt.data(), tt.size() * sizeof(TPackTile), cudaMemcpyHostToDevice, h->st));
     h->d_static_jobs = reinterpret_cast<PackJob*>(h->tcp_tables + so);
     h->n_static_jobs = (int)sjobs.size();
     h->static_items = smax;
@@ -872,7 +950,7 @@ int64_t tlr_mdd_workspace_bytes(const tlr_mdd_desc_t* d) {
     tlr_mdd_s tmp;
     std::string e;
     if (build_layout(d, tmp.L, e)) return -1;
-    tmp.nsplit = split_for(tmp.L);
+    tmp.nsplit = split_for(tmp.L, d->precision);
     Arena a;
     carve(&tmp, a);
     // plus the L-BFGS ring for the default memory (m = 10: 11 slots of s and y)
@@ -918,7 +996,7 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         delete h;
         return TLR_ERR_SHAPE;
     }
-    h->nsplit = split_for(L);
+    h->nsplit = split_for(L, d->precision);
     h->kchunk = (int)(((L.ns + h->nsplit - 1) / h->nsplit + 15) / 16 * 16);
     Arena a;
     carve(h, a);
@@ -1032,6 +1110,7 @@ static int forward(tlr_mdd_s* h, bool plain_apply) {
     const Layout& L = h->L;
     CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st));
     CK(h, run_gemm(h->Lc_x, h->st));
+    if (h->n_tpack) CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)L.ns, h->st));
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
     return TLR_OK;
 }
@@ -1297,7 +1376,9 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 CK(h, sv_dots3(S, part3, h->st));
                 CK(h, sv_line_search(S, part6, part3, rho, h->st));
                 CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
-                if (L.Ktot > 0)
+                if (h->n_tpack)
+                    CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, h->sc + SC_ALPHA, (int)L.ns, h->st));
+                else if (L.Ktot > 0)
                     CK(h, axpy_dev((float*)h->T, (const float*)h->Tp, 2LL * L.Ktot * L.ns, h->sc + SC_ALPHA, h->st));
                 CK(h, sv_step_theta(S, h->st));
                 rc = gradient(h);

@@ -103,6 +103,22 @@ struct GemmLaunch {
     int njobs = 0;
     long long max_items = 0;
 };
+// One row tile of the fused factor-product update (tpack): rows k0 .. k0+nk-1
+// of block i's gathered products T~_i (T~_i[k] = T[g[k]]), with the packed
+// destinations of that block: T~_i as a B operand with rows = ns and k = the
+// factor index (KN), and conj(T~_i) as a B operand with rows = the factor
+// index and k = ns (NK).
+struct TPackTile {
+    const int* g;   // block i's gather, indexed by k (0 .. K_i - 1)
+    int k0, nk, Ki;
+    void* kn;       // packed T~_i (KN), base of block i's buffer
+    void* nk_dst;   // packed conj(T~_i) (NK), base of block i's buffer
+};
+// T[r] += alpha T_p[r] (FP32 fmaf, alpha read on the device; alpha == nullptr
+// or *alpha == 0: no update) for every row reached through the tiles (each
+// row of T exactly once), then both packed forms of the updated rows.
+cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
+                  cudaStream_t st);
 // bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
 // pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);

@@ -184,6 +184,104 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 }
 
 // ---------------------------------------------------------------------------
+// tpack: fused update of the factor products and both of their packings
+// ---------------------------------------------------------------------------
+// A CTA takes one row tile (32 rows of one block's gathered T~_i) and 128
+// columns (n).  Phase 1 reads the 32 source rows of T (and T_p) coalesced
+// along n, applies the update, writes T back and keeps the tile in shared
+// memory; phase 2 writes the KN packing (thread = (n, k-group of 8)); phase 3
+// the conjugated NK packing (thread = (k, n-group of 8)).  Padding of the
+// packed buffers (k >= K_i, rows >= ns) is zero from the buffer's creation and
+// is never written.
+constexpr int TP_K = 32, TP_N = 128, TP_LD = TP_N + 1;
+static_assert(kPackTRB == 128 && KC == 16, "tpack writes 128-row, 16-deep B tiles");
+
+__device__ __forceinline__ void split_store(char* dst, int plane, const float2* v, float sgn) {
+    uint32_t w[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        const float x[2][2] = {{v[j].x, v[j + 1].x}, {v[j].y * sgn, v[j + 1].y * sgn}};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[p][0], x[p][1]);
+            const float2 hf = __bfloat1622float2(hi);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[p][0] - hf.x, x[p][1] - hf.y);
+            w[2 * p][j >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
+            w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(dst + q * plane) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+}
+
+__global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ tiles, cf* __restrict__ T,
+                                               const cf* __restrict__ Tp, const double* __restrict__ alpha,
+                                               int ns) {
+    __shared__ float2 s[TP_K * TP_LD];
+    const TPackTile& P = tiles[blockIdx.y];
+    const int n0 = blockIdx.x * TP_N;
+    const int nk = P.nk;
+    const float a = alpha ? (float)alpha[0] : 0.f;
+    // phase 1
+    {
+        const int n = threadIdx.x & (TP_N - 1);
+        for (int kk = threadIdx.x >> 7; kk < nk; kk += 2) {
+            float2 t = make_float2(0.f, 0.f);
+            if (n0 + n < ns) {
+                const long long o = (long long)P.g[P.k0 + kk] * ns + n0 + n;
+                t = T[o];
+                if (a != 0.f) {
+                    const float2 d = Tp[o];
+                    t.x = fmaf(a, d.x, t.x);
+                    t.y = fmaf(a, d.y, t.y);
+                    T[o] = t;
+                }
+            }
+            s[kk * TP_LD + n] = t;
+        }
+    }
+    __syncthreads();
+    constexpr int plane = 128 * 16 * 2;   // bytes of one BF16 plane of a 128 x 16 tile
+    // phase 2: KN, rows n, k = factor index; nk rows of this tile in k-groups of 8
+    {
+        const int nkcK = (P.Ki + 15) >> 4;
+        const int ngrp = (nk + 7) >> 3;
+        for (int it = threadIdx.x; it < TP_N * ngrp; it += blockDim.x) {
+            const int n = it & (TP_N - 1), kg = it >> 7;
+            if (n0 + n >= ns) continue;
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int kk = kg * 8 + j;
+                v[j] = kk < nk ? s[kk * TP_LD + n] : make_float2(0.f, 0.f);
+            }
+            const int k = P.k0 + kg * 8;   // multiple of 8
+            const int nn = n0 + n;
+            char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
+                        core_off(nn & 127, (k >> 3) & 1);
+            split_store(dst, plane, v, 1.f);
+        }
+    }
+    // phase 3: NK, rows = factor index, k = n; conjugated
+    {
+        const int nkcN = (ns + 15) >> 4;
+        for (int it = threadIdx.x; it < nk * (TP_N / 8); it += blockDim.x) {
+            const int kk = it >> 4, ng = it & 15;
+            const int nb = n0 + ng * 8;
+            if (nb >= ns) continue;
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
+            const int r = P.k0 + kk;
+            char* dst = reinterpret_cast<char*>(P.nk_dst) + ((long long)(r >> 7) * nkcN + (nb >> 4)) * 4 * plane +
+                        core_off(r & 127, (nb >> 3) & 1);
+            split_store(dst, plane, v, -1.f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // GEMM on packed operands
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
@@ -405,6 +503,15 @@ cudaError_t pack_operands(const PackJob* jobs, int njobs, long long max_items, c
     const long long rows = max_items >> 32, kgs = max_items & 0xffffffffLL;
     dim3 grid((unsigned)((rows + 255) / 256), (unsigned)njobs, (unsigned)((kgs + PACK_KG - 1) / PACK_KG));
     k_pack<<<grid, 256, 0, st>>>(jobs);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
+                  cudaStream_t st) {
+    if (ntiles == 0 || ns == 0) return cudaSuccess;
+    dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)ntiles);
+    k_tpack<<<grid, 256, 0, st>>>(d_tiles, T, Tp, alpha, ns);
     counted(1);
     return cudaGetLastError();
 }
