@@ -750,6 +750,31 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         const char* c = reinterpret_cast<const char*>(k.src);
         return c >= dlo && c < dhi;
     };
+    // The projection reads V~_i (V's rows gathered by partner, NK) only in
+    // packed form: the compression V = F^H Rf writes it there directly
+    // (EPI_PACKNK), so V is never stored in FP32 and never packed by a job.
+    // Row g of V is row k = partner[g] - Koff[i] of V~_i, i the block of partner[g].
+    std::map<const void*, size_t> v_nk;   // gather of block i -> packed V~_i (NK)
+    for (auto& ko : order)
+        if (ko.first.src == (const void*)h->Tp && ko.first.kcontig == 1 && ko.first.sgn > 0)
+            v_nk[ko.first.gr] = ko.second;
+    std::vector<char*> rowptr;
+    bool vpack = L.Ktot > 0;
+    for (int i = 0; i < L.N && vpack; ++i)
+        if (L.Kb[i] > 0 && !v_nk.count(h->d_partner + L.Koff[i])) vpack = false;
+    if (vpack) {
+        constexpr long long plane = 128 * 16 * 2;
+        const long long nkcN = (L.ns + 15) / 16;
+        rowptr.resize(L.Ktot);
+        for (int64_t gm = 0; gm < L.Ktot; ++gm) {
+            const int64_t pg = L.partner[gm];
+            const int i = (int)(std::upper_bound(L.Koff.begin(), L.Koff.end(), pg) - L.Koff.begin()) - 1;
+            const int64_t k = pg - L.Koff[i];
+            rowptr[gm] = h->packed + v_nk[h->d_partner + L.Koff[i]] + (k >> 7) * nkcN * 4 * plane +
+                         ((k & 127) >> 3) * 256 + (k & 7) * 16;
+        }
+    }
+    std::vector<std::pair<size_t, int64_t>> vfix;   // (problem index in Lc_v, Koff of its block)
     // pass 2: problems on packed operands and per-launch pack jobs
     std::vector<std::vector<PProb>> pp(tabs.size());
     std::vector<std::vector<PackJob>> jobs(tabs.size());
@@ -779,6 +804,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                 q.t[t].B = h->packed + offs[kb];
                 q.t[t].K = p.t[t].K;
                 for (const PackKey* k : {&ka, &kb}) {
+                    if (vpack && k->src == (const void*)h->Tp && k->kcontig == 1) continue;   // written by Lc_v
                     if (is_T(*k)) {
                         if (k->kcontig == 0 && k->sgn > 0)
                             t_kn[k->gk] = offs[*k];
@@ -800,6 +826,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                     }
                 }
             }
+            if (vpack && T.G == &h->Lc_v) vfix.push_back({pp[ti].size(), (int64_t)((p.C - h->Tp) / L.ns)});
             pp[ti].push_back(q);
         }
         if (T.G == &h->Le_a1) a1_keys = here;
@@ -835,7 +862,18 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     bytes += (sjobs.size() * sizeof(PackJob) + 255) & ~size_t(255);
     const size_t to = bytes;
     bytes += (tt.size() * sizeof(TPackTile) + 255) & ~size_t(255);
+    const size_t ro = bytes;
+    bytes += (rowptr.size() * sizeof(char*) + 255) & ~size_t(255);
     CK(h, cudaMallocAsync((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
+    if (vpack) {
+        char** d_rowptr = reinterpret_cast<char**>(h->tcp_tables + ro);
+        CK(h, cudaMemcpyAsync(d_rowptr, rowptr.data(), rowptr.size() * sizeof(char*), cudaMemcpyHostToDevice, h->st));
+        for (size_t ti = 0; ti < tabs.size(); ++ti)
+            if (tabs[ti].G == &h->Lc_v) {
+                for (auto& f : vfix) pp[ti][f.first].rowptr = d_rowptr + f.second;
+                h->Lc_v.epi = EPI_PACKNK;
+            }
+    }
     for (size_t ti = 0; ti < tabs.size(); ++ti) {
         GemmLaunch& G = *tabs[ti].G;
         G.d_pprobs = reinterpret_cast<PProb*>(h->tcp_tables + po[ti]);

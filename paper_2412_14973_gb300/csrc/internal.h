@@ -49,7 +49,10 @@ struct GProb {
     long long ldc;
 };
 
-enum Epi { EPI_STORE = 0, EPI_SUB = 1, EPI_ACCUM = 2, EPI_PARTIAL = 3 };
+// EPI_PACKNK (packed tensor-core path only): row m of the product is written in
+// the packed BF16-plane format as row rowptr[m] of an NK-packed B operand
+// (16 columns = one 16-deep chunk of that operand), not as FP32.
+enum Epi { EPI_STORE = 0, EPI_SUB = 1, EPI_ACCUM = 2, EPI_PARTIAL = 3, EPI_PACKNK = 4 };
 enum AMode { A_KM = 0, A_MK = 1 };
 enum BMode { B_KN = 0, B_NK = 1 };
 
@@ -83,6 +86,7 @@ struct PProb {
     cf* C;
     const cf* S;
     long long ldc;
+    char* const* rowptr;   // EPI_PACKNK: per output row, its first 16-byte group in the packed operand
 };
 
 struct GemmLaunch {

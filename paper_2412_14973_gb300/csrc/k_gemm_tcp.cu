@@ -419,7 +419,37 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
         if (threadIdx.x == 0 || !ok) atomicExch(err, TLR_ERR_TIMEOUT);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 8 && ok && !*abort_flag) {
+    if (warp < 8 && ok && !*abort_flag && epi == EPI_PACKNK) {
+        // Row m goes to one row of a packed NK operand: 16 columns are one
+        // 16-deep chunk there (two 16-byte groups per BF16 plane).  Lanes hold
+        // consecutive rows, which are 16 bytes apart in the packed tile.
+        const int lg = warp & 3, ch = warp >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
+        const int m = m0 + lg * 32 + lane;
+        constexpr int plane = 128 * 16 * 2;
+#pragma unroll 1
+        for (int cb = 0; cb < TN / 32; ++cb) {
+            const int col = ch * (TN / 2) + cb * 16;
+            if (n0 + col >= P.N) break;
+            float pr[16], pi[16];
+            if (C > 0) {
+                tmem_ld16(lane_addr + col, pr);
+                tmem_ld16(lane_addr + TN + col, pi);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
+            }
+            if (m < P.M) {
+                const int n = n0 + col;
+                float2 v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = n + j < P.N ? make_float2(pr[j], pi[j]) : make_float2(0.f, 0.f);
+                char* d = P.rowptr[m] + (long long)(n >> 4) * 4 * plane;
+                split_store(d, plane, v, 1.f);
+                split_store(d + 128, plane, v + 8, 1.f);
+            }
+        }
+    } else if (warp < 8 && ok && !*abort_flag) {
         // Each warp drains 32 rows x 16 columns at a time: tcgen05.ld gives a
         // thread one row; the block is transposed through shared memory (the
         // operand ring is idle once the last MMA has completed) so that each
