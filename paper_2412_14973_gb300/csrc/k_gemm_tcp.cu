@@ -190,11 +190,11 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 // columns (n).  Phase 1 reads the 32 source rows of T (and T_p) coalesced
 // along n, applies the update, writes T back and keeps the tile in shared
 // memory; phase 2 writes the KN packing (thread = (n, k-group of 8)); phase 3
-// the conjugated NK packing (thread = (k, n-group of 8)).  Padding of the
+// the conjugated NK packing (thread = (k, n-group of 8), lanes along k).  Padding of the
 // packed buffers (k >= K_i, rows >= ns) is zero from the buffer's creation and
 // is never written.
 constexpr int TP_K = 32, TP_N = 128, TP_LD = TP_N + 1;
-static_assert(kPackTRB == 128 && KC == 16, "tpack writes 128-row, 16-deep B tiles");
+static_assert(kPackTRB == 128 && KC == 16 && TP_K == 32, "tpack writes 128-row, 16-deep B tiles, 32 rows per CTA");
 
 __device__ __forceinline__ void split_store(char* dst, int plane, const float2* v, float sgn) {
     uint32_t w[4][4];
@@ -223,22 +223,37 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
     const int n0 = blockIdx.x * TP_N;
     const int nk = P.nk;
     const float a = alpha ? (float)alpha[0] : 0.f;
-    // phase 1
+    // phase 1 (source row indices staged first; four rows per thread in flight)
+    __shared__ long long srow[TP_K];
+    if (threadIdx.x < nk) srow[threadIdx.x] = (long long)P.g[P.k0 + threadIdx.x] * ns;
+    __syncthreads();
     {
-        const int n = threadIdx.x & (TP_N - 1);
-        for (int kk = threadIdx.x >> 7; kk < nk; kk += 2) {
-            float2 t = make_float2(0.f, 0.f);
-            if (n0 + n < ns) {
-                const long long o = (long long)P.g[P.k0 + kk] * ns + n0 + n;
-                t = T[o];
-                if (a != 0.f) {
-                    const float2 d = Tp[o];
-                    t.x = fmaf(a, d.x, t.x);
-                    t.y = fmaf(a, d.y, t.y);
-                    T[o] = t;
+        const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
+        const bool nv = n0 + n < ns;
+#pragma unroll 1
+        for (int kb = kq; kb < TP_K; kb += 8) {
+            float2 t[4], d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int kk = kb + 2 * u;
+                t[u] = d[u] = make_float2(0.f, 0.f);
+                if (kk < nk && nv) {
+                    const long long o = srow[kk] + n0 + n;
+                    t[u] = T[o];
+                    if (a != 0.f) d[u] = Tp[o];
                 }
             }
-            s[kk * TP_LD + n] = t;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int kk = kb + 2 * u;
+                if (kk >= nk) continue;
+                if (a != 0.f && nv) {
+                    t[u].x = fmaf(a, d[u].x, t[u].x);
+                    t[u].y = fmaf(a, d[u].y, t[u].y);
+                    T[srow[kk] + n0 + n] = t[u];
+                }
+                s[kk * TP_LD + n] = t[u];
+            }
         }
     }
     __syncthreads();
@@ -266,10 +281,12 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
     // phase 3: NK, rows = factor index, k = n; conjugated
     {
         const int nkcN = (ns + 15) >> 4;
-        for (int it = threadIdx.x; it < nk * (TP_N / 8); it += blockDim.x) {
-            const int kk = it >> 4, ng = it & 15;
+        // lanes take consecutive rows: conflict-free shared reads, and 16-byte
+        // stores 16 bytes apart in the packed tile
+        for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
+            const int kk = it & (TP_K - 1), ng = it >> 5;
             const int nb = n0 + ng * 8;
-            if (nb >= ns) continue;
+            if (kk >= nk || nb >= ns) continue;
             float2 v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
