@@ -340,6 +340,7 @@ struct tlr_mdd_s {
        *q = nullptr;
     // solver small state
     double *rho_h = nullptr, *sy_h = nullptr, *yy_h = nullptr, *acoef = nullptr, *sc = nullptr, *fhist = nullptr;
+    double *lbm = nullptr, *lbpart = nullptr;   // compact L-BFGS: S^T Y and Y^T Y by slot; partials
     int* ints = nullptr;
     // ring (allocated on first solve)
     float* ring = nullptr;
@@ -432,6 +433,8 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->sc = a.take<double>(SC_COUNT + 8);
     h->ints = a.take<int>(SI_COUNT + 8);
     h->fhist = a.take<double>(TLR_MAX_HIST);
+    h->lbm = a.take<double>(2 * 33 * 33);
+    h->lbpart = a.take<double>((size_t)kLbPartDoubles);
     // GEMM tables: 8 slots of at most 2N problems each
     h->tab_base = reinterpret_cast<char*>(a.take<GProb>(2 * (size_t)L.N + 1));
     for (int t = 1; t < 8; ++t) a.take<GProb>(2 * (size_t)L.N + 1);
@@ -1382,6 +1385,9 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     S.sy_h = h->sy_h;
     S.yy_h = h->yy_h;
     S.acoef = h->acoef;
+    S.SYm = h->lbm;
+    S.YYm = h->lbm + 33 * 33;
+    S.lbpart = h->lbpart;
     S.sc = h->sc;
     S.ints = h->ints;
     S.fhist = h->fhist;
@@ -1405,7 +1411,7 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
         for (int it = 0; it < o->admm_iters; ++it) {
             CK(h, sv_xupdate_start(S, rho, h->st));
             for (int t = 0; t < o->lbfgs_iters; ++t) {
-                CK(h, sv_two_loop(S, h->st));
+                CK(h, sv_direction(S, h->st));
                 CK(h, run_gemm(h->Lc_d, h->st));
                 CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.b, h->Zsd, h->st));
                 CK(h, run_gemm(h->Le_a1, h->st));

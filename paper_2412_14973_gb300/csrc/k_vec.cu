@@ -1,8 +1,8 @@
 // theta-space and reduction kernels: the layout maps between the stacked
 // unknown (Z-bar, L-bar, R-bar) and the block panels, the gradient split-K
 // reduction with the dense-tile symmetrisation (eq. 26), FP64 inner products,
-// the exact line search on the quartic phi(alpha), and the L-BFGS two-loop
-// recursion / ADMM updates (eq. 19-24) with every scalar kept on the device.
+// the exact line search on the quartic phi(alpha), and the L-BFGS direction
+// (compact form) / ADMM updates (eq. 19-24) with every scalar kept on the device.
 //
 // All reductions run on a fixed grid (kRedBlocks x kRedThreads) and sum their
 // per-block partials in a fixed order, so results are bitwise reproducible.
@@ -293,101 +293,203 @@ __device__ __forceinline__ int ring_idx(const SolverDev& S, int j) {
     return ((S.ints[SI_NEWEST] - j) % R + R) % R;
 }
 
-// The two-loop kernels pass partial sums along the chain in two ping-pong
-// slabs: kernel t reads slab pin (written by kernel t-1) in every block and
-// writes its own partials to pout, so no block overwrites what another reads.
+// L-BFGS direction d = -H g in the compact form of the inverse BFGS update
+// (Byrd, Nocedal and Schnabel 1994): with the k stored pairs ordered oldest
+// first, S = [s_1 .. s_k], Y = [y_1 .. y_k], R = triu(S^T Y), D = diag(S^T Y),
+// H0 = gamma I and gamma = <s,y>/<y,y> of the newest pair,
+//   H g = gamma g + S a - gamma Y u,  u = R^-1 S^T g,
+//   a = R^-T ((D + gamma Y^T Y) u - gamma Y^T g).
+// This is the matrix the two-loop recursion applies, evaluated in three
+// steps: the inner products (passes over groups of pairs; they also fill the
+// newest pair's row and column of S^T Y and Y^T Y, which are kept by slot),
+// the small FP64 triangular solves in one block, and one combination pass.
 
-// first pass, initial kernel: q = g; partial <s_0, q> if cnt > 0
-__global__ void __launch_bounds__(kRedThreads) k_tl1_init(SolverDev S, double* pout) {
+// partials per block: for pair j of the group, <s_j,g>, <y_j,g>, <s_j,y_n>,
+// <s_n,y_j>, <y_j,y_n> (n = the newest pair).  Per-thread sums are plain FP32
+// multiply-adds (a thread sums n2 / (kRedBlocks kRedThreads) terms, a few
+// dozen at these sizes), combined in FP64 across threads and blocks: these
+// products only set the direction's coefficients, whose rounding the exact
+// line search and the descent test absorb.
+__global__ void __launch_bounds__(kRedThreads, 2) k_lb_dots(SolverDev S, int j0) {
     __shared__ double sh[32];
     const int cnt = S.ints[SI_CNT];
-    const float* s0 = cnt > 0 ? S.sh + (long long)ring_idx(S, 0) * S.n2 : nullptr;
-    Acc acc;
+    if (j0 >= cnt) return;
+    const int jc = min(kLbGroup, cnt - j0);
+    const float* sp[kLbGroup];
+    const float* yp[kLbGroup];
+#pragma unroll
+    for (int jj = 0; jj < kLbGroup; ++jj) {
+        const int idx = ring_idx(S, jj < jc ? j0 + jj : j0);
+        sp[jj] = S.sh + (long long)idx * S.n2;
+        yp[jj] = S.yh + (long long)idx * S.n2;
+    }
+    const int nw = ring_idx(S, 0);
+    const float* sn = S.sh + (long long)nw * S.n2;
+    const float* yn = S.yh + (long long)nw * S.n2;
+    float acc[kLbGroup][5];
+#pragma unroll
+    for (int jj = 0; jj < kLbGroup; ++jj)
+#pragma unroll
+        for (int t = 0; t < 5; ++t) acc[jj][t] = 0.f;
     GRID_STRIDE(i, S.n2) {
-        const float q = S.g[i];
-        S.q[i] = q;
-        if (s0) acc.add(s0[i] * q);
-    }
-    const double t = block_sum(acc.val(), sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// first pass, step j (j-th newest pair): a_j = rho_j <s_j, q>; q -= a_j y_j;
-// partial <s_{j+1}, q> for the next step
-__global__ void __launch_bounds__(kRedThreads) k_tl1_step(SolverDev S, int j, const double* pin, double* pout) {
-    __shared__ double sh[32];
-    __shared__ double sh1[1];
-    const int cnt = S.ints[SI_CNT];
-    if (j >= cnt) return;
-    const int idx = ring_idx(S, j);
-    const double dot = sum_partials(pin, kRedBlocks, 1, 0, sh1);
-    const double a = S.rho_h[idx] * dot;
-    if (blockIdx.x == 0 && threadIdx.x == 0) S.acoef[j] = a;
-    const float af = (float)a;
-    const float* y = S.yh + (long long)idx * S.n2;
-    const float* sn = (j + 1 < cnt) ? S.sh + (long long)ring_idx(S, j + 1) * S.n2 : nullptr;
-    Acc acc;
-    GRID_STRIDE(i, S.n2) {
-        const float q = fmaf(-af, y[i], S.q[i]);
-        S.q[i] = q;
-        if (sn) acc.add(sn[i] * q);
-    }
-    const double t = block_sum(acc.val(), sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// second pass, initial kernel: r = gamma q with gamma = <s,y>/<y,y> of the
-// newest pair (1 without pairs); partial <y_jstart, r> if jstart < cnt
-__global__ void __launch_bounds__(kRedThreads) k_tl2_init(SolverDev S, int jstart, double* pout) {
-    __shared__ double sh[32];
-    const int cnt = S.ints[SI_CNT];
-    double gamma = 1.0;
-    if (cnt > 0) {
-        const int nw = ring_idx(S, 0);
-        gamma = S.sy_h[nw] / S.yy_h[nw];
-    }
-    const float gf = (float)gamma;
-    const float* yn = (jstart < cnt) ? S.yh + (long long)ring_idx(S, jstart) * S.n2 : nullptr;
-    Acc acc;
-    GRID_STRIDE(i, S.n2) {
-        const float r = gf * S.q[i];
-        S.q[i] = r;
-        if (yn) acc.add(yn[i] * r);
-    }
-    const double t = block_sum(acc.val(), sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// second pass, step j (j descending, oldest first): b = rho_j <y_j, r>;
-// r += (a_j - b) s_j; partial <y_{j-1}, r>; the last step (j == 0) writes d = -r.
-__global__ void __launch_bounds__(kRedThreads) k_tl2_step(SolverDev S, int j, const double* pin, double* pout) {
-    __shared__ double sh[32];
-    __shared__ double sh1[1];
-    const int cnt = S.ints[SI_CNT];
-    const bool active = j < cnt;
-    const bool need_next = (j - 1 >= 0) && (j - 1 < cnt);
-    if (!active && !need_next && j != 0) return;
-    float coef = 0.f;
-    const float* s = nullptr;
-    if (active) {
-        const int idx = ring_idx(S, j);
-        const double dot = sum_partials(pin, kRedBlocks, 1, 0, sh1);
-        coef = (float)(S.acoef[j] - S.rho_h[idx] * dot);
-        s = S.sh + (long long)idx * S.n2;
-    }
-    const float* yn = need_next ? S.yh + (long long)ring_idx(S, j - 1) * S.n2 : nullptr;
-    Acc acc;
-    GRID_STRIDE(i, S.n2) {
-        float r = S.q[i];
-        if (s) {
-            r = fmaf(coef, s[i], r);
-            S.q[i] = r;
+        const float gi = S.g[i], sni = sn[i], yni = yn[i];
+#pragma unroll
+        for (int jj = 0; jj < kLbGroup; ++jj) {
+            if (jj < jc) {
+                const float s = sp[jj][i], y = yp[jj][i];
+                acc[jj][0] = fmaf(s, gi, acc[jj][0]);
+                acc[jj][1] = fmaf(y, gi, acc[jj][1]);
+                acc[jj][2] = fmaf(s, yni, acc[jj][2]);
+                acc[jj][3] = fmaf(sni, y, acc[jj][3]);
+                acc[jj][4] = fmaf(y, yni, acc[jj][4]);
+            }
         }
-        if (yn) acc.add(yn[i] * r);
-        if (j == 0) S.d[i] = -r;
     }
-    const double t = block_sum(acc.val(), sh);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
+    double* out = S.lbpart + (long long)(j0 / kLbGroup) * kRedBlocks * (5 * kLbGroup) +
+                  (long long)blockIdx.x * (5 * kLbGroup);
+#pragma unroll
+    for (int jj = 0; jj < kLbGroup; ++jj) {
+        if (jj >= jc) break;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const double r = block_sum((double)acc[jj][t], sh);
+            if (threadIdx.x == 0) out[jj * 5 + t] = r;
+        }
+    }
+}
+
+// One block: finalise the partials (warp per value, fixed order), update the
+// newest pair's row / column of S^T Y and Y^T Y, then (thread 0) the
+// triangular solves; coefficients to acoef, gamma to sc[SC_GAMMA].
+__global__ void __launch_bounds__(kRedThreads) k_lb_solve(SolverDev S) {
+    __shared__ double val[32 * 5];
+    __shared__ double Rm[32 * 33];
+    __shared__ double Ym[32 * 33];
+    __shared__ double p[32], q[32], u[32], t[32];
+    const int cnt = S.ints[SI_CNT];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int v = w; v < 5 * cnt; v += kRedThreads / 32) {
+        const int j = v / 5, kind = v % 5;
+        const double* base = S.lbpart + (long long)(j / kLbGroup) * kRedBlocks * (5 * kLbGroup) +
+                             (j % kLbGroup) * 5 + kind;
+        double a = 0.0;
+        for (int b = l; b < kRedBlocks; b += 32) a += base[(long long)b * (5 * kLbGroup)];
+        a = warp_sum(a);
+        if (l == 0) val[v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (cnt == 0) {
+        S.sc[SC_GAMMA] = 1.0;
+        return;
+    }
+    const int R = S.ring;
+    const int nw = ring_idx(S, 0);
+    for (int j = 0; j < cnt; ++j) {
+        const int a = ring_idx(S, j);
+        S.SYm[a * R + nw] = val[j * 5 + 2];
+        S.SYm[nw * R + a] = val[j * 5 + 3];
+        S.YYm[a * R + nw] = val[j * 5 + 4];
+        S.YYm[nw * R + a] = val[j * 5 + 4];
+    }
+    // oldest first: position i holds the (cnt - 1 - i)-th newest pair
+    const int k = cnt;
+    for (int i = 0; i < k; ++i) {
+        const int si = ring_idx(S, k - 1 - i);
+        p[i] = val[(k - 1 - i) * 5 + 0];
+        q[i] = val[(k - 1 - i) * 5 + 1];
+        for (int j = 0; j < k; ++j) {
+            const int sj = ring_idx(S, k - 1 - j);
+            Rm[i * 33 + j] = S.SYm[si * R + sj];
+            Ym[i * 33 + j] = S.YYm[si * R + sj];
+        }
+    }
+    const double gamma = Rm[(k - 1) * 33 + (k - 1)] / Ym[(k - 1) * 33 + (k - 1)];
+    // u = R^-1 p (R upper triangular)
+    for (int i = k - 1; i >= 0; --i) {
+        double a = p[i];
+        for (int j = i + 1; j < k; ++j) a -= Rm[i * 33 + j] * u[j];
+        u[i] = a / Rm[i * 33 + i];
+    }
+    // t = D u + gamma Y^T Y u - gamma q
+    for (int i = 0; i < k; ++i) {
+        double a = Rm[i * 33 + i] * u[i] - gamma * q[i];
+        for (int j = 0; j < k; ++j) a += gamma * Ym[i * 33 + j] * u[j];
+        t[i] = a;
+    }
+    // a = R^-T t (R^T lower triangular), written over t
+    for (int i = 0; i < k; ++i) {
+        double a = t[i];
+        for (int j = 0; j < i; ++j) a -= Rm[j * 33 + i] * t[j];
+        t[i] = a / Rm[i * 33 + i];
+    }
+    for (int i = 0; i < k; ++i) {
+        const int j = k - 1 - i;   // j-th newest
+        S.acoef[j] = t[i];
+        S.acoef[32 + j] = -gamma * u[i];
+    }
+    S.sc[SC_GAMMA] = gamma;
+}
+
+// d = -(gamma g + sum_j a_j s_j + sum_j c_j y_j); four floats per thread and
+// four pairs per step in flight (the vectors start 16-byte aligned when n2 is
+// a multiple of 4, else a scalar loop)
+__global__ void __launch_bounds__(256) k_lb_dir(SolverDev S) {
+    __shared__ float cs[32], cy[32];
+    __shared__ const float* ps[32];
+    __shared__ const float* py[32];
+    const int cnt = S.ints[SI_CNT];
+    if (threadIdx.x < cnt) {
+        const int idx = ring_idx(S, threadIdx.x);
+        cs[threadIdx.x] = (float)S.acoef[threadIdx.x];
+        cy[threadIdx.x] = (float)S.acoef[32 + threadIdx.x];
+        ps[threadIdx.x] = S.sh + (long long)idx * S.n2;
+        py[threadIdx.x] = S.yh + (long long)idx * S.n2;
+    }
+    __syncthreads();
+    const float gamma = (float)S.sc[SC_GAMMA];
+    if ((S.n2 & 3) == 0) {
+        const long long n4 = S.n2 >> 2;
+        const float4* g4 = reinterpret_cast<const float4*>(S.g);
+        float4* d4 = reinterpret_cast<float4*>(S.d);
+        GRID_STRIDE(i, n4) {
+            const float4 gv = g4[i];
+            float4 r = make_float4(gamma * gv.x, gamma * gv.y, gamma * gv.z, gamma * gv.w);
+            int j = 0;
+            for (; j + 4 <= cnt; j += 4) {
+                float4 sv[4], yv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sv[u] = reinterpret_cast<const float4*>(ps[j + u])[i];
+                    yv[u] = reinterpret_cast<const float4*>(py[j + u])[i];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float a = cs[j + u], c = cy[j + u];
+                    r.x = fmaf(c, yv[u].x, fmaf(a, sv[u].x, r.x));
+                    r.y = fmaf(c, yv[u].y, fmaf(a, sv[u].y, r.y));
+                    r.z = fmaf(c, yv[u].z, fmaf(a, sv[u].z, r.z));
+                    r.w = fmaf(c, yv[u].w, fmaf(a, sv[u].w, r.w));
+                }
+            }
+            for (; j < cnt; ++j) {
+                const float4 sv = reinterpret_cast<const float4*>(ps[j])[i];
+                const float4 yv = reinterpret_cast<const float4*>(py[j])[i];
+                const float a = cs[j], c = cy[j];
+                r.x = fmaf(c, yv.x, fmaf(a, sv.x, r.x));
+                r.y = fmaf(c, yv.y, fmaf(a, sv.y, r.y));
+                r.z = fmaf(c, yv.z, fmaf(a, sv.z, r.z));
+                r.w = fmaf(c, yv.w, fmaf(a, sv.w, r.w));
+            }
+            d4[i] = make_float4(-r.x, -r.y, -r.z, -r.w);
+        }
+    } else {
+        GRID_STRIDE(i, S.n2) {
+            float r = gamma * S.g[i];
+            for (int j = 0; j < cnt; ++j) r = fmaf(cy[j], py[j][i], fmaf(cs[j], ps[j][i], r));
+            S.d[i] = -r;
+        }
+    }
 }
 
 // theta-space line-search inner products: <x - v, x - v>, <x - v, d>, <d, d>
@@ -644,23 +746,15 @@ cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st) {
     counted(1);
     return cudaGetLastError();
 }
-cudaError_t sv_two_loop(const SolverDev& S, cudaStream_t st) {
-    double* slab[2] = {S.part, S.part + kRedBlocks};
-    // first pass: newest -> oldest
-    k_tl1_init<<<kRedBlocks, kRedThreads, 0, st>>>(S, slab[0]);
-    counted(1);
-    for (int j = 0; j < S.m; ++j) {
-        k_tl1_step<<<kRedBlocks, kRedThreads, 0, st>>>(S, j, slab[j & 1], slab[(j + 1) & 1]);
+cudaError_t sv_direction(const SolverDev& S, cudaStream_t st) {
+    for (int j0 = 0; j0 < S.m; j0 += kLbGroup) {
+        k_lb_dots<<<kRedBlocks, kRedThreads, 0, st>>>(S, j0);
         counted(1);
     }
-    // second pass: oldest -> newest (j descending)
-    k_tl2_init<<<kRedBlocks, kRedThreads, 0, st>>>(S, S.m - 1, slab[0]);
+    k_lb_solve<<<1, kRedThreads, 0, st>>>(S);
     counted(1);
-    for (int t = 0; t < S.m; ++t) {
-        const int j = S.m - 1 - t;
-        k_tl2_step<<<kRedBlocks, kRedThreads, 0, st>>>(S, j, slab[t & 1], slab[(t + 1) & 1]);
-        counted(1);
-    }
+    k_lb_dir<<<1024, 256, 0, st>>>(S);
+    counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {

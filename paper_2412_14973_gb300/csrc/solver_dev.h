@@ -8,8 +8,13 @@
 
 namespace tlr {
 
-enum ScalarSlot { SC_ALPHA = 0, SC_F, SC_F0, SC_C0, SC_C1, SC_C2, SC_C3, SC_C4, SC_COUNT };
+enum ScalarSlot { SC_ALPHA = 0, SC_F, SC_F0, SC_C0, SC_C1, SC_C2, SC_C3, SC_C4, SC_GAMMA, SC_COUNT };
 enum IntSlot { SI_CNT = 0, SI_NEWEST, SI_ITERS, SI_RESTARTS, SI_STATUS, SI_COUNT };
+
+// compact L-BFGS: pairs per inner-product pass, and the partial storage for
+// the largest memory (32 pairs)
+constexpr int kLbGroup = 10;
+constexpr long long kLbPartDoubles = (long long)kRedBlocks * 5 * kLbGroup * ((32 + kLbGroup - 1) / kLbGroup);
 
 struct SolverDev {
     long long n2;        // floats per theta-space vector (2 * n_theta)
@@ -20,18 +25,21 @@ struct SolverDev {
     double* rho_h;       // [ring] 1 / <s, y>
     double* sy_h;        // [ring] <s, y>
     double* yy_h;        // [ring] <y, y>
-    double* acoef;       // [m] first-pass coefficients
+    double* acoef;       // [64] direction coefficients: [j] of s_j, [32 + j] of y_j (j-th newest)
+    double* SYm;         // [ring * ring] <s_a, y_b> by slot
+    double* YYm;         // [ring * ring] <y_a, y_b> by slot
+    double* lbpart;      // kRedBlocks * 5 * kLbGroup partials per group of pairs (direction inner products)
     double* sc;          // ScalarSlot values
     int* ints;           // IntSlot values
     double* fhist;       // [TLR_MAX_HIST]
-    double* part;        // 2 * kRedBlocks partial slabs for the two-loop chain
+    double* part;        // 2 * kRedBlocks partial slabs
 };
 
 cudaError_t sv_norm_part(const cf* R, long long n, double* part, cudaStream_t st);
 cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t st);
 cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st);
-cudaError_t sv_two_loop(const SolverDev& S, cudaStream_t st);
+cudaError_t sv_direction(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st);
 cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
                            cudaStream_t st);
