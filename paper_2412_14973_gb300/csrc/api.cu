@@ -358,6 +358,12 @@ struct tlr_mdd_s {
     long long static_items = 0;
     TPackTile* d_tpack = nullptr;      // fused update + packing of T (packs of T are not per-launch jobs)
     int n_tpack = 0;
+    // fused residual step + packing of R (packs of R are not per-launch jobs when on)
+    bool rstep_on = false;
+    char** d_rkn = nullptr;            // [N] packed R_i (KN) for the residual compression
+    char** d_rmk = nullptr;            // [N] packed R_i (MK) for the projection
+    double* rpart = nullptr;           // per-CTA partials of ||R||^2
+    long long n_rpart = 0;
     // asynchronous solve and its CUDA graph
     cf* th_io = nullptr;               // theta staging (stable address for the graph)
     HostStats* hstats = nullptr;       // pinned
@@ -408,6 +414,8 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->Zsd = a.take<cf>(nz);
     h->part = a.take<cf>((size_t)h->nsplit * L.nth);
     h->dpart = a.take<double>(16 * kRedBlocks);
+    h->n_rpart = L.b % 32 == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
+    h->rpart = a.take<double>((size_t)std::max<long long>(1, h->n_rpart));
     const size_t K = std::max<int64_t>(1, L.Ktot);
     h->d_partner = a.take<int>(K);
     long long* colsrc = a.take<long long>(K);
@@ -662,7 +670,8 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
 // once when the data are loaded.  The line-search pair A1 / A2 shares its
 // packs (A2 packs nothing).  The two packings of the factor products T (KN for
 // the expansions, conjugated NK for the projection) are written by tpack right
-// after T is formed or updated, so no contraction packs them.
+// after T is formed or updated, and the residual's two packings by the fused
+// residual step (rstep), so no contraction packs them.
 // ---------------------------------------------------------------------------
 struct PackKey {
     const void* src;
@@ -761,6 +770,35 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     for (auto& ko : order)
         if (ko.first.src == (const void*)h->Tp && ko.first.kcontig == 1 && ko.first.sgn > 0)
             v_nk[ko.first.gr] = ko.second;
+    // The residual's two packings (MK for the projection, KN for the residual
+    // compression) come from the fused residual step when the tile is a
+    // multiple of 32 and every block has both.
+    const char* rlo = reinterpret_cast<const char*>(h->R);
+    const char* rhi = rlo + (size_t)L.nr * L.ns * sizeof(cf);
+    auto is_R = [&](const PackKey& k) {
+        const char* c = reinterpret_cast<const char*>(k.src);
+        return c >= rlo && c < rhi;
+    };
+    std::vector<char*> rkn(L.N, nullptr), rmk(L.N, nullptr);
+    std::set<PackKey> rkeys;
+    for (auto& ko : order) {
+        const PackKey& k = ko.first;
+        if (!is_R(k) || k.gr || k.gk || k.sgn < 0 || k.ld != L.ns) continue;
+        const long long off = reinterpret_cast<const cf*>(k.src) - h->R;
+        if (off % ((long long)L.b * L.ns) != 0) continue;
+        const long long blk = off / ((long long)L.b * L.ns);
+        if (k.kcontig == 0 && k.R == L.ns && k.K == L.b) {
+            rkn[blk] = h->packed + ko.second;
+            rkeys.insert(k);
+        }
+        if (k.kcontig == 1 && k.R == L.b && k.K == L.ns) {
+            rmk[blk] = h->packed + ko.second;
+            rkeys.insert(k);
+        }
+    }
+    bool rfuse = L.b % 32 == 0 && h->n_rpart > 0;
+    for (int i = 0; i < L.N && rfuse; ++i)
+        if (!rkn[i] || !rmk[i]) rfuse = false;
     std::vector<char*> rowptr;
     bool vpack = L.Ktot > 0;
     for (int i = 0; i < L.N && vpack; ++i)
@@ -808,6 +846,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                 q.t[t].K = p.t[t].K;
                 for (const PackKey* k : {&ka, &kb}) {
                     if (vpack && k->src == (const void*)h->Tp && k->kcontig == 1) continue;   // written by Lc_v
+                    if (rfuse && rkeys.count(*k)) continue;                                    // written by rstep
                     if (is_T(*k)) {
                         if (k->kcontig == 0 && k->sgn > 0)
                             t_kn[k->gk] = offs[*k];
@@ -867,6 +906,8 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     bytes += (tt.size() * sizeof(TPackTile) + 255) & ~size_t(255);
     const size_t ro = bytes;
     bytes += (rowptr.size() * sizeof(char*) + 255) & ~size_t(255);
+    const size_t rpo = bytes;
+    bytes += (2 * (size_t)L.N * sizeof(char*) + 255) & ~size_t(255);
     CK(h, cudaMallocAsync((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
     if (vpack) {
         char** d_rowptr = reinterpret_cast<char**>(h->tcp_tables + ro);
@@ -889,6 +930,13 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         if (!jobs[ti].empty())
             CK(h, cudaMemcpyAsync(G.d_jobs, jobs[ti].data(), jobs[ti].size() * sizeof(PackJob),
                                   cudaMemcpyHostToDevice, h->st));
+    }
+    if (rfuse) {
+        h->d_rkn = reinterpret_cast<char**>(h->tcp_tables + rpo);
+        h->d_rmk = h->d_rkn + L.N;
+        CK(h, cudaMemcpyAsync(h->d_rkn, rkn.data(), L.N * sizeof(char*), cudaMemcpyHostToDevice, h->st));
+        CK(h, cudaMemcpyAsync(h->d_rmk, rmk.data(), L.N * sizeof(char*), cudaMemcpyHostToDevice, h->st));
+        h->rstep_on = true;
     }
     h->d_tpack = reinterpret_cast<TPackTile*>(h->tcp_tables + to);
     h->n_tpack = (int)tt.size();
@@ -1153,6 +1201,8 @@ static int forward(tlr_mdd_s* h, bool plain_apply) {
     CK(h, run_gemm(h->Lc_x, h->st));
     if (h->n_tpack) CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)L.ns, h->st));
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
+    if (!plain_apply && h->rstep_on)
+        CK(h, rstep(h->R, h->A1, h->A2, nullptr, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn, h->d_rmk, nullptr, h->st));
     return TLR_OK;
 }
 
@@ -1419,7 +1469,11 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));
                 CK(h, sv_dots3(S, part3, h->st));
                 CK(h, sv_line_search(S, part6, part3, rho, h->st));
-                CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
+                if (h->rstep_on)
+                    CK(h, rstep(h->R, h->A1, h->A2, h->sc + SC_ALPHA, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn,
+                                h->d_rmk, h->rpart, h->st));
+                else
+                    CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
                 if (h->n_tpack)
                     CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, h->sc + SC_ALPHA, (int)L.ns, h->st));
                 else if (L.Ktot > 0)
@@ -1428,7 +1482,10 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 rc = gradient(h);
                 if (rc) return rc;
                 CK(h, sv_pair_prep(S, rho, part3b, h->st));
-                CK(h, sv_pair_accept(S, part3b, partf, h->st));
+                if (h->rstep_on)
+                    CK(h, sv_pair_accept(S, part3b, h->rpart, (int)h->n_rpart, h->st));
+                else
+                    CK(h, sv_pair_accept(S, part3b, partf, kRedBlocks, h->st));
             }
             CK(h, sv_admm_zu(S, lam, rho, h->st));
         }

@@ -123,6 +123,16 @@ struct TPackTile {
 // row of T exactly once), then both packed forms of the updated rows.
 cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
                   cudaStream_t st);
+// Fused residual step of the tensor-core path: R += a A1 + a^2 A2 (FP32, the
+// same arithmetic as the plain residual step; a read on the device, alpha ==
+// nullptr: no update), the per-CTA partial of ||R||^2 (two-sum per thread,
+// FP64 across the CTA) into part[cta] when part != nullptr, and R in both
+// packed forms: block i's rows as an A operand with k = ns (MK, mk[i]) and
+// as a B operand with rows = ns and k = the receiver (KN, kn[i]).  b must be
+// a multiple of 32; rstep_ctas gives the number of CTAs (and partials).
+long long rstep_ctas(int nr, int ns);
+cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
+                  char* const* mk, double* part, cudaStream_t st);
 // bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
 // pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "reduce.h"
 
 namespace tlr {
 
@@ -299,6 +300,99 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 }
 
 // ---------------------------------------------------------------------------
+// rstep: fused residual step and both packings of the residual
+// ---------------------------------------------------------------------------
+// A CTA takes 32 receiver rows (inside one block, b a multiple of 32) and 128
+// columns: phase 1 reads R, A1, A2 coalesced along n, updates, writes R back,
+// accumulates ||R||^2 and keeps the tile in shared memory; phase 2 writes the
+// MK packing (rows = receivers, lanes along rows); phase 3 the KN packing
+// (rows = n, k = receiver, lanes along n).
+__global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __restrict__ A1,
+                                               const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
+                                               int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
+                                               double* __restrict__ part) {
+    __shared__ float2 s[TP_K * TP_LD];
+    __shared__ double sh[32];
+    const int n0 = blockIdx.x * TP_N, r0 = blockIdx.y * TP_K;
+    const int blk = r0 / b, rl0 = r0 - blk * b;
+    const float a = alpha ? (float)alpha[0] : 0.f;
+    const float a2 = alpha ? (float)(alpha[0] * alpha[0]) : 0.f;
+    Acc acc;
+    {
+        const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
+        const bool nv = n0 + n < ns;
+#pragma unroll 1
+        for (int kb = kq; kb < TP_K; kb += 8) {
+            float2 r[4], u[4], w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                r[q] = u[q] = w[q] = make_float2(0.f, 0.f);
+                if (nv) {
+                    const long long o = (long long)(r0 + kb + 2 * q) * ns + n0 + n;
+                    r[q] = R[o];
+                    if (a != 0.f) {
+                        u[q] = A1[o];
+                        w[q] = A2[o];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = kb + 2 * q;
+                if (nv) {
+                    if (a != 0.f) {
+                        r[q].x = fmaf(a2, w[q].x, fmaf(a, u[q].x, r[q].x));
+                        r[q].y = fmaf(a2, w[q].y, fmaf(a, u[q].y, r[q].y));
+                        R[(long long)(r0 + kk) * ns + n0 + n] = r[q];
+                    }
+                    acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
+                }
+                s[kk * TP_LD + n] = r[q];
+            }
+        }
+    }
+    if (part) {
+        const double t = block_sum(acc.val(), sh);   // includes the __syncthreads phase 2 needs
+        if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    } else {
+        __syncthreads();
+    }
+    constexpr int plane = 128 * 16 * 2;
+    // phase 2: MK, rows = receivers of block blk, k = n
+    {
+        const int nkcN = (ns + 15) >> 4;
+        char* const base = mk[blk];
+        for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
+            const int kk = it & (TP_K - 1), ng = it >> 5;
+            const int nb = n0 + ng * 8;
+            if (nb >= ns) continue;
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
+            const int rl = rl0 + kk;
+            char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + core_off(rl & 127, (nb >> 3) & 1);
+            split_store(dst, plane, v, 1.f);
+        }
+    }
+    // phase 3: KN, rows = n, k = receiver of block blk
+    {
+        const int nkcK = b >> 4;
+        char* const base = kn[blk];
+        for (int it = threadIdx.x; it < TP_N * (TP_K / 8); it += blockDim.x) {
+            const int n = it & (TP_N - 1), kg = it >> 7;
+            const int nn = n0 + n;
+            if (nn >= ns) continue;
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = s[(kg * 8 + j) * TP_LD + n];
+            const int k = rl0 + kg * 8;
+            char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + core_off(nn & 127, (k >> 3) & 1);
+            split_store(dst, plane, v, 1.f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // GEMM on packed operands
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
@@ -559,6 +653,18 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
     if (ntiles == 0 || ns == 0) return cudaSuccess;
     dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)ntiles);
     k_tpack<<<grid, 256, 0, st>>>(d_tiles, T, Tp, alpha, ns);
+    counted(1);
+    return cudaGetLastError();
+}
+
+long long rstep_ctas(int nr, int ns) { return (long long)((ns + TP_N - 1) / TP_N) * (nr / TP_K); }
+
+cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
+                  char* const* mk, double* part, cudaStream_t st) {
+    if (nr == 0 || ns == 0) return cudaSuccess;
+    if (b % TP_K != 0 || nr % b != 0) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
+    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part);
     counted(1);
     return cudaGetLastError();
 }

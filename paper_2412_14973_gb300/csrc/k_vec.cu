@@ -8,33 +8,13 @@
 // per-block partials in a fixed order, so results are bitwise reproducible.
 #include "internal.h"
 #include "solver_dev.h"
+#include "reduce.h"
 
 namespace tlr {
 
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-wide sum of v (blockDim.x == kRedThreads); result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-        r = warp_sum(r);
-    }
-    __syncthreads();
-    return r;
-}
-
 // Sum of part[i * stride + k] over i < nblk by warp 0 in a fixed order; every
 // block that calls this obtains the same value.  Result broadcast via shared.
 __device__ __forceinline__ double sum_partials(const double* part, int nblk, int stride, int k, double* sh1) {
@@ -49,22 +29,6 @@ __device__ __forceinline__ double sum_partials(const double* part, int nblk, int
     __syncthreads();
     return r;
 }
-
-// Per-thread partial sum: FP32 terms accumulated with Knuth's two-sum
-// compensation (error-free transformation), so a thread's partial is as good
-// as an FP64 sum of its FP32 terms while costing FP32 adds only; partials are
-// then combined in FP64.  Elementwise FP64 multiply-adds would cost far more on
-// this part than the memory traffic they sit on.
-struct Acc {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = s + x;
-        const float z = t - s;
-        c += (s - (t - z)) + (x - z);
-        s = t;
-    }
-    __device__ __forceinline__ double val() const { return (double)s + (double)c; }
-};
 
 #define GRID_STRIDE(i, n) \
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
@@ -656,13 +620,15 @@ __global__ void __launch_bounds__(kRedThreads) k_pair_prep(SolverDev S, double r
 }
 
 // one thread: accept the pair (s, y) when alpha > 0 and <s,y> > 1e-12 |s||y|;
-// record f = 0.5 ||R||^2 from the residual-norm partials.
-__global__ void __launch_bounds__(kRedThreads) k_pair_accept(SolverDev S, const double* part3, const double* partf) {
+// record f = 0.5 ||R||^2 from the nf residual-norm partials.
+__global__ void __launch_bounds__(kRedThreads) k_pair_accept(SolverDev S, const double* part3, const double* partf,
+                                                             int nf) {
     __shared__ double sh[32];
     double v[4];
     for (int k = 0; k < 4; ++k) {
         double a = 0.0;
-        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) a += k < 3 ? part3[i * 3 + k] : partf[i];
+        const int nb = k < 3 ? kRedBlocks : nf;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) a += k < 3 ? part3[i * 3 + k] : partf[i];
         v[k] = block_sum(a, sh);
     }
     if (threadIdx.x != 0) return;
@@ -784,8 +750,8 @@ cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStrea
     counted(1);
     return cudaGetLastError();
 }
-cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, cudaStream_t st) {
-    k_pair_accept<<<1, kRedThreads, 0, st>>>(S, part3, partf);
+cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, int nf, cudaStream_t st) {
+    k_pair_accept<<<1, kRedThreads, 0, st>>>(S, part3, partf, nf);
     counted(1);
     return cudaGetLastError();
 }

@@ -47,7 +47,7 @@ cudaError_t sv_step_residual(cf* R, const cf* A1, const cf* A2, long long n, con
                              double* partf, cudaStream_t st);
 cudaError_t sv_step_theta(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStream_t st);
-cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, cudaStream_t st);
+cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, int nf, cudaStream_t st);
 cudaError_t sv_admm_zu(const SolverDev& S, double lam, double rho, cudaStream_t st);
 
 }  // namespace tlr
