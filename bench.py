@@ -231,6 +231,8 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the frequencies are spread over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=3)
+    ap.add_argument("--bench-iters", type=int, default=20,
+                    help="CG iterations of the eq. (4) benchmark solver timed on frequency 0 (0: skip)")
     ap.add_argument("--serving", type=int, default=0,
                     help="also serve this many per-frequency requests of the serving mix (nr 1024-8192)")
     args = ap.parse_args()
@@ -434,6 +436,23 @@ def main():
                "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
                "accuracy": "both paths within 1e-5 (FP32) / 1e-5 (BF16x3, measured) of the FP64 oracle per operator; see tests"}
 
+    # the eq. (4) benchmark solver (warm-start stage) on frequency 0's handle:
+    # G = D^H D and D^H U once, then one nr^3 complex product per CG iteration
+    bsolve = None
+    if args.bench_iters > 0 and rank == 0:
+        Xb = torch.empty((NR, NR), dtype=torch.complex64, device=dev)
+        T.tlr_mdd_set_data(handles[0], D[0], U[0], T.TLR_MEM_DEVICE)
+        T.tlr_mdd_benchmark_solve(handles[0], 0.1, 2, 0.0, Xb)          # warm-up
+        bst = T.tlr_mdd_benchmark_solve(handles[0], 0.1, args.bench_iters, 0.0, Xb)
+        fl = 2 * 8.0 * NR * NR * NR + bst.iters * 8.0 * NR ** 3
+        tf = fl / (bst.gpu_ms / 1e3) / 1e12
+        bsolve = {"nr": NR, "ns": NR, "lambda": 0.1, "iters": bst.iters, "ms": round(bst.gpu_ms, 2),
+                  "ms_per_iter": round(bst.gpu_ms / max(1, bst.iters + 2), 3),
+                  "tflops": round(tf, 1), "frac": round(tf / roof["peak"], 4) if args.precision != "fp32" else None,
+                  "rel_res": bst.rel_res,
+                  "flops": "8 nr^2 ns (D^H D) + 8 nr^2 ns (D^H U) + iters x 8 nr^3, complex-counted"}
+        del Xb
+
     # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
     cpu = None
     acc = None
@@ -492,6 +511,8 @@ def main():
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "accuracy": acc, "fp32_comparison": cmp,
     }
+    if bsolve is not None:
+        line["benchmark_solver"] = bsolve
     if serve is not None:
         line["serving"] = serve
     print(json.dumps(line), flush=True)

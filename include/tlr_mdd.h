@@ -47,7 +47,7 @@ extern "C" {
 
 /* ---- precision of the complex contractions ---- */
 #define TLR_PREC_FP32   0  /* FP32 SIMT (CUDA cores), FP32 accumulation */
-#define TLR_PREC_BF16X3 1  /* tcgen05 tensor cores: BF16 hi/lo split (3 products), 3M complex, FP32 accumulation */
+#define TLR_PREC_BF16X3 1  /* tcgen05 tensor cores: BF16 hi/lo split (3 products), 4M complex, FP32 accumulation */
 
 /* ---- diagonal tile representation (eq. 6 / eq. 7) ---- */
 #define TLR_DIAG_RULE     0  /* dense iff k_ii >= tile/4 */
@@ -198,6 +198,30 @@ int tlr_mdd_solve_query(tlr_mdd_t* h);
 /* Waits for the pending solve, fills stats (HOST, may be NULL) and returns its
  * status (TLR_ERR_NONFINITE, TLR_ERR_TIMEOUT, ...). */
 int tlr_mdd_solve_wait(tlr_mdd_t* h, tlr_mdd_stats_t* stats);
+
+/* Benchmark solver of eq. (4) (least-squares preconditioned MDD) on the
+ * handle's data: min_Z 0.5 ||D-hat P Z - U-hat||_F^2 + lambda ||Z||_F^2 with
+ * P Z = (Z + Z^T)/2, solved by conjugate gradients on its normal equations
+ * P(D-hat^H D-hat P(Z)) + 2 lambda Z = P(D-hat^H U-hat) (real inner product
+ * Re tr(A^H B)) from Z = 0, for at most `iters` iterations, stopping once
+ * ||residual|| <= tol ||right-hand side||.  The iterates are symmetric, so
+ * the result X = P Z = Z is written to X: DEVICE complex64 nr x nr, Hilbert
+ * order (like X_h), row-major.  D-hat^H D-hat is formed once; every
+ * iteration is one nr x nr x nr complex product in the handle's precision.
+ * Work memory (6 nr^2 complex64, plus packed operands on the tensor-core
+ * path) is allocated on the handle's stream and released before return; the
+ * call synchronises.  lambda < 0 or non-finite, iters < 0, tol < 0, X NULL:
+ * TLR_ERR_ARG; a pending solve on the handle: TLR_ERR_STATE.
+ * stats (HOST, may be NULL): iterations taken, final ||r|| / ||b||, device
+ * time of the whole call. */
+typedef struct {
+    int32_t iters;
+    int32_t status;
+    double rel_res;
+    double gpu_ms;
+} tlr_mdd_bench_stats_t;
+int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double tol, void* X,
+                            tlr_mdd_bench_stats_t* stats);
 
 /* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);

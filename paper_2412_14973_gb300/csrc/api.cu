@@ -1304,6 +1304,177 @@ int tlr_mdd_adjoint(tlr_mdd_t* h, const void* V, void* G) {
     return TLR_OK;
 }
 
+// Benchmark solver of eq. (4) on the handle's data: conjugate gradients on
+// P(G P(Z)) + 2 lambda Z = P(D-hat^H U-hat) with G = D-hat^H D-hat formed once.
+// In the receiver-major panels D-hat^H D-hat = conj(Dfrak) Dfrak^T and
+// D-hat^H U-hat = conj(Dfrak) Ufrak^T.  The iterates stay exactly symmetric,
+// so X = P(Z) = Z.
+int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double tol, void* X,
+                            tlr_mdd_bench_stats_t* stats) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!X) FAIL(h, TLR_ERR_ARG, "X is NULL");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda) || iters < 0 || !(tol >= 0.0))
+        FAIL(h, TLR_ERR_ARG, "lambda must be finite and >= 0, iters >= 0, tol >= 0");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
+    const Layout& L = h->L;
+    const int n = (int)L.nr, ns = (int)L.ns;
+    const size_t n2 = (size_t)n * n;
+    const bool tc = h->d.precision == TLR_PREC_BF16X3;
+    const int np = cg_partials(n);
+    // work arrays: G, x, r, p, y, Ap; partials; scalars; tables; packed operands (tensor cores)
+    const size_t pk = tc ? (size_t)std::max(packed_bytes(n, ns, kPackTRA), packed_bytes(n, n, kPackTRA)) : 0;
+    const size_t tab = 4096;
+    const size_t bytes = 6 * n2 * sizeof(cf) + (size_t)np * sizeof(double) + 64 + tab + 2 * pk + 16 * 256;
+    char* buf = nullptr;
+    CK(h, cudaMallocAsync((void**)&buf, bytes, h->st));
+    Arena a;
+    a.base = buf;
+    cf* G = a.take<cf>(n2);
+    cf* x = a.take<cf>(n2);
+    cf* r = a.take<cf>(n2);
+    cf* pv = a.take<cf>(n2);
+    cf* y = a.take<cf>(n2);
+    cf* Ap = a.take<cf>(n2);
+    double* part = a.take<double>(np);
+    double* sc = a.take<double>(8);
+    char* tables = a.take<char>(tab);
+    char* pkA = tc ? a.take<char>(pk) : nullptr;
+    char* pkB = tc ? a.take<char>(pk) : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto blank = []() {
+        GProb q;
+        memset(&q, 0, sizeof(q));
+        return q;
+    };
+    // three products: G = conj(D) D^T, Bm = conj(D) U^T, y = G p
+    GemmLaunch GL[3];
+    if (!tc) {
+        GProb q[3] = {blank(), blank(), blank()};
+        q[0].t[0] = term(h->Dt, ns, h->Dt, ns, nullptr, ns, true, false);
+        q[1].t[0] = term(h->Dt, ns, h->Ut, ns, nullptr, ns, true, false);
+        q[2].t[0] = term(G, n, pv, n, nullptr, n, false, false);
+        cf* outs[3] = {G, y, y};
+        for (int i = 0; i < 3; ++i) {
+            q[i].nt = 1;
+            q[i].M = q[i].N = n;
+            q[i].C = outs[i];
+            q[i].ldc = n;
+        }
+        GProb* dq = reinterpret_cast<GProb*>(tables);
+        e = cudaMemcpyAsync(dq, q, sizeof(q), cudaMemcpyHostToDevice, h->st);
+        for (int i = 0; i < 3; ++i) {
+            GL[i].d_probs = dq + i;
+            GL[i].nprob = 1;
+            GL[i].maxM = GL[i].maxN = n;
+            GL[i].maxK = i < 2 ? ns : n;
+            GL[i].amode = A_MK;
+            GL[i].bmode = i < 2 ? B_NK : B_KN;
+            GL[i].epi = EPI_STORE;
+            GL[i].prec = TLR_PREC_FP32;
+            GL[i].err = h->ints + SI_COUNT + 1;
+        }
+    } else {
+        // pack jobs: 0 conj(D) (A, MK) -> pkA; 1 D (B, rows n) -> pkB; 2 U (B) -> pkB;
+        // 3 G (A, MK) -> pkA; 4 p (B; p is symmetric, so its rows serve) -> pkB
+        PackJob J[5];
+        const cf* src[5] = {h->Dt, h->Dt, h->Ut, G, pv};
+        const int Ks[5] = {ns, ns, ns, n, n};
+        for (int i = 0; i < 5; ++i) {
+            J[i].src = src[i];
+            J[i].ld = Ks[i];
+            J[i].g_row = nullptr;
+            J[i].g_k = nullptr;
+            J[i].kcontig = 1;
+            J[i].sgn = i == 0 ? -1.f : 1.f;
+            J[i].R = n;
+            J[i].K = Ks[i];
+            J[i].TR = (i == 0 || i == 3) ? kPackTRA : kPackTRB;
+            J[i].dst = (i == 0 || i == 3) ? (void*)pkA : (void*)pkB;
+        }
+        PProb q[3];
+        memset(q, 0, sizeof(q));
+        cf* outs[3] = {G, y, y};
+        for (int i = 0; i < 3; ++i) {
+            q[i].t[0].A = pkA;
+            q[i].t[0].B = pkB;
+            q[i].t[0].K = i < 2 ? ns : n;
+            q[i].nt = 1;
+            q[i].M = q[i].N = n;
+            q[i].C = outs[i];
+            q[i].ldc = n;
+        }
+        PProb* dq = reinterpret_cast<PProb*>(tables);
+        PackJob* dj = reinterpret_cast<PackJob*>(tables + 1024);
+        e = cudaMemcpyAsync(dq, q, sizeof(q), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dj, J, sizeof(J), cudaMemcpyHostToDevice, h->st);
+        auto items = [](long long R, long long K, int TR) {
+            return (((R + TR - 1) / TR * TR) << 32) | ((K + 15) / 16 * 2);
+        };
+        const int first[3] = {0, 2, 4}, cnt[3] = {2, 1, 1};
+        for (int i = 0; i < 3; ++i) {
+            GL[i].d_pprobs = dq + i;
+            GL[i].d_jobs = dj + first[i];
+            GL[i].njobs = cnt[i];
+            GL[i].max_items = items(n, i < 2 ? ns : n, kPackTRB);
+            GL[i].nprob = 1;
+            GL[i].maxM = GL[i].maxN = n;
+            GL[i].maxK = i < 2 ? ns : n;
+            GL[i].epi = EPI_STORE;
+            GL[i].prec = TLR_PREC_BF16X3;
+            GL[i].err = h->ints + SI_COUNT + 1;
+        }
+        static_assert(sizeof(PProb) * 3 <= 1024 && sizeof(PackJob) * 5 <= 3072, "table slots");
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->st);
+    if (e == cudaSuccess) e = gemm_any(GL[0], h->st);                          // G
+    if (e == cudaSuccess) e = gemm_any(GL[1], h->st);                          // Bm -> y
+    if (e == cudaSuccess) e = cg_sym(y, nullptr, 0.f, r, n, nullptr, h->st);   // b = P(Bm) -> r
+    if (e == cudaSuccess && tc) {                                              // G packed once, as A
+        PackJob* dj = reinterpret_cast<PackJob*>(tables + 1024);
+        e = pack_operands(dj + 3, 1, (((long long)(n + kPackTRA - 1) / kPackTRA * kPackTRA) << 32) | ((n + 15) / 16 * 2),
+                          h->st);
+    }
+    if (e == cudaSuccess) e = cg_start(x, r, pv, n, part, sc, h->st);
+    const float s2 = (float)(2.0 * lambda);
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        e = gemm_any(GL[2], h->st);                                            // y = G p
+        if (e == cudaSuccess) e = cg_sym(y, pv, s2, Ap, n, part, h->st);       // Ap = P(y) + 2 lambda p
+        if (e == cudaSuccess) e = cg_iteration_tail(x, r, pv, Ap, n, tol, part, sc, h->st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, x, n2 * sizeof(cf), cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->st);
+    double hs[8] = {0};
+    int werr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&werr, h->ints + SI_COUNT + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    cudaFreeAsync(buf, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    CK(h, e);
+    if (werr != 0) {
+        CK(h, cudaMemsetAsync(h->ints + SI_COUNT + 1, 0, sizeof(int), h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        FAIL(h, TLR_ERR_TIMEOUT, "a tensor-core contraction timed out on a barrier wait");
+    }
+    // slots of k_cg.cu: rr 0, <p,Ap> 1, alpha 2, beta 3, ||b||^2 4, done 5, iterations 6
+    const double rel = hs[4] > 0.0 ? std::sqrt(hs[0] / hs[4]) : 0.0;
+    const int status = std::isfinite(hs[0]) ? TLR_OK : TLR_ERR_NONFINITE;
+    if (stats) {
+        stats->iters = (int32_t)hs[6];
+        stats->status = status;
+        stats->rel_res = rel;
+        stats->gpu_ms = ms;
+    }
+    if (status != TLR_OK) FAIL(h, status, "non-finite value in the benchmark solver");
+    return TLR_OK;
+}
+
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");

@@ -133,6 +133,17 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 long long rstep_ctas(int nr, int ns);
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
                   char* const* mk, double* part, cudaStream_t st);
+// Benchmark solver of eq. (4) (k_cg.cu): the symmetrising pass
+// out = P(y) + s2 p (with partials of <p, out> when part != nullptr; p may be
+// nullptr: out = P(y)), the start (x = 0, r = p = b with b in r on entry),
+// and the CG tail of one iteration (alpha, step, beta, direction) on device
+// scalars sc[8] (slots in k_cg.cu: rr, <p,Ap>, alpha, beta, ||b||^2, done,
+// iterations).  cg_partials(n) = partial slots needed.
+int cg_partials(int n);
+cudaError_t cg_sym(const cf* y, const cf* p, float s2, cf* out, int n, double* part, cudaStream_t st);
+cudaError_t cg_start(cf* x, cf* r, cf* p, int n, double* part, double* sc, cudaStream_t st);
+cudaError_t cg_iteration_tail(cf* x, cf* r, cf* p, const cf* Ap, int n, double tol, double* part, double* sc,
+                              cudaStream_t st);
 // bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
 // pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);

@@ -21,8 +21,13 @@ __all__ = [
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "TLR_NOALLOC_SCRATCH_BYTES",
     "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
+    "tlr_mdd_benchmark_solve", "BenchStats",
+    "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
+    "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
 
+TLR_OK, TLR_ERR_ARG, TLR_ERR_SHAPE, TLR_ERR_UNSUPPORTED = 0, -1, -2, -3
+TLR_ERR_NOMEM, TLR_ERR_CUDA, TLR_ERR_NONFINITE, TLR_ERR_TIMEOUT, TLR_ERR_STATE = -4, -5, -6, -7, -8
 TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
 TLR_DIAG_RULE, TLR_DIAG_LOWRANK, TLR_DIAG_DENSE, TLR_DIAG_PER_TILE = 0, 1, 2, 3
 TLR_RECIP_SYMMETRIC, TLR_RECIP_NONE = 0, 1
@@ -38,7 +43,7 @@ EXPORTED = [
     "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
-    "tlr_mdd_set_data",
+    "tlr_mdd_set_data", "tlr_mdd_benchmark_solve",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -66,6 +71,15 @@ class SolveOpts(C.Structure):
         ("lam0", C.c_double), ("decay", C.c_double), ("stages", C.c_int32),
         ("admm_iters", C.c_int32), ("lbfgs_iters", C.c_int32), ("memory", C.c_int32),
         ("rho", C.c_double), ("theta_memory", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class BenchStats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("status", C.c_int32),
+        ("rel_res", C.c_double),
+        ("gpu_ms", C.c_double),
     ]
 
 
@@ -134,6 +148,7 @@ def lib():
         L.tlr_mdd_solve_wait.argtypes = [vp, C.POINTER(Stats)]
         L.tlr_mdd_solve_wait.restype = i32
         L.tlr_mdd_set_data.argtypes = [vp, vp, vp, C.c_int32]
+        L.tlr_mdd_benchmark_solve.argtypes = [vp, C.c_double, C.c_int32, C.c_double, vp, C.POINTER(BenchStats)]
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
@@ -298,6 +313,14 @@ def tlr_mdd_timing_read():
 
 def tlr_mdd_launch_count() -> int:
     return lib().tlr_mdd_launch_count()
+
+
+def tlr_mdd_benchmark_solve(h, lam, iters, tol, X) -> BenchStats:
+    """Benchmark solver of eq. (4) on the handle's data; X (nr x nr, Hilbert
+    order) receives the symmetric solution."""
+    st = BenchStats()
+    _check(lib().tlr_mdd_benchmark_solve(h, float(lam), int(iters), float(tol), _ptr(X), C.byref(st)), h)
+    return st
 
 
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):

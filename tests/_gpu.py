@@ -78,6 +78,11 @@ class Gpu:
         T.tlr_mdd_unpermute_dense(self.h, dev(theta), X)
         return host(X)
 
+    def benchmark(self, lam, iters, tol):
+        X = torch.empty((self.lay.nr, self.lay.nr), dtype=torch.complex64, device="cuda")
+        st = T.tlr_mdd_benchmark_solve(self.h, lam, iters, tol, X)
+        return host(X), st
+
     def solve(self, theta0, **opts):
         th = dev(theta0)
         st = T.tlr_mdd_solve(self.h, th, T.solve_opts(**opts))

@@ -126,3 +126,46 @@ def test_config0_style_solve_runs_and_decreases():
     assert st.iters == 30
     f0 = operator.misfit(th0, lay, Dh, Uh)
     assert st.f_hist[-1] < 0.5 * f0
+
+
+def test_benchmark_solver_unitary_closed_form():
+    # D-hat unitary (ns = nr): on symmetric matrices the normal operator of
+    # eq. (4) is (1 + 2 lambda) I, so Z = P(D-hat^H U-hat) / (1 + 2 lambda)
+    import tlr_synth as synth
+    g = synth.rng(11)
+    n, lam = 12, 0.3
+    Dh = synth.haar_unitary(n, g)
+    Uh = synth.cn(g, (n, n))
+    Z = benchmark.solve_eq4(Dh, Uh, lam)
+    B = Dh.conj().T @ Uh
+    Zc = 0.5 * (B + B.T) / (1.0 + 2.0 * lam)
+    assert np.linalg.norm(Z - Zc) <= 1e-12 * np.linalg.norm(Zc)
+
+
+def test_benchmark_solver_matches_brute_force_real_system():
+    # the objective of eq. (4) as a real least-squares problem in the 2 n^2
+    # real unknowns of Z, built column by column from its definition and solved
+    # densely; the CG minimiser must agree
+    import tlr_synth as synth
+    g = synth.rng(12)
+    n, ns, lam = 3, 5, 0.05
+    Dh = synth.cn(g, (ns, n))
+    Uh = synth.cn(g, (ns, n))
+
+    def residual_vec(Z):
+        R = Dh @ (0.5 * (Z + Z.T))
+        return np.concatenate([R.real.ravel(), R.imag.ravel(),
+                               np.sqrt(2 * lam) * Z.real.ravel(), np.sqrt(2 * lam) * Z.imag.ravel()])
+
+    cols = []
+    for part in (1.0, 1j):
+        for idx in range(n * n):
+            E = np.zeros(n * n, np.complex128)
+            E[idx] = part
+            cols.append(residual_vec(E.reshape(n, n)))
+    A = np.stack(cols, axis=1)
+    rhs = np.concatenate([Uh.real.ravel(), Uh.imag.ravel(), np.zeros(2 * n * n)])
+    sol = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    Zb = (sol[: n * n] + 1j * sol[n * n:]).reshape(n, n)
+    Z = benchmark.solve_eq4(Dh, Uh, lam)
+    assert np.linalg.norm(Z - Zb) <= 1e-9 * np.linalg.norm(Zb)
