@@ -223,6 +223,41 @@ typedef struct {
 int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double tol, void* X,
                             tlr_mdd_bench_stats_t* stats);
 
+/* Tile rank rule of the hyper-parameter selection (Examples section, steps
+ * 1-3): the lower tiles of the nr x nr matrix X (DEVICE complex64, row-major;
+ * e.g. the benchmark solution in Hilbert order) in b x b tiles, their
+ * singular values (one-sided Jacobi SVD per tile on the GPU), v0 = the
+ * largest singular value over all tiles, and per tile the numerical rank
+ * k = #{sigma >= eps v0} (a tile with none below the threshold is full rank).
+ * ranks: HOST int32 [N (N + 1) / 2] in the descriptor's order (N diagonal
+ * tiles, then the pairs in the stacking order of tlr_mdd_theta_layout).
+ * entries (HOST, may be NULL): complex entries of the factors, sum over pairs
+ * of k (d_i + d_j) plus, per diagonal tile, b k, or b^2 where 4 k >= b (the
+ * diagonal rule); the entry count ratio is nr^2 / entries.  v0: HOST, may
+ * be NULL.  b <= 512 and nr % b == 0 (else TLR_ERR_SHAPE), 0 < eps <= 1.
+ * Allocates its work (about nr^2 / 2 complex64) on `stream`; synchronises. */
+int tlr_mdd_tile_ranks(const void* X, int64_t nr, int64_t b, double eps, int32_t* ranks, int64_t* entries,
+                       double* v0, void* stream);
+
+/* Tile size selection: among the candidate tile sizes (HOST int64 [ncand];
+ * those that do not divide nr or exceed 512 are skipped) the one whose rank
+ * rule gives the fewest factor entries (the largest entry count ratio); the
+ * first candidate wins ties.  best_b, best_entries: HOST. */
+int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, int32_t ncand, double eps,
+                        int64_t* best_b, int64_t* best_entries, void* stream);
+
+/* Warm start (hyper-parameter selection and initialisation section) for the
+ * handle's layout from X (DEVICE complex64 nr x nr, Hilbert order, e.g. the
+ * benchmark solution): for each pair (i > j) with rank k the truncated SVD
+ * X_ij ~ U_k Sigma_k V_k^H gives L = U_k Sigma_k^1/2 and R = conj(V_k)
+ * Sigma_k^1/2 (so L R^T = U_k Sigma_k V_k^H); a low-rank diagonal tile gets
+ * the Takagi form Q = conj(V_k) E_k Sigma_k^1/2, E = diag(V^T U)^1/2, whose
+ * Q Q^T is the same truncation (the Q Q^T = X_ii initialisation); a dense
+ * diagonal tile gets Z = X_ii.
+ * theta: DEVICE complex64 [n_theta].  Needs tile <= 512.  Allocates its work
+ * (2 b^2 complex64 per low-rank tile) on the handle's stream; synchronises. */
+int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta);
+
 /* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);
 

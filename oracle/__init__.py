@@ -21,6 +21,9 @@ arXiv 2412.14973 and cites the passage it follows:
                   search, lambda continuation.
 * ``benchmark``-- the preconditioned benchmark objective, eq. (4), solved by
                   conjugate gradients (a closed-form pin for one dense tile).
+* ``warmstart``-- the tile rank rule, the entry count and tile-size choice,
+                  and the SVD / Takagi warm start (hyper-parameter selection
+                  and initialisation section; Examples section, steps 1-3).
 
 Pins for every function live in ``tests/test_oracle_*.py`` (CPU only).
 """

@@ -1475,6 +1475,170 @@ int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double t
     return TLR_OK;
 }
 
+// Tile rank rule: the lower tiles (diagonal tiles, then the pairs in the
+// stacking order) of X in b x b tiles, their singular values by the tile SVD,
+// v0 = the largest of all, k = #{sigma >= eps v0}; entries = the number of
+// complex entries of the factors with dense diagonals where 4 k >= b.
+namespace {
+int tile_ranks_impl(const cf* X, int64_t nr, int64_t b, double eps, std::vector<int32_t>& ranks, int64_t* entries,
+                    double* v0, cudaStream_t st, std::string& err) {
+    const int N = (int)(nr / b), P = N * (N - 1) / 2, nt = N + P;
+    std::vector<int2> tl(nt);
+    for (int i = 0; i < N; ++i) tl[i] = make_int2(i, i);
+    for (int j = 0; j < N; ++j)
+        for (int i = j + 1; i < N; ++i) tl[N + j * N - j * (j + 1) / 2 + (i - j - 1)] = make_int2(i, j);
+    Arena a;
+    a.take<cf>(tile_svd_work_bytes(nt, (int)b, false) / sizeof(cf));
+    a.take<float>((size_t)nt * b);
+    a.take<int2>(nt);
+    a.take<int>(nt);
+    a.take<double>(1);
+    char* buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&buf, a.used, st);
+    if (e != cudaSuccess) {
+        err = std::string("tile ranks: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? TLR_ERR_NOMEM : TLR_ERR_CUDA;
+    }
+    Arena w;
+    w.base = buf;
+    cf* work = w.take<cf>(tile_svd_work_bytes(nt, (int)b, false) / sizeof(cf));
+    float* sig = w.take<float>((size_t)nt * b);
+    int2* dtl = w.take<int2>(nt);
+    int* dr = w.take<int>(nt);
+    double* dv0 = w.take<double>(1);
+    ranks.assign(nt, 0);
+    double hv0 = 0.0;
+    e = cudaMemcpyAsync(dtl, tl.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = tile_svd(X, nr, dtl, nt, (int)b, work, false, 30, 1e-5f, sig, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = rank_rule(sig, nt, (int)b, eps, dr, dv0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ranks.data(), dr, nt * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hv0, dv0, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        err = std::string("tile ranks: ") + cudaGetErrorString(e);
+        return TLR_ERR_CUDA;
+    }
+    int64_t ent = 0;
+    for (int i = 0; i < N; ++i) ent += 4LL * ranks[i] >= b ? b * b : b * ranks[i];
+    for (int p = 0; p < P; ++p) ent += 2 * b * (int64_t)ranks[N + p];
+    if (entries) *entries = ent;
+    if (v0) *v0 = hv0;
+    return TLR_OK;
+}
+}  // namespace
+
+int tlr_mdd_tile_ranks(const void* X, int64_t nr, int64_t b, double eps, int32_t* ranks, int64_t* entries,
+                       double* v0, void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!X || !ranks) FAIL(h, TLR_ERR_ARG, "X or ranks is NULL");
+    if (nr <= 0 || b <= 0 || b > 512 || nr % b != 0) FAIL(h, TLR_ERR_SHAPE, "need 0 < b <= 512 and nr % b == 0");
+    if (!(eps > 0.0) || !(eps <= 1.0)) FAIL(h, TLR_ERR_ARG, "eps must lie in (0, 1]");
+    std::vector<int32_t> r;
+    std::string err;
+    const int rc = tile_ranks_impl((const cf*)X, nr, b, eps, r, entries, v0, (cudaStream_t)stream, err);
+    if (rc) FAIL(h, rc, err);
+    std::copy(r.begin(), r.end(), ranks);
+    return TLR_OK;
+}
+
+int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, int32_t ncand, double eps,
+                        int64_t* best_b, int64_t* best_entries, void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!X || !candidates || !best_b || ncand <= 0) FAIL(h, TLR_ERR_ARG, "X, candidates or best_b is NULL");
+    if (!(eps > 0.0) || !(eps <= 1.0)) FAIL(h, TLR_ERR_ARG, "eps must lie in (0, 1]");
+    int64_t bb = 0, be = 0;
+    for (int c = 0; c < ncand; ++c) {
+        const int64_t b = candidates[c];
+        if (b <= 0 || b > 512 || nr % b != 0) continue;
+        std::vector<int32_t> r;
+        int64_t ent = 0;
+        std::string err;
+        const int rc = tile_ranks_impl((const cf*)X, nr, b, eps, r, &ent, nullptr, (cudaStream_t)stream, err);
+        if (rc) FAIL(h, rc, err);
+        if (bb == 0 || ent < be) {
+            bb = b;
+            be = ent;
+        }
+    }
+    if (bb == 0) FAIL(h, TLR_ERR_SHAPE, "no candidate divides nr (with 0 < b <= 512)");
+    *best_b = bb;
+    if (best_entries) *best_entries = be;
+    return TLR_OK;
+}
+
+// Warm start: the handle's layout decides each tile's form and rank; X is
+// cut into tiles and each low-rank tile initialised from its truncated SVD
+// (pairs: L = U Sigma^1/2, R = conj(V) Sigma^1/2; low-rank diagonals: the
+// Takagi form Q with Q Q^T the rank-k truncation), dense diagonals copied.
+int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!X || !theta) FAIL(h, TLR_ERR_ARG, "X or theta is NULL");
+    const Layout& L = h->L;
+    if (L.b > 512) FAIL(h, TLR_ERR_SHAPE, "warm start needs tile <= 512");
+    const int N = L.N, b = (int)L.b;
+    std::vector<int2> tl;
+    std::vector<WarmTile> wt;
+    for (int i = 0; i < N; ++i) {
+        WarmTile w{};
+        w.i = w.j = i;
+        w.offL = L.off_diag[i];
+        w.offR = 0;
+        if (L.dense[i]) {
+            w.kind = 2;
+            w.k = b;
+            w.svd = -1;
+        } else {
+            if (L.kd[i] == 0) continue;
+            w.kind = 1;
+            w.k = L.kd[i];
+            w.svd = (int)tl.size();
+            tl.push_back(make_int2(i, i));
+        }
+        wt.push_back(w);
+    }
+    for (int j = 0; j < N; ++j)
+        for (int i = j + 1; i < N; ++i) {
+            const int p = j * N - j * (j + 1) / 2 + (i - j - 1);
+            if (L.kp[p] == 0) continue;
+            WarmTile w{};
+            w.i = i;
+            w.j = j;
+            w.kind = 0;
+            w.k = L.kp[p];
+            w.offL = L.off_l[p];
+            w.offR = L.off_r[p];
+            w.svd = (int)tl.size();
+            tl.push_back(make_int2(i, j));
+            wt.push_back(w);
+        }
+    const int nsvd = (int)tl.size(), nw = (int)wt.size();
+    Arena a;
+    a.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), b, true) / sizeof(cf));
+    a.take<float>((size_t)std::max(1, nsvd) * b);
+    a.take<int>((size_t)std::max(1, nsvd) * b);
+    a.take<int2>(std::max(1, nsvd));
+    a.take<WarmTile>(std::max(1, nw));
+    char* buf = nullptr;
+    CK(h, cudaMallocAsync((void**)&buf, a.used, h->st));
+    Arena w;
+    w.base = buf;
+    cf* work = w.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), b, true) / sizeof(cf));
+    float* sig = w.take<float>((size_t)std::max(1, nsvd) * b);
+    int* ord = w.take<int>((size_t)std::max(1, nsvd) * b);
+    int2* dtl = w.take<int2>(std::max(1, nsvd));
+    WarmTile* dwt = w.take<WarmTile>(std::max(1, nw));
+    cudaError_t e = cudaSuccess;
+    if (nsvd) e = cudaMemcpyAsync(dtl, tl.data(), nsvd * sizeof(int2), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess && nw) e = cudaMemcpyAsync(dwt, wt.data(), nw * sizeof(WarmTile), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = tile_svd((const cf*)X, L.nr, dtl, nsvd, b, work, true, 30, 1e-5f, sig, ord, nullptr, h->st);
+    if (e == cudaSuccess) e = warm_fill((const cf*)X, L.nr, dwt, nw, b, work, sig, ord, (cf*)theta, h->st);
+    cudaFreeAsync(buf, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);   // the host tables above go out of scope
+    CK(h, e);
+    return TLR_OK;
+}
+
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");

@@ -144,6 +144,25 @@ cudaError_t cg_sym(const cf* y, const cf* p, float s2, cf* out, int n, double* p
 cudaError_t cg_start(cf* x, cf* r, cf* p, int n, double* part, double* sc, cudaStream_t st);
 cudaError_t cg_iteration_tail(cf* x, cf* r, cf* p, const cf* Ap, int n, double tol, double* part, double* sc,
                               cudaStream_t st);
+// Tile SVDs (k_svd.cu) for the rank rule and the warm start.  tile_svd: one
+// one-sided Jacobi SVD per listed b x b tile (tile (i, j) = rows i b.., cols
+// j b.. of the row-major X), b <= 512, work = tile_svd_work_bytes; sig[t b ..]
+// decreasing singular values, order[t b + m] the column of the m-th (may be
+// nullptr), sweeps[t] sweeps used (may be nullptr).  rank_rule: v0 = max
+// sigma, ranks[t] = #{sigma >= eps v0}.  warm_fill: the warm-start factors
+// (kinds: 0 pair L, R; 1 low-rank diagonal Q by the Takagi form; 2 dense Z =
+// tile) written into theta at the given offsets.
+struct WarmTile {
+    int i, j, kind, k;
+    long long offL, offR;   // theta offsets (R unused for diagonals)
+    int svd;                // index of the tile's SVD (-1 for dense)
+};
+size_t tile_svd_work_bytes(int ntiles, int b, bool vec);
+cudaError_t tile_svd(const cf* X, long long ldx, const int2* tiles, int ntiles, int b, cf* work, bool vec,
+                     int max_sweeps, float tol, float* sig, int* order, int* sweeps, cudaStream_t st);
+cudaError_t rank_rule(const float* sig, int ntiles, int b, double eps, int* ranks, double* v0, cudaStream_t st);
+cudaError_t warm_fill(const cf* X, long long ldx, const WarmTile* wt, int nt, int b, const cf* work, const float* sig,
+                      const int* order, cf* theta, cudaStream_t st);
 // bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
 // pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);

@@ -21,7 +21,7 @@ __all__ = [
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "TLR_NOALLOC_SCRATCH_BYTES",
     "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
-    "tlr_mdd_benchmark_solve", "BenchStats",
+    "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -43,7 +43,8 @@ EXPORTED = [
     "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
-    "tlr_mdd_set_data", "tlr_mdd_benchmark_solve",
+    "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
+    "tlr_mdd_warm_start",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -149,6 +150,11 @@ def lib():
         L.tlr_mdd_solve_wait.restype = i32
         L.tlr_mdd_set_data.argtypes = [vp, vp, vp, C.c_int32]
         L.tlr_mdd_benchmark_solve.argtypes = [vp, C.c_double, C.c_int32, C.c_double, vp, C.POINTER(BenchStats)]
+        L.tlr_mdd_tile_ranks.argtypes = [vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int64), C.POINTER(C.c_double), vp]
+        L.tlr_mdd_choose_tile.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_double,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
+        L.tlr_mdd_warm_start.argtypes = [vp, vp, vp]
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
@@ -321,6 +327,30 @@ def tlr_mdd_benchmark_solve(h, lam, iters, tol, X) -> BenchStats:
     st = BenchStats()
     _check(lib().tlr_mdd_benchmark_solve(h, float(lam), int(iters), float(tol), _ptr(X), C.byref(st)), h)
     return st
+
+
+def tlr_mdd_tile_ranks(X, nr, b, eps=0.01, stream=None):
+    """Numerical ranks of the lower b x b tiles of X (device, nr x nr): returns
+    (ranks in the descriptor's order, factor entry count, v0)."""
+    N = nr // b if b > 0 and nr % b == 0 else 0
+    r = (C.c_int32 * max(1, N * (N + 1) // 2))()
+    ent, v0 = C.c_int64(), C.c_double()
+    _check(lib().tlr_mdd_tile_ranks(_ptr(X), nr, b, float(eps), r, C.byref(ent), C.byref(v0), _stream(stream)))
+    return list(r)[: N * (N + 1) // 2], ent.value, v0.value
+
+
+def tlr_mdd_choose_tile(X, nr, candidates, eps=0.01, stream=None):
+    """Tile size with the fewest factor entries among ``candidates``: (b, entries)."""
+    c = (C.c_int64 * len(candidates))(*candidates)
+    bb, be = C.c_int64(), C.c_int64()
+    _check(lib().tlr_mdd_choose_tile(_ptr(X), nr, c, len(candidates), float(eps), C.byref(bb), C.byref(be),
+                                     _stream(stream)))
+    return bb.value, be.value
+
+
+def tlr_mdd_warm_start(h, X, theta):
+    """Warm-start factors (device theta) of the handle's layout from X (device, Hilbert order)."""
+    _check(lib().tlr_mdd_warm_start(h, _ptr(X), _ptr(theta)), h)
 
 
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
