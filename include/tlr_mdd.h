@@ -99,8 +99,22 @@ typedef struct {
     int32_t memory;          /* L-BFGS memory m (1..32) */
     double rho;              /* ADMM penalty rho > 0 */
     int32_t theta_memory;    /* TLR_MEM_* of theta_inout */
-    int32_t reserved;
+    int32_t flags;           /* TLR_SOLVE_* bits, 0 by default */
 } tlr_mdd_solve_opts_t;
+
+/* Checkpoint / resume (the paper has none).  The L-BFGS memory is cleared at
+ * every x-update, so the solver's state at an ADMM-iteration boundary is
+ * theta, z and u.  TLR_SOLVE_RESUME: start from the handle's z, u (left by
+ * the previous solve on the handle, or set with tlr_mdd_set_state) instead of
+ * z = theta, u = 0.  TLR_SOLVE_REFRESH: recompute the residual and the factor
+ * products from theta at every x-update after the first of the call (one
+ * extra forward product and gradient per ADMM iteration) instead of carrying
+ * the in-place updates; with it a solve split at ADMM-iteration boundaries
+ * reproduces the uninterrupted solve bit for bit.  To continue a schedule at
+ * lambda stage s, pass lam0 * decay^s (exactly) as lam0 and the remaining
+ * stages; to split inside a stage, run its ADMM iterations in two calls. */
+#define TLR_SOLVE_RESUME  1
+#define TLR_SOLVE_REFRESH 2
 
 #define TLR_MAX_HIST 1024
 typedef struct {
@@ -257,6 +271,14 @@ int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, in
  * theta: DEVICE complex64 [n_theta].  Needs tile <= 512.  Allocates its work
  * (2 b^2 complex64 per low-rank tile) on the handle's stream; synchronises. */
 int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta);
+
+/* Solver state for checkpoint / resume: z and u of the ADMM split (eq.
+ * 22-24, scaled dual), DEVICE complex64 [n_theta] each in theta's stacking
+ * order.  get: copies the handle's current z, u out (after a solve on the
+ * handle); set: loads them for a following solve with TLR_SOLVE_RESUME.
+ * Both run on the handle's stream and synchronise. */
+int tlr_mdd_get_state(tlr_mdd_t* h, void* z, void* u);
+int tlr_mdd_set_state(tlr_mdd_t* h, const void* z, const void* u);
 
 /* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);

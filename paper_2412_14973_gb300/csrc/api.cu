@@ -113,10 +113,10 @@ struct HostStats {
 
 struct GraphKey {
     double lam0 = -1, decay = 0, rho = 0;
-    int stages = -1, admm = -1, lbfgs = -1, mem = -1, timing = -1;
+    int stages = -1, admm = -1, lbfgs = -1, mem = -1, timing = -1, flags = -1;
     bool operator==(const GraphKey& o) const {
         return lam0 == o.lam0 && decay == o.decay && rho == o.rho && stages == o.stages && admm == o.admm &&
-               lbfgs == o.lbfgs && mem == o.mem && timing == o.timing;
+               lbfgs == o.lbfgs && mem == o.mem && timing == o.timing && flags == o.flags;
     }
 };
 
@@ -1639,6 +1639,26 @@ int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
     return TLR_OK;
 }
 
+int tlr_mdd_get_state(tlr_mdd_t* h, void* z, void* u) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!z || !u) FAIL(h, TLR_ERR_ARG, "z or u is NULL");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
+    CK(h, panel_to_theta(h->pm, h->z, (cf*)z, h->st));
+    CK(h, panel_to_theta(h->pm, h->u, (cf*)u, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return TLR_OK;
+}
+
+int tlr_mdd_set_state(tlr_mdd_t* h, const void* z, const void* u) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (!z || !u) FAIL(h, TLR_ERR_ARG, "z or u is NULL");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
+    CK(h, theta_to_panel(h->pm, (const cf*)z, h->z, h->st));
+    CK(h, theta_to_panel(h->pm, (const cf*)u, h->u, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return TLR_OK;
+}
+
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");
@@ -1743,6 +1763,7 @@ static int check_opts(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     if (o->memory < 1 || o->memory > 32) FAIL(h, TLR_ERR_ARG, "memory must lie in [1, 32]");
     if (!(o->rho > 0.0) || o->stages < 0 || o->admm_iters < 0 || o->lbfgs_iters < 0 || !(o->lam0 >= 0.0))
         FAIL(h, TLR_ERR_ARG, "invalid solver options");
+    if (o->flags & ~(TLR_SOLVE_RESUME | TLR_SOLVE_REFRESH)) FAIL(h, TLR_ERR_ARG, "unknown solver flags");
     return TLR_OK;
 }
 
@@ -1784,16 +1805,27 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     const double rho = o->rho;
 
     CK(h, theta_to_panel(h->pm, h->th_io, h->x, h->st));
-    CK(h, sv_admm_init(S, h->st));
+    if (o->flags & TLR_SOLVE_RESUME)
+        CK(h, sv_admm_resume(S, h->st));
+    else
+        CK(h, sv_admm_init(S, h->st));
     int rc = forward(h, false);
     if (rc) return rc;
     CK(h, sv_norm_part(h->R, nrs, partf, h->st));
     CK(h, sv_record_f0(S, partf, h->st));
     rc = gradient(h);
     if (rc) return rc;
+    int xu = 0;   // x-updates of this call
     for (int s = 0; s < o->stages; ++s) {
         const double lam = o->lam0 * std::pow(o->decay, (double)s);
-        for (int it = 0; it < o->admm_iters; ++it) {
+        for (int it = 0; it < o->admm_iters; ++it, ++xu) {
+            if ((o->flags & TLR_SOLVE_REFRESH) && xu > 0) {
+                // fresh residual, products and gradient at theta (what a resumed call starts from)
+                rc = forward(h, false);
+                if (rc) return rc;
+                rc = gradient(h);
+                if (rc) return rc;
+            }
             CK(h, sv_xupdate_start(S, rho, h->st));
             for (int t = 0; t < o->lbfgs_iters; ++t) {
                 CK(h, sv_direction(S, h->st));
@@ -1860,6 +1892,7 @@ static int enqueue_body(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     k.admm = o->admm_iters;
     k.lbfgs = o->lbfgs_iters;
     k.mem = o->memory;
+    k.flags = o->flags;
     {
         std::lock_guard<std::mutex> lk(g_tmu);
         k.timing = g_timing ? 1 : 0;

@@ -17,7 +17,7 @@ namespace tlr {
 
 namespace {
 
-constexpr int SVD_THREADS = 256;
+constexpr int SVD_THREADS = 1024;   // 32 warps: the pairs of a round run in parallel
 
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll

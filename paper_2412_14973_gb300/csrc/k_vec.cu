@@ -680,6 +680,18 @@ __global__ void k_admm_init(SolverDev S) {
     }
 }
 
+// resumed solve: v = z - u from the stored split; counters cleared
+__global__ void k_admm_resume(SolverDev S) {
+    GRID_STRIDE(i, S.n2) S.v[i] = S.z[i] - S.u[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.ints[SI_CNT] = 0;
+        S.ints[SI_NEWEST] = 0;
+        S.ints[SI_ITERS] = 0;
+        S.ints[SI_RESTARTS] = 0;
+        S.ints[SI_STATUS] = 0;
+    }
+}
+
 // record f0 = 0.5 ||R||^2
 __global__ void k_record_f0(SolverDev S, const double* partf) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -704,6 +716,11 @@ cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t s
 }
 cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st) {
     k_admm_init<<<1024, 256, 0, st>>>(S);
+    counted(1);
+    return cudaGetLastError();
+}
+cudaError_t sv_admm_resume(const SolverDev& S, cudaStream_t st) {
+    k_admm_resume<<<1024, 256, 0, st>>>(S);
     counted(1);
     return cudaGetLastError();
 }

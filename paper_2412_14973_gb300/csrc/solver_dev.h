@@ -38,6 +38,7 @@ struct SolverDev {
 cudaError_t sv_norm_part(const cf* R, long long n, double* part, cudaStream_t st);
 cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t st);
 cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st);
+cudaError_t sv_admm_resume(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st);
 cudaError_t sv_direction(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st);

@@ -22,6 +22,7 @@ __all__ = [
     "tlr_mdd_adjoint_noalloc", "TLR_NOALLOC_SCRATCH_BYTES",
     "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
     "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
+    "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -29,6 +30,7 @@ __all__ = [
 TLR_OK, TLR_ERR_ARG, TLR_ERR_SHAPE, TLR_ERR_UNSUPPORTED = 0, -1, -2, -3
 TLR_ERR_NOMEM, TLR_ERR_CUDA, TLR_ERR_NONFINITE, TLR_ERR_TIMEOUT, TLR_ERR_STATE = -4, -5, -6, -7, -8
 TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
+TLR_SOLVE_RESUME, TLR_SOLVE_REFRESH = 1, 2
 TLR_DIAG_RULE, TLR_DIAG_LOWRANK, TLR_DIAG_DENSE, TLR_DIAG_PER_TILE = 0, 1, 2, 3
 TLR_RECIP_SYMMETRIC, TLR_RECIP_NONE = 0, 1
 TLR_MEM_DEVICE, TLR_MEM_HOST = 0, 1
@@ -44,7 +46,7 @@ EXPORTED = [
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
     "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
-    "tlr_mdd_warm_start",
+    "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -71,7 +73,7 @@ class SolveOpts(C.Structure):
     _fields_ = [
         ("lam0", C.c_double), ("decay", C.c_double), ("stages", C.c_int32),
         ("admm_iters", C.c_int32), ("lbfgs_iters", C.c_int32), ("memory", C.c_int32),
-        ("rho", C.c_double), ("theta_memory", C.c_int32), ("reserved", C.c_int32),
+        ("rho", C.c_double), ("theta_memory", C.c_int32), ("flags", C.c_int32),
     ]
 
 
@@ -155,6 +157,8 @@ def lib():
         L.tlr_mdd_choose_tile.argtypes = [vp, C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_double,
                                           C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
         L.tlr_mdd_warm_start.argtypes = [vp, vp, vp]
+        L.tlr_mdd_get_state.argtypes = [vp, vp, vp]
+        L.tlr_mdd_set_state.argtypes = [vp, vp, vp]
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
@@ -351,6 +355,16 @@ def tlr_mdd_choose_tile(X, nr, candidates, eps=0.01, stream=None):
 def tlr_mdd_warm_start(h, X, theta):
     """Warm-start factors (device theta) of the handle's layout from X (device, Hilbert order)."""
     _check(lib().tlr_mdd_warm_start(h, _ptr(X), _ptr(theta)), h)
+
+
+def tlr_mdd_get_state(h, z, u):
+    """Copy the handle's ADMM state z, u (device, theta order) out."""
+    _check(lib().tlr_mdd_get_state(h, _ptr(z), _ptr(u)), h)
+
+
+def tlr_mdd_set_state(h, z, u):
+    """Load z, u (device, theta order) for a solve with TLR_SOLVE_RESUME."""
+    _check(lib().tlr_mdd_set_state(h, _ptr(z), _ptr(u)), h)
 
 
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
