@@ -280,6 +280,29 @@ int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta);
 int tlr_mdd_get_state(tlr_mdd_t* h, void* z, void* u);
 int tlr_mdd_set_state(tlr_mdd_t* h, const void* z, const void* u);
 
+/* Time <-> frequency stacks (Numerical Examples: the separated wavefields are
+ * transformed to the frequency domain and the MDD solved per frequency; the
+ * Green's function returns to time-offset gathers by the inverse transform).
+ * Traces are trace-major: x_t DEVICE float [ntr][nt] (for data tr = s nr + r,
+ * for X tr = a nr + b).  Stacks are frequency-major: X_w DEVICE complex64
+ * [nf][ntr], so frequency f is one row-major panel (ns x nr for D and U,
+ * nr x nr for X).  time_to_freq: X_w[f][tr] = sum_t x_t[tr][t]
+ * exp(-2 pi i (f0 + f) t / nt), the bins f0 .. f0 + nf - 1 of the real DFT
+ * (f0 + nf <= nt / 2 + 1).  freq_to_time: the inverse real DFT of the band
+ * (bins outside it zero, the imaginary parts of bins 0 and nt/2 ignored), with
+ * the factor 1 / nt, so freq_to_time(time_to_freq(x)) = x when the band is the
+ * whole spectrum.  Real FFTs by cuFFT over chunks of traces (work memory about
+ * 256 MB plus cuFFT's own, allocated and released per call); synchronises.
+ * Invalid sizes: TLR_ERR_ARG. */
+int tlr_mdd_time_to_freq(const float* x_t, int64_t ntr, int64_t nt, int64_t f0, int64_t nf, void* X_w,
+                         void* stream);
+int tlr_mdd_freq_to_time(const void* X_w, int64_t ntr, int64_t nt, int64_t f0, int64_t nf, float* x_t,
+                         void* stream);
+/* alpha = max |D(omega)| over a whole stack (n complex64 values, DEVICE): the
+ * normalisation of the hyper-parameter section, to pass as desc.alpha to every
+ * frequency of the stack.  alpha: HOST.  Synchronises. */
+int tlr_mdd_stack_alpha(const void* D_w, int64_t n, double* alpha, void* stream);
+
 /* X = S X_h S^T in natural receiver order (eq. 11), nr x nr complex64 DEVICE. */
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);
 

@@ -27,6 +27,11 @@ def _nvcc() -> str:
     return "nvcc"
 
 
+def _which(cmd: str) -> str:
+    import shutil
+    return shutil.which(cmd) or "/usr/local/cuda/bin/nvcc"
+
+
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
 
@@ -67,7 +72,10 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
     relink = force or bool(jobs) or not os.path.exists(LIB) or \
         any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
     if relink:
-        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs])
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc if os.path.isabs(nvcc) else
+                                                                              _which(nvcc)))), "lib64")
+        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs, "-L" + cuda_lib, "-lcufft",
+             "-Xlinker", "-rpath", "-Xlinker", cuda_lib])
     return LIB
 
 

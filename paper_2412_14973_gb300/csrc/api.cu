@@ -1659,6 +1659,56 @@ int tlr_mdd_set_state(tlr_mdd_t* h, const void* z, const void* u) {
     return TLR_OK;
 }
 
+namespace {
+int check_stack(long long ntr, long long nt, long long f0, long long nf, std::string& err) {
+    if (ntr <= 0 || nt <= 0 || nt > 0x7fffffffLL || f0 < 0 || nf <= 0 || f0 + nf > nt / 2 + 1) {
+        err = "need ntr > 0, 0 < nt < 2^31, f0 >= 0, nf > 0, f0 + nf <= nt / 2 + 1";
+        return TLR_ERR_ARG;
+    }
+    return TLR_OK;
+}
+}  // namespace
+
+int tlr_mdd_time_to_freq(const float* x_t, int64_t ntr, int64_t nt, int64_t f0, int64_t nf, void* X_w,
+                         void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!x_t || !X_w) FAIL(h, TLR_ERR_ARG, "x_t or X_w is NULL");
+    std::string err;
+    int rc = check_stack(ntr, nt, f0, nf, err);
+    if (rc) FAIL(h, rc, err);
+    rc = fft_stack(true, x_t, nullptr, ntr, nt, f0, nf, (cf*)X_w, nullptr, (cudaStream_t)stream, err);
+    if (rc) FAIL(h, rc, err);
+    return TLR_OK;
+}
+
+int tlr_mdd_freq_to_time(const void* X_w, int64_t ntr, int64_t nt, int64_t f0, int64_t nf, float* x_t,
+                         void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!x_t || !X_w) FAIL(h, TLR_ERR_ARG, "x_t or X_w is NULL");
+    std::string err;
+    int rc = check_stack(ntr, nt, f0, nf, err);
+    if (rc) FAIL(h, rc, err);
+    rc = fft_stack(false, nullptr, (const cf*)X_w, ntr, nt, f0, nf, nullptr, x_t, (cudaStream_t)stream, err);
+    if (rc) FAIL(h, rc, err);
+    return TLR_OK;
+}
+
+int tlr_mdd_stack_alpha(const void* D_w, int64_t n, double* alpha, void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!D_w || !alpha || n <= 0) FAIL(h, TLR_ERR_ARG, "D_w or alpha is NULL, or n <= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* buf = nullptr;
+    CK(h, cudaMallocAsync((void**)&buf, (kRedBlocks + 1) * sizeof(double), st));
+    double a = 0.0;
+    cudaError_t e = max_abs2((const cf*)D_w, n, buf + 1, kRedBlocks, buf, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&a, buf, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    CK(h, e);
+    *alpha = a;
+    return TLR_OK;
+}
+
 int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");

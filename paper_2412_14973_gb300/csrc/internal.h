@@ -163,6 +163,12 @@ cudaError_t tile_svd(const cf* X, long long ldx, const int2* tiles, int ntiles, 
 cudaError_t rank_rule(const float* sig, int ntiles, int b, double eps, int* ranks, double* v0, cudaStream_t st);
 cudaError_t warm_fill(const cf* X, long long ldx, const WarmTile* wt, int nt, int b, const cf* work, const float* sig,
                       const int* order, cf* theta, cudaStream_t st);
+// Time <-> frequency stack (fourier.cu): forward: x_t_in [ntr][nt] real ->
+// X_out [nf][ntr], the bins f0 .. f0 + nf - 1 of the unnormalised real DFT;
+// inverse: X_in [nf][ntr] (band, zero elsewhere) -> x_t_out [ntr][nt] with
+// the 1 / nt factor.  Synchronises (returns a TLR_* code, message in err).
+int fft_stack(bool forward, const float* x_t_in, const cf* X_in, long long ntr, long long nt, long long f0,
+              long long nf, cf* X_out, float* x_t_out, cudaStream_t st, std::string& err);
 // bytes of one operand (R rows x K) in the packed tile format with TR-row tiles;
 // pack_operands: max_items = (largest padded row count << 32) | largest k-group count
 long long packed_bytes(long long R, long long K, int TR);

@@ -23,6 +23,7 @@ __all__ = [
     "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
     "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
     "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
+    "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -46,7 +47,8 @@ EXPORTED = [
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
     "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
-    "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state",
+    "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state", "tlr_mdd_time_to_freq",
+    "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -158,6 +160,9 @@ def lib():
                                           C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
         L.tlr_mdd_warm_start.argtypes = [vp, vp, vp]
         L.tlr_mdd_get_state.argtypes = [vp, vp, vp]
+        L.tlr_mdd_time_to_freq.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, vp, vp]
+        L.tlr_mdd_freq_to_time.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, vp, vp]
+        L.tlr_mdd_stack_alpha.argtypes = [vp, C.c_int64, C.POINTER(C.c_double), vp]
         L.tlr_mdd_set_state.argtypes = [vp, vp, vp]
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
@@ -365,6 +370,23 @@ def tlr_mdd_get_state(h, z, u):
 def tlr_mdd_set_state(h, z, u):
     """Load z, u (device, theta order) for a solve with TLR_SOLVE_RESUME."""
     _check(lib().tlr_mdd_set_state(h, _ptr(z), _ptr(u)), h)
+
+
+def tlr_mdd_time_to_freq(x_t, ntr, nt, f0, nf, X_w, stream=None):
+    """Frequency stack [nf][ntr] (device complex64) of trace-major x_t [ntr][nt] (device float)."""
+    _check(lib().tlr_mdd_time_to_freq(_ptr(x_t), ntr, nt, f0, nf, _ptr(X_w), _stream(stream)))
+
+
+def tlr_mdd_freq_to_time(X_w, ntr, nt, f0, nf, x_t, stream=None):
+    """Traces [ntr][nt] (device float) from the band [f0, f0 + nf) of a frequency stack."""
+    _check(lib().tlr_mdd_freq_to_time(_ptr(X_w), ntr, nt, f0, nf, _ptr(x_t), _stream(stream)))
+
+
+def tlr_mdd_stack_alpha(D_w, n, stream=None) -> float:
+    """max |D| over a whole frequency stack of n complex64 values (device)."""
+    a = C.c_double()
+    _check(lib().tlr_mdd_stack_alpha(_ptr(D_w), n, C.byref(a), _stream(stream)))
+    return a.value
 
 
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
