@@ -78,4 +78,24 @@ def test_tc_config0_solve():
     e = rel(X, Xo)
     print(f"tc config0 solve: rel X {e:.2e}")
     assert st.iters == 30 and st.status == 0
-    assert e <= 1e-2
+    assert e <= 1e-3   # final Green's function bound (measured ~3e-6)
+
+
+@pytest.mark.parametrize("nx,ny,b,k,ns", [(12, 8, 48, 5, 203), (8, 8, 16, 3, 64)])
+def test_tc_solve_tiles_off_the_fused_residual_path(nx, ny, b, k, ns):
+    # tiles that are not a multiple of 32 take the plain residual step and the
+    # per-launch residual packs instead of the fused residual step
+    D, U, perm, lay, _ = problem(nx, ny, b, k, "lowrank", ns=ns, seed=3, snr_db=20)
+    nr = nx * ny
+    th0 = (0.1 * synth.planted_theta(nr, b, k, lay.dense, 78)).astype(np.complex64).astype(np.complex128)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dh.T, Uh.T), th0)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha, precision=T.TLR_PREC_BF16X3)
+    th, st = g.solve(th0)
+    g.close()
+    Xo = operator.assemble_xh(tho, lay)
+    X = operator.assemble_xh(th, lay)
+    e = rel(X, Xo)
+    print(f"tc solve b {b}: rel X {e:.2e}, f {st.f_hist[st.n_hist - 1]:.4e} vs {sto.f_hist[-1]:.4e}")
+    assert st.iters == 30 and st.status == 0
+    assert e <= 1e-3   # measured ~1e-5
