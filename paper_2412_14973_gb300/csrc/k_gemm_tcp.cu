@@ -114,7 +114,7 @@ __device__ __forceinline__ int core_off(int r, int kg) { return ((r >> 3) * 2 + 
 // 16-byte tile writes are both coalesced across a warp; row-contiguous
 // sources are read 16 bytes at a time.  All index arithmetic is 32-bit and
 // TR is a power of two.
-constexpr int PACK_KG = 8;
+constexpr int PACK_KG = 2;
 
 __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) {
     const PackJob& J = jobs[blockIdx.y];
