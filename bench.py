@@ -621,7 +621,9 @@ def reference_arm(args, world, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "
                                    "64 frequencies, tile 256, rank 4->48, low-rank diagonal, 10 dB SNR",
-                       "nr": NR, "ns": NR, "frequencies_per_gpu": args.freqs, "tile": TILE},
+                       "nr": NR, "ns": NR, "frequencies_per_gpu": args.freqs, "tile": TILE,
+                       "ranks": f"{RANK_LO}->{RANK_HI} linear", "iters_per_solve": ITERS_PER_SOLVE,
+                       "precision": "fp64 (oracle)", "parallelism": f"frequency sharding x{world}"},
             "cpu_baseline": {"value": round(v, 6), "unit": "freq-solves/s", "cores": blas_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 6), "unit": "freq-solves/s", "h2d_bytes_per_step": 0,
