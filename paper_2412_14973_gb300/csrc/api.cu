@@ -589,7 +589,11 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
         GemmLaunch& G = which == 0 ? h->Lc_x : (which == 1 ? h->Lc_d : h->Lc_v);
         if (upload(G, v, A_KM, B_KN, EPI_STORE)) return -1;
     }
-    // expand: forward residual (SUB Ufrak), plain apply (STORE), A1, A2
+    // expand: forward residual (SUB Ufrak), plain apply (STORE), A1, A2.  The
+    // line-search pair runs as one grouped launch (A1's problems, then A2's):
+    // their tiles share the operand packs and one launch fills the last wave
+    // better than two; Le_a2 stays empty.
+    std::vector<GProb> a12;
     for (int which = 0; which < 4; ++which) {
         std::vector<GProb> v;
         for (int i = 0; i < L.N; ++i) {
@@ -621,7 +625,18 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             p.ldc = ns;
             v.push_back(p);
         }
-        GemmLaunch& G = which == 0 ? h->Le_fwd : which == 1 ? h->Le_apply : which == 2 ? h->Le_a1 : h->Le_a2;
+        if (which == 2) {
+            a12 = v;
+            continue;
+        }
+        if (which == 3) {
+            a12.insert(a12.end(), v.begin(), v.end());
+            std::vector<GProb> none;
+            if (upload(h->Le_a1, a12, A_MK, B_KN, EPI_STORE)) return -1;
+            if (upload(h->Le_a2, none, A_MK, B_KN, EPI_STORE)) return -1;
+            continue;
+        }
+        GemmLaunch& G = which == 0 ? h->Le_fwd : h->Le_apply;
         if (upload(G, v, A_MK, B_KN, which == 0 ? EPI_SUB : EPI_STORE)) return -1;
     }
     // project: split-K partials of grad F_i and G_ii
