@@ -414,7 +414,7 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->Zsd = a.take<cf>(nz);
     h->part = a.take<cf>((size_t)h->nsplit * L.nth);
     h->dpart = a.take<double>(16 * kRedBlocks);
-    h->n_rpart = L.b % 32 == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
+    h->n_rpart = L.b % kFuseRows == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
     h->rpart = a.take<double>((size_t)std::max<long long>(1, h->n_rpart));
     const size_t K = std::max<int64_t>(1, L.Ktot);
     h->d_partner = a.take<int>(K);
@@ -787,7 +787,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             v_nk[ko.first.gr] = ko.second;
     // The residual's two packings (MK for the projection, KN for the residual
     // compression) come from the fused residual step when the tile is a
-    // multiple of 32 and every block has both.
+    // multiple of kFuseRows and every block has both.
     const char* rlo = reinterpret_cast<const char*>(h->R);
     const char* rhi = rlo + (size_t)L.nr * L.ns * sizeof(cf);
     auto is_R = [&](const PackKey& k) {
@@ -811,7 +811,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             rkeys.insert(k);
         }
     }
-    bool rfuse = L.b % 32 == 0 && h->n_rpart > 0;
+    bool rfuse = L.b % kFuseRows == 0 && h->n_rpart > 0;
     for (int i = 0; i < L.N && rfuse; ++i)
         if (!rkn[i] || !rmk[i]) rfuse = false;
     std::vector<char*> rowptr;
@@ -904,11 +904,11 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         const int* gi = h->d_partner + L.Koff[i];
         auto a = t_kn.find(gi), c = t_nk.find(gi);
         if (a == t_kn.end() || c == t_nk.end()) FAIL(h, TLR_ERR_STATE, "internal: T packing not planned");
-        for (int k0 = 0; k0 < Ki; k0 += 32) {
+        for (int k0 = 0; k0 < Ki; k0 += kFuseRows) {
             TPackTile t;
             t.g = gi;
             t.k0 = k0;
-            t.nk = std::min(32, Ki - k0);
+            t.nk = std::min(kFuseRows, Ki - k0);
             t.Ki = Ki;
             t.kn = h->packed + a->second;
             t.nk_dst = h->packed + c->second;

@@ -74,6 +74,11 @@ struct PackJob {
 };
 // row-tile heights of packed A (M) and B (N) operands: the GEMM tile's M and N
 constexpr int kPackTRA = 128, kPackTRB = 128;
+// rows per CTA of the fused update-and-pack kernels (tpack, rstep): 16 rows x
+// 128 columns keep their shared memory at 16.5 KB, so one of their CTAs fits
+// beside the two GEMM CTAs an SM holds (2 x 97 KB) and they overlap
+// contractions of other streams; the tiles of rstep need 16 | b
+constexpr int kFuseRows = 16;
 struct PTerm {
     const void* A;   // packed A of this problem (TR = kPackTRA), all row blocks
     const void* B;   // packed B of this problem (TR = kPackTRB)
@@ -107,7 +112,7 @@ struct GemmLaunch {
     int njobs = 0;
     long long max_items = 0;
 };
-// One row tile of the fused factor-product update (tpack): rows k0 .. k0+nk-1
+// One row tile of the fused factor-product update (tpack): rows k0 .. k0+nk-1 (nk <= kFuseRows)
 // of block i's gathered products T~_i (T~_i[k] = T[g[k]]), with the packed
 // destinations of that block: T~_i as a B operand with rows = ns and k = the
 // factor index (KN), and conj(T~_i) as a B operand with rows = the factor
@@ -129,7 +134,7 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 // FP64 across the CTA) into part[cta] when part != nullptr, and R in both
 // packed forms: block i's rows as an A operand with k = ns (MK, mk[i]) and
 // as a B operand with rows = ns and k = the receiver (KN, kn[i]).  b must be
-// a multiple of 32; rstep_ctas gives the number of CTAs (and partials).
+// a multiple of kFuseRows; rstep_ctas gives the number of CTAs (and partials).
 long long rstep_ctas(int nr, int ns);
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
                   char* const* mk, double* part, cudaStream_t st);

@@ -187,15 +187,17 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 // ---------------------------------------------------------------------------
 // tpack: fused update of the factor products and both of their packings
 // ---------------------------------------------------------------------------
-// A CTA takes one row tile (32 rows of one block's gathered T~_i) and 128
-// columns (n).  Phase 1 reads the 32 source rows of T (and T_p) coalesced
+// A CTA takes one row tile (TP_K rows of one block's gathered T~_i) and 128
+// columns (n).  Phase 1 reads the TP_K source rows of T (and T_p) coalesced
 // along n, applies the update, writes T back and keeps the tile in shared
 // memory; phase 2 writes the KN packing (thread = (n, k-group of 8)); phase 3
 // the conjugated NK packing (thread = (k, n-group of 8), lanes along k).  Padding of the
 // packed buffers (k >= K_i, rows >= ns) is zero from the buffer's creation and
 // is never written.
-constexpr int TP_K = 32, TP_N = 128, TP_LD = TP_N + 1;
-static_assert(kPackTRB == 128 && KC == 16 && TP_K == 32, "tpack writes 128-row, 16-deep B tiles, 32 rows per CTA");
+constexpr int TP_K = kFuseRows, TP_N = 128, TP_LD = TP_N + 1;
+constexpr int TP_KS = TP_K == 16 ? 4 : 5;   // log2(TP_K)
+static_assert(kPackTRB == 128 && KC == 16 && (TP_K == 16 || TP_K == 32),
+              "tpack writes 128-row, 16-deep B tiles, 16 or 32 rows per CTA");
 
 __device__ __forceinline__ void split_store(char* dst, int plane, const float2* v, float sgn) {
     uint32_t w[4][4];
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
         // lanes take consecutive rows: conflict-free shared reads, and 16-byte
         // stores 16 bytes apart in the packed tile
         for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-            const int kk = it & (TP_K - 1), ng = it >> 5;
+            const int kk = it & (TP_K - 1), ng = it >> TP_KS;
             const int nb = n0 + ng * 8;
             if (kk >= nk || nb >= ns) continue;
             float2 v[8];
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 // ---------------------------------------------------------------------------
 // rstep: fused residual step and both packings of the residual
 // ---------------------------------------------------------------------------
-// A CTA takes 32 receiver rows (inside one block, b a multiple of 32) and 128
+// A CTA takes TP_K receiver rows (inside one block, b a multiple of TP_K) and 128
 // columns: phase 1 reads R, A1, A2 coalesced along n, updates, writes R back,
 // accumulates ||R||^2 and keeps the tile in shared memory; phase 2 writes the
 // MK packing (rows = receivers, lanes along rows); phase 3 the KN packing
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
         const int nkcN = (ns + 15) >> 4;
         char* const base = mk[blk];
         for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-            const int kk = it & (TP_K - 1), ng = it >> 5;
+            const int kk = it & (TP_K - 1), ng = it >> TP_KS;
             const int nb = n0 + ng * 8;
             if (nb >= ns) continue;
             float2 v[8];
