@@ -291,7 +291,9 @@ __device__ __forceinline__ int ring_idx(const SolverDev& S, int j) {
 // dozen at these sizes), combined in FP64 across threads and blocks: these
 // products only set the direction's coefficients, whose rounding the exact
 // line search and the descent test absorb.
-__global__ void __launch_bounds__(kRedThreads, 2) k_lb_dots(SolverDev S, int j0) {
+// 128 threads of <= 128 registers: a CTA fits beside the two GEMM CTAs of an SM
+constexpr int kLbThreads = 128;
+__global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) {
     __shared__ double sh[32];
     const int cnt = S.ints[SI_CNT];
     if (j0 >= cnt) return;
@@ -748,7 +750,7 @@ cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st) {
 }
 cudaError_t sv_direction(const SolverDev& S, cudaStream_t st) {
     for (int j0 = 0; j0 < S.m; j0 += kLbGroup) {
-        k_lb_dots<<<kRedBlocks, kRedThreads, 0, st>>>(S, j0);
+        k_lb_dots<<<kRedBlocks, kLbThreads, 0, st>>>(S, j0);
         counted(1);
     }
     k_lb_solve<<<1, kRedThreads, 0, st>>>(S);
