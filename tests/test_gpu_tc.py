@@ -1,4 +1,4 @@
-"""tcgen05 BF16x3 / 3M path vs the FP64 oracle.
+"""tcgen05 BF16x3 / 4M path vs the FP64 oracle.
 
 Tolerance for the tensor-core path: relative Frobenius error <= 1e-3 per
 operator application (BF16x3 keeps about 16 significant bits of each operand;
