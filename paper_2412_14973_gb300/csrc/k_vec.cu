@@ -180,7 +180,17 @@ __global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R,
         const float4* R4 = reinterpret_cast<const float4*>(R);
         const float4* A4 = reinterpret_cast<const float4*>(A1);
         const float4* C4 = reinterpret_cast<const float4*>(A2);
-        GRID_STRIDE(i, n >> 1) {
+        const long long n4 = n >> 1, stride = (long long)gridDim.x * blockDim.x;
+        long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        for (; i + stride < n4; i += 2 * stride) {   // two elements of each array in flight
+            const float4 r = R4[i], a = A4[i], c = C4[i];
+            const float4 r2 = R4[i + stride], a2 = A4[i + stride], c2 = C4[i + stride];
+            dots6_add(s, r.x, r.y, a.x, a.y, c.x, c.y);
+            dots6_add(s, r.z, r.w, a.z, a.w, c.z, c.w);
+            dots6_add(s, r2.x, r2.y, a2.x, a2.y, c2.x, c2.y);
+            dots6_add(s, r2.z, r2.w, a2.z, a2.w, c2.z, c2.w);
+        }
+        if (i < n4) {
             const float4 r = R4[i], a = A4[i], c = C4[i];
             dots6_add(s, r.x, r.y, a.x, a.y, c.x, c.y);
             dots6_add(s, r.z, r.w, a.z, a.w, c.z, c.w);
@@ -344,14 +354,18 @@ __global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) 
 // One block: finalise the partials (warp per value, fixed order), update the
 // newest pair's row / column of S^T Y and Y^T Y, then (thread 0) the
 // triangular solves; coefficients to acoef, gamma to sc[SC_GAMMA].
-__global__ void __launch_bounds__(kRedThreads) k_lb_solve(SolverDev S) {
+// single-block finalisers on the solve's critical path: 1024 threads sum the
+// partial slabs (fixed order per thread, then the block tree)
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads) k_lb_solve(SolverDev S) {
     __shared__ double val[32 * 5];
     __shared__ double Rm[32 * 33];
     __shared__ double Ym[32 * 33];
     __shared__ double p[32], q[32], u[32], t[32];
     const int cnt = S.ints[SI_CNT];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int v = w; v < 5 * cnt; v += kRedThreads / 32) {
+    for (int v = w; v < 5 * cnt; v += kFinThreads / 32) {
         const int j = v / 5, kind = v % 5;
         const double* base = S.lbpart + (long long)(j / kLbGroup) * kRedBlocks * (5 * kLbGroup) +
                              (j % kLbGroup) * 5 + kind;
@@ -558,7 +572,7 @@ __device__ bool quartic_argmin(const double* c, double* out) {
 
 // One thread: finalise the 6 + 3 inner products, form phi's coefficients,
 // check descent, pick alpha; alpha = 0 and a memory reset when no step.
-__global__ void __launch_bounds__(kRedThreads) k_line_search(SolverDev S, const double* part6, const double* part3,
+__global__ void __launch_bounds__(kFinThreads) k_line_search(SolverDev S, const double* part6, const double* part3,
                                                              double rho) {
     __shared__ double sh[32];
     double d6[6], d3[3];
@@ -640,7 +654,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pair_prep(SolverDev S, double r
 
 // one thread: accept the pair (s, y) when alpha > 0 and <s,y> > 1e-12 |s||y|;
 // record f = 0.5 ||R||^2 from the nf residual-norm partials.
-__global__ void __launch_bounds__(kRedThreads) k_pair_accept(SolverDev S, const double* part3, const double* partf,
+__global__ void __launch_bounds__(kFinThreads) k_pair_accept(SolverDev S, const double* part3, const double* partf,
                                                              int nf) {
     __shared__ double sh[32];
     double v[4];
@@ -753,7 +767,7 @@ cudaError_t sv_direction(const SolverDev& S, cudaStream_t st) {
         k_lb_dots<<<kRedBlocks, kLbThreads, 0, st>>>(S, j0);
         counted(1);
     }
-    k_lb_solve<<<1, kRedThreads, 0, st>>>(S);
+    k_lb_solve<<<1, kFinThreads, 0, st>>>(S);
     counted(1);
     k_lb_dir<<<1024, 256, 0, st>>>(S);
     counted(1);
@@ -766,7 +780,7 @@ cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {
 }
 cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
                            cudaStream_t st) {
-    k_line_search<<<1, kRedThreads, 0, st>>>(S, part6, part3, rho);
+    k_line_search<<<1, kFinThreads, 0, st>>>(S, part6, part3, rho);
     counted(1);
     return cudaGetLastError();
 }
@@ -787,7 +801,7 @@ cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStrea
     return cudaGetLastError();
 }
 cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, int nf, cudaStream_t st) {
-    k_pair_accept<<<1, kRedThreads, 0, st>>>(S, part3, partf, nf);
+    k_pair_accept<<<1, kFinThreads, 0, st>>>(S, part3, partf, nf);
     counted(1);
     return cudaGetLastError();
 }

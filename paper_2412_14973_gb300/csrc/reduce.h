@@ -12,7 +12,7 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block-wide sum of v (blockDim.x == kRedThreads); result valid in thread 0.
+// Block-wide sum of v (blockDim.x a multiple of 32, at most 1024); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
