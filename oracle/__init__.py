@@ -24,6 +24,8 @@ arXiv 2412.14973 and cites the passage it follows:
 * ``warmstart``-- the tile rank rule, the entry count and tile-size choice,
                   and the SVD / Takagi warm start (hyper-parameter selection
                   and initialisation section; Examples section, steps 1-3).
+* ``general``  -- the general (non-reciprocal) TLR form: every tile free,
+                  its assembly, misfit, factor gradients and line quartic.
 * ``fourier``  -- time <-> frequency stacks and the stack-wide alpha
                   (Numerical Examples; hyper-parameter selection section).
 
