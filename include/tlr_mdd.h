@@ -57,7 +57,10 @@ extern "C" {
 
 /* ---- reciprocity constraint (Receivers re-ordering / eq. 9) ---- */
 #define TLR_RECIP_SYMMETRIC 0  /* X = X^T, super-diagonal tiles are plain transposes */
-#define TLR_RECIP_NONE      1  /* general TLR X: not implemented (TLR_ERR_UNSUPPORTED) */
+#define TLR_RECIP_NONE      1  /* general TLR X (the form the reciprocity reduction starts from,
+                                  Tile Low-rank MDD section): every tile free, X_ij = L_ij R_ij^T
+                                  for all i != j, X_ii = L_ii R_ii^T or dense Z_ii (no
+                                  symmetrisation); the model is still D-hat X = U-hat */
 
 /* ---- where a buffer lives ---- */
 #define TLR_MEM_DEVICE 0
@@ -77,7 +80,9 @@ typedef struct {
     int32_t rank;            /* uniform rank k of every tile, used when ranks == NULL */
     const int32_t* ranks;    /* optional HOST array [N + N(N-1)/2], N = nr/b: the N
                                 diagonal ranks, then the sub-diagonal pair ranks in
-                                stacking order (column j ascending, row i > j ascending) */
+                                stacking order (column j ascending, row i > j ascending).
+                                TLR_RECIP_NONE: [N + N(N-1)], the ordered pairs (i, j),
+                                i != j, column j ascending, row i ascending */
     int32_t diag_mode;       /* TLR_DIAG_* */
     const uint8_t* diag_dense; /* HOST [N], used with TLR_DIAG_PER_TILE */
     int32_t reciprocity;     /* TLR_RECIP_* */
@@ -143,7 +148,10 @@ int tlr_mdd_theta_size(const tlr_mdd_desc_t* d, int64_t* n_theta);
  * order, then L-bar, then R-bar; every block row-major.  R_ij is stored as the
  * b x k matrix whose transpose is the paper's k x b factor: X_ij = L_ij R_ij^T,
  * X_ji = R_ij L_ij^T.  dense_out[N] (HOST, may be NULL) receives the resolved
- * diagonal representation. */
+ * diagonal representation.  TLR_RECIP_NONE: P = N(N-1) ordered pairs (order as
+ * for ranks), X_ij = L_ij R_ij^T for each; a low-rank diagonal block is L_ii
+ * (b x k_ii) at off_diag[i] followed by R_ii (b x k_ii), X_ii = L_ii R_ii^T; a
+ * dense one is Z_ii with X_ii = Z_ii. */
 int tlr_mdd_theta_layout(const tlr_mdd_desc_t* d, int64_t* off_diag, int64_t* off_l,
                          int64_t* off_r, uint8_t* dense_out);
 
@@ -260,7 +268,8 @@ int tlr_mdd_tile_ranks(const void* X, int64_t nr, int64_t b, double eps, int32_t
 int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, int32_t ncand, double eps,
                         int64_t* best_b, int64_t* best_entries, void* stream);
 
-/* Warm start (hyper-parameter selection and initialisation section) for the
+/* Warm start (hyper-parameter selection and initialisation section; reciprocal
+ * form only, TLR_ERR_UNSUPPORTED for TLR_RECIP_NONE) for the
  * handle's layout from X (DEVICE complex64 nr x nr, Hilbert order, e.g. the
  * benchmark solution): for each pair (i > j) with rank k the truncated SVD
  * X_ij ~ U_k Sigma_k V_k^H gives L = U_k Sigma_k^1/2 and R = conj(V_k)

@@ -137,20 +137,32 @@ struct Arena {
     }
 };
 
+// Panels.  Expand side (A): block i holds the factors that multiply the
+// products T into row block i of Y (the right factors of the tiles X_ji);
+// compress side (B): block j holds the factors that compress column block j
+// of Dfrak (the left factors of the tiles X_ji).  In the reciprocal form the
+// two sides are the same panel (Q_ii, L_ij for j < i, R_ji for j > i serve
+// both); in the general form (reciprocity NONE) they are disjoint: A panels
+// first, then B panels, in one panel vector.
 struct Layout {
     int64_t nr = 0, ns = 0, b = 0;
-    int N = 0, P = 0;
+    int N = 0, P = 0;              // P: stored pairs (N(N-1)/2 reciprocal, N(N-1) general)
+    bool general = false;
     std::vector<int> kd, kp;
     std::vector<uint8_t> dense;
-    std::vector<int64_t> off_diag, off_l, off_r;
+    std::vector<int64_t> off_diag, off_l, off_r;   // general low-rank diagonal: L_ii at off_diag, R_ii after it
     int64_t ntheta = 0;
-    // panel
+    // expand side (A): columns 0 .. Ktot-1
     std::vector<int> Kb;
     std::vector<int64_t> Koff;
+    // compress side (B): columns 0 .. KtotB-1 (the rows of T)
+    std::vector<int> KbB;
+    std::vector<int64_t> KoffB;
+    std::vector<int64_t> panA, panB;   // panel offset of block i's A / B panel
     std::vector<int> dslot;   // dense slot of block i or -1
-    int64_t Ktot = 0, nlr = 0, ndense = 0, nth = 0;
-    // maps (host copies)
-    std::vector<int> partner, colstride, panstride;
+    int64_t Ktot = 0, KtotB = 0, ncol = 0, nlr = 0, ndense = 0, nth = 0;
+    // maps (host copies): partner[A column] = row of T (B column); partnerB[B column] = row of V (A column)
+    std::vector<int> partner, partnerB, colstride, panstride;
     std::vector<long long> colsrc, colpan, zsrc;
 };
 
@@ -171,9 +183,9 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
         err = "nr and ns must be below 2^30";
         return TLR_ERR_SHAPE;
     }
-    if (d->reciprocity != TLR_RECIP_SYMMETRIC) {
-        err = "only the reciprocal (symmetric) parametrisation is implemented";
-        return TLR_ERR_UNSUPPORTED;
+    if (d->reciprocity != TLR_RECIP_SYMMETRIC && d->reciprocity != TLR_RECIP_NONE) {
+        err = "unknown reciprocity mode";
+        return TLR_ERR_ARG;
     }
     if (d->precision != TLR_PREC_FP32 && d->precision != TLR_PREC_BF16X3) {
         err = "unknown precision mode";
@@ -183,7 +195,8 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
     L.ns = d->ns;
     L.b = d->tile;
     L.N = (int)(d->nr / d->tile);
-    L.P = L.N * (L.N - 1) / 2;
+    L.general = d->reciprocity == TLR_RECIP_NONE;
+    L.P = L.general ? L.N * (L.N - 1) : L.N * (L.N - 1) / 2;
     const int N = L.N, P = L.P;
     L.kd.assign(N, d->rank);
     L.kp.assign(P, d->rank);
@@ -217,12 +230,13 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
             default: err = "unknown diag_mode"; return TLR_ERR_ARG;
         }
     }
-    // theta (paper stacking): diagonal blocks, then L-bar, then R-bar
+    // theta (paper stacking): diagonal blocks, then L-bar, then R-bar (general
+    // form: the ordered pairs (i, j), i != j, column j outer, row i inner)
     int64_t o = 0;
     L.off_diag.resize(N);
     for (int i = 0; i < N; ++i) {
         L.off_diag[i] = o;
-        o += L.b * (L.dense[i] ? L.b : L.kd[i]);
+        o += L.b * (L.dense[i] ? L.b : (L.general ? 2 : 1) * L.kd[i]);
     }
     L.off_l.resize(P);
     L.off_r.resize(P);
@@ -236,60 +250,135 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
     }
     L.ntheta = o;
 
-    // panels.  pair index p(i, j) = j N - j(j+1)/2 + (i - j - 1), i > j
-    auto pidx = [N](int i, int j) { return j * N - j * (j + 1) / 2 + (i - j - 1); };
-    // factor list per block: (theta offset, rank, partner factor id); factor ids:
-    // Q_i -> i ; L_p -> N + p ; R_p -> N + P + p
+    // panels.  Factor lists per block: (theta offset, rank, partner factor id).
     struct Fac {
         int id;
         int64_t off;
         int k;
         int partner;
     };
-    std::vector<std::vector<Fac>> blk(N);
-    for (int i = 0; i < N; ++i) {
-        if (!L.dense[i] && L.kd[i] > 0) blk[i].push_back({i, L.off_diag[i], L.kd[i], i});
-        for (int j = 0; j < i; ++j) {
-            const int p = pidx(i, j);
-            if (L.kp[p] > 0) blk[i].push_back({N + p, L.off_l[p], L.kp[p], N + P + p});
+    std::vector<std::vector<Fac>> blkA(N), blkB(N);
+    if (!L.general) {
+        // pair index p(i, j) = j N - j(j+1)/2 + (i - j - 1), i > j; factor ids:
+        // Q_i -> i ; L_p -> N + p ; R_p -> N + P + p
+        auto pidx = [N](int i, int j) { return j * N - j * (j + 1) / 2 + (i - j - 1); };
+        for (int i = 0; i < N; ++i) {
+            if (!L.dense[i] && L.kd[i] > 0) blkA[i].push_back({i, L.off_diag[i], L.kd[i], i});
+            for (int j = 0; j < i; ++j) {
+                const int p = pidx(i, j);
+                if (L.kp[p] > 0) blkA[i].push_back({N + p, L.off_l[p], L.kp[p], N + P + p});
+            }
+            for (int j = i + 1; j < N; ++j) {
+                const int p = pidx(j, i);
+                if (L.kp[p] > 0) blkA[i].push_back({N + P + p, L.off_r[p], L.kp[p], N + p});
+            }
         }
-        for (int j = i + 1; j < N; ++j) {
-            const int p = pidx(j, i);
-            if (L.kp[p] > 0) blk[i].push_back({N + P + p, L.off_r[p], L.kp[p], N + p});
-        }
+    } else {
+        // ordered pair index of tile (r, c), r != c: c (N - 1) + r - (r > c); factor
+        // ids: L of tile t -> t, R of tile t -> N^2 + t with t = r N + c.  Y = X^T Dfrak:
+        // row block i of Y takes R_ji (A side of block i), column block j of Dfrak
+        // is compressed by L_ji (B side of block j).
+        auto op = [N](int r, int c) { return c * (N - 1) + r - (r > c ? 1 : 0); };
+        const int NN = N * N;
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                const int t = j * N + i;   // tile (j, i)
+                int k;
+                int64_t offL, offR;
+                if (i == j) {
+                    if (L.dense[i] || L.kd[i] == 0) continue;
+                    k = L.kd[i];
+                    offL = L.off_diag[i];
+                    offR = L.off_diag[i] + L.b * k;
+                } else {
+                    const int q = op(j, i);
+                    k = L.kp[q];
+                    if (k == 0) continue;
+                    offL = L.off_l[q];
+                    offR = L.off_r[q];
+                }
+                blkA[i].push_back({NN + t, offR, k, t});
+                blkB[j].push_back({t, offL, k, NN + t});
+            }
     }
+    // columns: A side first (0 .. Ktot-1), then B side (general form only)
+    const int nid = L.general ? 2 * N * N : N + 2 * P;
+    std::vector<int64_t> fac_col(nid, -1), fac_b(nid, -1);
     L.Kb.assign(N, 0);
     L.Koff.assign(N, 0);
-    std::vector<int64_t> fac_col(N + 2 * P, -1);
     int64_t K = 0;
     for (int i = 0; i < N; ++i) {
         L.Koff[i] = K;
-        for (auto& f : blk[i]) {
+        for (auto& f : blkA[i]) {
             fac_col[f.id] = K + L.Kb[i];
             L.Kb[i] += f.k;
         }
         K += L.Kb[i];
     }
     L.Ktot = K;
-    L.nlr = L.b * K;
-    L.partner.resize(K);
-    L.colsrc.resize(K);
-    L.colstride.resize(K);
-    L.colpan.resize(K);
-    L.panstride.resize(K);
+    if (L.general) {
+        L.KbB.assign(N, 0);
+        L.KoffB.assign(N, 0);
+        int64_t KB = 0;
+        for (int j = 0; j < N; ++j) {
+            L.KoffB[j] = KB;
+            for (auto& f : blkB[j]) {
+                fac_b[f.id] = KB + L.KbB[j];
+                L.KbB[j] += f.k;
+            }
+            KB += L.KbB[j];
+        }
+        L.KtotB = KB;
+    } else {
+        L.KbB = L.Kb;
+        L.KoffB = L.Koff;
+        L.KtotB = L.Ktot;
+    }
+    L.ncol = L.general ? L.Ktot + L.KtotB : L.Ktot;
+    L.nlr = L.b * L.ncol;
+    L.panA.assign(N, 0);
+    L.panB.assign(N, 0);
+    for (int i = 0; i < N; ++i) {
+        L.panA[i] = L.b * L.Koff[i];
+        L.panB[i] = L.general ? L.b * (L.Ktot + L.KoffB[i]) : L.panA[i];
+    }
+    L.partner.resize(L.Ktot);
+    L.partnerB.resize(L.KtotB);
+    L.colsrc.resize(L.ncol);
+    L.colstride.resize(L.ncol);
+    L.colpan.resize(L.ncol);
+    L.panstride.resize(L.ncol);
     for (int i = 0; i < N; ++i) {
         int64_t c = 0;
-        for (auto& f : blk[i]) {
+        for (auto& f : blkA[i]) {
             for (int q = 0; q < f.k; ++q) {
                 const int64_t g = L.Koff[i] + c + q;
-                L.partner[g] = (int)(fac_col[f.partner] + q);
+                L.partner[g] = (int)((L.general ? fac_b[f.partner] : fac_col[f.partner]) + q);
                 L.colsrc[g] = f.off + q;
                 L.colstride[g] = f.k;
-                L.colpan[g] = L.b * L.Koff[i] + c + q;
+                L.colpan[g] = L.panA[i] + c + q;
                 L.panstride[g] = L.Kb[i];
             }
             c += f.k;
         }
+    }
+    if (L.general) {
+        for (int j = 0; j < N; ++j) {
+            int64_t c = 0;
+            for (auto& f : blkB[j]) {
+                for (int q = 0; q < f.k; ++q) {
+                    const int64_t g = L.KoffB[j] + c + q;
+                    L.partnerB[g] = (int)(fac_col[f.partner] + q);
+                    L.colsrc[L.Ktot + g] = f.off + q;
+                    L.colstride[L.Ktot + g] = f.k;
+                    L.colpan[L.Ktot + g] = L.panB[j] + c + q;
+                    L.panstride[L.Ktot + g] = L.KbB[j];
+                }
+                c += f.k;
+            }
+        }
+    } else {
+        L.partnerB = L.partner;
     }
     L.dslot.assign(N, -1);
     for (int i = 0; i < N; ++i)
@@ -333,7 +422,8 @@ struct tlr_mdd_s {
     int nsplit = 1;
     int kchunk = 0;
     double* dpart = nullptr;   // reduction partial slabs
-    int* d_partner = nullptr;
+    int* d_partner = nullptr;    // [Ktot] row of T for each A column
+    int* d_partnerB = nullptr;   // [KtotB] row of V for each B column (= d_partner when reciprocal)
     PanelMap pm{};
     // theta-space vectors
     cf *x = nullptr, *z = nullptr, *u = nullptr, *v = nullptr, *g = nullptr, *gf = nullptr, *dd = nullptr,
@@ -399,7 +489,9 @@ namespace {
 // Lay out (or size, when a.base == nullptr) the handle's device arena.
 void carve(tlr_mdd_s* h, Arena& a) {
     const Layout& L = h->L;
-    const size_t nrs = (size_t)L.nr * L.ns, kns = (size_t)std::max<int64_t>(1, L.Ktot) * L.ns;
+    // T has a row per B column; Tp holds T_p (B rows) or V (A rows)
+    const size_t nrs = (size_t)L.nr * L.ns, kns = (size_t)std::max<int64_t>(1, L.KtotB) * L.ns;
+    const size_t knsp = (size_t)std::max<int64_t>(1, std::max(L.Ktot, L.KtotB)) * L.ns;
     h->perm = a.take<int32_t>(2 * L.nr);
     h->scal = a.take<double>(16);
     h->Dt = a.take<cf>(nrs);
@@ -408,7 +500,7 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->A1 = a.take<cf>(nrs);
     h->A2 = a.take<cf>(nrs);
     h->T = a.take<cf>(kns);
-    h->Tp = a.take<cf>(kns);
+    h->Tp = a.take<cf>(knsp);
     const size_t nz = std::max<size_t>(1, (size_t)L.ndense * L.b * L.b);
     h->Zs = a.take<cf>(nz);
     h->Zsd = a.take<cf>(nz);
@@ -416,14 +508,15 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->dpart = a.take<double>(16 * kRedBlocks);
     h->n_rpart = L.b % kFuseRows == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
     h->rpart = a.take<double>((size_t)std::max<long long>(1, h->n_rpart));
-    const size_t K = std::max<int64_t>(1, L.Ktot);
-    h->d_partner = a.take<int>(K);
+    const size_t K = std::max<int64_t>(1, L.ncol);
+    h->d_partner = a.take<int>(std::max<int64_t>(1, L.general ? L.Ktot + L.KtotB : L.Ktot));
+    h->d_partnerB = L.general ? h->d_partner + L.Ktot : h->d_partner;
     long long* colsrc = a.take<long long>(K);
     int* colstride = a.take<int>(K);
     long long* colpan = a.take<long long>(K);
     int* panstride = a.take<int>(K);
     long long* zsrc = a.take<long long>(std::max<int64_t>(1, L.ndense));
-    h->pm = PanelMap{colsrc, colstride, colpan, panstride, zsrc, L.Ktot, L.b, L.ndense, L.nlr};
+    h->pm = PanelMap{colsrc, colstride, colpan, panstride, zsrc, L.ncol, L.b, L.ndense, L.nlr};
     const size_t nth = std::max<int64_t>(1, L.nth);
     h->x = a.take<cf>(nth);
     h->z = a.take<cf>(nth);
@@ -443,9 +536,9 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->fhist = a.take<double>(TLR_MAX_HIST);
     h->lbm = a.take<double>(2 * 33 * 33);
     h->lbpart = a.take<double>((size_t)kLbPartDoubles);
-    // GEMM tables: 8 slots of at most 2N problems each
-    h->tab_base = reinterpret_cast<char*>(a.take<GProb>(2 * (size_t)L.N + 1));
-    for (int t = 1; t < 8; ++t) a.take<GProb>(2 * (size_t)L.N + 1);
+    // GEMM tables: 8 slots of at most 3N + 1 problems each
+    h->tab_base = reinterpret_cast<char*>(a.take<GProb>(3 * (size_t)L.N + 1));
+    for (int t = 1; t < 8; ++t) a.take<GProb>(3 * (size_t)L.N + 1);
 }
 
 // Upper bound of the packed-operand storage of the tensor-core path (the
@@ -455,7 +548,7 @@ long long packed_estimate(const Layout& L) {
     const long long b = L.b, ns = L.ns;
     long long t = 0;
     for (int i = 0; i < L.N; ++i) {
-        const long long Ki = L.Kb[i];
+        const long long Ki = std::max(L.Kb[i], L.KbB[i]);   // upper bound for both sides
         if (Ki > 0) {
             t += 3 * pb(Ki, b, kPackTRA) + 2 * pb(b, Ki, kPackTRA);     // F, conj F, F_d (KM); F, F_d (MK)
             t += 2 * pb(ns, Ki, kPackTRB) + 2 * pb(Ki, ns, kPackTRB);   // T~, T~_p (KN); conj T~, V~ (NK)
@@ -490,6 +583,7 @@ int split_for(const Layout& L, int prec) {
         long long tiles = 0;
         for (int i = 0; i < L.N; ++i) {
             tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.Kb[i] + kPackTRB - 1) / kPackTRB);
+            if (L.general) tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.KbB[i] + kPackTRB - 1) / kPackTRB);
             if (L.dense[i]) tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.b + kPackTRB - 1) / kPackTRB);
         }
         tiles = std::max(1LL, tiles);
@@ -508,6 +602,7 @@ int split_for(const Layout& L, int prec) {
     long long tiles = 0;
     for (int i = 0; i < L.N; ++i) {
         tiles += ((L.b + 63) / 64) * ((L.Kb[i] + 63) / 64);
+        if (L.general) tiles += ((L.b + 63) / 64) * ((L.KbB[i] + 63) / 64);
         if (L.dense[i]) tiles += ((L.b + 63) / 64) * ((L.b + 63) / 64);
     }
     return choose_split(std::max(1LL, tiles), L.ns);
@@ -535,7 +630,7 @@ struct HostTable {
 int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
     const Layout& L = h->L;
     const long long ns = L.ns, b = L.b;
-    const size_t slot = ((sizeof(GProb) * (2 * (size_t)L.N + 1)) + 255) & ~size_t(255);
+    const size_t slot = ((sizeof(GProb) * (3 * (size_t)L.N + 1)) + 255) & ~size_t(255);
     int ti = 0;
     auto upload = [&](GemmLaunch& G, std::vector<GProb>& v, int am, int bm, int epi) -> int {
         GProb* dst = reinterpret_cast<GProb*>(tab_base + slot * ti++);
@@ -568,21 +663,24 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
     };
     const cf* X = h->x;
     const cf* Dd = h->dd;
-    // compress: T_i = F_i^T Dfrak_i (src x), Tp (src d), V = F_i^H Rf_i (into Tp)
+    // compress: T_j = B_j^T Dfrak_j (src x), T_p (src d) over the B panels;
+    // V_i = A_i^H Rf_i (into Tp) over the A panels
     for (int which = 0; which < 3; ++which) {
         std::vector<GProb> v;
+        const bool aside = which == 2;
         for (int i = 0; i < L.N; ++i) {
-            if (L.Kb[i] == 0) continue;
+            const int Ki = aside ? L.Kb[i] : L.KbB[i];
+            if (Ki == 0) continue;
             GProb p = blank();
             const cf* src = which == 1 ? Dd : X;
             const cf* data = which == 2 ? h->R : h->Dt;
             cf* out = which == 0 ? h->T : h->Tp;
-            p.t[0] = term(src + b * L.Koff[i], L.Kb[i], data + (long long)i * b * ns, ns, nullptr, (int)b,
+            p.t[0] = term(src + (aside ? L.panA[i] : L.panB[i]), Ki, data + (long long)i * b * ns, ns, nullptr, (int)b,
                           which == 2, false);
             p.nt = 1;
-            p.M = L.Kb[i];
+            p.M = Ki;
             p.N = (int)ns;
-            p.C = out + L.Koff[i] * ns;
+            p.C = out + (aside ? L.Koff[i] : L.KoffB[i]) * ns;
             p.ldc = ns;
             v.push_back(p);
         }
@@ -600,8 +698,8 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             GProb p = blank();
             const int* gi = h->d_partner + L.Koff[i];
             const int Ki = L.Kb[i];
-            const cf* Fi = X + b * L.Koff[i];
-            const cf* Fd = Dd + b * L.Koff[i];
+            const cf* Fi = X + L.panA[i];
+            const cf* Fd = Dd + L.panA[i];
             const cf* Di = h->Dt + (long long)i * b * ns;
             int nt = 0;
             if (which <= 1) {
@@ -645,7 +743,8 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
         for (int i = 0; i < L.N; ++i) {
             const cf* Ri = h->R + (long long)i * b * ns;
             const cf* Di = h->Dt + (long long)i * b * ns;
-            if (L.Kb[i] > 0) {
+            if (!L.general && L.Kb[i] > 0) {
+                // reciprocal: block i's panel takes both terms
                 GProb p = blank();
                 const int* gi = h->d_partner + L.Koff[i];
                 p.t[0] = term(Ri, ns, h->T, ns, gi, (int)ns, false, true);
@@ -653,8 +752,28 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
                 p.nt = 2;
                 p.M = (int)b;
                 p.N = L.Kb[i];
-                p.C = h->part + b * L.Koff[i];
+                p.C = h->part + L.panA[i];
                 p.ldc = L.Kb[i];
+                v.push_back(p);
+            }
+            if (L.general && L.Kb[i] > 0) {   // A panel i: Rf_i T~_i^H
+                GProb p = blank();
+                p.t[0] = term(Ri, ns, h->T, ns, h->d_partner + L.Koff[i], (int)ns, false, true);
+                p.nt = 1;
+                p.M = (int)b;
+                p.N = L.Kb[i];
+                p.C = h->part + L.panA[i];
+                p.ldc = L.Kb[i];
+                v.push_back(p);
+            }
+            if (L.general && L.KbB[i] > 0) {   // B panel i: conj(Dfrak_i) V~_i^T
+                GProb p = blank();
+                p.t[0] = term(Di, ns, h->Tp, ns, h->d_partnerB + L.KoffB[i], (int)ns, true, false);
+                p.nt = 1;
+                p.M = (int)b;
+                p.N = L.KbB[i];
+                p.C = h->part + L.panB[i];
+                p.ldc = L.KbB[i];
                 v.push_back(p);
             }
             if (L.dense[i]) {
@@ -816,17 +935,18 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         if (!rkn[i] || !rmk[i]) rfuse = false;
     std::vector<char*> rowptr;
     bool vpack = L.Ktot > 0;
-    for (int i = 0; i < L.N && vpack; ++i)
-        if (L.Kb[i] > 0 && !v_nk.count(h->d_partner + L.Koff[i])) vpack = false;
+    for (int j = 0; j < L.N && vpack; ++j)
+        if (L.KbB[j] > 0 && !v_nk.count(h->d_partnerB + L.KoffB[j])) vpack = false;
     if (vpack) {
         constexpr long long plane = 128 * 16 * 2;
         const long long nkcN = (L.ns + 15) / 16;
         rowptr.resize(L.Ktot);
         for (int64_t gm = 0; gm < L.Ktot; ++gm) {
+            // V row gm (A column) is read by B column partner[gm] of V~
             const int64_t pg = L.partner[gm];
-            const int i = (int)(std::upper_bound(L.Koff.begin(), L.Koff.end(), pg) - L.Koff.begin()) - 1;
-            const int64_t k = pg - L.Koff[i];
-            rowptr[gm] = h->packed + v_nk[h->d_partner + L.Koff[i]] + (k >> 7) * nkcN * 4 * plane +
+            const int i = (int)(std::upper_bound(L.KoffB.begin(), L.KoffB.end(), pg) - L.KoffB.begin()) - 1;
+            const int64_t k = pg - L.KoffB[i];
+            rowptr[gm] = h->packed + v_nk[h->d_partnerB + L.KoffB[i]] + (k >> 7) * nkcN * 4 * plane +
                          ((k & 127) >> 3) * 256 + (k & 7) * 16;
         }
     }
@@ -1161,12 +1281,15 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         }
     }
     // maps
-    if (L.Ktot > 0) {
+    if (L.Ktot > 0)
         CKF(cudaMemcpyAsync(h->d_partner, L.partner.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaMemcpyAsync((void*)h->pm.colsrc, L.colsrc.data(), L.Ktot * sizeof(long long), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaMemcpyAsync((void*)h->pm.colstride, L.colstride.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaMemcpyAsync((void*)h->pm.colpan, L.colpan.data(), L.Ktot * sizeof(long long), cudaMemcpyHostToDevice, h->st));
-        CKF(cudaMemcpyAsync((void*)h->pm.panstride, L.panstride.data(), L.Ktot * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    if (L.general && L.KtotB > 0)
+        CKF(cudaMemcpyAsync(h->d_partnerB, L.partnerB.data(), L.KtotB * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    if (L.ncol > 0) {
+        CKF(cudaMemcpyAsync((void*)h->pm.colsrc, L.colsrc.data(), L.ncol * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colstride, L.colstride.data(), L.ncol * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colpan, L.colpan.data(), L.ncol * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.panstride, L.panstride.data(), L.ncol * sizeof(int), cudaMemcpyHostToDevice, h->st));
     }
     if (L.ndense > 0)
         CKF(cudaMemcpyAsync((void*)h->pm.zsrc, L.zsrc.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
@@ -1212,7 +1335,7 @@ int tlr_mdd_set_data(tlr_mdd_t* h, const void* D, const void* U, int32_t input_m
 
 static int forward(tlr_mdd_s* h, bool plain_apply) {
     const Layout& L = h->L;
-    CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st));
+    CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st, L.general));
     CK(h, run_gemm(h->Lc_x, h->st));
     if (h->n_tpack) CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)L.ns, h->st));
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
@@ -1225,7 +1348,7 @@ static int gradient(tlr_mdd_s* h) {
     const Layout& L = h->L;
     CK(h, run_gemm(h->Lc_v, h->st));
     CK(h, run_gemm(h->Lp, h->st));
-    CK(h, reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.b, h->gf, h->st));
+    CK(h, reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.b, h->gf, h->st, L.general));
     return TLR_OK;
 }
 
@@ -1590,6 +1713,7 @@ int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!X || !theta) FAIL(h, TLR_ERR_ARG, "X or theta is NULL");
     const Layout& L = h->L;
+    if (L.general) FAIL(h, TLR_ERR_UNSUPPORTED, "the warm start is defined for the reciprocal form");
     if (L.b > 512) FAIL(h, TLR_ERR_SHAPE, "warm start needs tile <= 512");
     const int N = L.N, b = (int)L.b;
     std::vector<int2> tl;
@@ -1729,16 +1853,33 @@ int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!theta || !X) FAIL(h, TLR_ERR_ARG, "theta or X is NULL");
     const Layout& L = h->L;
     const long long nr = L.nr;
-    std::vector<AsmTile> tiles(L.N + L.P);
-    for (int i = 0; i < L.N; ++i)
-        tiles[i] = AsmTile{L.off_diag[i], L.off_diag[i], L.dense[i] ? (int)L.b : L.kd[i], (int)L.dense[i]};
-    for (int p = 0; p < L.P; ++p) tiles[L.N + p] = AsmTile{L.off_l[p], L.off_r[p], L.kp[p], 0};
+    std::vector<AsmTile> tiles;
+    if (!L.general) {
+        tiles.resize(L.N + L.P);
+        for (int i = 0; i < L.N; ++i)
+            tiles[i] = AsmTile{L.off_diag[i], L.off_diag[i], L.dense[i] ? (int)L.b : L.kd[i], (int)L.dense[i]};
+        for (int p = 0; p < L.P; ++p) tiles[L.N + p] = AsmTile{L.off_l[p], L.off_r[p], L.kp[p], 0};
+    } else {
+        // every tile, row-major; ordered pair index of (i, j): j (N - 1) + i - (i > j)
+        tiles.resize((size_t)L.N * L.N);
+        for (int i = 0; i < L.N; ++i)
+            for (int j = 0; j < L.N; ++j) {
+                if (i == j) {
+                    const int k = L.dense[i] ? (int)L.b : L.kd[i];
+                    tiles[i * L.N + j] = AsmTile{L.off_diag[i], L.off_diag[i] + (L.dense[i] ? 0 : L.b * k), k,
+                                                 (int)L.dense[i]};
+                } else {
+                    const int q = j * (L.N - 1) + i - (i > j ? 1 : 0);
+                    tiles[i * L.N + j] = AsmTile{L.off_l[q], L.off_r[q], L.kp[q], 0};
+                }
+            }
+    }
     cf* Xh = nullptr;
     AsmTile* dt = nullptr;
     CK(h, cudaMallocAsync((void**)&Xh, (size_t)nr * nr * sizeof(cf), h->st));
     cudaError_t e = cudaMallocAsync((void**)&dt, tiles.size() * sizeof(AsmTile), h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(AsmTile), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess) e = assemble_dense((const cf*)theta, nr, L.b, L.N, dt, Xh, h->st);
+    if (e == cudaSuccess) e = assemble_dense((const cf*)theta, nr, L.b, L.N, dt, Xh, h->st, L.general);
     if (e == cudaSuccess) e = unpermute_dense(Xh, nr, h->perm, (cf*)X, h->st);
     if (dt) cudaFreeAsync(dt, h->st);
     cudaFreeAsync(Xh, h->st);
@@ -1895,7 +2036,7 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
             for (int t = 0; t < o->lbfgs_iters; ++t) {
                 CK(h, sv_direction(S, h->st));
                 CK(h, run_gemm(h->Lc_d, h->st));
-                CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.b, h->Zsd, h->st));
+                CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.b, h->Zsd, h->st, L.general));
                 CK(h, run_gemm(h->Le_a1, h->st));
                 CK(h, run_gemm(h->Le_a2, h->st));
                 CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));
@@ -1908,8 +2049,8 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                     CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
                 if (h->n_tpack)
                     CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, h->sc + SC_ALPHA, (int)L.ns, h->st));
-                else if (L.Ktot > 0)
-                    CK(h, axpy_dev((float*)h->T, (const float*)h->Tp, 2LL * L.Ktot * L.ns, h->sc + SC_ALPHA, h->st));
+                else if (L.KtotB > 0)
+                    CK(h, axpy_dev((float*)h->T, (const float*)h->Tp, 2LL * L.KtotB * L.ns, h->sc + SC_ALPHA, h->st));
                 CK(h, sv_step_theta(S, h->st));
                 rc = gradient(h);
                 if (rc) return rc;

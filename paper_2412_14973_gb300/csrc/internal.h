@@ -212,7 +212,7 @@ struct AsmTile {
     int dense;
 };
 cudaError_t assemble_dense(const cf* theta, long long nr, long long b, int N, const AsmTile* tiles, cf* Xh,
-                           cudaStream_t st);
+                           cudaStream_t st, int general = 0);
 // X[perm[a], perm[c]] = Xh[a, c]
 cudaError_t unpermute_dense(const cf* Xh, long long nr, const int32_t* perm, cf* X, cudaStream_t st);
 
@@ -234,11 +234,13 @@ struct PanelMap {
 cudaError_t theta_to_panel(const PanelMap& m, const cf* theta, cf* pan, cudaStream_t st);
 cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStream_t st);
 // Zs = (Z + Z^T)/2 for every dense tile of a panel vector
-cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st);
-// grad[e] = sum_c part[c * stride + e] (LR part), dense tiles symmetrised: (G + G^T)/2;
-// then, if rho != 0: grad += rho (x - v)   (x, v may be null when rho == 0)
+// (general != 0: Zs = Z^T, the general form's dense tiles)
+cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st,
+                      int general = 0);
+// grad[e] = sum_c part[c * stride + e] (LR part), dense tiles symmetrised: (G + G^T)/2
+// (general != 0: G^T, the general form's dense tiles)
 cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
-                        long long b, cf* grad, cudaStream_t st);
+                        long long b, cf* grad, cudaStream_t st, int general = 0);
 
 // partial FP64 real dot sums over float arrays (2 per complex) -> part[kRedBlocks]
 cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st);

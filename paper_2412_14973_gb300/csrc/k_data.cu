@@ -179,13 +179,35 @@ cudaError_t permute_normalise(const cf* D, long long ns, long long nr, const int
 // 15).  An entry of a super-diagonal tile evaluates exactly the expression of
 // its mirror in the sub-diagonal tile (same products, same order), so the
 // result is bitwise symmetric, as X_ji = X_ij^T demands.
+// General form (general != 0): the tiles are listed row-major (i N + j) and
+// every entry is its own tile's L R^T (or Z entry), without mirroring.
 __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b, int N, const AsmTile* __restrict__ t,
-                           cf* __restrict__ Xh) {
+                           cf* __restrict__ Xh, int general) {
     const long long n2 = nr * nr;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
          e += (long long)gridDim.x * blockDim.x) {
         long long r = e / nr, c = e % nr;
         int i = (int)(r / b), j = (int)(c / b);
+        if (general) {
+            const AsmTile& a = t[i * N + j];
+            const long long rr = r - i * b, cc = c - j * b;
+            float x = 0.f, y = 0.f;
+            if (i == j && a.dense) {
+                const cf u = th[a.off_l + rr * b + cc];
+                x = u.x;
+                y = u.y;
+            } else {
+                const cf* L = th + a.off_l + rr * a.k;
+                const cf* R = th + a.off_r + cc * a.k;
+                for (int q = 0; q < a.k; ++q) {
+                    const cf l = L[q], m = R[q];
+                    x = fmaf(l.x, m.x, fmaf(-l.y, m.y, x));
+                    y = fmaf(l.x, m.y, fmaf(l.y, m.x, y));
+                }
+            }
+            Xh[e] = make_float2(x, y);
+            continue;
+        }
         if (i < j) {  // mirror into the sub-diagonal tile
             const long long tr = r;
             r = c;
@@ -220,8 +242,8 @@ __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b,
 }
 
 cudaError_t assemble_dense(const cf* theta, long long nr, long long b, int N, const AsmTile* tiles, cf* Xh,
-                           cudaStream_t st) {
-    k_assemble<<<1024, 256, 0, st>>>(theta, nr, b, N, tiles, Xh);
+                           cudaStream_t st, int general) {
+    k_assemble<<<1024, 256, 0, st>>>(theta, nr, b, N, tiles, Xh, general);
     counted(1);
     return cudaGetLastError();
 }

@@ -74,27 +74,31 @@ cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStre
 }
 
 // Zs = (Z + Z^T)/2 (the symmetrisation preconditioner P of eq. 7)
+// Zs = (Z + Z^T)/2 (reciprocal form, X_ii = P Z_ii) or Z^T (general form: row
+// block i of Y = X^T Dfrak takes X_ii^T)
 __global__ void k_sym_dense(const cf* __restrict__ pan, long long zbase, long long ndense, long long b,
-                            cf* __restrict__ Zs) {
+                            cf* __restrict__ Zs, int general) {
     const long long bb = b * b;
     GRID_STRIDE(e, ndense * bb) {
         const long long t = e / bb, r = (e % bb) / b, c = e % b;
         const cf u = pan[zbase + t * bb + r * b + c];
         const cf v = pan[zbase + t * bb + c * b + r];
-        Zs[e] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y + v.y));
+        Zs[e] = general ? v : make_float2(0.5f * (u.x + v.x), 0.5f * (u.y + v.y));
     }
 }
 
-cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st) {
+cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st,
+                      int general) {
     if (ndense == 0) return cudaSuccess;
-    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs);
+    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs, general);
     counted(1);
     return cudaGetLastError();
 }
 
 // grad = sum of split-K partials (FP64, fixed order); dense tiles: (G + G^T)/2
+// (reciprocal form) or G^T (general form)
 __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long stride, long long nlr,
-                              long long ndense, long long b, cf* __restrict__ grad) {
+                              long long ndense, long long b, cf* __restrict__ grad, int general) {
     GRID_STRIDE(e, nlr) {
         Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
@@ -110,20 +114,23 @@ __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long
         const long long e1 = nlr + t * bb + r * b + q, e2 = nlr + t * bb + q * b + r;
         Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
-            const cf u = part[c * stride + e1];
             const cf v = part[c * stride + e2];
-            x.add(u.x);
+            if (!general) {
+                const cf u = part[c * stride + e1];
+                x.add(u.x);
+                y.add(u.y);
+            }
             x.add(v.x);
-            y.add(u.y);
             y.add(v.y);
         }
-        grad[nlr + e] = make_float2((float)(0.5 * x.val()), (float)(0.5 * y.val()));
+        const double s = general ? 1.0 : 0.5;
+        grad[nlr + e] = make_float2((float)(s * x.val()), (float)(s * y.val()));
     }
 }
 
 cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
-                        long long b, cf* grad, cudaStream_t st) {
-    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad);
+                        long long b, cf* grad, cudaStream_t st, int general) {
+    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad, general);
     counted(1);
     return cudaGetLastError();
 }

@@ -245,7 +245,7 @@ def tlr_mdd_theta_size(d: Desc) -> int:
 
 def tlr_mdd_theta_layout(d: Desc):
     N = d.nr // d.tile
-    P = N * (N - 1) // 2
+    P = N * (N - 1) if d.reciprocity == TLR_RECIP_NONE else N * (N - 1) // 2
     od = (C.c_int64 * max(N, 1))()
     ol = (C.c_int64 * max(P, 1))()
     orr = (C.c_int64 * max(P, 1))()

@@ -27,12 +27,12 @@ class Gpu:
     """One handle on device copies of D, U (paper layout)."""
 
     def __init__(self, D, U, lay, nx=0, ny=0, perm=None, alpha=0.0, precision=T.TLR_PREC_FP32,
-                 host_inputs=False, stream=None):
+                 host_inputs=False, stream=None, desc=None):
         self.lay = lay
         self.ns = D.shape[0]
         self.stream = stream
         mem = T.TLR_MEM_HOST if host_inputs else T.TLR_MEM_DEVICE
-        self.d = abi_desc(lay, self.ns, nx, ny, perm, alpha, precision, mem)
+        self.d = desc if desc is not None else abi_desc(lay, self.ns, nx, ny, perm, alpha, precision, mem)
         if host_inputs:
             self._D = np.ascontiguousarray(D.astype(np.complex64))
             self._U = np.ascontiguousarray(U.astype(np.complex64))

@@ -58,12 +58,32 @@ def test_per_tile_diag_mode():
     assert T.tlr_mdd_theta_size(d) == lay.size
 
 
+@pytest.mark.parametrize("nr,b,ranks,dense", [
+    (48, 16, 3, [False, True, False]),
+    (64, 16, [1, 0, 4, 2] + [k % 5 for k in range(12)], [False, False, True, False]),
+])
+def test_general_theta_layout_bit_exact(nr, b, ranks, dense):
+    # the general (non-reciprocal) stacking: diagonal blocks (Z, or L then R),
+    # then L and R of the ordered pairs, column outer, row inner
+    from oracle import general
+    _lib()
+    n = nr // b
+    rl = ranks if isinstance(ranks, list) else [ranks] * (n + n * (n - 1))
+    d = T.desc(nr, 10, b, ranks=rl, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense,
+               reciprocity=T.TLR_RECIP_NONE)
+    lay = general.make_general_layout(nr, b, rl, dense)
+    od, ol, orr, dn = T.tlr_mdd_theta_layout(d)
+    assert od == lay.off_diag and ol == lay.off_l and orr == lay.off_r
+    assert dn == lay.dense
+    assert T.tlr_mdd_theta_size(d) == lay.size
+
+
 @pytest.mark.parametrize("kw,code", [
     (dict(nr=100, ns=10, tile=64, rank=4), -2),          # tile does not divide nr
     (dict(nr=128, ns=10, tile=64, rank=65), -2),         # rank above tile
     (dict(nr=128, ns=10, tile=64, rank=-1), -2),
     (dict(nr=128, ns=0, tile=64, rank=4), -2),
-    (dict(nr=128, ns=10, tile=64, rank=4, reciprocity=1), -3),  # general TLR not implemented
+    (dict(nr=128, ns=10, tile=64, rank=4, reciprocity=2), -1),  # unknown reciprocity mode
     (dict(nr=128, ns=10, tile=64, rank=4, precision=7), -1),
     (dict(nr=128, ns=10, tile=64, rank=4, diag_mode=9), -1),
 ])
