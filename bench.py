@@ -233,6 +233,8 @@ def main():
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--bench-iters", type=int, default=20,
                     help="CG iterations of the eq. (4) benchmark solver timed on frequency 0 (0: skip)")
+    ap.add_argument("--general-rank", type=int, default=26,
+                    help="rank of one timed solve of the general (non-reciprocal) form on frequency 0 (0: skip)")
     ap.add_argument("--serving", type=int, default=0,
                     help="also serve this many per-frequency requests of the serving mix (nr 1024-8192)")
     args = ap.parse_args()
@@ -453,6 +455,30 @@ def main():
                   "flops": "8 nr^2 ns (D^H D) + 8 nr^2 ns (D^H U) + iters x 8 nr^3, complex-counted"}
         del Xb
 
+    # the general (non-reciprocal) form: one solve of frequency 0's data at a
+    # given rank (same contraction flops per iteration as the reciprocal form
+    # at that rank, twice the unknowns)
+    gsolve = None
+    if args.general_rank > 0 and rank == 0:
+        kg = args.general_rank
+        dg = T.desc(NR, NR, TILE, rank=kg, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
+                    precision=prec, reciprocity=T.TLR_RECIP_NONE)
+        hg = T.tlr_mdd_create(dg, D[0], U[0], streams[0])
+        gen = torch.Generator(device=dev).manual_seed(args.seed + 5)
+        ntg = T.tlr_mdd_theta_size(dg)
+        th_g0 = 0.01 * torch.randn(ntg, dtype=torch.complex64, device=dev, generator=gen)
+        th_g = th_g0.clone()
+        torch.cuda.synchronize()
+        T.tlr_mdd_solve(hg, th_g, opts)                                   # records the graph
+        th_g.copy_(th_g0)
+        torch.cuda.synchronize()
+        gst = T.tlr_mdd_solve(hg, th_g, opts)
+        gf = flops_per_solve(NR, NR, TILE, kg)
+        gsolve = {"rank": kg, "n_theta": ntg, "ms": round(gst.gpu_ms, 2),
+                  "tflops": round(gf / (gst.gpu_ms / 1e3) / 1e12, 1), "iters": gst.iters,
+                  "note": "one solve, one stream; flops as for the reciprocal form at this rank"}
+        T.tlr_mdd_destroy(hg)
+
     # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
     cpu = None
     acc = None
@@ -513,6 +539,8 @@ def main():
     }
     if bsolve is not None:
         line["benchmark_solver"] = bsolve
+    if gsolve is not None:
+        line["general_form"] = gsolve
     if serve is not None:
         line["serving"] = serve
     print(json.dumps(line), flush=True)
