@@ -11,7 +11,8 @@ Every function is a plain, slow, FP64 numpy restatement of a definition in
 arXiv 2412.14973 and cites the passage it follows:
 
 * ``hilbert``  -- Hilbert-curve receiver reordering, eq. (10)-(14).
-* ``layout``   -- stacked unknowns Z-bar, L-bar, R-bar (Tile Low-rank MDD).
+* ``layout``   -- stacked unknowns Z-bar, L-bar, R-bar (Tile Low-rank MDD),
+                  for uniform tiles or any tile sizes d_i.
 * ``operator`` -- dense-literal operator C(theta) -> X_h (eq. 6-9, 15), the
                   misfit f (eq. 17a), W and W' and the factor gradients
                   (eq. 25-27), the adjoint and the back-mapping (eq. 11).

@@ -4,9 +4,10 @@ The reciprocity-aware method ties X_ji to X_ij (X = X^T).  Without that
 constraint (the general TLR form the paper builds on, Tile Low-rank MDD
 section, before the reciprocity reduction) every tile is free:
 
-* diagonal tile i: X_ii = L_ii R_ii^T (low rank, b x k each) or X_ii = Z_ii
+* diagonal tile i: X_ii = L_ii R_ii^T (low rank, d_i x k each) or X_ii = Z_ii
   (dense, no symmetrisation);
-* every off-diagonal tile (i, j), i != j: X_ij = L_ij R_ij^T.
+* every off-diagonal tile (i, j), i != j: X_ij = L_ij R_ij^T with L_ij
+  d_i x k and R_ij d_j x k (tile sizes d_i as in ``layout``: uniform or not).
 
 Stacking: the diagonal blocks in i order (Z_ii, or L_ii then R_ii), then the
 L factors of the ordered pairs (column j outer, row i inner, i != j), then
@@ -22,6 +23,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .layout import partition
+
 
 def ordered_pairs(n: int) -> list:
     return [(i, j) for j in range(n) for i in range(n) if i != j]
@@ -30,7 +33,7 @@ def ordered_pairs(n: int) -> list:
 @dataclass
 class GeneralLayout:
     nr: int
-    b: int
+    b: int | None        # the tile size of a uniform partition, else None
     n: int
     k_diag: list
     dense: list
@@ -40,15 +43,16 @@ class GeneralLayout:
     off_l: list = field(default_factory=list)
     off_r: list = field(default_factory=list)
     size: int = 0
+    d: list = field(default_factory=list)      # tile sizes d_i
+    roff: list = field(default_factory=list)   # first row of block i
 
     def rows(self, i):
-        return slice(i * self.b, (i + 1) * self.b)
+        return slice(self.roff[i], self.roff[i] + self.d[i])
 
 
-def make_general_layout(nr: int, b: int, ranks, diag_mode="rule") -> GeneralLayout:
-    if b <= 0 or nr % b != 0:
-        raise ValueError("tile size must divide n_r")
-    n = nr // b
+def make_general_layout(nr: int, b, ranks, diag_mode="rule", tiles=None) -> GeneralLayout:
+    d, roff = partition(nr, b, tiles)
+    n = len(d)
     pl = ordered_pairs(n)
     if isinstance(ranks, (int, np.integer)):
         kd, kp = [int(ranks)] * n, [int(ranks)] * len(pl)
@@ -57,36 +61,43 @@ def make_general_layout(nr: int, b: int, ranks, diag_mode="rule") -> GeneralLayo
         if len(ranks) != n + len(pl):
             raise ValueError("need N + N(N-1) ranks")
         kd, kp = ranks[:n], ranks[n:]
+    for i in range(n):
+        if kd[i] < 0 or kd[i] > d[i]:
+            raise ValueError("diagonal ranks must lie in [0, d_i]")
+    for p, (i, j) in enumerate(pl):
+        if kp[p] < 0 or kp[p] > min(d[i], d[j]):
+            raise ValueError("pair ranks must lie in [0, min(d_i, d_j)]")
     if isinstance(diag_mode, str):
-        dense = {"rule": [4 * k >= b for k in kd], "lowrank": [False] * n, "dense": [True] * n}[diag_mode]
+        dense = {"rule": [4 * kd[i] >= d[i] for i in range(n)], "lowrank": [False] * n,
+                 "dense": [True] * n}[diag_mode]
     else:
         dense = [bool(x) for x in diag_mode]
-    lay = GeneralLayout(nr, b, n, kd, dense, kp, pl)
+    uniform = b if tiles is None else (d[0] if len(set(d)) == 1 else None)
+    lay = GeneralLayout(nr, uniform, n, kd, dense, kp, pl, d=d, roff=roff)
     o = 0
     for i in range(n):
         lay.off_diag.append(o)
-        o += b * b if dense[i] else 2 * b * kd[i]
-    for p in range(len(pl)):
+        o += d[i] * d[i] if dense[i] else 2 * d[i] * kd[i]
+    for p, (i, j) in enumerate(pl):
         lay.off_l.append(o)
-        o += b * kp[p]
-    for p in range(len(pl)):
+        o += d[i] * kp[p]
+    for p, (i, j) in enumerate(pl):
         lay.off_r.append(o)
-        o += b * kp[p]
+        o += d[j] * kp[p]
     lay.size = o
     return lay
 
 
 def _blocks(theta, lay, i=None, p=None):
-    b = lay.b
     if p is None:
-        o = lay.off_diag[i]
+        o, di = lay.off_diag[i], lay.d[i]
         if lay.dense[i]:
-            return theta[o:o + b * b].reshape(b, b), None
+            return theta[o:o + di * di].reshape(di, di), None
         k = lay.k_diag[i]
-        return theta[o:o + b * k].reshape(b, k), theta[o + b * k:o + 2 * b * k].reshape(b, k)
-    k = lay.k_pair[p]
-    return (theta[lay.off_l[p]:lay.off_l[p] + b * k].reshape(b, k),
-            theta[lay.off_r[p]:lay.off_r[p] + b * k].reshape(b, k))
+        return theta[o:o + di * k].reshape(di, k), theta[o + di * k:o + 2 * di * k].reshape(di, k)
+    (i, j), k = lay.pair_list[p], lay.k_pair[p]
+    return (theta[lay.off_l[p]:lay.off_l[p] + lay.d[i] * k].reshape(lay.d[i], k),
+            theta[lay.off_r[p]:lay.off_r[p] + lay.d[j] * k].reshape(lay.d[j], k))
 
 
 def assemble_x(theta, lay: GeneralLayout) -> np.ndarray:
@@ -110,23 +121,22 @@ def gradient(theta, lay, Dh, Uh) -> np.ndarray:
     theta = np.asarray(theta, np.complex128)
     W = Dh.conj().T @ (Dh @ assemble_x(theta, lay) - Uh)
     g = np.zeros(lay.size, np.complex128)
-    b = lay.b
     for i in range(lay.n):
         Wii = W[lay.rows(i), lay.rows(i)]
         o = lay.off_diag[i]
         A, B = _blocks(theta, lay, i=i)
         if lay.dense[i]:
-            g[o:o + b * b] = Wii.ravel()
+            g[o:o + Wii.size] = Wii.ravel()
         else:
-            k = lay.k_diag[i]
-            g[o:o + b * k] = (Wii @ B.conj()).ravel()
-            g[o + b * k:o + 2 * b * k] = (Wii.T @ A.conj()).ravel()
+            gl, gr = Wii @ B.conj(), Wii.T @ A.conj()
+            g[o:o + gl.size] = gl.ravel()
+            g[o + gl.size:o + gl.size + gr.size] = gr.ravel()
     for p, (i, j) in enumerate(lay.pair_list):
         L, R = _blocks(theta, lay, p=p)
         Wij = W[lay.rows(i), lay.rows(j)]
-        k = lay.k_pair[p]
-        g[lay.off_l[p]:lay.off_l[p] + b * k] = (Wij @ R.conj()).ravel()
-        g[lay.off_r[p]:lay.off_r[p] + b * k] = (Wij.T @ L.conj()).ravel()
+        gl, gr = Wij @ R.conj(), Wij.T @ L.conj()
+        g[lay.off_l[p]:lay.off_l[p] + gl.size] = gl.ravel()
+        g[lay.off_r[p]:lay.off_r[p] + gr.size] = gr.ravel()
     return g
 
 

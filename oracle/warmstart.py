@@ -85,14 +85,14 @@ def warm_start(X, lay: lay_mod.Layout) -> np.ndarray:
     """theta of ``lay`` initialised from X (Hilbert order)."""
     X = np.asarray(X, np.complex128)
     th = np.zeros(lay.size, np.complex128)
-    b = lay.b
     for i in range(lay.n):
         T = X[lay.rows(i), lay.rows(i)]
         o = lay.off_diag[i]
         if lay.dense[i]:
-            th[o:o + b * b] = T.ravel()
+            th[o:o + T.size] = T.ravel()
         elif lay.k_diag[i] > 0:
-            th[o:o + b * lay.k_diag[i]] = takagi(T, lay.k_diag[i]).ravel()
+            Q = takagi(T, lay.k_diag[i])
+            th[o:o + Q.size] = Q.ravel()
     for p, (i, j) in enumerate(lay.pair_list):
         k = lay.k_pair[p]
         if k == 0:
@@ -101,6 +101,6 @@ def warm_start(X, lay: lay_mod.Layout) -> np.ndarray:
         rs = np.sqrt(s[:k])
         L = U[:, :k] * rs
         R = Vh[:k, :].T * rs                  # conj(V_k) Sigma_k^1/2
-        th[lay.off_l[p]:lay.off_l[p] + b * k] = L.ravel()
-        th[lay.off_r[p]:lay.off_r[p] + b * k] = R.ravel()
+        th[lay.off_l[p]:lay.off_l[p] + L.size] = L.ravel()
+        th[lay.off_r[p]:lay.off_r[p] + R.size] = R.ravel()
     return th

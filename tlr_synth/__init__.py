@@ -99,14 +99,17 @@ class TileSpec:
     cols: int
 
 
-def theta_tiles(nr: int, b: int, ranks, diag_dense) -> list:
+def theta_tiles(nr: int, b, ranks, diag_dense, tiles=None) -> list:
     """The tiles of the stacked unknown (Z-bar, L-bar, R-bar) in storage order.
 
     ``ranks``: an int (uniform) or a sequence of N diagonal ranks followed by
     N(N-1)/2 pair ranks in stacking order (tile column j ascending, then tile
-    row i > j ascending).  ``diag_dense``: sequence of N booleans.
+    row i > j ascending).  ``diag_dense``: sequence of N booleans.  ``tiles``:
+    the block sizes d_i of a non-uniform partition (None: N = nr / b blocks of
+    size b).
     """
-    n = nr // b
+    d = [int(b)] * (nr // b) if tiles is None else [int(t) for t in tiles]
+    n = len(d)
     pairs = [(i, j) for j in range(n) for i in range(j + 1, n)]
     if isinstance(ranks, (int, np.integer)):
         kd = [int(ranks)] * n
@@ -115,35 +118,37 @@ def theta_tiles(nr: int, b: int, ranks, diag_dense) -> list:
         ranks = [int(r) for r in ranks]
         kd, kp = ranks[:n], ranks[n:]
     tiles = []
+    out = []
     for i in range(n):
         if diag_dense[i]:
-            tiles.append(TileSpec("Z", i, i, b, b))
+            out.append(TileSpec("Z", i, i, d[i], d[i]))
         else:
-            tiles.append(TileSpec("Q", i, i, b, kd[i]))
+            out.append(TileSpec("Q", i, i, d[i], kd[i]))
     for p, (i, j) in enumerate(pairs):
-        tiles.append(TileSpec("L", i, j, b, kp[p]))
+        out.append(TileSpec("L", i, j, d[i], kp[p]))
     for p, (i, j) in enumerate(pairs):
-        tiles.append(TileSpec("R", i, j, b, kp[p]))
-    return tiles
+        out.append(TileSpec("R", i, j, d[j], kp[p]))
+    return out
 
 
-def planted_theta(nr: int, b: int, ranks, diag_dense, seed: int) -> np.ndarray:
+def planted_theta(nr: int, b, ranks, diag_dense, seed: int, tiles=None) -> np.ndarray:
     """Planted factor values, complex128, in the stacked storage order.
 
-    L, R, Q ~ CN(0,1)/sqrt(b k), scaled by 1/(1+|i-j|) so that energy sits near
+    L, R, Q ~ CN(0,1)/sqrt(d k), scaled by 1/(1+|i-j|) so that energy sits near
     the diagonal as it does for Hilbert-ordered Green's functions; a dense
-    diagonal tile is a symmetric CN(0, 1/b) block.
+    diagonal tile is a symmetric CN(0, 1/d) block (d: the factor's rows, the
+    tile size b of a uniform partition).
     """
     g = rng(seed)
     parts = []
-    for t in theta_tiles(nr, b, ranks, diag_dense):
+    for t in theta_tiles(nr, b, ranks, diag_dense, tiles):
         if t.kind == "Z":
-            a = cn(g, (b, b)) / math.sqrt(b)
+            a = cn(g, (t.rows, t.rows)) / math.sqrt(t.rows)
             parts.append(((a + a.T) * 0.5).ravel())
         else:
             if t.cols == 0:
                 continue
-            s = 1.0 / ((1 + abs(t.i - t.j)) * math.sqrt(b * t.cols))
+            s = 1.0 / ((1 + abs(t.i - t.j)) * math.sqrt(t.rows * t.cols))
             parts.append((cn(g, (t.rows, t.cols)) * s).ravel())
     if not parts:
         return np.zeros(0, dtype=np.complex128)
