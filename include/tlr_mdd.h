@@ -37,7 +37,8 @@ extern "C" {
 /* ---- status codes ---- */
 #define TLR_OK               0
 #define TLR_ERR_ARG         -1  /* NULL or out-of-range argument */
-#define TLR_ERR_SHAPE       -2  /* nr % tile != 0, nx*ny != nr, rank outside [0, tile] */
+#define TLR_ERR_SHAPE       -2  /* nr % tile != 0 (or tile sizes not summing to nr), nx*ny != nr,
+                                   rank outside [0, min(d_i, d_j)] */
 #define TLR_ERR_UNSUPPORTED -3  /* a valid option this build does not implement */
 #define TLR_ERR_NOMEM       -4  /* device allocation failed */
 #define TLR_ERR_CUDA        -5  /* a CUDA runtime call failed */
@@ -50,7 +51,7 @@ extern "C" {
 #define TLR_PREC_BF16X3 1  /* tcgen05 tensor cores: BF16 hi/lo split (3 products), 4M complex, FP32 accumulation */
 
 /* ---- diagonal tile representation (eq. 6 / eq. 7) ---- */
-#define TLR_DIAG_RULE     0  /* dense iff k_ii >= tile/4 */
+#define TLR_DIAG_RULE     0  /* dense iff k_ii >= d_i/4 (d_i: the tile size) */
 #define TLR_DIAG_LOWRANK  1  /* every X_ii = Q_ii Q_ii^T */
 #define TLR_DIAG_DENSE    2  /* every X_ii = P Z_ii = (Z_ii + Z_ii^T)/2 */
 #define TLR_DIAG_PER_TILE 3  /* diag_dense[i] != 0 -> dense */
@@ -76,20 +77,28 @@ typedef struct {
                                 Ignored when perm != NULL. */
     const int32_t* perm;     /* optional HOST array [nr]: perm[a] = natural index of the
                                 receiver at position a (overrides the Hilbert order) */
-    int32_t tile;            /* tile size b; nr % b == 0 (uniform partition) */
+    int32_t tile;            /* tile size b; nr % b == 0 (uniform partition, N = nr/b).
+                                Ignored when tiles != NULL. */
     int32_t rank;            /* uniform rank k of every tile, used when ranks == NULL */
-    const int32_t* ranks;    /* optional HOST array [N + N(N-1)/2], N = nr/b: the N
-                                diagonal ranks, then the sub-diagonal pair ranks in
-                                stacking order (column j ascending, row i > j ascending).
+    const int32_t* ranks;    /* optional HOST array [N + N(N-1)/2]: the N diagonal
+                                ranks, then the sub-diagonal pair ranks in stacking
+                                order (column j ascending, row i > j ascending).
                                 TLR_RECIP_NONE: [N + N(N-1)], the ordered pairs (i, j),
-                                i != j, column j ascending, row i ascending */
+                                i != j, column j ascending, row i ascending.  Tile (i, j)
+                                takes 0 <= k <= min(d_i, d_j). */
     int32_t diag_mode;       /* TLR_DIAG_* */
     const uint8_t* diag_dense; /* HOST [N], used with TLR_DIAG_PER_TILE */
     int32_t reciprocity;     /* TLR_RECIP_* */
     int32_t precision;       /* TLR_PREC_* */
     double alpha;            /* normalisation; 0 -> max_{s,r} |D[s,r]| of this D */
     int32_t input_memory;    /* TLR_MEM_* for D and U passed to tlr_mdd_create */
-    int32_t reserved;
+    int32_t ntiles;          /* N when tiles != NULL, else ignored */
+    const int32_t* tiles;    /* optional HOST array [ntiles]: the tile sizes d_i >= 1
+                                (block i = the d_i receivers after those of blocks
+                                < i in Hilbert order), sum d_i == nr.  The paper's
+                                partition is uniform but need not be (Tile Low-rank MDD
+                                section); NULL -> N = nr/tile tiles of size tile.
+                                tlr_mdd_warm_start needs a uniform partition. */
 } tlr_mdd_desc_t;
 
 /* Solver options (ADMM solver section; values the paper leaves open are
@@ -143,15 +152,16 @@ void tlr_mdd_solve_opts_init(tlr_mdd_solve_opts_t* o);
 int tlr_mdd_theta_size(const tlr_mdd_desc_t* d, int64_t* n_theta);
 
 /* Offsets (complex entries) of each block of theta, written to HOST arrays:
- * off_diag[N] (Q_ii b x k_ii, or Z_ii b x b), off_l[P] and off_r[P] (b x k_ij,
- * P = N(N-1)/2, pair order as for ranks).  Layout: all diagonal blocks in i
- * order, then L-bar, then R-bar; every block row-major.  R_ij is stored as the
- * b x k matrix whose transpose is the paper's k x b factor: X_ij = L_ij R_ij^T,
+ * off_diag[N] (Q_ii d_i x k_ii, or Z_ii d_i x d_i), off_l[P] (L_ij, d_i x k_ij)
+ * and off_r[P] (R_ij, d_j x k_ij), P = N(N-1)/2, pair order as for ranks; d_i
+ * = b for a uniform partition.  Layout: all diagonal blocks in i order, then
+ * L-bar, then R-bar; every block row-major.  R_ij is stored as the d_j x k
+ * matrix whose transpose is the paper's k x d_j factor: X_ij = L_ij R_ij^T,
  * X_ji = R_ij L_ij^T.  dense_out[N] (HOST, may be NULL) receives the resolved
  * diagonal representation.  TLR_RECIP_NONE: P = N(N-1) ordered pairs (order as
- * for ranks), X_ij = L_ij R_ij^T for each; a low-rank diagonal block is L_ii
- * (b x k_ii) at off_diag[i] followed by R_ii (b x k_ii), X_ii = L_ii R_ii^T; a
- * dense one is Z_ii with X_ii = Z_ii. */
+ * for ranks), X_ij = L_ij R_ij^T for each (L_ij d_i x k, R_ij d_j x k); a
+ * low-rank diagonal block is L_ii (d_i x k_ii) at off_diag[i] followed by R_ii
+ * (d_i x k_ii), X_ii = L_ii R_ii^T; a dense one is Z_ii with X_ii = Z_ii. */
 int tlr_mdd_theta_layout(const tlr_mdd_desc_t* d, int64_t* off_diag, int64_t* off_l,
                          int64_t* off_r, uint8_t* dense_out);
 

@@ -5,7 +5,7 @@
 // Internal representation.  Every factor of the TLR parametrisation acts on
 // exactly one block column of Dfrak in the forward product and on exactly one
 // block row of Y, and for a symmetric X both are the same block: block i holds
-//   F_i = [ Q_ii | L_ij (j < i) | R_ji (j > i) ]   (b x K_i, row-major panel)
+//   F_i = [ Q_ii | L_ij (j < i) | R_ji (j > i) ]   (d_i x K_i, row-major panel)
 // so that, with T_i = F_i^T Dfrak_i (compress) and T~ the rows of T taken at
 // each column's partner factor (L_ij <-> R_ij, Q_ii <-> itself),
 //   Y_i = X_h Dfrak |_i = F_i T~_i + P(Z_ii) Dfrak_i            (eq. 6-9, 15)
@@ -145,9 +145,12 @@ struct Arena {
 // both); in the general form (reciprocity NONE) they are disjoint: A panels
 // first, then B panels, in one panel vector.
 struct Layout {
-    int64_t nr = 0, ns = 0, b = 0;
+    int64_t nr = 0, ns = 0;
+    int64_t b = 0;                 // tile size of a uniform partition, 0 for a non-uniform one
+    int64_t dmax = 0;              // the largest tile size
     int N = 0, P = 0;              // P: stored pairs (N(N-1)/2 reciprocal, N(N-1) general)
     bool general = false;
+    std::vector<int64_t> d, roff;  // tile sizes d_i; roff[i] = first row of block i (roff[N] = nr)
     std::vector<int> kd, kp;
     std::vector<uint8_t> dense;
     std::vector<int64_t> off_diag, off_l, off_r;   // general low-rank diagonal: L_ii at off_diag, R_ii after it
@@ -162,8 +165,8 @@ struct Layout {
     std::vector<int> dslot;   // dense slot of block i or -1
     int64_t Ktot = 0, KtotB = 0, ncol = 0, nlr = 0, ndense = 0, nth = 0;
     // maps (host copies): partner[A column] = row of T (B column); partnerB[B column] = row of V (A column)
-    std::vector<int> partner, partnerB, colstride, panstride;
-    std::vector<long long> colsrc, colpan, zsrc;
+    std::vector<int> partner, partnerB, colstride, panstride, colrows, zdim;
+    std::vector<long long> colsrc, colpan, zsrc, zoff;   // zoff[slot]: dense tile offset after the low-rank panels
 };
 
 int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
@@ -171,16 +174,33 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
         err = "desc is NULL";
         return TLR_ERR_ARG;
     }
-    if (d->nr <= 0 || d->ns <= 0 || d->tile <= 0) {
+    if (d->nr <= 0 || d->ns <= 0 || (!d->tiles && d->tile <= 0)) {
         err = "nr, ns and tile must be positive";
-        return TLR_ERR_SHAPE;
-    }
-    if (d->nr % d->tile != 0) {
-        err = "tile must divide nr (uniform partition)";
         return TLR_ERR_SHAPE;
     }
     if (d->nr > (int64_t)1 << 30 || d->ns > (int64_t)1 << 30) {
         err = "nr and ns must be below 2^30";
+        return TLR_ERR_SHAPE;
+    }
+    if (d->tiles) {
+        if (d->ntiles <= 0 || d->ntiles > d->nr) {
+            err = "ntiles must lie in [1, nr]";
+            return TLR_ERR_SHAPE;
+        }
+        int64_t sum = 0;
+        for (int i = 0; i < d->ntiles; ++i) {
+            if (d->tiles[i] <= 0) {
+                err = "tile sizes must be positive";
+                return TLR_ERR_SHAPE;
+            }
+            sum += d->tiles[i];
+        }
+        if (sum != d->nr) {
+            err = "tile sizes must sum to nr";
+            return TLR_ERR_SHAPE;
+        }
+    } else if (d->nr % d->tile != 0) {
+        err = "tile must divide nr (uniform partition)";
         return TLR_ERR_SHAPE;
     }
     if (d->reciprocity != TLR_RECIP_SYMMETRIC && d->reciprocity != TLR_RECIP_NONE) {
@@ -193,31 +213,49 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
     }
     L.nr = d->nr;
     L.ns = d->ns;
-    L.b = d->tile;
-    L.N = (int)(d->nr / d->tile);
+    L.N = d->tiles ? d->ntiles : (int)(d->nr / d->tile);
+    L.d.assign(L.N, d->tiles ? 0 : d->tile);
+    if (d->tiles)
+        for (int i = 0; i < L.N; ++i) L.d[i] = d->tiles[i];
+    L.roff.assign(L.N + 1, 0);
+    for (int i = 0; i < L.N; ++i) L.roff[i + 1] = L.roff[i] + L.d[i];
+    L.dmax = *std::max_element(L.d.begin(), L.d.end());
+    L.b = std::all_of(L.d.begin(), L.d.end(), [&](int64_t x) { return x == L.d[0]; }) ? L.d[0] : 0;
     L.general = d->reciprocity == TLR_RECIP_NONE;
     L.P = L.general ? L.N * (L.N - 1) : L.N * (L.N - 1) / 2;
     const int N = L.N, P = L.P;
+    // row / column block of every stored pair, in stacking order
+    std::vector<int> prow(P), pcol(P);
+    {
+        int p = 0;
+        for (int j = 0; j < N; ++j)
+            for (int i = L.general ? 0 : j + 1; i < N; ++i) {
+                if (i == j) continue;
+                prow[p] = i;
+                pcol[p] = j;
+                ++p;
+            }
+    }
     L.kd.assign(N, d->rank);
     L.kp.assign(P, d->rank);
     if (d->ranks) {
         for (int i = 0; i < N; ++i) L.kd[i] = d->ranks[i];
         for (int p = 0; p < P; ++p) L.kp[p] = d->ranks[N + p];
     }
-    for (int k : L.kd)
-        if (k < 0 || k > L.b) {
+    for (int i = 0; i < N; ++i)
+        if (L.kd[i] < 0 || L.kd[i] > L.d[i]) {
             err = "rank outside [0, tile]";
             return TLR_ERR_SHAPE;
         }
-    for (int k : L.kp)
-        if (k < 0 || k > L.b) {
+    for (int p = 0; p < P; ++p)
+        if (L.kp[p] < 0 || L.kp[p] > std::min(L.d[prow[p]], L.d[pcol[p]])) {
             err = "rank outside [0, tile]";
             return TLR_ERR_SHAPE;
         }
     L.dense.assign(N, 0);
     for (int i = 0; i < N; ++i) {
         switch (d->diag_mode) {
-            case TLR_DIAG_RULE: L.dense[i] = (4LL * L.kd[i] >= L.b); break;
+            case TLR_DIAG_RULE: L.dense[i] = (4LL * L.kd[i] >= L.d[i]); break;
             case TLR_DIAG_LOWRANK: L.dense[i] = 0; break;
             case TLR_DIAG_DENSE: L.dense[i] = 1; break;
             case TLR_DIAG_PER_TILE:
@@ -232,21 +270,22 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
     }
     // theta (paper stacking): diagonal blocks, then L-bar, then R-bar (general
     // form: the ordered pairs (i, j), i != j, column j outer, row i inner)
+    // (L_ij: d_i x k, R_ij: d_j x k; diagonal blocks d_i x k or d_i x d_i)
     int64_t o = 0;
     L.off_diag.resize(N);
     for (int i = 0; i < N; ++i) {
         L.off_diag[i] = o;
-        o += L.b * (L.dense[i] ? L.b : (L.general ? 2 : 1) * L.kd[i]);
+        o += L.d[i] * (L.dense[i] ? L.d[i] : (L.general ? 2 : 1) * L.kd[i]);
     }
     L.off_l.resize(P);
     L.off_r.resize(P);
     for (int p = 0; p < P; ++p) {
         L.off_l[p] = o;
-        o += L.b * L.kp[p];
+        o += L.d[prow[p]] * L.kp[p];
     }
     for (int p = 0; p < P; ++p) {
         L.off_r[p] = o;
-        o += L.b * L.kp[p];
+        o += L.d[pcol[p]] * L.kp[p];
     }
     L.ntheta = o;
 
@@ -289,7 +328,7 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
                     if (L.dense[i] || L.kd[i] == 0) continue;
                     k = L.kd[i];
                     offL = L.off_diag[i];
-                    offR = L.off_diag[i] + L.b * k;
+                    offR = L.off_diag[i] + L.d[i] * k;
                 } else {
                     const int q = op(j, i);
                     k = L.kp[q];
@@ -335,19 +374,29 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
         L.KtotB = L.Ktot;
     }
     L.ncol = L.general ? L.Ktot + L.KtotB : L.Ktot;
-    L.nlr = L.b * L.ncol;
+    // panel i: d_i x K_i row-major; A panels first, then (general form) B panels
     L.panA.assign(N, 0);
     L.panB.assign(N, 0);
+    int64_t po = 0;
     for (int i = 0; i < N; ++i) {
-        L.panA[i] = L.b * L.Koff[i];
-        L.panB[i] = L.general ? L.b * (L.Ktot + L.KoffB[i]) : L.panA[i];
+        L.panA[i] = po;
+        po += L.d[i] * L.Kb[i];
     }
+    if (L.general)
+        for (int j = 0; j < N; ++j) {
+            L.panB[j] = po;
+            po += L.d[j] * L.KbB[j];
+        }
+    else
+        L.panB = L.panA;
+    L.nlr = po;
     L.partner.resize(L.Ktot);
     L.partnerB.resize(L.KtotB);
     L.colsrc.resize(L.ncol);
     L.colstride.resize(L.ncol);
     L.colpan.resize(L.ncol);
     L.panstride.resize(L.ncol);
+    L.colrows.resize(L.ncol);
     for (int i = 0; i < N; ++i) {
         int64_t c = 0;
         for (auto& f : blkA[i]) {
@@ -358,6 +407,7 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
                 L.colstride[g] = f.k;
                 L.colpan[g] = L.panA[i] + c + q;
                 L.panstride[g] = L.Kb[i];
+                L.colrows[g] = (int)L.d[i];
             }
             c += f.k;
         }
@@ -373,6 +423,7 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
                     L.colstride[L.Ktot + g] = f.k;
                     L.colpan[L.Ktot + g] = L.panB[j] + c + q;
                     L.panstride[L.Ktot + g] = L.KbB[j];
+                    L.colrows[L.Ktot + g] = (int)L.d[j];
                 }
                 c += f.k;
             }
@@ -381,12 +432,16 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
         L.partnerB = L.partner;
     }
     L.dslot.assign(N, -1);
+    int64_t zo = 0;
     for (int i = 0; i < N; ++i)
         if (L.dense[i]) {
             L.dslot[i] = (int)L.ndense++;
             L.zsrc.push_back(L.off_diag[i]);
+            L.zoff.push_back(zo);
+            L.zdim.push_back((int)L.d[i]);
+            zo += L.d[i] * L.d[i];
         }
-    L.nth = L.nlr + L.ndense * L.b * L.b;
+    L.nth = L.nlr + zo;
     if (L.nth != L.ntheta) {
         err = "internal: panel size differs from theta size";
         return TLR_ERR_STATE;
@@ -424,6 +479,7 @@ struct tlr_mdd_s {
     double* dpart = nullptr;   // reduction partial slabs
     int* d_partner = nullptr;    // [Ktot] row of T for each A column
     int* d_partnerB = nullptr;   // [KtotB] row of V for each B column (= d_partner when reciprocal)
+    long long* d_roff = nullptr; // [N + 1] first row of each block
     PanelMap pm{};
     // theta-space vectors
     cf *x = nullptr, *z = nullptr, *u = nullptr, *v = nullptr, *g = nullptr, *gf = nullptr, *dd = nullptr,
@@ -501,12 +557,14 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->A2 = a.take<cf>(nrs);
     h->T = a.take<cf>(kns);
     h->Tp = a.take<cf>(knsp);
-    const size_t nz = std::max<size_t>(1, (size_t)L.ndense * L.b * L.b);
+    const size_t nz = std::max<size_t>(1, (size_t)(L.nth - L.nlr));
     h->Zs = a.take<cf>(nz);
     h->Zsd = a.take<cf>(nz);
     h->part = a.take<cf>((size_t)h->nsplit * L.nth);
     h->dpart = a.take<double>(16 * kRedBlocks);
-    h->n_rpart = L.b % kFuseRows == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
+    // the fused residual step works on 16-row tiles of one block each: equal
+    // tiles, a multiple of 16
+    h->n_rpart = L.b > 0 && L.b % kFuseRows == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
     h->rpart = a.take<double>((size_t)std::max<long long>(1, h->n_rpart));
     const size_t K = std::max<int64_t>(1, L.ncol);
     h->d_partner = a.take<int>(std::max<int64_t>(1, L.general ? L.Ktot + L.KtotB : L.Ktot));
@@ -515,8 +573,14 @@ void carve(tlr_mdd_s* h, Arena& a) {
     int* colstride = a.take<int>(K);
     long long* colpan = a.take<long long>(K);
     int* panstride = a.take<int>(K);
-    long long* zsrc = a.take<long long>(std::max<int64_t>(1, L.ndense));
-    h->pm = PanelMap{colsrc, colstride, colpan, panstride, zsrc, L.ncol, L.b, L.ndense, L.nlr};
+    int* colrows = a.take<int>(K);
+    const size_t nd = std::max<int64_t>(1, L.ndense);
+    long long* zsrc = a.take<long long>(nd);
+    long long* zoff = a.take<long long>(nd);
+    int* zdim = a.take<int>(nd);
+    h->d_roff = a.take<long long>((size_t)L.N + 1);
+    h->pm = PanelMap{colsrc, colstride, colpan, panstride, colrows, zsrc, zoff, zdim,
+                     L.ncol, L.dmax, L.ndense, L.nlr};
     const size_t nth = std::max<int64_t>(1, L.nth);
     h->x = a.take<cf>(nth);
     h->z = a.take<cf>(nth);
@@ -545,9 +609,10 @@ void carve(tlr_mdd_s* h, Arena& a) {
 // distinct operands listed in build_tc; 1 KB alignment per operand).
 long long packed_estimate(const Layout& L) {
     auto pb = [](long long R, long long K, int TR) { return (packed_bytes(R, K, TR) + 1023) & ~1023LL; };
-    const long long b = L.b, ns = L.ns;
+    const long long ns = L.ns;
     long long t = 0;
     for (int i = 0; i < L.N; ++i) {
+        const long long b = L.d[i];
         const long long Ki = std::max(L.Kb[i], L.KbB[i]);   // upper bound for both sides
         if (Ki > 0) {
             t += 3 * pb(Ki, b, kPackTRA) + 2 * pb(b, Ki, kPackTRA);     // F, conj F, F_d (KM); F, F_d (MK)
@@ -582,9 +647,10 @@ int split_for(const Layout& L, int prec) {
     if (prec == TLR_PREC_BF16X3) {
         long long tiles = 0;
         for (int i = 0; i < L.N; ++i) {
-            tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.Kb[i] + kPackTRB - 1) / kPackTRB);
-            if (L.general) tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.KbB[i] + kPackTRB - 1) / kPackTRB);
-            if (L.dense[i]) tiles += ((L.b + kPackTRA - 1) / kPackTRA) * ((L.b + kPackTRB - 1) / kPackTRB);
+            const long long b = L.d[i];
+            tiles += ((b + kPackTRA - 1) / kPackTRA) * ((L.Kb[i] + kPackTRB - 1) / kPackTRB);
+            if (L.general) tiles += ((b + kPackTRA - 1) / kPackTRA) * ((L.KbB[i] + kPackTRB - 1) / kPackTRB);
+            if (L.dense[i]) tiles += ((b + kPackTRA - 1) / kPackTRA) * ((b + kPackTRB - 1) / kPackTRB);
         }
         tiles = std::max(1LL, tiles);
         const long long sms = sm_count(), smax = std::max(1LL, std::min(16LL, (long long)L.ns / 256));
@@ -601,9 +667,10 @@ int split_for(const Layout& L, int prec) {
     }
     long long tiles = 0;
     for (int i = 0; i < L.N; ++i) {
-        tiles += ((L.b + 63) / 64) * ((L.Kb[i] + 63) / 64);
-        if (L.general) tiles += ((L.b + 63) / 64) * ((L.KbB[i] + 63) / 64);
-        if (L.dense[i]) tiles += ((L.b + 63) / 64) * ((L.b + 63) / 64);
+        const long long b = L.d[i];
+        tiles += ((b + 63) / 64) * ((L.Kb[i] + 63) / 64);
+        if (L.general) tiles += ((b + 63) / 64) * ((L.KbB[i] + 63) / 64);
+        if (L.dense[i]) tiles += ((b + 63) / 64) * ((b + 63) / 64);
     }
     return choose_split(std::max(1LL, tiles), L.ns);
 }
@@ -629,7 +696,7 @@ struct HostTable {
 // Build the grouped problems for every contraction of the handle and upload.
 int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
     const Layout& L = h->L;
-    const long long ns = L.ns, b = L.b;
+    const long long ns = L.ns;
     const size_t slot = ((sizeof(GProb) * (3 * (size_t)L.N + 1)) + 255) & ~size_t(255);
     int ti = 0;
     auto upload = [&](GemmLaunch& G, std::vector<GProb>& v, int am, int bm, int epi) -> int {
@@ -675,7 +742,7 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             const cf* src = which == 1 ? Dd : X;
             const cf* data = which == 2 ? h->R : h->Dt;
             cf* out = which == 0 ? h->T : h->Tp;
-            p.t[0] = term(src + (aside ? L.panA[i] : L.panB[i]), Ki, data + (long long)i * b * ns, ns, nullptr, (int)b,
+            p.t[0] = term(src + (aside ? L.panA[i] : L.panB[i]), Ki, data + L.roff[i] * ns, ns, nullptr, (int)L.d[i],
                           which == 2, false);
             p.nt = 1;
             p.M = Ki;
@@ -700,17 +767,19 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             const int Ki = L.Kb[i];
             const cf* Fi = X + L.panA[i];
             const cf* Fd = Dd + L.panA[i];
-            const cf* Di = h->Dt + (long long)i * b * ns;
+            const long long b = L.d[i];
+            const cf* Di = h->Dt + L.roff[i] * ns;
+            const long long zo = L.dense[i] ? L.zoff[L.dslot[i]] : 0;
             int nt = 0;
             if (which <= 1) {
                 if (Ki > 0) p.t[nt++] = term(Fi, Ki, h->T, ns, gi, Ki, false, false);
-                if (L.dense[i]) p.t[nt++] = term(h->Zs + L.dslot[i] * b * b, b, Di, ns, nullptr, (int)b, false, false);
+                if (L.dense[i]) p.t[nt++] = term(h->Zs + zo, b, Di, ns, nullptr, (int)b, false, false);
             } else if (which == 2) {
                 if (Ki > 0) {
                     p.t[nt++] = term(Fd, Ki, h->T, ns, gi, Ki, false, false);
                     p.t[nt++] = term(Fi, Ki, h->Tp, ns, gi, Ki, false, false);
                 }
-                if (L.dense[i]) p.t[nt++] = term(h->Zsd + L.dslot[i] * b * b, b, Di, ns, nullptr, (int)b, false, false);
+                if (L.dense[i]) p.t[nt++] = term(h->Zsd + zo, b, Di, ns, nullptr, (int)b, false, false);
             } else {
                 if (Ki > 0) p.t[nt++] = term(Fd, Ki, h->Tp, ns, gi, Ki, false, false);
             }
@@ -718,8 +787,8 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             p.M = (int)b;
             p.N = (int)ns;
             cf* out = which <= 1 ? h->R : (which == 2 ? h->A1 : h->A2);
-            p.C = out + (long long)i * b * ns;
-            p.S = h->Ut + (long long)i * b * ns;
+            p.C = out + L.roff[i] * ns;
+            p.S = h->Ut + L.roff[i] * ns;
             p.ldc = ns;
             v.push_back(p);
         }
@@ -741,8 +810,9 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
     {
         std::vector<GProb> v;
         for (int i = 0; i < L.N; ++i) {
-            const cf* Ri = h->R + (long long)i * b * ns;
-            const cf* Di = h->Dt + (long long)i * b * ns;
+            const long long b = L.d[i];
+            const cf* Ri = h->R + L.roff[i] * ns;
+            const cf* Di = h->Dt + L.roff[i] * ns;
             if (!L.general && L.Kb[i] > 0) {
                 // reciprocal: block i's panel takes both terms
                 GProb p = blank();
@@ -782,7 +852,7 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
                 p.nt = 1;
                 p.M = (int)b;
                 p.N = (int)b;
-                p.C = h->part + L.nlr + L.dslot[i] * b * b;
+                p.C = h->part + L.nlr + L.zoff[L.dslot[i]];
                 p.ldc = b;
                 v.push_back(p);
             }
@@ -917,6 +987,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     std::set<PackKey> rkeys;
     for (auto& ko : order) {
         const PackKey& k = ko.first;
+        if (L.b == 0) break;   // non-uniform tiles: no fused residual step
         if (!is_R(k) || k.gr || k.gk || k.sgn < 0 || k.ld != L.ns) continue;
         const long long off = reinterpret_cast<const cf*>(k.src) - h->R;
         if (off % ((long long)L.b * L.ns) != 0) continue;
@@ -930,7 +1001,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             rkeys.insert(k);
         }
     }
-    bool rfuse = L.b % kFuseRows == 0 && h->n_rpart > 0;
+    bool rfuse = L.b > 0 && L.b % kFuseRows == 0 && h->n_rpart > 0;
     for (int i = 0; i < L.N && rfuse; ++i)
         if (!rkn[i] || !rmk[i]) rfuse = false;
     std::vector<char*> rowptr;
@@ -1207,6 +1278,7 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
     h->d.perm = nullptr;
     h->d.ranks = nullptr;
     h->d.diag_dense = nullptr;
+    h->d.tiles = nullptr;
     h->st = (cudaStream_t)stream;
     int rc = build_layout(d, h->L, h->err);
     if (rc) {
@@ -1290,9 +1362,14 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         CKF(cudaMemcpyAsync((void*)h->pm.colstride, L.colstride.data(), L.ncol * sizeof(int), cudaMemcpyHostToDevice, h->st));
         CKF(cudaMemcpyAsync((void*)h->pm.colpan, L.colpan.data(), L.ncol * sizeof(long long), cudaMemcpyHostToDevice, h->st));
         CKF(cudaMemcpyAsync((void*)h->pm.panstride, L.panstride.data(), L.ncol * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.colrows, L.colrows.data(), L.ncol * sizeof(int), cudaMemcpyHostToDevice, h->st));
     }
-    if (L.ndense > 0)
+    if (L.ndense > 0) {
         CKF(cudaMemcpyAsync((void*)h->pm.zsrc, L.zsrc.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.zoff, L.zoff.data(), L.ndense * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+        CKF(cudaMemcpyAsync((void*)h->pm.zdim, L.zdim.data(), L.ndense * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    }
+    CKF(cudaMemcpyAsync(h->d_roff, L.roff.data(), (L.N + 1) * sizeof(long long), cudaMemcpyHostToDevice, h->st));
     // solver counters and the contraction kernels' error word start at zero
     CKF(cudaMemsetAsync(h->ints, 0, (SI_COUNT + 8) * sizeof(int), h->st));
     std::vector<HostTable> tabs;
@@ -1335,7 +1412,7 @@ int tlr_mdd_set_data(tlr_mdd_t* h, const void* D, const void* U, int32_t input_m
 
 static int forward(tlr_mdd_s* h, bool plain_apply) {
     const Layout& L = h->L;
-    CK(h, sym_dense(h->x, L.nlr, L.ndense, L.b, h->Zs, h->st, L.general));
+    CK(h, sym_dense(h->x, L.nlr, L.ndense, L.dmax, h->Zs, h->st, L.general, h->pm.zoff, h->pm.zdim));
     CK(h, run_gemm(h->Lc_x, h->st));
     if (h->n_tpack) CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)L.ns, h->st));
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
@@ -1348,7 +1425,8 @@ static int gradient(tlr_mdd_s* h) {
     const Layout& L = h->L;
     CK(h, run_gemm(h->Lc_v, h->st));
     CK(h, run_gemm(h->Lp, h->st));
-    CK(h, reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.b, h->gf, h->st, L.general));
+    CK(h, reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.dmax, h->gf, h->st, L.general, h->pm.zoff,
+                      h->pm.zdim));
     return TLR_OK;
 }
 
@@ -1714,6 +1792,7 @@ int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
     if (!X || !theta) FAIL(h, TLR_ERR_ARG, "X or theta is NULL");
     const Layout& L = h->L;
     if (L.general) FAIL(h, TLR_ERR_UNSUPPORTED, "the warm start is defined for the reciprocal form");
+    if (L.b == 0) FAIL(h, TLR_ERR_UNSUPPORTED, "the warm start needs a uniform tile partition");
     if (L.b > 512) FAIL(h, TLR_ERR_SHAPE, "warm start needs tile <= 512");
     const int N = L.N, b = (int)L.b;
     std::vector<int2> tl;
@@ -1857,7 +1936,7 @@ int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     if (!L.general) {
         tiles.resize(L.N + L.P);
         for (int i = 0; i < L.N; ++i)
-            tiles[i] = AsmTile{L.off_diag[i], L.off_diag[i], L.dense[i] ? (int)L.b : L.kd[i], (int)L.dense[i]};
+            tiles[i] = AsmTile{L.off_diag[i], L.off_diag[i], L.dense[i] ? (int)L.d[i] : L.kd[i], (int)L.dense[i]};
         for (int p = 0; p < L.P; ++p) tiles[L.N + p] = AsmTile{L.off_l[p], L.off_r[p], L.kp[p], 0};
     } else {
         // every tile, row-major; ordered pair index of (i, j): j (N - 1) + i - (i > j)
@@ -1865,8 +1944,8 @@ int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
         for (int i = 0; i < L.N; ++i)
             for (int j = 0; j < L.N; ++j) {
                 if (i == j) {
-                    const int k = L.dense[i] ? (int)L.b : L.kd[i];
-                    tiles[i * L.N + j] = AsmTile{L.off_diag[i], L.off_diag[i] + (L.dense[i] ? 0 : L.b * k), k,
+                    const int k = L.dense[i] ? (int)L.d[i] : L.kd[i];
+                    tiles[i * L.N + j] = AsmTile{L.off_diag[i], L.off_diag[i] + (L.dense[i] ? 0 : L.d[i] * k), k,
                                                  (int)L.dense[i]};
                 } else {
                     const int q = j * (L.N - 1) + i - (i > j ? 1 : 0);
@@ -1879,7 +1958,8 @@ int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X) {
     CK(h, cudaMallocAsync((void**)&Xh, (size_t)nr * nr * sizeof(cf), h->st));
     cudaError_t e = cudaMallocAsync((void**)&dt, tiles.size() * sizeof(AsmTile), h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(AsmTile), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess) e = assemble_dense((const cf*)theta, nr, L.b, L.N, dt, Xh, h->st, L.general);
+    if (e == cudaSuccess)
+        e = assemble_dense((const cf*)theta, nr, L.dmax, L.N, dt, Xh, h->st, L.general, L.b > 0 ? nullptr : h->d_roff);
     if (e == cudaSuccess) e = unpermute_dense(Xh, nr, h->perm, (cf*)X, h->st);
     if (dt) cudaFreeAsync(dt, h->st);
     cudaFreeAsync(Xh, h->st);
@@ -2036,7 +2116,7 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
             for (int t = 0; t < o->lbfgs_iters; ++t) {
                 CK(h, sv_direction(S, h->st));
                 CK(h, run_gemm(h->Lc_d, h->st));
-                CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.b, h->Zsd, h->st, L.general));
+                CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.dmax, h->Zsd, h->st, L.general, h->pm.zoff, h->pm.zdim));
                 CK(h, run_gemm(h->Le_a1, h->st));
                 CK(h, run_gemm(h->Le_a2, h->st));
                 CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));

@@ -211,8 +211,10 @@ struct AsmTile {
     int k;
     int dense;
 };
+// roff: nullptr for N tiles of size b, else DEVICE [N + 1] block row offsets
+// (roff[N] = nr) of a non-uniform partition
 cudaError_t assemble_dense(const cf* theta, long long nr, long long b, int N, const AsmTile* tiles, cf* Xh,
-                           cudaStream_t st, int general = 0);
+                           cudaStream_t st, int general = 0, const long long* roff = nullptr);
 // X[perm[a], perm[c]] = Xh[a, c]
 cudaError_t unpermute_dense(const cf* Xh, long long nr, const int32_t* perm, cf* X, cudaStream_t st);
 
@@ -228,19 +230,26 @@ struct PanelMap {
     const int* colstride;      // [Ktot] row stride in theta (rank of the factor)
     const long long* colpan;   // [Ktot] panel offset of row 0 of this column
     const int* panstride;      // [Ktot] row stride in the panel (K of its block)
+    const int* colrows;        // [Ktot] rows of this column's block (its tile size d_i)
     const long long* zsrc;     // [ndense] theta offset of each dense tile
-    long long Ktot, b, ndense, zbase;  // zbase = b * Ktot
+    const long long* zoff;     // [ndense] offset of each dense tile after zbase
+    const int* zdim;           // [ndense] size d_i of each dense tile
+    long long Ktot, b, ndense, zbase;  // b = the largest tile size; zbase = low-rank panel entries
 };
 cudaError_t theta_to_panel(const PanelMap& m, const cf* theta, cf* pan, cudaStream_t st);
 cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStream_t st);
-// Zs = (Z + Z^T)/2 for every dense tile of a panel vector
-// (general != 0: Zs = Z^T, the general form's dense tiles)
+// Dense tiles of a panel vector: ndense tiles of size b stored one after the
+// other (zoff == nullptr), or tile t of size zdim[t] at zoff[t] (DEVICE arrays;
+// b is then the largest size).
+// Zs = (Z + Z^T)/2 for every dense tile (general != 0: Zs = Z^T, the general
+// form's dense tiles); Zs has the same tile offsets.
 cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st,
-                      int general = 0);
+                      int general = 0, const long long* zoff = nullptr, const int* zdim = nullptr);
 // grad[e] = sum_c part[c * stride + e] (LR part), dense tiles symmetrised: (G + G^T)/2
 // (general != 0: G^T, the general form's dense tiles)
 cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
-                        long long b, cf* grad, cudaStream_t st, int general = 0);
+                        long long b, cf* grad, cudaStream_t st, int general = 0, const long long* zoff = nullptr,
+                        const int* zdim = nullptr);
 
 // partial FP64 real dot sums over float arrays (2 per complex) -> part[kRedBlocks]
 cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st);

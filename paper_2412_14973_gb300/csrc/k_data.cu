@@ -175,25 +175,42 @@ cudaError_t permute_normalise(const cf* D, long long ns, long long nr, const int
     return cudaGetLastError();
 }
 
+// Block of row r: r / b for equal tiles, else the largest i with roff[i] <= r.
+__device__ __forceinline__ int block_of(long long r, long long b, const long long* roff, int N) {
+    if (!roff) return (int)(r / b);
+    int lo = 0, hi = N - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (roff[mid] <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // X_h = C(theta) assembled entry by entry from the stacked unknown (eq. 6-9,
 // 15).  An entry of a super-diagonal tile evaluates exactly the expression of
 // its mirror in the sub-diagonal tile (same products, same order), so the
 // result is bitwise symmetric, as X_ji = X_ij^T demands.
 // General form (general != 0): the tiles are listed row-major (i N + j) and
 // every entry is its own tile's L R^T (or Z entry), without mirroring.
+// roff == nullptr: N tiles of size b; else block i covers rows roff[i] ..
+// roff[i + 1] - 1.
 __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b, int N, const AsmTile* __restrict__ t,
-                           cf* __restrict__ Xh, int general) {
+                           cf* __restrict__ Xh, int general, const long long* __restrict__ roff) {
     const long long n2 = nr * nr;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
          e += (long long)gridDim.x * blockDim.x) {
         long long r = e / nr, c = e % nr;
-        int i = (int)(r / b), j = (int)(c / b);
+        int i = block_of(r, b, roff, N), j = block_of(c, b, roff, N);
         if (general) {
             const AsmTile& a = t[i * N + j];
-            const long long rr = r - i * b, cc = c - j * b;
+            const long long rr = r - (roff ? roff[i] : i * b), cc = c - (roff ? roff[j] : j * b);
+            const long long di = roff ? roff[i + 1] - roff[i] : b;
             float x = 0.f, y = 0.f;
             if (i == j && a.dense) {
-                const cf u = th[a.off_l + rr * b + cc];
+                const cf u = th[a.off_l + rr * di + cc];
                 x = u.x;
                 y = u.y;
             } else {
@@ -216,7 +233,7 @@ __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b,
             i = j;
             j = ti;
         }
-        long long rr = r - i * b, cc = c - j * b;
+        long long rr = r - (roff ? roff[i] : i * b), cc = c - (roff ? roff[j] : j * b);
         if (i == j && rr > cc) {  // low-rank diagonal: evaluate the upper triangle's entry
             const long long t2 = rr;
             rr = cc;
@@ -225,7 +242,8 @@ __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b,
         const AsmTile& a = t[i == j ? i : N + (j * N - j * (j + 1) / 2 + (i - j - 1))];
         float x = 0.f, y = 0.f;
         if (i == j && a.dense) {
-            const cf u = th[a.off_l + rr * b + cc], v = th[a.off_l + cc * b + rr];
+            const long long di = roff ? roff[i + 1] - roff[i] : b;
+            const cf u = th[a.off_l + rr * di + cc], v = th[a.off_l + cc * di + rr];
             x = 0.5f * (u.x + v.x);
             y = 0.5f * (u.y + v.y);
         } else {
@@ -242,8 +260,8 @@ __global__ void k_assemble(const cf* __restrict__ th, long long nr, long long b,
 }
 
 cudaError_t assemble_dense(const cf* theta, long long nr, long long b, int N, const AsmTile* tiles, cf* Xh,
-                           cudaStream_t st, int general) {
-    k_assemble<<<1024, 256, 0, st>>>(theta, nr, b, N, tiles, Xh, general);
+                           cudaStream_t st, int general, const long long* roff) {
+    k_assemble<<<1024, 256, 0, st>>>(theta, nr, b, N, tiles, Xh, general, roff);
     counted(1);
     return cudaGetLastError();
 }

@@ -40,12 +40,12 @@ __global__ void k_theta_to_panel(PanelMap m, const cf* __restrict__ th, cf* __re
     const long long nlr = m.Ktot * m.b;
     GRID_STRIDE(e, nlr) {
         const long long g = e % m.Ktot, a = e / m.Ktot;
-        pan[m.colpan[g] + a * m.panstride[g]] = th[m.colsrc[g] + a * m.colstride[g]];
+        if (a < m.colrows[g]) pan[m.colpan[g] + a * m.panstride[g]] = th[m.colsrc[g] + a * m.colstride[g]];
     }
-    const long long nz = m.ndense * m.b * m.b;
-    GRID_STRIDE(e, nz) {
-        const long long t = e / (m.b * m.b), r = e % (m.b * m.b);
-        pan[m.zbase + e] = th[m.zsrc[t] + r];
+    const long long bb = m.b * m.b;
+    GRID_STRIDE(e, m.ndense * bb) {
+        const long long t = e / bb, r = (e % bb) / m.b, c = e % m.b, n = m.zdim[t];
+        if (r < n && c < n) pan[m.zbase + m.zoff[t] + r * n + c] = th[m.zsrc[t] + r * n + c];
     }
 }
 
@@ -53,12 +53,12 @@ __global__ void k_panel_to_theta(PanelMap m, const cf* __restrict__ pan, cf* __r
     const long long nlr = m.Ktot * m.b;
     GRID_STRIDE(e, nlr) {
         const long long g = e % m.Ktot, a = e / m.Ktot;
-        th[m.colsrc[g] + a * m.colstride[g]] = pan[m.colpan[g] + a * m.panstride[g]];
+        if (a < m.colrows[g]) th[m.colsrc[g] + a * m.colstride[g]] = pan[m.colpan[g] + a * m.panstride[g]];
     }
-    const long long nz = m.ndense * m.b * m.b;
-    GRID_STRIDE(e, nz) {
-        const long long t = e / (m.b * m.b), r = e % (m.b * m.b);
-        th[m.zsrc[t] + r] = pan[m.zbase + e];
+    const long long bb = m.b * m.b;
+    GRID_STRIDE(e, m.ndense * bb) {
+        const long long t = e / bb, r = (e % bb) / m.b, c = e % m.b, n = m.zdim[t];
+        if (r < n && c < n) th[m.zsrc[t] + r * n + c] = pan[m.zbase + m.zoff[t] + r * n + c];
     }
 }
 
@@ -73,24 +73,42 @@ cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStre
     return cudaGetLastError();
 }
 
-// Zs = (Z + Z^T)/2 (the symmetrisation preconditioner P of eq. 7)
-// Zs = (Z + Z^T)/2 (reciprocal form, X_ii = P Z_ii) or Z^T (general form: row
-// block i of Y = X^T Dfrak takes X_ii^T)
+// Dense tile t of a panel-ordered region: (offset, size) from the per-tile
+// tables, or the t-th of equal tiles of size b.
+__device__ __forceinline__ bool dense_tile(long long e, long long b, const long long* zoff, const int* zdim,
+                                           long long& base, long long& n, long long& r, long long& c) {
+    const long long bb = b * b, t = e / bb;
+    r = (e % bb) / b;
+    c = e % b;
+    if (!zoff) {
+        base = t * bb;
+        n = b;
+        return true;
+    }
+    base = zoff[t];
+    n = zdim[t];
+    return r < n && c < n;
+}
+
+// Zs = (Z + Z^T)/2 (reciprocal form: the symmetrisation preconditioner P of
+// eq. 7, X_ii = P Z_ii) or Z^T (general form: row block i of Y = X^T Dfrak
+// takes X_ii^T)
 __global__ void k_sym_dense(const cf* __restrict__ pan, long long zbase, long long ndense, long long b,
-                            cf* __restrict__ Zs, int general) {
-    const long long bb = b * b;
-    GRID_STRIDE(e, ndense * bb) {
-        const long long t = e / bb, r = (e % bb) / b, c = e % b;
-        const cf u = pan[zbase + t * bb + r * b + c];
-        const cf v = pan[zbase + t * bb + c * b + r];
-        Zs[e] = general ? v : make_float2(0.5f * (u.x + v.x), 0.5f * (u.y + v.y));
+                            cf* __restrict__ Zs, int general, const long long* __restrict__ zoff,
+                            const int* __restrict__ zdim) {
+    GRID_STRIDE(e, ndense * b * b) {
+        long long base, n, r, c;
+        if (!dense_tile(e, b, zoff, zdim, base, n, r, c)) continue;
+        const cf u = pan[zbase + base + r * n + c];
+        const cf v = pan[zbase + base + c * n + r];
+        Zs[base + r * n + c] = general ? v : make_float2(0.5f * (u.x + v.x), 0.5f * (u.y + v.y));
     }
 }
 
 cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st,
-                      int general) {
+                      int general, const long long* zoff, const int* zdim) {
     if (ndense == 0) return cudaSuccess;
-    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs, general);
+    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs, general, zoff, zdim);
     counted(1);
     return cudaGetLastError();
 }
@@ -98,7 +116,8 @@ cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long lon
 // grad = sum of split-K partials (FP64, fixed order); dense tiles: (G + G^T)/2
 // (reciprocal form) or G^T (general form)
 __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long stride, long long nlr,
-                              long long ndense, long long b, cf* __restrict__ grad, int general) {
+                              long long ndense, long long b, cf* __restrict__ grad, int general,
+                              const long long* __restrict__ zoff, const int* __restrict__ zdim) {
     GRID_STRIDE(e, nlr) {
         Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
@@ -108,10 +127,10 @@ __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long
         }
         grad[e] = make_float2((float)x.val(), (float)y.val());
     }
-    const long long bb = b * b;
-    GRID_STRIDE(e, ndense * bb) {
-        const long long t = e / bb, r = (e % bb) / b, q = e % b;
-        const long long e1 = nlr + t * bb + r * b + q, e2 = nlr + t * bb + q * b + r;
+    GRID_STRIDE(e, ndense * b * b) {
+        long long base, n, r, q;
+        if (!dense_tile(e, b, zoff, zdim, base, n, r, q)) continue;
+        const long long e1 = nlr + base + r * n + q, e2 = nlr + base + q * n + r;
         Acc x, y;
         for (int c = 0; c < nsplit; ++c) {
             const cf v = part[c * stride + e2];
@@ -124,13 +143,14 @@ __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long
             y.add(v.y);
         }
         const double s = general ? 1.0 : 0.5;
-        grad[nlr + e] = make_float2((float)(s * x.val()), (float)(s * y.val()));
+        grad[e1] = make_float2((float)(s * x.val()), (float)(s * y.val()));
     }
 }
 
 cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
-                        long long b, cf* grad, cudaStream_t st, int general) {
-    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad, general);
+                        long long b, cf* grad, cudaStream_t st, int general, const long long* zoff,
+                        const int* zdim) {
+    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad, general, zoff, zdim);
     counted(1);
     return cudaGetLastError();
 }

@@ -67,7 +67,7 @@ class Desc(C.Structure):
         ("ranks", C.POINTER(C.c_int32)), ("diag_mode", C.c_int32),
         ("diag_dense", C.POINTER(C.c_uint8)), ("reciprocity", C.c_int32),
         ("precision", C.c_int32), ("alpha", C.c_double), ("input_memory", C.c_int32),
-        ("reserved", C.c_int32),
+        ("ntiles", C.c_int32), ("tiles", C.POINTER(C.c_int32)),
     ]
 
 
@@ -206,13 +206,19 @@ class _Keep:
 
 def desc(nr, ns, tile, rank=0, nx=0, ny=0, perm=None, ranks=None, diag_mode=TLR_DIAG_RULE,
          diag_dense=None, precision=TLR_PREC_FP32, alpha=0.0, input_memory=TLR_MEM_DEVICE,
-         reciprocity=TLR_RECIP_SYMMETRIC) -> Desc:
+         reciprocity=TLR_RECIP_SYMMETRIC, tiles=None) -> Desc:
+    """``tiles``: the tile sizes d_i of a non-uniform partition (``tile`` is then ignored)."""
     d = Desc()
     lib().tlr_mdd_desc_init(C.byref(d))
-    d.nr, d.ns, d.tile, d.rank, d.nx, d.ny = nr, ns, tile, rank, nx, ny
+    d.nr, d.ns, d.tile, d.rank, d.nx, d.ny = nr, ns, tile or 0, rank, nx, ny
     d.diag_mode, d.precision, d.alpha, d.input_memory = diag_mode, precision, float(alpha), input_memory
     d.reciprocity = reciprocity
     keep = []
+    if tiles is not None:
+        a = (C.c_int32 * max(1, len(tiles)))(*[int(v) for v in tiles])
+        keep.append(a)
+        d.tiles = C.cast(a, C.POINTER(C.c_int32))
+        d.ntiles = len(tiles)
     if perm is not None:
         a = (C.c_int32 * len(perm))(*[int(v) for v in perm])
         keep.append(a)
@@ -243,8 +249,13 @@ def tlr_mdd_theta_size(d: Desc) -> int:
     return n.value
 
 
+def ntiles(d: Desc) -> int:
+    """N, the number of tile rows of the description's partition."""
+    return d.ntiles if d.tiles else d.nr // d.tile
+
+
 def tlr_mdd_theta_layout(d: Desc):
-    N = d.nr // d.tile
+    N = ntiles(d)
     P = N * (N - 1) if d.reciprocity == TLR_RECIP_NONE else N * (N - 1) // 2
     od = (C.c_int64 * max(N, 1))()
     ol = (C.c_int64 * max(P, 1))()

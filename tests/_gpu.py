@@ -16,11 +16,11 @@ def host(t):
 
 def abi_desc(lay, ns, nx=0, ny=0, perm=None, alpha=0.0, precision=T.TLR_PREC_FP32,
              input_memory=T.TLR_MEM_DEVICE):
-    n = lay.n
     ranks = list(lay.k_diag) + list(lay.k_pair)
-    return T.desc(lay.nr, ns, lay.b, ranks=ranks, nx=nx, ny=ny, perm=perm,
+    tiles = None if lay.b is not None else list(lay.d)   # non-uniform partition
+    return T.desc(lay.nr, ns, lay.b or 0, ranks=ranks, nx=nx, ny=ny, perm=perm,
                   diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=list(lay.dense),
-                  precision=precision, alpha=alpha, input_memory=input_memory)
+                  precision=precision, alpha=alpha, input_memory=input_memory, tiles=tiles)
 
 
 class Gpu:

@@ -78,6 +78,58 @@ def test_general_theta_layout_bit_exact(nr, b, ranks, dense):
     assert T.tlr_mdd_theta_size(d) == lay.size
 
 
+@pytest.mark.parametrize("tiles,ranks,dense,recip", [
+    ([3, 5, 2], [1, 2, 2, 2, 1, 2], [False, True, False], False),
+    ([48, 80, 16, 112], 9, [False, True, False, False], False),
+    ([100, 28, 128], [5, 28, 7] + [3, 0, 28], [False, True, False], False),
+    ([3, 5, 2], [1, 2, 2] + [2, 1, 3, 2, 2, 1], [False, True, False], True),
+    ([40, 24, 64], 6, [True, False, False], True),
+])
+def test_nonuniform_theta_layout_bit_exact(tiles, ranks, dense, recip):
+    # tile sizes d_i: L_ij is d_i x k, R_ij is d_j x k, diagonal blocks d_i x k or d_i x d_i
+    from oracle import general
+    _lib()
+    nr, n = sum(tiles), len(tiles)
+    npair = n * (n - 1) if recip else n * (n - 1) // 2
+    rl = ranks if isinstance(ranks, list) else [ranks] * (n + npair)
+    d = T.desc(nr, 10, 0, ranks=rl, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense, tiles=tiles,
+               reciprocity=T.TLR_RECIP_NONE if recip else T.TLR_RECIP_SYMMETRIC)
+    if recip:
+        lay = general.make_general_layout(nr, None, rl, dense, tiles=tiles)
+    else:
+        lay = layout.make_layout(nr, None, rl, dense, tiles=tiles)
+    od, ol, orr, dn = T.tlr_mdd_theta_layout(d)
+    assert od == lay.off_diag and ol == lay.off_l and orr == lay.off_r
+    assert dn == lay.dense
+    assert T.tlr_mdd_theta_size(d) == lay.size
+    assert T.tlr_mdd_workspace_bytes(d) > 0
+
+
+def test_nonuniform_rule_uses_each_tile_size():
+    # dense iff 4 k_ii >= d_i: with k = 8, tiles of 32 are dense, tiles of 33 are not
+    _lib()
+    tiles = [32, 33, 31, 40]
+    d = T.desc(sum(tiles), 10, 0, rank=8, tiles=tiles)
+    lay = layout.make_layout(sum(tiles), None, 8, "rule", tiles=tiles)
+    assert T.tlr_mdd_theta_layout(d)[3] == lay.dense == [True, False, True, False]
+    assert T.tlr_mdd_theta_size(d) == lay.size
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nr=10, ns=10, tile=0, rank=1, tiles=[3, 5, 1]), -2),      # sizes do not sum to nr
+    (dict(nr=10, ns=10, tile=0, rank=1, tiles=[3, 0, 7]), -2),      # an empty tile
+    (dict(nr=10, ns=10, tile=0, rank=3, tiles=[2, 8]), -2),         # rank above d_0
+    (dict(nr=10, ns=10, tile=0, ranks=[1, 1, 4], tiles=[3, 7]), -2),  # pair rank above min(d_i, d_j)
+    (dict(nr=10, ns=10, tile=0, rank=1, tiles=[]), -2),             # no tiles
+])
+def test_invalid_partitions_rejected(kw, code):
+    _lib()
+    d = T.desc(**kw)
+    with pytest.raises(T.TLRError) as ei:
+        T.tlr_mdd_theta_size(d)
+    assert ei.value.code == code
+
+
 @pytest.mark.parametrize("kw,code", [
     (dict(nr=100, ns=10, tile=64, rank=4), -2),          # tile does not divide nr
     (dict(nr=128, ns=10, tile=64, rank=65), -2),         # rank above tile

@@ -1,0 +1,123 @@
+"""Non-uniform tile partitions (tile sizes d_i) on the GPU vs the oracle.
+
+Block i of the Hilbert-ordered receivers holds d_i of them; tile (i, j) is
+d_i x d_j with L_ij d_i x k and R_ij d_j x k.  Tolerances as for equal tiles:
+1e-5 (FP32) and 1e-3 (tensor cores) relative per operator application, 1e-3
+on the final X of a solve."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2412_14973_gb300 as T
+import tlr_synth as synth
+from oracle import general, operator, solver
+
+from _cases import problem
+from _gpu import Gpu, dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # name: (nx, ny, tiles, ranks (diagonal, then pairs) or int, dense diagonal flags, ns)
+    "ragged4": (16, 16, [48, 80, 16, 112], 9, [False, True, False, False], 203),
+    "mixed": (12, 8, [40, 8, 31, 17], [5, 8, 0, 17] + [8, 0, 17, 3, 8, 6], [False, False, True, False], 77),
+    "big_small": (8, 8, [60, 4], [3, 4, 4], [False, False], 64),
+    "many_tc_tiles": (32, 32, [200, 312, 128, 384], 24, [False, False, True, False], 1024),
+}
+PRECS = [(T.TLR_PREC_FP32, 1e-5), (T.TLR_PREC_BF16X3, 1e-3)]
+
+
+def _setup(name, prec, seed=0):
+    nx, ny, tiles, ranks, dense, ns = CASES[name]
+    D, U, perm, lay, _ = problem(nx, ny, None, ranks, dense, ns=ns, seed=40 + seed, snr_db=10, planted=False,
+                                 tiles=tiles)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, precision=prec)
+    _, alpha, _, _ = g.data()
+    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    th = (0.2 * synth.cn(synth.rng(45 + seed), lay.size)).astype(np.complex64).astype(np.complex128)
+    return g, lay, th, Dh, Uh, perm
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_apply_grad_unpermute(name, prec, tol):
+    g, lay, th, Dh, Uh, perm = _setup(name, prec)
+    Y = g.apply(th)
+    Yo = operator.apply_y(th, lay, Dh)
+    f, gr = g.grad(th)
+    fo = operator.misfit(th, lay, Dh, Uh)
+    go = operator.gradient(th, lay, Dh, Uh)
+    X = g.unpermute(th)
+    Xo = operator.unpermute(operator.assemble_xh(th, lay), perm)
+    print(f"tiles {name} prec {prec}: apply {rel(Y, Yo):.2e} grad {rel(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
+    assert rel(Y, Yo) <= tol
+    assert rel(gr, go) <= tol and abs(f - fo) <= tol * fo
+    assert rel(X, Xo) <= 1e-5
+    assert np.array_equal(X, X.T)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", [T.TLR_PREC_FP32, T.TLR_PREC_BF16X3])
+def test_solve_matches_oracle(prec):
+    g, lay, th, Dh, Uh, perm = _setup("mixed", prec, seed=3)
+    th0 = 0.5 * th
+    ths, st = g.solve(th0)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dh.T, Uh.T), th0)
+    e = rel(operator.assemble_xh(ths, lay), operator.assemble_xh(tho, lay))
+    print(f"tiles solve prec {prec}: rel X {e:.2e}, f {st.f_hist[st.n_hist - 1]:.4e} vs {sto.f_hist[-1]:.4e}")
+    assert st.iters == 30 and st.status == 0
+    assert e <= 1e-3
+    g.close()
+
+
+@pytest.mark.parametrize("prec", [T.TLR_PREC_FP32, T.TLR_PREC_BF16X3])
+def test_explicit_equal_tiles_are_the_uniform_partition(prec):
+    # tiles = [b] * N takes exactly the uniform path: bitwise equal results
+    D, U, perm, lay, _ = problem(8, 8, 16, 3, "lowrank", ns=70, seed=5, snr_db=10, planted=False)
+    th = (0.2 * synth.cn(synth.rng(6), lay.size)).astype(np.complex64)
+    out = []
+    for tiles in (None, [16] * 4):
+        d = T.desc(64, 70, 16, rank=3, nx=8, ny=8, diag_mode=T.TLR_DIAG_LOWRANK, precision=prec, tiles=tiles)
+        g = Gpu(D, U, lay, desc=d)
+        out.append((g.apply(th), g.grad(th)))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1][0] == out[1][1][0] and np.array_equal(out[0][1][1], out[1][1][1])
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_general_form_on_nonuniform_tiles(prec, tol):
+    tiles, dense = [20, 36, 8], [False, True, False]
+    n = len(tiles)
+    rl = [4, 9, 8] + [min(tiles[i], tiles[j], 3 + i + 2 * j) for (i, j) in general.ordered_pairs(n)]
+    glay = general.make_general_layout(64, None, rl, dense, tiles=tiles)
+    D, U, perm, _, _ = problem(8, 8, 16, 1, "lowrank", ns=90, seed=91, snr_db=10)
+    d = T.desc(64, 90, 0, ranks=rl, nx=8, ny=8, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense,
+               precision=prec, reciprocity=T.TLR_RECIP_NONE, tiles=tiles)
+    g = Gpu(D, U, glay, desc=d)
+    _, alpha, _, _ = g.data()
+    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    th = (0.2 * synth.cn(synth.rng(92), glay.size)).astype(np.complex64).astype(np.complex128)
+    Y = g.apply(th)
+    f, gr = g.grad(th)
+    X = g.unpermute(th)
+    assert rel(Y, general.apply_y(th, glay, Dh)) <= tol
+    go, fo = general.gradient(th, glay, Dh, Uh), general.misfit(th, glay, Dh, Uh)
+    assert rel(gr, go) <= tol and abs(f - fo) <= tol * fo
+    assert rel(X, operator.unpermute(general.assemble_x(th, glay), perm)) <= 1e-5
+    if prec == T.TLR_PREC_FP32:
+        ths, st = g.solve(0.5 * th)
+        tho, _, _, _ = solver.admm(general.GeneralProblem(glay, Dh.T, Uh.T), 0.5 * th)
+        assert st.iters == 30 and st.status == 0
+        assert rel(general.assemble_x(ths, glay), general.assemble_x(tho, glay)) <= 1e-3
+    g.close()
+
+
+def test_warm_start_needs_a_uniform_partition():
+    g, lay, th, Dh, Uh, perm = _setup("big_small", T.TLR_PREC_FP32)
+    X = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
+    t = torch.zeros(lay.size, dtype=torch.complex64, device="cuda")
+    with pytest.raises(T.TLRError) as e:
+        T.tlr_mdd_warm_start(g.h, X, t)
+    assert e.value.code == T.TLR_ERR_UNSUPPORTED
+    g.close()
