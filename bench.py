@@ -235,6 +235,9 @@ def main():
                     help="CG iterations of the eq. (4) benchmark solver timed on frequency 0 (0: skip)")
     ap.add_argument("--general-rank", type=int, default=26,
                     help="rank of one timed solve of the general (non-reciprocal) form on frequency 0 (0: skip)")
+    ap.add_argument("--tiles-rank", type=int, default=26,
+                    help="rank of one timed solve on a non-uniform partition (tiles of 192 and 320 "
+                         "receivers alternating) of frequency 0 (0: skip)")
     ap.add_argument("--serving", type=int, default=0,
                     help="also serve this many per-frequency requests of the serving mix (nr 1024-8192)")
     args = ap.parse_args()
@@ -479,6 +482,44 @@ def main():
                   "note": "one solve, one stream; flops as for the reciprocal form at this rank"}
         T.tlr_mdd_destroy(hg)
 
+    # a non-uniform partition: 16 tiles of 192 and 320 receivers alternating
+    # (sum 4096), the same rank on every tile; with N tiles and rank k the
+    # low-rank entries are N k nr, as for equal tiles
+    tsolve = None
+    if args.tiles_rank > 0 and rank == 0 and NR == 4096:
+        kt = args.tiles_rank
+        tiles = [192, 320] * 8
+        dt = T.desc(NR, NR, 0, rank=kt, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
+                    precision=prec, tiles=tiles)
+        ht = T.tlr_mdd_create(dt, D[0], U[0], streams[0])
+        gen = torch.Generator(device=dev).manual_seed(args.seed + 6)
+        ntt = T.tlr_mdd_theta_size(dt)
+        th_t0 = 0.01 * torch.randn(ntt, dtype=torch.complex64, device=dev, generator=gen)
+        th_t = th_t0.clone()
+        torch.cuda.synchronize()
+        T.tlr_mdd_solve(ht, th_t, opts)                                   # records the graph
+        th_t.copy_(th_t0)
+        torch.cuda.synchronize()
+        tst = T.tlr_mdd_solve(ht, th_t, opts)
+        T.tlr_mdd_destroy(ht)
+        # the same rank on 16 equal tiles, for comparison
+        du = T.desc(NR, NR, NR // 16, rank=kt, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE, precision=prec)
+        hu = T.tlr_mdd_create(du, D[0], U[0], streams[0])
+        th_u0 = 0.01 * torch.randn(T.tlr_mdd_theta_size(du), dtype=torch.complex64, device=dev, generator=gen)
+        th_u = th_u0.clone()
+        torch.cuda.synchronize()
+        T.tlr_mdd_solve(hu, th_u, opts)
+        th_u.copy_(th_u0)
+        torch.cuda.synchronize()
+        ust = T.tlr_mdd_solve(hu, th_u, opts)
+        T.tlr_mdd_destroy(hu)
+        tf = (ITERS_PER_SOLVE * 56.0 + 40.0) * NR * ntt
+        tsolve = {"tiles": "192,320 alternating x8", "rank": kt, "n_theta": ntt, "ms": round(tst.gpu_ms, 2),
+                  "tflops": round(tf / (tst.gpu_ms / 1e3) / 1e12, 1), "iters": tst.iters,
+                  "equal_tiles_ms": round(ust.gpu_ms, 2),
+                  "note": "one solve, one stream; equal_tiles_ms: 16 tiles of 256 at the same rank "
+                          "(same flops); 192- and 320-row blocks fill 75% and 83% of their 128-row MMA tiles"}
+
     # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
     cpu = None
     acc = None
@@ -541,6 +582,8 @@ def main():
         line["benchmark_solver"] = bsolve
     if gsolve is not None:
         line["general_form"] = gsolve
+    if tsolve is not None:
+        line["nonuniform_tiles"] = tsolve
     if serve is not None:
         line["serving"] = serve
     print(json.dumps(line), flush=True)

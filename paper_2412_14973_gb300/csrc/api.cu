@@ -562,9 +562,11 @@ void carve(tlr_mdd_s* h, Arena& a) {
     h->Zsd = a.take<cf>(nz);
     h->part = a.take<cf>((size_t)h->nsplit * L.nth);
     h->dpart = a.take<double>(16 * kRedBlocks);
-    // the fused residual step works on 16-row tiles of one block each: equal
-    // tiles, a multiple of 16
-    h->n_rpart = L.b > 0 && L.b % kFuseRows == 0 ? rstep_ctas((int)L.nr, (int)L.ns) : 0;
+    // the fused residual step works on 16-row tiles of one block each: every
+    // tile size a multiple of 16
+    h->n_rpart = std::all_of(L.d.begin(), L.d.end(), [](int64_t x) { return x % kFuseRows == 0; })
+                     ? rstep_ctas((int)L.nr, (int)L.ns)
+                     : 0;
     h->rpart = a.take<double>((size_t)std::max<long long>(1, h->n_rpart));
     const size_t K = std::max<int64_t>(1, L.ncol);
     h->d_partner = a.take<int>(std::max<int64_t>(1, L.general ? L.Ktot + L.KtotB : L.Ktot));
@@ -975,7 +977,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         if (ko.first.src == (const void*)h->Tp && ko.first.kcontig == 1 && ko.first.sgn > 0)
             v_nk[ko.first.gr] = ko.second;
     // The residual's two packings (MK for the projection, KN for the residual
-    // compression) come from the fused residual step when the tile is a
+    // compression) come from the fused residual step when every tile size is a
     // multiple of kFuseRows and every block has both.
     const char* rlo = reinterpret_cast<const char*>(h->R);
     const char* rhi = rlo + (size_t)L.nr * L.ns * sizeof(cf);
@@ -987,21 +989,22 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     std::set<PackKey> rkeys;
     for (auto& ko : order) {
         const PackKey& k = ko.first;
-        if (L.b == 0) break;   // non-uniform tiles: no fused residual step
         if (!is_R(k) || k.gr || k.gk || k.sgn < 0 || k.ld != L.ns) continue;
         const long long off = reinterpret_cast<const cf*>(k.src) - h->R;
-        if (off % ((long long)L.b * L.ns) != 0) continue;
-        const long long blk = off / ((long long)L.b * L.ns);
-        if (k.kcontig == 0 && k.R == L.ns && k.K == L.b) {
+        if (off % L.ns != 0) continue;
+        const auto at = std::lower_bound(L.roff.begin(), L.roff.end() - 1, off / L.ns);
+        if (at == L.roff.end() - 1 || *at != off / L.ns) continue;
+        const long long blk = at - L.roff.begin(), db = L.d[blk];
+        if (k.kcontig == 0 && k.R == L.ns && k.K == db) {
             rkn[blk] = h->packed + ko.second;
             rkeys.insert(k);
         }
-        if (k.kcontig == 1 && k.R == L.b && k.K == L.ns) {
+        if (k.kcontig == 1 && k.R == db && k.K == L.ns) {
             rmk[blk] = h->packed + ko.second;
             rkeys.insert(k);
         }
     }
-    bool rfuse = L.b > 0 && L.b % kFuseRows == 0 && h->n_rpart > 0;
+    bool rfuse = h->n_rpart > 0;
     for (int i = 0; i < L.N && rfuse; ++i)
         if (!rkn[i] || !rmk[i]) rfuse = false;
     std::vector<char*> rowptr;
@@ -1417,7 +1420,8 @@ static int forward(tlr_mdd_s* h, bool plain_apply) {
     if (h->n_tpack) CK(h, tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)L.ns, h->st));
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
     if (!plain_apply && h->rstep_on)
-        CK(h, rstep(h->R, h->A1, h->A2, nullptr, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn, h->d_rmk, nullptr, h->st));
+        CK(h, rstep(h->R, h->A1, h->A2, nullptr, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn, h->d_rmk, nullptr, h->st,
+                    L.b > 0 ? nullptr : h->d_roff, L.N));
     return TLR_OK;
 }
 
@@ -2124,7 +2128,7 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 CK(h, sv_line_search(S, part6, part3, rho, h->st));
                 if (h->rstep_on)
                     CK(h, rstep(h->R, h->A1, h->A2, h->sc + SC_ALPHA, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn,
-                                h->d_rmk, h->rpart, h->st));
+                                h->d_rmk, h->rpart, h->st, L.b > 0 ? nullptr : h->d_roff, L.N));
                 else
                     CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
                 if (h->n_tpack)

@@ -77,7 +77,7 @@ constexpr int kPackTRA = 128, kPackTRB = 128;
 // rows per CTA of the fused update-and-pack kernels (tpack, rstep): 16 rows x
 // 128 columns keep their shared memory at 16.5 KB, so one of their CTAs fits
 // beside the two GEMM CTAs an SM holds (2 x 97 KB) and they overlap
-// contractions of other streams; the tiles of rstep need 16 | b
+// contractions of other streams; the tiles of rstep need 16 | d_i for every tile
 constexpr int kFuseRows = 16;
 struct PTerm {
     const void* A;   // packed A of this problem (TR = kPackTRA), all row blocks
@@ -133,11 +133,13 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 // nullptr: no update), the per-CTA partial of ||R||^2 (two-sum per thread,
 // FP64 across the CTA) into part[cta] when part != nullptr, and R in both
 // packed forms: block i's rows as an A operand with k = ns (MK, mk[i]) and
-// as a B operand with rows = ns and k = the receiver (KN, kn[i]).  b must be
-// a multiple of kFuseRows; rstep_ctas gives the number of CTAs (and partials).
+// as a B operand with rows = ns and k = the receiver (KN, kn[i]).  Blocks of
+// b rows (roff == nullptr) or block i = rows roff[i] .. roff[i+1]-1 (DEVICE
+// [nblk + 1]); every block size a multiple of kFuseRows.  rstep_ctas gives the
+// number of CTAs (and partials).
 long long rstep_ctas(int nr, int ns);
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
-                  char* const* mk, double* part, cudaStream_t st);
+                  char* const* mk, double* part, cudaStream_t st, const long long* roff = nullptr, int nblk = 0);
 // Benchmark solver of eq. (4) (k_cg.cu): the symmetrising pass
 // out = P(y) + s2 p (with partials of <p, out> when part != nullptr; p may be
 // nullptr: out = P(y)), the start (x = 0, r = p = b with b in r on entry),

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 // ---------------------------------------------------------------------------
 // rstep: fused residual step and both packings of the residual
 // ---------------------------------------------------------------------------
-// A CTA takes TP_K receiver rows (inside one block, b a multiple of TP_K) and 128
+// A CTA takes TP_K receiver rows (inside one block, every block a multiple of TP_K) and 128
 // columns: phase 1 reads R, A1, A2 coalesced along n, updates, writes R back,
 // accumulates ||R||^2 and keeps the tile in shared memory; phase 2 writes the
 // MK packing (rows = receivers, lanes along rows); phase 3 the KN packing
@@ -312,11 +312,31 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __restrict__ A1,
                                                const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
                                                int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
-                                               double* __restrict__ part) {
+                                               double* __restrict__ part, const long long* __restrict__ roff,
+                                               int nblk) {
     __shared__ float2 s[TP_K * TP_LD];
     __shared__ double sh[32];
     const int n0 = blockIdx.x * TP_N, r0 = blockIdx.y * TP_K;
-    const int blk = r0 / b, rl0 = r0 - blk * b;
+    // block of this row tile: r0 / b for equal tiles, else the largest i with
+    // roff[i] <= r0 (every roff[i] is a multiple of TP_K, so the tile lies in it)
+    int blk, rl0, bK;
+    if (roff) {
+        int lo = 0, hi = nblk - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (roff[mid] <= r0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        blk = lo;
+        rl0 = r0 - (int)roff[blk];
+        bK = (int)(roff[blk + 1] - roff[blk]);
+    } else {
+        blk = r0 / b;
+        rl0 = r0 - blk * b;
+        bK = b;
+    }
     const float a = alpha ? (float)alpha[0] : 0.f;
     const float a2 = alpha ? (float)(alpha[0] * alpha[0]) : 0.f;
     Acc acc;
@@ -378,7 +398,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
     }
     // phase 3: KN, rows = n, k = receiver of block blk
     {
-        const int nkcK = b >> 4;
+        const int nkcK = bK >> 4;
         char* const base = kn[blk];
         for (int it = threadIdx.x; it < TP_N * (TP_K / 8); it += blockDim.x) {
             const int n = it & (TP_N - 1), kg = it >> 7;
@@ -662,11 +682,13 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 long long rstep_ctas(int nr, int ns) { return (long long)((ns + TP_N - 1) / TP_N) * (nr / TP_K); }
 
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
-                  char* const* mk, double* part, cudaStream_t st) {
+                  char* const* mk, double* part, cudaStream_t st, const long long* roff, int nblk) {
     if (nr == 0 || ns == 0) return cudaSuccess;
-    if (b % TP_K != 0 || nr % b != 0) return cudaErrorInvalidValue;
+    if (nr % TP_K != 0) return cudaErrorInvalidValue;
+    if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
+    if (roff && nblk <= 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
-    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part);
+    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk);
     counted(1);
     return cudaGetLastError();
 }
