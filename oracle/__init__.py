@@ -26,7 +26,8 @@ arXiv 2412.14973 and cites the passage it follows:
                   and the SVD / Takagi warm start (hyper-parameter selection
                   and initialisation section; Examples section, steps 1-3).
 * ``general``  -- the general (non-reciprocal) TLR form: every tile free,
-                  its assembly, misfit, factor gradients and line quartic.
+                  its assembly, misfit, factor gradients, line quartic and
+                  truncated-SVD warm start.
 * ``fourier``  -- time <-> frequency stacks and the stack-wide alpha
                   (Numerical Examples; hyper-parameter selection section).
 

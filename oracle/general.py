@@ -140,6 +140,35 @@ def gradient(theta, lay, Dh, Uh) -> np.ndarray:
     return g
 
 
+def warm_start(X, lay: GeneralLayout) -> np.ndarray:
+    """theta of ``lay`` initialised from X (Hilbert order), the initialisation
+    paragraph's factors without the reciprocal pairing: every low-rank tile,
+    diagonal ones included, from its truncated SVD, L = U_k Sigma_k^1/2 and
+    R = conj(V_k) Sigma_k^1/2 (so L R^T = U_k Sigma_k V_k^H); a dense diagonal
+    tile is copied (X_ii = Z_ii)."""
+    X = np.asarray(X, np.complex128)
+    th = np.zeros(lay.size, np.complex128)
+
+    def put(o_l, o_r, tile, k):
+        U, s, Vh = np.linalg.svd(tile, full_matrices=False)
+        rs = np.sqrt(s[:k])
+        L, R = U[:, :k] * rs, Vh[:k, :].T * rs
+        th[o_l:o_l + L.size] = L.ravel()
+        th[o_r:o_r + R.size] = R.ravel()
+
+    for i in range(lay.n):
+        T = X[lay.rows(i), lay.rows(i)]
+        o = lay.off_diag[i]
+        if lay.dense[i]:
+            th[o:o + T.size] = T.ravel()
+        elif lay.k_diag[i] > 0:
+            put(o, o + lay.d[i] * lay.k_diag[i], T, lay.k_diag[i])
+    for p, (i, j) in enumerate(lay.pair_list):
+        if lay.k_pair[p] > 0:
+            put(lay.off_l[p], lay.off_r[p], X[lay.rows(i), lay.rows(j)], lay.k_pair[p])
+    return th
+
+
 def apply_y(theta, lay, Dh) -> np.ndarray:
     """Receiver-major Y = (D-hat X)^T = X^T Dfrak."""
     return (Dh @ assemble_x(theta, lay)).T

@@ -190,3 +190,51 @@ def test_invalid_partitions_rejected(tiles, ranks):
     with pytest.raises(ValueError):
         general.make_general_layout(10, None, ranks if isinstance(ranks, int) else ranks + [4], "lowrank",
                                     tiles=tiles)
+
+
+def _eckart_young(X, W, k):
+    s = np.linalg.svd(X, compute_uv=False)
+    assert np.linalg.norm(X - W) ** 2 == pytest.approx(float(np.sum(s[k:] ** 2)), abs=1e-10 * float(np.sum(s ** 2)))
+
+
+def test_warm_start_on_unequal_tiles_is_the_truncated_svd_of_every_tile():
+    # reciprocal form: each kept tile of X_h (d_i x d_j) is the best rank-k
+    # approximation of X's tile, dense diagonals are copied
+    g = synth.rng(11)
+    tiles = [5, 9, 3, 7]
+    A = synth.cn(g, (24, 24))
+    X = A + A.T
+    lay = layout.make_layout(24, None, [2, 9, 1, 0] + [3, 2, 4, 1, 5, 3], [False, True, False, False],
+                             tiles=tiles)
+    Xh = operator.assemble_xh(warmstart.warm_start(X, lay), lay)
+    for i in range(4):
+        for j in range(i + 1):
+            T, W = X[lay.rows(i), lay.rows(j)], Xh[lay.rows(i), lay.rows(j)]
+            if i == j and lay.dense[i]:
+                np.testing.assert_allclose(W, T, atol=1e-13)
+                continue
+            _eckart_young(T, W, lay.k_diag[i] if i == j else lay.k_pair[layout.pair_index(i, j, 4)])
+
+
+@pytest.mark.parametrize("tiles", [[4, 4, 4], [3, 6, 2]])
+def test_general_warm_start_is_the_truncated_svd_of_every_tile(tiles):
+    # general form: every tile, above and below the diagonal and low-rank
+    # diagonals, is its own truncated SVD; dense diagonals are copied; full
+    # ranks reproduce X
+    g = synth.rng(12)
+    nr, n = sum(tiles), len(tiles)
+    X = synth.cn(g, (nr, nr))
+    pl = general.ordered_pairs(n)
+    ranks = [2, tiles[1], 1] + [min(tiles[i], tiles[j], 1 + (i + 2 * j) % 3) for (i, j) in pl]
+    lay = general.make_general_layout(nr, None, ranks, [False, True, False], tiles=tiles)
+    W = general.assemble_x(general.warm_start(X, lay), lay)
+    for i in range(n):
+        for j in range(n):
+            T, Wt = X[lay.rows(i), lay.rows(j)], W[lay.rows(i), lay.rows(j)]
+            if i == j and lay.dense[i]:
+                np.testing.assert_allclose(Wt, T, atol=1e-13)
+                continue
+            _eckart_young(T, Wt, lay.k_diag[i] if i == j else lay.k_pair[pl.index((i, j))])
+    full = [tiles[i] for i in range(n)] + [min(tiles[i], tiles[j]) for (i, j) in pl]
+    lf = general.make_general_layout(nr, None, full, "lowrank", tiles=tiles)
+    np.testing.assert_allclose(general.assemble_x(general.warm_start(X, lf), lf), X, atol=1e-12)
