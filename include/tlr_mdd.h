@@ -97,8 +97,7 @@ typedef struct {
                                 (block i = the d_i receivers after those of blocks
                                 < i in Hilbert order), sum d_i == nr.  The paper's
                                 partition is uniform but need not be (Tile Low-rank MDD
-                                section); NULL -> N = nr/tile tiles of size tile.
-                                tlr_mdd_warm_start needs a uniform partition. */
+                                section); NULL -> N = nr/tile tiles of size tile. */
 } tlr_mdd_desc_t;
 
 /* Solver options (ADMM solver section; values the paper leaves open are
@@ -278,17 +277,19 @@ int tlr_mdd_tile_ranks(const void* X, int64_t nr, int64_t b, double eps, int32_t
 int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, int32_t ncand, double eps,
                         int64_t* best_b, int64_t* best_entries, void* stream);
 
-/* Warm start (hyper-parameter selection and initialisation section; reciprocal
- * form only, TLR_ERR_UNSUPPORTED for TLR_RECIP_NONE) for the
+/* Warm start (hyper-parameter selection and initialisation section) for the
  * handle's layout from X (DEVICE complex64 nr x nr, Hilbert order, e.g. the
- * benchmark solution): for each pair (i > j) with rank k the truncated SVD
+ * benchmark solution): for each stored tile (i, j) with rank k (reciprocal
+ * form: i > j; TLR_RECIP_NONE: every i != j) the truncated SVD
  * X_ij ~ U_k Sigma_k V_k^H gives L = U_k Sigma_k^1/2 and R = conj(V_k)
- * Sigma_k^1/2 (so L R^T = U_k Sigma_k V_k^H); a low-rank diagonal tile gets
- * the Takagi form Q = conj(V_k) E_k Sigma_k^1/2, E = diag(V^T U)^1/2, whose
- * Q Q^T is the same truncation (the Q Q^T = X_ii initialisation); a dense
- * diagonal tile gets Z = X_ii.
- * theta: DEVICE complex64 [n_theta].  Needs tile <= 512.  Allocates its work
- * (2 b^2 complex64 per low-rank tile) on the handle's stream; synchronises. */
+ * Sigma_k^1/2 (so L R^T = U_k Sigma_k V_k^H); a low-rank diagonal tile gets,
+ * in the reciprocal form, the Takagi form Q = conj(V_k) E_k Sigma_k^1/2,
+ * E = diag(V^T U)^1/2, whose Q Q^T is the same truncation (the Q Q^T = X_ii
+ * initialisation), and L_ii, R_ii as any tile in the general form; a dense
+ * diagonal tile gets Z = X_ii.  Equal or unequal tiles.
+ * theta: DEVICE complex64 [n_theta].  Needs every tile <= 512.  Allocates its
+ * work (2 d_max^2 complex64 per low-rank tile) on the handle's stream;
+ * synchronises. */
 int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta);
 
 /* Solver state for checkpoint / resume: z and u of the ADMM split (eq.

@@ -1703,14 +1703,15 @@ namespace {
 int tile_ranks_impl(const cf* X, int64_t nr, int64_t b, double eps, std::vector<int32_t>& ranks, int64_t* entries,
                     double* v0, cudaStream_t st, std::string& err) {
     const int N = (int)(nr / b), P = N * (N - 1) / 2, nt = N + P;
-    std::vector<int2> tl(nt);
-    for (int i = 0; i < N; ++i) tl[i] = make_int2(i, i);
+    const int bi = (int)b;
+    std::vector<SvdTile> tl(nt);
+    for (int i = 0; i < N; ++i) tl[i] = SvdTile{i * bi, i * bi, bi, bi, 0};
     for (int j = 0; j < N; ++j)
-        for (int i = j + 1; i < N; ++i) tl[N + j * N - j * (j + 1) / 2 + (i - j - 1)] = make_int2(i, j);
+        for (int i = j + 1; i < N; ++i) tl[N + j * N - j * (j + 1) / 2 + (i - j - 1)] = SvdTile{i * bi, j * bi, bi, bi, 0};
     Arena a;
     a.take<cf>(tile_svd_work_bytes(nt, (int)b, false) / sizeof(cf));
     a.take<float>((size_t)nt * b);
-    a.take<int2>(nt);
+    a.take<SvdTile>(nt);
     a.take<int>(nt);
     a.take<double>(1);
     char* buf = nullptr;
@@ -1723,12 +1724,12 @@ int tile_ranks_impl(const cf* X, int64_t nr, int64_t b, double eps, std::vector<
     w.base = buf;
     cf* work = w.take<cf>(tile_svd_work_bytes(nt, (int)b, false) / sizeof(cf));
     float* sig = w.take<float>((size_t)nt * b);
-    int2* dtl = w.take<int2>(nt);
+    SvdTile* dtl = w.take<SvdTile>(nt);
     int* dr = w.take<int>(nt);
     double* dv0 = w.take<double>(1);
     ranks.assign(nt, 0);
     double hv0 = 0.0;
-    e = cudaMemcpyAsync(dtl, tl.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(dtl, tl.data(), nt * sizeof(SvdTile), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tile_svd(X, nr, dtl, nt, (int)b, work, false, 30, 1e-5f, sig, nullptr, nullptr, st);
     if (e == cudaSuccess) e = rank_rule(sig, nt, (int)b, eps, dr, dv0, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ranks.data(), dr, nt * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1789,72 +1790,92 @@ int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, in
 
 // Warm start: the handle's layout decides each tile's form and rank; X is
 // cut into tiles and each low-rank tile initialised from its truncated SVD
-// (pairs: L = U Sigma^1/2, R = conj(V) Sigma^1/2; low-rank diagonals: the
-// Takagi form Q with Q Q^T the rank-k truncation), dense diagonals copied.
+// (L = U Sigma^1/2, R = conj(V) Sigma^1/2; low-rank diagonals of the
+// reciprocal form: the Takagi form Q with Q Q^T the rank-k truncation; of the
+// general form: L, R as for any tile), dense diagonals copied.  Tiles of any
+// sizes d_i <= 512; a wide tile's SVD runs on its transpose.
 int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!X || !theta) FAIL(h, TLR_ERR_ARG, "X or theta is NULL");
     const Layout& L = h->L;
-    if (L.general) FAIL(h, TLR_ERR_UNSUPPORTED, "the warm start is defined for the reciprocal form");
-    if (L.b == 0) FAIL(h, TLR_ERR_UNSUPPORTED, "the warm start needs a uniform tile partition");
-    if (L.b > 512) FAIL(h, TLR_ERR_SHAPE, "warm start needs tile <= 512");
-    const int N = L.N, b = (int)L.b;
-    std::vector<int2> tl;
+    if (L.dmax > 512) FAIL(h, TLR_ERR_SHAPE, "warm start needs tiles <= 512");
+    const int N = L.N;
+    std::vector<SvdTile> tl;
     std::vector<WarmTile> wt;
-    for (int i = 0; i < N; ++i) {
+    // a low-rank tile (i, j) with factors at offL (rows of block i) and offR (rows of block j)
+    auto lowrank = [&](int i, int j, int k, long long offL, long long offR) {
         WarmTile w{};
-        w.i = w.j = i;
-        w.offL = L.off_diag[i];
-        w.offR = 0;
-        if (L.dense[i]) {
-            w.kind = 2;
-            w.k = b;
-            w.svd = -1;
-        } else {
-            if (L.kd[i] == 0) continue;
-            w.kind = 1;
-            w.k = L.kd[i];
-            w.svd = (int)tl.size();
-            tl.push_back(make_int2(i, i));
-        }
+        w.r0 = (int)L.roff[i];
+        w.c0 = (int)L.roff[j];
+        w.m = (int)L.d[i];
+        w.n = (int)L.d[j];
+        w.kind = 0;
+        w.k = k;
+        w.offL = offL;
+        w.offR = offR;
+        w.trans = w.n > w.m;
+        w.svd = (int)tl.size();
+        tl.push_back(SvdTile{w.r0, w.c0, w.m, w.n, w.trans});
         wt.push_back(w);
-    }
-    for (int j = 0; j < N; ++j)
-        for (int i = j + 1; i < N; ++i) {
-            const int p = j * N - j * (j + 1) / 2 + (i - j - 1);
-            if (L.kp[p] == 0) continue;
+    };
+    for (int i = 0; i < N; ++i) {
+        const int di = (int)L.d[i];
+        if (L.dense[i]) {
             WarmTile w{};
-            w.i = i;
-            w.j = j;
-            w.kind = 0;
-            w.k = L.kp[p];
-            w.offL = L.off_l[p];
-            w.offR = L.off_r[p];
-            w.svd = (int)tl.size();
-            tl.push_back(make_int2(i, j));
+            w.r0 = w.c0 = (int)L.roff[i];
+            w.m = w.n = di;
+            w.kind = 2;
+            w.k = di;
+            w.offL = L.off_diag[i];
+            w.svd = -1;
             wt.push_back(w);
+        } else if (L.kd[i] > 0) {
+            if (L.general) {
+                lowrank(i, i, L.kd[i], L.off_diag[i], L.off_diag[i] + (long long)di * L.kd[i]);
+            } else {
+                WarmTile w{};
+                w.r0 = w.c0 = (int)L.roff[i];
+                w.m = w.n = di;
+                w.kind = 1;
+                w.k = L.kd[i];
+                w.offL = L.off_diag[i];
+                w.svd = (int)tl.size();
+                tl.push_back(SvdTile{w.r0, w.c0, di, di, 0});
+                wt.push_back(w);
+            }
+        }
+    }
+    // stored pairs in stacking order: (i, j), column j outer, row i inner
+    // (reciprocal: i > j; general: every i != j)
+    for (int p = 0, j = 0; j < N; ++j)
+        for (int i = L.general ? 0 : j + 1; i < N; ++i) {
+            if (i == j) continue;
+            if (L.kp[p] > 0) lowrank(i, j, L.kp[p], L.off_l[p], L.off_r[p]);
+            ++p;
         }
     const int nsvd = (int)tl.size(), nw = (int)wt.size();
+    const int bmax = (int)L.dmax;
     Arena a;
-    a.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), b, true) / sizeof(cf));
-    a.take<float>((size_t)std::max(1, nsvd) * b);
-    a.take<int>((size_t)std::max(1, nsvd) * b);
-    a.take<int2>(std::max(1, nsvd));
+    a.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), bmax, true) / sizeof(cf));
+    a.take<float>((size_t)std::max(1, nsvd) * bmax);
+    a.take<int>((size_t)std::max(1, nsvd) * bmax);
+    a.take<SvdTile>(std::max(1, nsvd));
     a.take<WarmTile>(std::max(1, nw));
     char* buf = nullptr;
     CK(h, cudaMallocAsync((void**)&buf, a.used, h->st));
     Arena w;
     w.base = buf;
-    cf* work = w.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), b, true) / sizeof(cf));
-    float* sig = w.take<float>((size_t)std::max(1, nsvd) * b);
-    int* ord = w.take<int>((size_t)std::max(1, nsvd) * b);
-    int2* dtl = w.take<int2>(std::max(1, nsvd));
+    cf* work = w.take<cf>(tile_svd_work_bytes(std::max(1, nsvd), bmax, true) / sizeof(cf));
+    float* sig = w.take<float>((size_t)std::max(1, nsvd) * bmax);
+    int* ord = w.take<int>((size_t)std::max(1, nsvd) * bmax);
+    SvdTile* dtl = w.take<SvdTile>(std::max(1, nsvd));
     WarmTile* dwt = w.take<WarmTile>(std::max(1, nw));
     cudaError_t e = cudaSuccess;
-    if (nsvd) e = cudaMemcpyAsync(dtl, tl.data(), nsvd * sizeof(int2), cudaMemcpyHostToDevice, h->st);
+    if (nsvd) e = cudaMemcpyAsync(dtl, tl.data(), nsvd * sizeof(SvdTile), cudaMemcpyHostToDevice, h->st);
     if (e == cudaSuccess && nw) e = cudaMemcpyAsync(dwt, wt.data(), nw * sizeof(WarmTile), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess) e = tile_svd((const cf*)X, L.nr, dtl, nsvd, b, work, true, 30, 1e-5f, sig, ord, nullptr, h->st);
-    if (e == cudaSuccess) e = warm_fill((const cf*)X, L.nr, dwt, nw, b, work, sig, ord, (cf*)theta, h->st);
+    if (e == cudaSuccess)
+        e = tile_svd((const cf*)X, L.nr, dtl, nsvd, bmax, work, true, 30, 1e-5f, sig, ord, nullptr, h->st);
+    if (e == cudaSuccess) e = warm_fill((const cf*)X, L.nr, dwt, nw, bmax, work, sig, ord, (cf*)theta, h->st);
     cudaFreeAsync(buf, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);   // the host tables above go out of scope
     CK(h, e);

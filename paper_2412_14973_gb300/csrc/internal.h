@@ -152,24 +152,31 @@ cudaError_t cg_start(cf* x, cf* r, cf* p, int n, double* part, double* sc, cudaS
 cudaError_t cg_iteration_tail(cf* x, cf* r, cf* p, const cf* Ap, int n, double tol, double* part, double* sc,
                               cudaStream_t st);
 // Tile SVDs (k_svd.cu) for the rank rule and the warm start.  tile_svd: one
-// one-sided Jacobi SVD per listed b x b tile (tile (i, j) = rows i b.., cols
-// j b.. of the row-major X), b <= 512, work = tile_svd_work_bytes; sig[t b ..]
-// decreasing singular values, order[t b + m] the column of the m-th (may be
-// nullptr), sweeps[t] sweeps used (may be nullptr).  rank_rule: v0 = max
-// sigma, ranks[t] = #{sigma >= eps v0}.  warm_fill: the warm-start factors
-// (kinds: 0 pair L, R; 1 low-rank diagonal Q by the Takagi form; 2 dense Z =
-// tile) written into theta at the given offsets.
+// one-sided Jacobi SVD per listed tile (rows r0 .. r0+m-1, columns c0 ..
+// c0+n-1 of the row-major X; trans: the SVD of its transpose, for n > m),
+// m, n <= bmax <= 512, work = tile_svd_work_bytes(ntiles, bmax, vec);
+// sig[t bmax ..] the decreasing singular values (as many as the columns the
+// sweeps work on) then -1, order[t bmax + q] the column of the q-th (may be
+// nullptr), sweeps[t] sweeps used (may be nullptr).  rank_rule (equal tiles,
+// bmax = b): v0 = max sigma, ranks[t] = #{sigma >= eps v0}.  warm_fill: the
+// warm-start factors (kinds: 0 low-rank tile L, R; 1 low-rank diagonal Q by
+// the Takagi form; 2 dense Z = tile) written into theta at the given offsets.
+struct SvdTile {
+    int r0, c0, m, n, trans;
+};
 struct WarmTile {
-    int i, j, kind, k;
-    long long offL, offR;   // theta offsets (R unused for diagonals)
+    int r0, c0, m, n;       // the tile of X: rows r0.., columns c0.., m x n
+    int kind, k;
+    long long offL, offR;   // theta offsets (R unused for kinds 1 and 2)
     int svd;                // index of the tile's SVD (-1 for dense)
+    int trans;              // that SVD ran on the transpose
 };
 size_t tile_svd_work_bytes(int ntiles, int b, bool vec);
-cudaError_t tile_svd(const cf* X, long long ldx, const int2* tiles, int ntiles, int b, cf* work, bool vec,
+cudaError_t tile_svd(const cf* X, long long ldx, const SvdTile* tiles, int ntiles, int bmax, cf* work, bool vec,
                      int max_sweeps, float tol, float* sig, int* order, int* sweeps, cudaStream_t st);
 cudaError_t rank_rule(const float* sig, int ntiles, int b, double eps, int* ranks, double* v0, cudaStream_t st);
-cudaError_t warm_fill(const cf* X, long long ldx, const WarmTile* wt, int nt, int b, const cf* work, const float* sig,
-                      const int* order, cf* theta, cudaStream_t st);
+cudaError_t warm_fill(const cf* X, long long ldx, const WarmTile* wt, int nt, int bmax, const cf* work,
+                      const float* sig, const int* order, cf* theta, cudaStream_t st);
 // Time <-> frequency stack (fourier.cu): forward: x_t_in [ntr][nt] real ->
 // X_out [nf][ntr], the bins f0 .. f0 + nf - 1 of the unnormalised real DFT;
 // inverse: X_in [nf][ntr] (band, zero elsewhere) -> x_t_out [ntr][nt] with

@@ -76,11 +76,28 @@ def test_general_solve_matches_oracle(prec):
     g.close()
 
 
-def test_general_warm_start_is_unsupported():
-    g, glay, th, Dh, Uh, perm = _setup("lowrank", T.TLR_PREC_FP32)
-    X = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
-    t = torch.zeros(glay.size, dtype=torch.complex64, device="cuda")
-    with pytest.raises(T.TLRError) as e:
-        T.tlr_mdd_warm_start(g.h, X, t)
-    assert e.value.code == T.TLR_ERR_UNSUPPORTED
+@pytest.mark.parametrize("tiles", [None, [20, 36, 8]])
+def test_general_warm_start_matches_oracle(tiles):
+    # a random (non-symmetric) X: every kept tile, diagonal ones included, is
+    # its truncated SVD L R^T; dense diagonals copied.  Bound 1e-3 as for the
+    # reciprocal warm start
+    nr, b = 64, 16
+    ts = tiles or [b] * (nr // b)
+    n = len(ts)
+    X = synth.cn(synth.rng(80), (nr, nr))
+    dense = [False, True] + [False] * (n - 2)
+    rl = [min(3, ts[i]) for i in range(n)] + [min(ts[i], ts[j], 1 + (2 * i + j) % 5)
+                                             for (i, j) in general.ordered_pairs(n)]
+    glay = general.make_general_layout(nr, None if tiles else b, rl, dense, tiles=tiles)
+    D = synth.make_d(nr, nr, 1, 4)[0]
+    d = T.desc(nr, nr, 0 if tiles else b, ranks=rl, nx=8, ny=8, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense,
+               reciprocity=T.TLR_RECIP_NONE, tiles=tiles)
+    g = Gpu(D, D, glay, desc=d)
+    th = torch.zeros(glay.size, dtype=torch.complex64, device="cuda")
+    T.tlr_mdd_warm_start(g.h, dev(X), th)
+    Xg = general.assemble_x(host(th), glay)
+    Xo = general.assemble_x(general.warm_start(X, glay), glay)
+    err = rel(Xg, Xo)
+    print(f"general warm start, tiles {ts}: rel {err:.2e}")
+    assert err <= 1e-3
     g.close()

@@ -10,7 +10,7 @@ import torch
 
 import paper_2412_14973_gb300 as T
 import tlr_synth as synth
-from oracle import general, operator, solver
+from oracle import general, layout, operator, solver, warmstart
 
 from _cases import problem
 from _gpu import Gpu, dev, host, rel
@@ -116,11 +116,25 @@ def test_general_form_on_nonuniform_tiles(prec, tol):
     g.close()
 
 
-def test_warm_start_needs_a_uniform_partition():
-    g, lay, th, Dh, Uh, perm = _setup("big_small", T.TLR_PREC_FP32)
-    X = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
-    t = torch.zeros(lay.size, dtype=torch.complex64, device="cuda")
-    with pytest.raises(T.TLRError) as e:
-        T.tlr_mdd_warm_start(g.h, X, t)
-    assert e.value.code == T.TLR_ERR_UNSUPPORTED
-    g.close()
+def test_warm_start_on_unequal_tiles_matches_oracle():
+    # a random complex symmetric X on tiles 48, 80, 16, 112: every kept tile is
+    # its truncated SVD (wide tiles, e.g. 16 x 80, run the SVD on their
+    # transpose), dense diagonals copied.  Bound as for equal tiles: 1e-3
+    # (FP32 Jacobi to 1e-5 orthogonality; a starting point)
+    tiles = [48, 80, 16, 112]
+    nr = sum(tiles)
+    g = synth.rng(70)
+    A = synth.cn(g, (nr, nr))
+    X = A + A.T
+    ks = [11, 0, 3, 27] + [13, 4, 30, 9, 41, 2]
+    lay = layout.make_layout(nr, None, ks, [False, True, False, False], tiles=tiles)
+    D = synth.make_d(nr, nr, 1, 3)[0]
+    gp = Gpu(D, D, lay, nx=16, ny=16)
+    th = torch.zeros(lay.size, dtype=torch.complex64, device="cuda")
+    T.tlr_mdd_warm_start(gp.h, dev(X), th)
+    Xg = operator.assemble_xh(host(th), lay)
+    Xo = operator.assemble_xh(warmstart.warm_start(X, lay), lay)
+    err = rel(Xg, Xo)
+    print(f"unequal tiles: |X_h(warm, GPU) - X_h(warm, oracle)| = {err:.2e}")
+    assert err <= 1e-3
+    gp.close()
