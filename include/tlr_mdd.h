@@ -292,6 +292,16 @@ int tlr_mdd_choose_tile(const void* X, int64_t nr, const int64_t* candidates, in
  * synchronises. */
 int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta);
 
+/* Failure detection: every barrier wait in the tensor-core contraction
+ * kernels is bounded (2 s of the GPU's global timer, or earlier once another
+ * CTA of the launch has given up); a wait that runs out records
+ * TLR_ERR_TIMEOUT for the host and the kernel returns, leaving the context
+ * usable.  This self-test runs that wait on an mbarrier that nothing arrives
+ * at, with the limit limit_ns (0 < limit_ns <= 1e10): *status (HOST) receives
+ * TLR_ERR_TIMEOUT and *waited_ms (HOST, may be NULL) the time the wait took.
+ * Returns TLR_OK when the kernel ran; synchronises the stream. */
+int tlr_mdd_wait_selftest(int64_t limit_ns, int32_t* status, double* waited_ms, void* stream);
+
 /* Solver state for checkpoint / resume: z and u of the ADMM split (eq.
  * 22-24, scaled dual), DEVICE complex64 [n_theta] each in theta's stacking
  * order.  get: copies the handle's current z, u out (after a solve on the

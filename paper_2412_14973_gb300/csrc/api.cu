@@ -1882,6 +1882,29 @@ int tlr_mdd_warm_start(tlr_mdd_t* h, const void* X, void* theta) {
     return TLR_OK;
 }
 
+int tlr_mdd_wait_selftest(int64_t limit_ns, int32_t* status, double* waited_ms, void* stream) {
+    tlr_mdd_s* h = nullptr;
+    if (!status) FAIL(h, TLR_ERR_ARG, "status is NULL");
+    if (limit_ns <= 0 || limit_ns > 10000000000LL) FAIL(h, TLR_ERR_ARG, "limit_ns must lie in (0, 1e10]");
+    const cudaStream_t st = (cudaStream_t)stream;
+    char* buf = nullptr;
+    CK(h, cudaMallocAsync((void**)&buf, 16, st));
+    int* dst = reinterpret_cast<int*>(buf);
+    unsigned long long* dw = reinterpret_cast<unsigned long long*>(buf + 8);
+    int hs = 0;
+    unsigned long long hw = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
+    if (e == cudaSuccess) e = wait_selftest(dst, (unsigned long long)limit_ns, dw, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, dst, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hw, dw, sizeof(hw), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    CK(h, e);
+    *status = hs;
+    if (waited_ms) *waited_ms = (double)hw * 1e-6;
+    return TLR_OK;
+}
+
 int tlr_mdd_get_state(tlr_mdd_t* h, void* z, void* u) {
     if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
     if (!z || !u) FAIL(h, TLR_ERR_ARG, "z or u is NULL");

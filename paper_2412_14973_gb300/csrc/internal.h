@@ -188,6 +188,11 @@ int fft_stack(bool forward, const float* x_t_in, const cf* X_in, long long ntr, 
 long long packed_bytes(long long R, long long K, int TR);
 cudaError_t pack_operands(const PackJob* d_jobs, int njobs, long long max_items, cudaStream_t st);
 cudaError_t gemm_tcp_prepare();
+// Bounded-wait self-test: one thread waits, with the contraction kernels'
+// wait, on an mbarrier that nothing arrives at; after limit_ns the wait gives
+// up and *status (DEVICE, zero on entry) becomes TLR_ERR_TIMEOUT, *waited_ns
+// (DEVICE) the time it waited.
+cudaError_t wait_selftest(int* status, unsigned long long limit_ns, unsigned long long* waited_ns, cudaStream_t st);
 cudaError_t gemm_tcp(const GemmLaunch& L, cudaStream_t st);
 
 // SIMT path (k_gemm_simt.cu)

@@ -66,7 +66,8 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err,
+                                          unsigned long long limit_ns = WAIT_NS) {
     const unsigned long long t0 = now_ns();
     for (unsigned it = 0;; ++it) {
         uint32_t ok;
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if ((it & 255u) == 255u && (*err != 0 || now_ns() - t0 > WAIT_NS)) return false;
+        if ((it & 255u) == 255u && (*err != 0 || now_ns() - t0 > limit_ns)) return false;
     }
 }
 
@@ -653,6 +654,23 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
     }
 }
 
+// Self-test of the contraction kernels' bounded barrier wait: one thread
+// waits on an mbarrier that nothing arrives at; the wait gives up after
+// limit_ns and the kernel records TLR_ERR_TIMEOUT (and the nanoseconds it
+// waited) for the host.
+__global__ void k_wait_selftest(int* status, unsigned long long limit_ns, unsigned long long* waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const unsigned long long t0 = now_ns();
+    const bool ok = mbar_wait(b, 0u, status, limit_ns);
+    *waited_ns = now_ns() - t0;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(b) : "memory");
+    *status = ok ? TLR_OK : TLR_ERR_TIMEOUT;
+}
+
 }  // namespace
 
 long long packed_bytes(long long R, long long K, int TR) {
@@ -689,6 +707,13 @@ cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
     k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t wait_selftest(int* status, unsigned long long limit_ns, unsigned long long* waited_ns,
+                          cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(status, limit_ns, waited_ns);
     counted(1);
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ __all__ = [
     "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait", "tlr_mdd_set_data",
     "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
     "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
-    "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha",
+    "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -48,7 +48,7 @@ EXPORTED = [
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
     "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
     "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state", "tlr_mdd_time_to_freq",
-    "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha",
+    "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -163,6 +163,7 @@ def lib():
         L.tlr_mdd_time_to_freq.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, vp, vp]
         L.tlr_mdd_freq_to_time.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, C.c_int64, vp, vp]
         L.tlr_mdd_stack_alpha.argtypes = [vp, C.c_int64, C.POINTER(C.c_double), vp]
+        L.tlr_mdd_wait_selftest.argtypes = [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
         L.tlr_mdd_set_state.argtypes = [vp, vp, vp]
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
@@ -398,6 +399,14 @@ def tlr_mdd_stack_alpha(D_w, n, stream=None) -> float:
     a = C.c_double()
     _check(lib().tlr_mdd_stack_alpha(_ptr(D_w), n, C.byref(a), _stream(stream)))
     return a.value
+
+
+def tlr_mdd_wait_selftest(limit_ns, stream=None):
+    """Run the contraction kernels' bounded barrier wait on a barrier that
+    nothing completes: (status the kernel recorded, milliseconds it waited)."""
+    st, ms = C.c_int32(), C.c_double()
+    _check(lib().tlr_mdd_wait_selftest(int(limit_ns), C.byref(st), C.byref(ms), _stream(stream)))
+    return st.value, ms.value
 
 
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):

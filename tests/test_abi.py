@@ -147,3 +147,11 @@ def test_invalid_descriptions_rejected(kw, code):
     assert ei.value.code == code
     assert T.tlr_mdd_workspace_bytes(d) == -1
     assert T.tlr_mdd_last_error()
+
+
+@pytest.mark.parametrize("limit", [0, -5, 20_000_000_000])
+def test_wait_selftest_rejects_bad_limits(limit):
+    _lib()
+    with pytest.raises(T.TLRError) as ei:
+        T.tlr_mdd_wait_selftest(limit)
+    assert ei.value.code == T.TLR_ERR_ARG
