@@ -199,6 +199,18 @@ __device__ __forceinline__ void dots6_add(Acc* s, float rx, float ry, float ax, 
     s[5].add(fmaf(cx, cx, cy * cy));
 }
 
+// the six products of one complex element added to t (plain FP32: a group of
+// up to four elements is summed like this before one compensated add, so
+// the group's rounding is of the order of the products' own)
+__device__ __forceinline__ void dots6_group(float* t, float rx, float ry, float ax, float ay, float cx, float cy) {
+    t[0] += fmaf(rx, rx, ry * ry);
+    t[1] += fmaf(rx, ax, ry * ay);
+    t[2] += fmaf(rx, cx, ry * cy);
+    t[3] += fmaf(ax, ax, ay * ay);
+    t[4] += fmaf(ax, cx, ay * cy);
+    t[5] += fmaf(cx, cx, cy * cy);
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R, const cf* __restrict__ A1,
                                                       const cf* __restrict__ A2, long long n, double* part) {
     __shared__ double sh[32];
@@ -209,18 +221,24 @@ __global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R,
         const float4* C4 = reinterpret_cast<const float4*>(A2);
         const long long n4 = n >> 1, stride = (long long)gridDim.x * blockDim.x;
         long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        for (; i + stride < n4; i += 2 * stride) {   // two elements of each array in flight
+        for (; i + stride < n4; i += 2 * stride) {   // two 16-byte loads of each array in flight
             const float4 r = R4[i], a = A4[i], c = C4[i];
             const float4 r2 = R4[i + stride], a2 = A4[i + stride], c2 = C4[i + stride];
-            dots6_add(s, r.x, r.y, a.x, a.y, c.x, c.y);
-            dots6_add(s, r.z, r.w, a.z, a.w, c.z, c.w);
-            dots6_add(s, r2.x, r2.y, a2.x, a2.y, c2.x, c2.y);
-            dots6_add(s, r2.z, r2.w, a2.z, a2.w, c2.z, c2.w);
+            float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            dots6_group(t, r.x, r.y, a.x, a.y, c.x, c.y);
+            dots6_group(t, r.z, r.w, a.z, a.w, c.z, c.w);
+            dots6_group(t, r2.x, r2.y, a2.x, a2.y, c2.x, c2.y);
+            dots6_group(t, r2.z, r2.w, a2.z, a2.w, c2.z, c2.w);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k].add(t[k]);
         }
         if (i < n4) {
             const float4 r = R4[i], a = A4[i], c = C4[i];
-            dots6_add(s, r.x, r.y, a.x, a.y, c.x, c.y);
-            dots6_add(s, r.z, r.w, a.z, a.w, c.z, c.w);
+            float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            dots6_group(t, r.x, r.y, a.x, a.y, c.x, c.y);
+            dots6_group(t, r.z, r.w, a.z, a.w, c.z, c.w);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k].add(t[k]);
         }
     } else {
         GRID_STRIDE(i, n) {
