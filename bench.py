@@ -597,7 +597,8 @@ def serving_leg(T, torch, n, seed, dev):
     Poisson arrivals.  Measures one-at-a-time throughput on the FP32 and the
     tensor-core paths, then serves the stream with continuous batching (4
     slots, HBM budget 200 GB) at 90% of the tensor-core one-at-a-time capacity
-    and reports p50 / p99 latency.  One seeded D, U per problem size is shared
+    and at 0.7x and 1.3x the FP32 one-at-a-time capacity, and reports p50 /
+    p99 latency.  One seeded D, U per problem size is shared
     by the requests of that size (work does not depend on the values)."""
     import tlr_synth as synth
     from paper_2412_14973_gb300 import serving
@@ -644,6 +645,21 @@ def serving_leg(T, torch, n, seed, dev):
     ok = [r for r in res if r.status == 0]
     pc = serving.percentiles(res)
     same = all(torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, res) if a.status == 0 and b.status == 0)
+    # the tensor-core server at 0.7x and 1.3x the FP32 path's one-at-a-time
+    # capacity (the FP32 path alone would keep up with the first and not the second)
+    loads = []
+    for x in (0.7, 1.3):
+        rx = x * n / t_fp32
+        ax = list(np.cumsum(np.random.default_rng(seed + 20).exponential(1.0 / rx, n)))
+        sx = serving.Server(budget, max_active=4)
+        t0 = time.perf_counter()
+        rs = sx.run(make(T.TLR_PREC_BF16X3, ax), realtime=True)
+        tx = time.perf_counter() - t0
+        px = serving.percentiles(rs)
+        loads.append({"x_fp32_capacity": x, "arrival_rate_hz": round(rx, 3),
+                      "completed": sum(1 for r in rs if r.status == 0), "served_solves_per_s": round(n / tx, 3),
+                      "p50_ms": round(1e3 * px[50], 1) if px[50] else None,
+                      "p99_ms": round(1e3 * px[99], 1) if px[99] else None})
     return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
             "fp32_one_at_a_time_solves_per_s": round(n / t_fp32, 3),
             "tc_one_at_a_time_solves_per_s": round(n / t_tc1, 3),
@@ -652,6 +668,7 @@ def serving_leg(T, torch, n, seed, dev):
             "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,
             "peak_active": srv.peak_active, "peak_budget_gb": round(srv.peak_used / 2**30, 1),
             "results_identical_alone_and_in_mix": bool(same),
+            "fp32_capacity_load_points": loads,
             "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson"}
 
 
