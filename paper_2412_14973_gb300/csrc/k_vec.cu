@@ -399,9 +399,11 @@ __global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) 
 // One block: finalise the partials (warp per value, fixed order), update the
 // newest pair's row / column of S^T Y and Y^T Y, then (thread 0) the
 // triangular solves; coefficients to acoef, gamma to sc[SC_GAMMA].
-// single-block finalisers on the solve's critical path: 1024 threads sum the
-// partial slabs (fixed order per thread, then the block tree)
-constexpr int kFinThreads = 1024;
+// single-block finalisers on the solve's critical path: 256 threads sum the
+// partial slabs (fixed order per thread, then the block tree); at 256 threads
+// (56 registers at most) a finaliser fits on an SM beside two contraction
+// CTAs, so with several solves in flight it never waits for a free SM
+constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) k_lb_solve(SolverDev S) {
     __shared__ double val[32 * 5];
