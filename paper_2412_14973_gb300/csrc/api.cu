@@ -1034,6 +1034,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     std::set<PackKey> static_done;
     std::set<PackKey> a1_keys;
     std::map<const void*, size_t> t_kn, t_nk;   // gather of block i -> packed T~_i (KN), conj T~_i (NK)
+    std::map<const void*, std::pair<size_t, int>> tp_kn;   // gather of block i -> packed T~_p,i (KN), K_i
     auto is_T = [&](const PackKey& k) { return k.src == (const void*)h->T; };
     for (size_t ti = 0; ti < tabs.size(); ++ti) {
         auto& T = tabs[ti];
@@ -1055,6 +1056,11 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                 q.t[t].K = p.t[t].K;
                 for (const PackKey* k : {&ka, &kb}) {
                     if (vpack && k->src == (const void*)h->Tp && k->kcontig == 1) continue;   // written by Lc_v
+                    if (T.G == &h->Le_a1 && k->src == (const void*)h->Tp && k->kcontig == 0 && k->gk &&
+                        k->sgn > 0 && k->ld == L.ns && k->R == L.ns) {
+                        tp_kn[k->gk] = std::make_pair(offs[*k], k->K);   // gathered pack of T_p (tpack)
+                        continue;
+                    }
                     if (rfuse && rkeys.count(*k)) continue;                                    // written by rstep
                     if (is_T(*k)) {
                         if (k->kcontig == 0 && k->sgn > 0)
@@ -1109,6 +1115,24 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             tt.push_back(t);
         }
     }
+    // the line-search expansion's gathered packs of T_p (KN only): tpack's
+    // packing phase on 16-row tiles instead of per-element pack jobs
+    std::vector<TPackTile> ttp;
+    for (auto& kv : tp_kn) {
+        const int Ki = kv.second.second;
+        for (int k0 = 0; k0 < Ki; k0 += kFuseRows) {
+            TPackTile t;
+            t.g = (const int*)kv.first;
+            t.k0 = k0;
+            t.nk = std::min(kFuseRows, Ki - k0);
+            t.Ki = Ki;
+            t.kn = h->packed + kv.second.first;
+            t.nk_dst = nullptr;
+            ttp.push_back(t);
+        }
+    }
+    const size_t tpo = bytes;
+    bytes += (ttp.size() * sizeof(TPackTile) + 255) & ~size_t(255);
     const size_t so = bytes;
     bytes += (sjobs.size() * sizeof(PackJob) + 255) & ~size_t(255);
     const size_t to = bytes;
@@ -1146,6 +1170,14 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         CK(h, cudaMemcpyAsync(h->d_rkn, rkn.data(), L.N * sizeof(char*), cudaMemcpyHostToDevice, h->st));
         CK(h, cudaMemcpyAsync(h->d_rmk, rmk.data(), L.N * sizeof(char*), cudaMemcpyHostToDevice, h->st));
         h->rstep_on = true;
+    }
+    if (!ttp.empty()) {
+        TPackTile* d_ttp = reinterpret_cast<TPackTile*>(h->tcp_tables + tpo);
+        CK(h, cudaMemcpyAsync(d_ttp, ttp.data(), ttp.size() * sizeof(TPackTile), cudaMemcpyHostToDevice, h->st));
+        h->Le_a1.d_gpack = d_ttp;
+        h->Le_a1.n_gpack = (int)ttp.size();
+        h->Le_a1.gpack_src = h->Tp;
+        h->Le_a1.gpack_ns = (int)L.ns;
     }
     h->d_tpack = reinterpret_cast<TPackTile*>(h->tcp_tables + to);
     h->n_tpack = (int)tt.size();

@@ -94,6 +94,7 @@ struct PProb {
     char* const* rowptr;   // EPI_PACKNK: per output row, its first 16-byte group in the packed operand
 };
 
+struct TPackTile;
 struct GemmLaunch {
     GProb* d_probs = nullptr;   // device copy
     int nprob = 0;
@@ -111,6 +112,12 @@ struct GemmLaunch {
     PackJob* d_jobs = nullptr;
     int njobs = 0;
     long long max_items = 0;
+    // gathered KN packs of a product matrix (rows of gpack_src, ns columns)
+    // written by tpack's packing phase (no update) before the other packs
+    const TPackTile* d_gpack = nullptr;
+    int n_gpack = 0;
+    cf* gpack_src = nullptr;
+    int gpack_ns = 0;
 };
 // One row tile of the fused factor-product update (tpack): rows k0 .. k0+nk-1 (nk <= kFuseRows)
 // of block i's gathered products T~_i (T~_i[k] = T[g[k]]), with the packed
@@ -125,7 +132,8 @@ struct TPackTile {
 };
 // T[r] += alpha T_p[r] (FP32 fmaf, alpha read on the device; alpha == nullptr
 // or *alpha == 0: no update) for every row reached through the tiles (each
-// row of T exactly once), then both packed forms of the updated rows.
+// row of T exactly once), then both packed forms of the updated rows (the NK
+// form only for tiles with nk_dst != nullptr).
 cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
                   cudaStream_t st);
 // Fused residual step of the tensor-core path: R += a A1 + a^2 A2 (FP32, the
@@ -204,7 +212,9 @@ cudaError_t gemm_tc_prepare();
 inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
     if (L.prec != TLR_PREC_BF16X3) return gemm_simt(L, st);
     if (!L.d_pprobs) return gemm_tc(L, st);
-    cudaError_t e = pack_operands(L.d_jobs, L.njobs, L.max_items, st);
+    cudaError_t e = cudaSuccess;
+    if (L.n_gpack) e = tpack(L.d_gpack, L.n_gpack, L.gpack_src, nullptr, nullptr, L.gpack_ns, st);
+    if (e == cudaSuccess) e = pack_operands(L.d_jobs, L.njobs, L.max_items, st);
     return e == cudaSuccess ? gemm_tcp(L, st) : e;
 }
 

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
         }
     }
     // phase 3: NK, rows = factor index, k = n; conjugated
-    {
+    if (P.nk_dst) {
         const int nkcN = (ns + 15) >> 4;
         // lanes take consecutive rows: conflict-free shared reads, and 16-byte
         // stores 16 bytes apart in the packed tile
