@@ -189,12 +189,16 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 // tpack: fused update of the factor products and both of their packings
 // ---------------------------------------------------------------------------
 // A CTA takes one row tile (TP_K rows of one block's gathered T~_i) and 128
-// columns (n).  Phase 1 reads the TP_K source rows of T (and T_p) coalesced
-// along n, applies the update, writes T back and keeps the tile in shared
-// memory; phase 2 writes the KN packing (thread = (n, k-group of 8)); phase 3
-// the conjugated NK packing (thread = (k, n-group of 8), lanes along k).  Padding of the
-// packed buffers (k >= K_i, rows >= ns) is zero from the buffer's creation and
-// is never written.
+// columns (n).  Phase 1 either reads the TP_K source rows of T coalesced
+// along n (packing only: alpha == nullptr), or, for the update, reads the
+// tile's current values from its own KN packing (one 16 KB packed tile: the
+// carried products live in packed form between forward products, each
+// update re-rounding them to the hi + lo pair) and the rows of T_p, applies
+// T += alpha T_p; it keeps the tile in shared memory; phase 2 writes the KN
+// packing (thread = (n, k-group of 8)); phase 3 the conjugated NK packing
+// (thread = (k, n-group of 8), lanes along k).  Padding of the packed buffers
+// (k >= K_i, rows >= ns) is zero from the buffer's creation and is never
+// written.
 constexpr int TP_K = kFuseRows, TP_N = 128, TP_LD = TP_N + 1;
 constexpr int TP_KS = TP_K == 16 ? 4 : 5;   // log2(TP_K)
 static_assert(kPackTRB == 128 && KC == 16 && (TP_K == 16 || TP_K == 32),
@@ -227,11 +231,44 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
     const int n0 = blockIdx.x * TP_N;
     const int nk = P.nk;
     const float a = alpha ? (float)alpha[0] : 0.f;
+    constexpr int plane = 128 * 16 * 2;   // bytes of one BF16 plane of a 128 x 16 tile
     // phase 1 (source row indices staged first; four rows per thread in flight)
     __shared__ long long srow[TP_K];
     if (threadIdx.x < nk) srow[threadIdx.x] = (long long)P.g[P.k0 + threadIdx.x] * ns;
     __syncthreads();
-    {
+    if (alpha) {
+        // thread = (n, k-group of 8): four 16-byte loads (one per BF16 plane)
+        // give 8 complex values of the tile, then the 8 rows of T_p at n
+        static_assert(TP_K == 16, "the update reads one 16-deep packed tile");
+        const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+        const int nkcK = (P.Ki + 15) >> 4;
+        const char* src = reinterpret_cast<const char*>(P.kn) +
+                          ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + core_off(n, kg);
+        uint4 w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = *reinterpret_cast<const uint4*>(src + q * plane);
+        const bool nv = n0 + n < ns;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int kk = kg * 8 + j;
+            const uint32_t sh = (j & 1) * 16;
+            const uint32_t* wr = reinterpret_cast<const uint32_t*>(&w[0]);
+            const uint32_t* wl = reinterpret_cast<const uint32_t*>(&w[1]);
+            const uint32_t* wi = reinterpret_cast<const uint32_t*>(&w[2]);
+            const uint32_t* wm = reinterpret_cast<const uint32_t*>(&w[3]);
+            // bf16 -> fp32 is the bit pattern shifted into the high half
+            float2 t = make_float2(__uint_as_float(((wr[j >> 1] >> sh) & 0xffffu) << 16) +
+                                       __uint_as_float(((wl[j >> 1] >> sh) & 0xffffu) << 16),
+                                   __uint_as_float(((wi[j >> 1] >> sh) & 0xffffu) << 16) +
+                                       __uint_as_float(((wm[j >> 1] >> sh) & 0xffffu) << 16));
+            if (kk < nk && nv && a != 0.f) {
+                const float2 d = Tp[srow[kk] + n0 + n];
+                t.x = fmaf(a, d.x, t.x);
+                t.y = fmaf(a, d.y, t.y);
+            }
+            s[kk * TP_LD + n] = kk < nk ? t : make_float2(0.f, 0.f);
+        }
+    } else {
         const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
         const bool nv = n0 + n < ns;
 #pragma unroll 1
@@ -251,17 +288,11 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
             for (int u = 0; u < 4; ++u) {
                 const int kk = kb + 2 * u;
                 if (kk >= nk) continue;
-                if (a != 0.f && nv) {
-                    t[u].x = fmaf(a, d[u].x, t[u].x);
-                    t[u].y = fmaf(a, d[u].y, t[u].y);
-                    T[srow[kk] + n0 + n] = t[u];
-                }
                 s[kk * TP_LD + n] = t[u];
             }
         }
     }
     __syncthreads();
-    constexpr int plane = 128 * 16 * 2;   // bytes of one BF16 plane of a 128 x 16 tile
     // phase 2: KN, rows n, k = factor index; nk rows of this tile in k-groups of 8
     {
         const int nkcK = (P.Ki + 15) >> 4;
