@@ -23,6 +23,8 @@ CASES = {
     "mixed": (12, 8, [40, 8, 31, 17], [5, 8, 0, 17] + [8, 0, 17, 3, 8, 6], [False, False, True, False], 77),
     "big_small": (8, 8, [60, 4], [3, 4, 4], [False, False], 64),
     "many_tc_tiles": (32, 32, [200, 312, 128, 384], 24, [False, False, True, False], 1024),
+    # a one-receiver tile (ranks 0 and 1 only), a dense 1 x 1 diagonal, k = 0 pairs
+    "unit_tile": (4, 4, [1, 9, 1, 5], [1, 3, 1, 2] + [1, 0, 1, 0, 3, 1], [False, False, True, False], 37),
 }
 PRECS = [(T.TLR_PREC_FP32, 1e-5), (T.TLR_PREC_BF16X3, 1e-3)]
 
