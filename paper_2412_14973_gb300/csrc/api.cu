@@ -2199,9 +2199,17 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 CK(h, sym_dense(h->dd, L.nlr, L.ndense, L.dmax, h->Zsd, h->st, L.general, h->pm.zoff, h->pm.zdim));
                 CK(h, run_gemm(h->Le_a1, h->st));
                 CK(h, run_gemm(h->Le_a2, h->st));
-                CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));
-                CK(h, sv_dots3(S, part3, h->st));
-                CK(h, sv_line_search(S, part6, part3, rho, h->st));
+                if (h->rstep_on) {
+                    // the carried residual lives in its packed forms
+                    CK(h, dots6_packed(h->d_rkn, h->A1, h->A2, (int)L.nr, (int)L.ns, (int)L.b, part6, h->st,
+                                       L.b > 0 ? nullptr : h->d_roff, L.N));
+                    CK(h, sv_dots3(S, part3, h->st));
+                    CK(h, sv_line_search(S, part6, kRedBlocks, part3, rho, h->st));
+                } else {
+                    CK(h, dots6_part(h->R, h->A1, h->A2, nrs, part6, h->st));
+                    CK(h, sv_dots3(S, part3, h->st));
+                    CK(h, sv_line_search(S, part6, kRedBlocks, part3, rho, h->st));
+                }
                 if (h->rstep_on)
                     CK(h, rstep(h->R, h->A1, h->A2, h->sc + SC_ALPHA, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn,
                                 h->d_rmk, h->rpart, h->st, L.b > 0 ? nullptr : h->d_roff, L.N));

@@ -137,15 +137,22 @@ struct TPackTile {
 cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
                   cudaStream_t st);
 // Fused residual step of the tensor-core path: R += a A1 + a^2 A2 (FP32, the
-// same arithmetic as the plain residual step; a read on the device, alpha ==
-// nullptr: no update), the per-CTA partial of ||R||^2 (two-sum per thread,
-// FP64 across the CTA) into part[cta] when part != nullptr, and R in both
-// packed forms: block i's rows as an A operand with k = ns (MK, mk[i]) and
-// as a B operand with rows = ns and k = the receiver (KN, kn[i]).  Blocks of
+// same arithmetic as the plain residual step; a read on the device), with R
+// read from and written back to its packed forms only (the FP32 R of the
+// forward product is read when alpha == nullptr: packing, no update); the
+// per-CTA partial of ||R||^2 (two-sum per thread, FP64 across the CTA) into
+// part[cta] when part != nullptr, and R in both packed forms: block i's rows
+// as an A operand with k = ns (MK, mk[i]) and as a B operand with rows = ns
+// and k = the receiver (KN, kn[i]).  Blocks of
 // b rows (roff == nullptr) or block i = rows roff[i] .. roff[i+1]-1 (DEVICE
 // [nblk + 1]); every block size a multiple of kFuseRows.  rstep_ctas gives the
 // number of CTAs (and partials).
 long long rstep_ctas(int nr, int ns);
+// The six line-search inner products with R read from its KN packing (kn[i],
+// as rstep writes it), over rstep's tiles: part[blk * 6 + k], kRedBlocks
+// partials (a fixed grid, so the sums are reproducible).
+cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, int ns, int b, double* part,
+                         cudaStream_t st, const long long* roff = nullptr, int nblk = 0);
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
                   char* const* mk, double* part, cudaStream_t st, const long long* roff = nullptr, int nblk = 0);
 // Benchmark solver of eq. (4) (k_cg.cu): the symmetrising pass

@@ -223,6 +223,28 @@ __device__ __forceinline__ void split_store(char* dst, int plane, const float2* 
         *reinterpret_cast<uint4*>(dst + q * plane) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
+// The 8 complex values of k-group kg of one row of a 16-deep packed tile
+// (src = the row's 16-byte group in plane 0): hi + lo of each part, the
+// BF16 halves widened by moving their bits into the high half of an FP32 word.
+__device__ __forceinline__ void unpack8(const char* src, float2* v) {
+    constexpr int plane = 128 * 16 * 2;
+    uint4 w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = *reinterpret_cast<const uint4*>(src + q * plane);
+    const uint32_t* wr = reinterpret_cast<const uint32_t*>(&w[0]);
+    const uint32_t* wl = reinterpret_cast<const uint32_t*>(&w[1]);
+    const uint32_t* wi = reinterpret_cast<const uint32_t*>(&w[2]);
+    const uint32_t* wm = reinterpret_cast<const uint32_t*>(&w[3]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t sh = (j & 1) * 16;
+        v[j] = make_float2(__uint_as_float(((wr[j >> 1] >> sh) & 0xffffu) << 16) +
+                               __uint_as_float(((wl[j >> 1] >> sh) & 0xffffu) << 16),
+                           __uint_as_float(((wi[j >> 1] >> sh) & 0xffffu) << 16) +
+                               __uint_as_float(((wm[j >> 1] >> sh) & 0xffffu) << 16));
+    }
+}
+
 __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ tiles, cf* __restrict__ T,
                                                const cf* __restrict__ Tp, const double* __restrict__ alpha,
                                                int ns) {
@@ -244,23 +266,13 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
         const int nkcK = (P.Ki + 15) >> 4;
         const char* src = reinterpret_cast<const char*>(P.kn) +
                           ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + core_off(n, kg);
-        uint4 w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = *reinterpret_cast<const uint4*>(src + q * plane);
+        float2 v[8];
+        unpack8(src, v);
         const bool nv = n0 + n < ns;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int kk = kg * 8 + j;
-            const uint32_t sh = (j & 1) * 16;
-            const uint32_t* wr = reinterpret_cast<const uint32_t*>(&w[0]);
-            const uint32_t* wl = reinterpret_cast<const uint32_t*>(&w[1]);
-            const uint32_t* wi = reinterpret_cast<const uint32_t*>(&w[2]);
-            const uint32_t* wm = reinterpret_cast<const uint32_t*>(&w[3]);
-            // bf16 -> fp32 is the bit pattern shifted into the high half
-            float2 t = make_float2(__uint_as_float(((wr[j >> 1] >> sh) & 0xffffu) << 16) +
-                                       __uint_as_float(((wl[j >> 1] >> sh) & 0xffffu) << 16),
-                                   __uint_as_float(((wi[j >> 1] >> sh) & 0xffffu) << 16) +
-                                       __uint_as_float(((wm[j >> 1] >> sh) & 0xffffu) << 16));
+            float2 t = v[j];
             if (kk < nk && nv && a != 0.f) {
                 const float2 d = Tp[srow[kk] + n0 + n];
                 t.x = fmaf(a, d.x, t.x);
@@ -341,17 +353,15 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 // accumulates ||R||^2 and keeps the tile in shared memory; phase 2 writes the
 // MK packing (rows = receivers, lanes along rows); phase 3 the KN packing
 // (rows = n, k = receiver, lanes along n).
-__global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __restrict__ A1,
-                                               const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
-                                               int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
-                                               double* __restrict__ part, const long long* __restrict__ roff,
-                                               int nblk) {
-    __shared__ float2 s[TP_K * TP_LD];
-    __shared__ double sh[32];
-    const int n0 = blockIdx.x * TP_N, r0 = blockIdx.y * TP_K;
-    // block of this row tile: r0 / b for equal tiles, else the largest i with
-    // roff[i] <= r0 (every roff[i] is a multiple of TP_K, so the tile lies in it)
+// Block of the 16-row residual tile starting at row r0: r0 / b for equal
+// tiles, else the largest i with roff[i] <= r0 (every roff[i] is a multiple
+// of TP_K, so the tile lies in it); rl0 = its first row in the block, bK =
+// the block's size.
+struct RTile {
     int blk, rl0, bK;
+};
+__device__ __forceinline__ RTile rtile(int r0, int b, const long long* roff, int nblk) {
+    RTile t;
     if (roff) {
         int lo = 0, hi = nblk - 1;
         while (lo < hi) {
@@ -361,46 +371,69 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
             else
                 hi = mid - 1;
         }
-        blk = lo;
-        rl0 = r0 - (int)roff[blk];
-        bK = (int)(roff[blk + 1] - roff[blk]);
+        t.blk = lo;
+        t.rl0 = r0 - (int)roff[lo];
+        t.bK = (int)(roff[lo + 1] - roff[lo]);
     } else {
-        blk = r0 / b;
-        rl0 = r0 - blk * b;
-        bK = b;
+        t.blk = r0 / b;
+        t.rl0 = r0 - t.blk * b;
+        t.bK = b;
     }
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __restrict__ A1,
+                                               const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
+                                               int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
+                                               double* __restrict__ part, const long long* __restrict__ roff,
+                                               int nblk) {
+    __shared__ float2 s[TP_K * TP_LD];
+    __shared__ double sh[32];
+    constexpr int plane = 128 * 16 * 2;
+    const int n0 = blockIdx.x * TP_N, r0 = blockIdx.y * TP_K;
+    const RTile tl = rtile(r0, b, roff, nblk);
+    const int blk = tl.blk, rl0 = tl.rl0, bK = tl.bK;
     const float a = alpha ? (float)alpha[0] : 0.f;
     const float a2 = alpha ? (float)(alpha[0] * alpha[0]) : 0.f;
     Acc acc;
-    {
+    if (alpha) {
+        // the step: the tile's current values from its own KN packing (one
+        // 16-deep packed tile; thread = (n, k-group of 8)), then A1, A2
+        const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+        const bool nv = n0 + n < ns;
+        float2 v[8];
+        unpack8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + core_off(n, kg), v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int kk = kg * 8 + j;
+            float2 r = v[j];
+            if (nv) {
+                if (a != 0.f) {
+                    const long long o = (long long)(r0 + kk) * ns + n0 + n;
+                    const float2 u = A1[o], w = A2[o];
+                    r.x = fmaf(a2, w.x, fmaf(a, u.x, r.x));
+                    r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
+                }
+                acc.add(fmaf(r.x, r.x, r.y * r.y));
+            }
+            s[kk * TP_LD + n] = r;
+        }
+    } else {
+        // packing only (after a forward product): the FP32 rows of R
         const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
         const bool nv = n0 + n < ns;
 #pragma unroll 1
         for (int kb = kq; kb < TP_K; kb += 8) {
-            float2 r[4], u[4], w[4];
+            float2 r[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                r[q] = u[q] = w[q] = make_float2(0.f, 0.f);
-                if (nv) {
-                    const long long o = (long long)(r0 + kb + 2 * q) * ns + n0 + n;
-                    r[q] = R[o];
-                    if (a != 0.f) {
-                        u[q] = A1[o];
-                        w[q] = A2[o];
-                    }
-                }
+                r[q] = make_float2(0.f, 0.f);
+                if (nv) r[q] = R[(long long)(r0 + kb + 2 * q) * ns + n0 + n];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = kb + 2 * q;
-                if (nv) {
-                    if (a != 0.f) {
-                        r[q].x = fmaf(a2, w[q].x, fmaf(a, u[q].x, r[q].x));
-                        r[q].y = fmaf(a2, w[q].y, fmaf(a, u[q].y, r[q].y));
-                        R[(long long)(r0 + kk) * ns + n0 + n] = r[q];
-                    }
-                    acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
-                }
+                if (nv) acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
                 s[kk * TP_LD + n] = r[q];
             }
         }
@@ -411,7 +444,6 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
     } else {
         __syncthreads();
     }
-    constexpr int plane = 128 * 16 * 2;
     // phase 2: MK, rows = receivers of block blk, k = n
     {
         const int nkcN = (ns + 15) >> 4;
@@ -443,6 +475,55 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
             char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + core_off(nn & 127, (k >> 3) & 1);
             split_store(dst, plane, v, 1.f);
         }
+    }
+}
+
+// The six line-search inner products Re<R,R>, Re<R,A1>, Re<R,A2>, Re<A1,A1>,
+// Re<A1,A2>, Re<A2,A2> over rstep's 16-row x 128-column tiles, with R read
+// from its KN packing (the form it is carried in between forward products)
+// and A1, A2 in FP32; products of four elements summed in FP32 before each
+// compensated add.  A fixed grid walks the tiles in a fixed order and leaves
+// one partial per dot and CTA (few partials for the one-block finaliser).
+__global__ void __launch_bounds__(256) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
+                                                const cf* __restrict__ A2, int ns, int nr, int b,
+                                                const long long* __restrict__ roff, int nblk,
+                                                double* __restrict__ part) {
+    __shared__ double sh[32];
+    constexpr int plane = 128 * 16 * 2;
+    const int gx = (ns + TP_N - 1) / TP_N;
+    const long long ntiles = (long long)gx * (nr / TP_K);
+    const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+    Acc acc[6];
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int n0 = (int)(tt % gx) * TP_N, r0 = (int)(tt / gx) * TP_K;
+        if (n0 + n >= ns) continue;
+        const RTile tl = rtile(r0, b, roff, nblk);
+        float2 v[8];
+        unpack8(kn[tl.blk] + ((long long)(n0 >> 7) * (tl.bK >> 4) + (tl.rl0 >> 4)) * 4 * plane + core_off(n, kg), v);
+        float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const long long o = (long long)(r0 + kg * 8 + j) * ns + n0 + n;
+            const float2 r = v[j], x = A1[o], c = A2[o];
+            g[0] += fmaf(r.x, r.x, r.y * r.y);
+            g[1] += fmaf(r.x, x.x, r.y * x.y);
+            g[2] += fmaf(r.x, c.x, r.y * c.y);
+            g[3] += fmaf(x.x, x.x, x.y * x.y);
+            g[4] += fmaf(x.x, c.x, x.y * c.y);
+            g[5] += fmaf(c.x, c.x, c.y * c.y);
+            if ((j & 3) == 3) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    acc[k].add(g[k]);
+                    g[k] = 0.f;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double t = block_sum(acc[k].val(), sh);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * 6 + k] = t;
     }
 }
 
@@ -738,6 +819,17 @@ cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
     k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, int ns, int b, double* part,
+                         cudaStream_t st, const long long* roff, int nblk) {
+    if (nr == 0 || ns == 0) return cudaSuccess;
+    if (nr % TP_K != 0) return cudaErrorInvalidValue;
+    if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
+    if (roff && nblk <= 0) return cudaErrorInvalidValue;
+    k_dots6p<<<kRedBlocks, 256, 0, st>>>(kn, A1, A2, ns, nr, b, roff, nblk, part);
     counted(1);
     return cudaGetLastError();
 }

@@ -619,13 +619,13 @@ __device__ bool quartic_argmin(const double* c, double* out) {
 
 // One thread: finalise the 6 + 3 inner products, form phi's coefficients,
 // check descent, pick alpha; alpha = 0 and a memory reset when no step.
-__global__ void __launch_bounds__(kFinThreads) k_line_search(SolverDev S, const double* part6, const double* part3,
-                                                             double rho) {
+__global__ void __launch_bounds__(kFinThreads) k_line_search(SolverDev S, const double* part6, int nb6,
+                                                             const double* part3, double rho) {
     __shared__ double sh[32];
     double d6[6], d3[3];
     for (int k = 0; k < 6; ++k) {
         double v = 0.0;
-        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += part6[i * 6 + k];
+        for (int i = threadIdx.x; i < nb6; i += blockDim.x) v += part6[i * 6 + k];
         d6[k] = block_sum(v, sh);
     }
     for (int k = 0; k < 3; ++k) {
@@ -825,9 +825,9 @@ cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {
     counted(1);
     return cudaGetLastError();
 }
-cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
+cudaError_t sv_line_search(const SolverDev& S, const double* part6, int nb6, const double* part3, double rho,
                            cudaStream_t st) {
-    k_line_search<<<1, kFinThreads, 0, st>>>(S, part6, part3, rho);
+    k_line_search<<<1, kFinThreads, 0, st>>>(S, part6, nb6, part3, rho);
     counted(1);
     return cudaGetLastError();
 }

@@ -42,7 +42,9 @@ cudaError_t sv_admm_resume(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st);
 cudaError_t sv_direction(const SolverDev& S, cudaStream_t st);
 cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st);
-cudaError_t sv_line_search(const SolverDev& S, const double* part6, const double* part3, double rho,
+// part6: nb6 blocks of 6 partial sums (kRedBlocks from dots6_part, or one per
+// CTA of the packed-residual inner products)
+cudaError_t sv_line_search(const SolverDev& S, const double* part6, int nb6, const double* part3, double rho,
                            cudaStream_t st);
 cudaError_t sv_step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha,
                              double* partf, cudaStream_t st);
