@@ -348,11 +348,15 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
 // ---------------------------------------------------------------------------
 // rstep: fused residual step and both packings of the residual
 // ---------------------------------------------------------------------------
-// A CTA takes TP_K receiver rows (inside one block, every block a multiple of TP_K) and 128
-// columns: phase 1 reads R, A1, A2 coalesced along n, updates, writes R back,
-// accumulates ||R||^2 and keeps the tile in shared memory; phase 2 writes the
-// MK packing (rows = receivers, lanes along rows); phase 3 the KN packing
-// (rows = n, k = receiver, lanes along n).
+// A CTA takes TP_K receiver rows (inside one block, every block a multiple of
+// TP_K) and 128 columns: phase 1 either reads the FP32 rows of R left by a
+// forward product (packing only), or, for the step, reads the tile from R's
+// own KN packing (the residual is carried in packed form between forward
+// products) with A1, A2 coalesced along n and applies it; it accumulates
+// ||R||^2 and keeps the tile in shared memory; phase 2 writes the MK packing
+// (rows = receivers, lanes along rows); phase 3 the KN packing (rows = n,
+// k = receiver, lanes along n).
+
 // Block of the 16-row residual tile starting at row r0: r0 / b for equal
 // tiles, else the largest i with roff[i] <= r0 (every roff[i] is a multiple
 // of TP_K, so the tile lies in it); rl0 = its first row in the block, bK =
