@@ -30,29 +30,30 @@ def test_assembly_written_out():
     assert not np.allclose(X, X.T)
 
 
-def test_reduces_to_the_reciprocal_form():
+@pytest.mark.parametrize("tiles", [None, [3, 6, 3], [5, 2, 5]])
+def test_reduces_to_the_reciprocal_form(tiles):
     # mirrored factors (L_ji = R_ij, R_ji = L_ij, L_ii = R_ii = Q_ii, Z_ii
-    # symmetric) give the reciprocal X_h and the same misfit
+    # symmetric) give the reciprocal X_h and the same misfit; equal tiles of
+    # 4 or the unequal partitions given
     nr, b = 12, 4
-    ranks = [2, 3, 0] + [1, 2, 3]
-    sym = layout.make_layout(nr, b, ranks, [False, True, False])
+    ranks = [2, 2, 0] + [1, 2, 2]
+    sym = layout.make_layout(nr, None if tiles else b, ranks, [False, True, False], tiles=tiles)
     ths = _theta(sym, 2)
     n = sym.n
     kp = {}
     for p, (i, j) in enumerate(sym.pair_list):
         kp[(i, j)] = kp[(j, i)] = sym.k_pair[p]
     gen_ranks = list(sym.k_diag) + [kp[(i, j)] for (i, j) in general.ordered_pairs(n)]
-    gen = general.make_general_layout(nr, b, gen_ranks, sym.dense)
+    gen = general.make_general_layout(nr, None if tiles else b, gen_ranks, sym.dense, tiles=tiles)
     thg = np.zeros(gen.size, np.complex128)
     for i in range(n):
         B = sym.diag_block(ths, i)
         o = gen.off_diag[i]
         if sym.dense[i]:
-            thg[o:o + b * b] = (0.5 * (B + B.T)).ravel()
+            thg[o:o + B.size] = (0.5 * (B + B.T)).ravel()
         else:
-            k = B.shape[1]
-            thg[o:o + b * k] = B.ravel()
-            thg[o + b * k:o + 2 * b * k] = B.ravel()
+            thg[o:o + B.size] = B.ravel()
+            thg[o + B.size:o + 2 * B.size] = B.ravel()
     pos = {ij: p for p, ij in enumerate(gen.pair_list)}
     for p, (i, j) in enumerate(sym.pair_list):
         L, R = sym.l_block(ths, p), sym.r_block(ths, p)
