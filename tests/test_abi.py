@@ -155,3 +155,31 @@ def test_wait_selftest_rejects_bad_limits(limit):
     with pytest.raises(T.TLRError) as ei:
         T.tlr_mdd_wait_selftest(limit)
     assert ei.value.code == T.TLR_ERR_ARG
+
+
+def test_random_partitions_match_the_oracle_layout():
+    # random tile sizes, ranks within [0, min(d_i, d_j)], per-tile diagonal
+    # modes, both forms: the library's stacking equals the oracle's
+    from oracle import general
+    import numpy as np
+    _lib()
+    g = np.random.default_rng(2412)
+    for trial in range(60):
+        n = int(g.integers(1, 7))
+        tiles = [int(x) for x in g.integers(1, 40, n)]
+        nr = sum(tiles)
+        dense = [bool(x) for x in g.integers(0, 2, n)]
+        recip = bool(trial % 2)
+        pairs = general.ordered_pairs(n) if recip else layout.pairs(n)
+        kd = [int(g.integers(0, tiles[i] + 1)) for i in range(n)]
+        kp = [int(g.integers(0, min(tiles[i], tiles[j]) + 1)) for (i, j) in pairs]
+        d = T.desc(nr, 7, 0, ranks=kd + kp, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense, tiles=tiles,
+                   reciprocity=T.TLR_RECIP_NONE if recip else T.TLR_RECIP_SYMMETRIC)
+        if recip:
+            lay = general.make_general_layout(nr, None, kd + kp, dense, tiles=tiles)
+        else:
+            lay = layout.make_layout(nr, None, kd + kp, dense, tiles=tiles)
+        od, ol, orr, dn = T.tlr_mdd_theta_layout(d)
+        assert (od, ol, orr, dn) == (lay.off_diag, lay.off_l, lay.off_r, lay.dense), (tiles, kd, kp, dense)
+        assert T.tlr_mdd_theta_size(d) == lay.size
+        assert T.tlr_mdd_workspace_bytes(d) > 0
