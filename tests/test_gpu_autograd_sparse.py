@@ -61,5 +61,5 @@ def test_sparse_sampling_noisy_solve_matches_oracle():
     g.close()
     assert st.iters == 30 and st.status == 0
     e = rel(operator.assemble_xh(th, lay), operator.assemble_xh(tho, lay))
-    print(f"config3 sparse noisy TC solve: rel X {e:.2e}")
+    print(f"nr 1024 sparse-source noisy TC solve: rel X {e:.2e}")
     assert e <= 1e-3

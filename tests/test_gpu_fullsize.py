@@ -1,9 +1,9 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
-configs[1]: nr = ns = 4096 (64 x 64 grid), tile 256, ranks 4 and 48, low-rank
+The batched workload, nr = ns = 4096 (64 x 64 grid), tile 256, ranks 4 and 48, low-rank
 diagonals: sampled columns of Y = X_h Dfrak and the full gradient against the
 FP64 oracle's TLR-structured forms, on both paths.
-configs[2]: nr = ns = 9216 (96 x 96 grid), tile 384, rank 64: sampled columns
+The large workload, nr = ns = 9216 (96 x 96 grid), tile 384, rank 64: sampled columns
 of Y on the tensor-core path, and the adjoint identity <X Dfrak, V> =
 <X, V Dfrak^H> with the GPU's own products at full size.
 Inputs: complex Gaussian D (the operator parity does not depend on D's
@@ -31,7 +31,7 @@ def _big(nx, ny, b, k, seed):
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-4)])
 @pytest.mark.parametrize("k", [4, 48])
-def test_config1_columns_and_full_gradient(prec, tol, k):
+def test_nr4096_tile256_columns_and_full_gradient(prec, tol, k):
     D, U, lay, th = _big(64, 64, 256, k, 100 + k)
     g = Gpu(D, U, lay, nx=64, ny=64, precision=prec)
     perm, alpha, Dt, Ut = g.data()
@@ -47,7 +47,7 @@ def test_config1_columns_and_full_gradient(prec, tol, k):
     g.close()
 
 
-def test_config2_columns_tensor_core():
+def test_nr9216_tile384_columns_tensor_core():
     D, U, lay, th = _big(96, 96, 384, 64, 300)
     g = Gpu(D, U, lay, nx=96, ny=96, precision=T.TLR_PREC_BF16X3)
     perm, alpha, Dt, Ut = g.data()

@@ -18,7 +18,7 @@ TOL, ETOL = 1e-5, 1e-4
 
 CASES = {
     # name: (nx, ny, b, ranks, mode, ns)
-    "config0": (16, 16, 64, 8, "dense", 256),
+    "dense256": (16, 16, 64, 8, "dense", 256),
     "ragged": (12, 8, 48, 5, "lowrank", 203),
     "mixed": (8, 8, 16, [3, 0, 16, 2, 1, 0, 4, 5, 2, 1], [False, True, True, False], 77),
     "one_tile_dense": (4, 4, 16, 0, "dense", 33),
@@ -65,7 +65,7 @@ def test_grad_and_misfit(name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["config0", "ragged", "mixed"])
+@pytest.mark.parametrize("name", ["dense256", "ragged", "mixed"])
 def test_adjoint_and_dot_product(name):
     g, lay, th, Dh, Uh, _ = _setup(name)
     V = synth.cn(synth.rng(17), (lay.nr, Dh.shape[0])).astype(np.complex64).astype(np.complex128)
@@ -82,7 +82,7 @@ def test_adjoint_and_dot_product(name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["config0", "mixed", "one_tile_lr"])
+@pytest.mark.parametrize("name", ["dense256", "mixed", "one_tile_lr"])
 def test_unpermute_dense(name):
     g, lay, th, Dh, Uh, perm = _setup(name)
     th = th.astype(np.complex64).astype(np.complex128)
@@ -96,7 +96,7 @@ def test_unpermute_dense(name):
 def test_gradient_of_zero_theta_is_minus_adjoint_image():
     # at theta = 0 the low-rank gradients vanish and the dense ones are
     # -(D^H U + (D^H U)^T)/2 restricted to the diagonal tiles
-    g, lay, th, Dh, Uh, _ = _setup("config0")
+    g, lay, th, Dh, Uh, _ = _setup("dense256")
     f, gr = g.grad(np.zeros(lay.size))
     go = operator.gradient(np.zeros(lay.size), lay, Dh, Uh)
     assert rel(gr, go) <= TOL

@@ -23,7 +23,7 @@ def _oracle_solve(D, U, perm, lay, th0, **kw):
     return th, st, alpha
 
 
-def test_config0_final_x_within_1e_3():
+def test_nr256_dense_diagonal_final_x_within_1e_3():
     # nr = ns = 256 (16 x 16 grid), tile 64, rank 8, dense diagonal, 20 dB, 30 iterations
     D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
     th0 = _start(lay)

@@ -53,7 +53,7 @@ def test_tc_grad(name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["config0", "ragged"])
+@pytest.mark.parametrize("name", ["dense256", "ragged"])
 def test_tc_adjoint(name):
     g, lay, th, Dh, Uh = _setup(name)
     V = synth.cn(synth.rng(17), (lay.nr, Dh.shape[0])).astype(np.complex64).astype(np.complex128)
@@ -65,7 +65,7 @@ def test_tc_adjoint(name):
     g.close()
 
 
-def test_tc_config0_solve():
+def test_tc_dense256_solve():
     D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
     th0 = (0.1 * synth.planted_theta(256, 64, 8, lay.dense, 77)).astype(np.complex64).astype(np.complex128)
     Dh, Uh, alpha = operator.normalise(D, U, perm)
@@ -76,7 +76,7 @@ def test_tc_config0_solve():
     Xo = operator.unpermute(operator.assemble_xh(tho, lay), perm)
     X = operator.unpermute(operator.assemble_xh(th, lay), perm)
     e = rel(X, Xo)
-    print(f"tc config0 solve: rel X {e:.2e}")
+    print(f"tc dense256 solve: rel X {e:.2e}")
     assert st.iters == 30 and st.status == 0
     assert e <= 1e-3   # final Green's function bound (measured ~3e-6)
 

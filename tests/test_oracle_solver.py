@@ -116,7 +116,7 @@ def test_planted_recovery_noise_free():
     assert np.linalg.norm(X - Xt) <= 1e-6 * np.linalg.norm(Xt)
 
 
-def test_config0_style_solve_runs_and_decreases():
+def test_nr256_dense_diagonal_solve_runs_and_decreases():
     D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
     Dh, Uh, _ = operator.normalise(D, U, perm)
     prob = solver.Problem(lay, Dh.T, Uh.T)
