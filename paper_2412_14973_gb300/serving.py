@@ -18,6 +18,7 @@ the mix.
 from __future__ import annotations
 
 import collections
+import json
 import time
 from dataclasses import dataclass, field
 
@@ -148,3 +149,37 @@ def percentiles(results, ps=(50, 99)):
         i = min(len(lat) - 1, max(0, int(-(-p * len(lat) // 100)) - 1))
         out[p] = lat[i]
     return out
+
+
+def records(requests, results) -> list:
+    """One log record per request: its problem (nr, ns, tile or tile count,
+    rank, precision), queue wait, latency and device time in ms, solver
+    iterations and status.  ``desc`` may be any object with those fields."""
+    by_id = {r.rid: r for r in requests}
+    out = []
+    for res in results:
+        d = by_id[res.rid].desc
+        tiles = getattr(d, "tiles", None)
+        prec = getattr(d, "precision", None)
+        out.append({
+            "rid": res.rid,
+            "nr": int(getattr(d, "nr", 0)), "ns": int(getattr(d, "ns", 0)),
+            "tile": None if tiles else int(getattr(d, "tile", 0)),
+            "ntiles": int(getattr(d, "ntiles", 0)) if tiles else None,
+            "rank": int(getattr(d, "rank", 0)),
+            "precision": {T.TLR_PREC_FP32: "fp32", T.TLR_PREC_BF16X3: "bf16x3"}.get(prec),
+            "queue_wait_ms": round(1e3 * res.queue_wait, 3),
+            "latency_ms": round(1e3 * res.latency, 3),
+            "gpu_ms": round(float(res.gpu_ms), 3),
+            "iters": int(res.iters),
+            "status": int(res.status),
+            "message": res.message,
+        })
+    return out
+
+
+def write_jsonl(path, recs) -> None:
+    """The records, one JSON object per line."""
+    with open(path, "w") as fh:
+        for r in recs:
+            fh.write(json.dumps(r) + "\n")

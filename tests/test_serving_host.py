@@ -84,3 +84,24 @@ def test_first_come_first_served(fake):
     srv.run([_req(0, "s1"), _req(1, "big"), _req(2, "s2")], realtime=False)
     # s2 does not overtake the big request that arrived before it
     assert f.order == ["s1", "big", "s2"]
+
+
+def test_records_one_json_line_per_request(fake, monkeypatch, tmp_path):
+    import json
+    fake({"a": 10, "huge": 1000})
+    reqs = [_req(0, "a", 0.0), _req(1, "huge", 0.0)]
+    for r in reqs:
+        r.desc = types.SimpleNamespace(nr=64, ns=48, tile=16, tiles=None, ntiles=0, rank=3,
+                                       precision=serving.T.TLR_PREC_BF16X3, key=r.desc)
+    # the fake library keys its sizes by the description
+    monkeypatch.setattr(serving.T, "tlr_mdd_workspace_bytes", lambda d: {"a": 10, "huge": 1000}[d.key])
+    srv = serving.Server(100, max_active=2, stream_factory=object, poll_s=0)
+    out = srv.run(reqs, realtime=False)
+    recs = serving.records(reqs, out)
+    assert [r["rid"] for r in recs] == [0, 1]
+    assert recs[0]["status"] == 0 and recs[0]["iters"] == 30 and recs[0]["precision"] == "bf16x3"
+    assert recs[1]["status"] == -4 and recs[1]["tile"] == 16
+    p = tmp_path / "log.jsonl"
+    serving.write_jsonl(p, recs)
+    lines = p.read_text().splitlines()
+    assert [json.loads(x)["rid"] for x in lines] == [0, 1]
