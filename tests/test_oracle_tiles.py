@@ -238,3 +238,41 @@ def test_general_warm_start_is_the_truncated_svd_of_every_tile(tiles):
     full = [tiles[i] for i in range(n)] + [min(tiles[i], tiles[j]) for (i, j) in pl]
     lf = general.make_general_layout(nr, None, full, "lowrank", tiles=tiles)
     np.testing.assert_allclose(general.assemble_x(general.warm_start(X, lf), lf), X, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_partitions_gradients_and_structured_forms(seed):
+    # random tile sizes, ranks, diagonal modes and data (both forms): the
+    # gradients match central differences, and the TLR-structured forms the
+    # dense-literal ones
+    g = np.random.default_rng(100 + seed)
+    n = int(g.integers(1, 5))
+    tiles = [int(x) for x in g.integers(1, 6, n)]
+    nr, ns = sum(tiles), int(g.integers(3, 9))
+    dense = [bool(x) for x in g.integers(0, 2, n)]
+    kd = [int(g.integers(0, tiles[i] + 1)) for i in range(n)]
+    Dh = synth.cn(synth.rng(200 + seed), (ns, nr))
+    Uh = synth.cn(synth.rng(300 + seed), (ns, nr))
+    pl = layout.pairs(n)
+    kp = [int(g.integers(0, min(tiles[i], tiles[j]) + 1)) for (i, j) in pl]
+    lay = layout.make_layout(nr, None, kd + kp, dense, tiles=tiles)
+    th = 0.5 * synth.cn(synth.rng(400 + seed), lay.size)
+    if lay.size:
+        gr = operator.gradient(th, lay, Dh, Uh)
+        f = lambda t: operator.misfit(t, lay, Dh, Uh)  # noqa: E731
+        idx = sorted(set(int(x) for x in g.integers(0, lay.size, 6)))
+        fd = _fd(f, th, idx)
+        assert np.max(np.abs(fd - gr[idx])) <= 1e-6 * max(1.0, np.max(np.abs(gr)))
+        fs, gs, _ = tlr.fgrad(th, lay, Dh.T, Uh.T)
+        assert abs(fs - f(th)) <= 1e-12 * max(1.0, f(th))
+        assert np.linalg.norm(gs - gr) <= 1e-12 * max(1.0, np.linalg.norm(gr))
+    gp = general.ordered_pairs(n)
+    gk = [int(g.integers(0, min(tiles[i], tiles[j]) + 1)) for (i, j) in gp]
+    glay = general.make_general_layout(nr, None, kd + gk, dense, tiles=tiles)
+    tg = 0.5 * synth.cn(synth.rng(500 + seed), glay.size)
+    if glay.size:
+        gg = general.gradient(tg, glay, Dh, Uh)
+        f2 = lambda t: general.misfit(t, glay, Dh, Uh)  # noqa: E731
+        idx = sorted(set(int(x) for x in g.integers(0, glay.size, 6)))
+        fd2 = _fd(f2, tg, idx)
+        assert np.max(np.abs(fd2 - gg[idx])) <= 1e-6 * max(1.0, np.max(np.abs(gg)))
