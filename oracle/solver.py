@@ -20,9 +20,14 @@ Readings where the paper is silent (each is listed in the design notes):
 * the line search is exact: C is bilinear in the factors, so
   phi(a) = f(theta + a d) + rho/2 ||theta + a d - v||^2 is a quartic in a; its
   minimiser over a > 0 is taken among the real roots of phi'(a);
-* when d is not a descent direction (or phi has no minimiser on a > 0) the
-  iteration takes no step and clears the L-BFGS memory, so the next direction
-  is steepest descent; a pair (s, y) is kept only if <s,y> > 1e-12 |s||y|;
+* restart (the usual safeguard of L-BFGS, Liu & Nocedal 1989; Nocedal &
+  Wright, Numerical Optimization, ch. 7): when the two-loop direction d is not
+  a descent direction (Re<g, d> >= 0) the memory is cleared and the same
+  iteration continues along d = -g; when the exact line search then finds no
+  minimiser on a > 0 (g = 0, a stationary point, or a degenerate quartic) the
+  iteration takes no step and clears the memory.  An iteration that does
+  either counts as one restart.  A pair (s, y) is kept only if
+  <s,y> > 1e-12 |s||y|;
 * the returned iterate is theta (the x-block).
 """
 from __future__ import annotations
@@ -157,13 +162,21 @@ def lbfgs(prob: Problem, theta, v, rho: float, iters: int, memory: int,
     S, Y = [], []
     for _ in range(iters):
         d = two_loop(g, S, Y)
+        restarted = False
+        if not (_re(g, d) < 0.0):
+            # not a descent direction: clear the memory and continue this
+            # iteration along steepest descent
+            S, Y = [], []
+            d = -g
+            restarted = True
+            stats.restarts += 1
         c = prob.coefficients(theta, d, rho, v)
         a = quartic_argmin(c) if c[1] < 0.0 else None
         if a is None:
-            # no descent along d (or no minimiser on a > 0): take no step this
-            # iteration and clear the memory, so the next direction is -g
+            # no minimiser on a > 0 along d: no step, memory cleared
             S, Y = [], []
-            stats.restarts += 1
+            if not restarted:
+                stats.restarts += 1
             stats.f_hist.append(f)
             stats.alphas.append(0.0)
             stats.iters += 1

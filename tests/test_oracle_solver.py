@@ -169,3 +169,117 @@ def test_benchmark_solver_matches_brute_force_real_system():
     Zb = (sol[: n * n] + 1j * sol[n * n:]).reshape(n, n)
     Z = benchmark.solve_eq4(Dh, Uh, lam)
     assert np.linalg.norm(Z - Zb) <= 1e-9 * np.linalg.norm(Zb)
+
+
+# ---- restart branches of the L-BFGS x-update (reading of the ADMM solver
+# section's eq. 19: L-BFGS with the usual steepest-descent restart) ----
+
+def _restart_problem():
+    D, U, perm, lay, _ = problem(4, 4, 8, 2, "lowrank", ns=20, seed=21, snr_db=10, planted=False)
+    Dh, Uh, _ = operator.normalise(D, U, perm)
+    prob = solver.Problem(lay, Dh.T, Uh.T)
+    th0 = 0.3 * synth.planted_theta(16, 8, 2, lay.dense, 22)
+    v = 0.1 * synth.cn(synth.rng(23), lay.size)
+    return prob, lay, Dh, Uh, th0, v
+
+
+def _phi(th, lay, Dh, Uh, rho, v):
+    # the x-update objective of eq. (19), from the dense-literal misfit
+    w = th - v
+    return operator.misfit(th, lay, Dh, Uh) + 0.5 * rho * float(np.vdot(w, w).real)
+
+
+def test_ascent_direction_restarts_along_minus_g_in_the_same_iteration(monkeypatch):
+    prob, lay, Dh, Uh, th0, v = _restart_problem()
+    rho = 0.5
+    th2, _, _ = solver.lbfgs(prob, th0, v, rho, 2, 10)
+    th3_plain, _, _ = solver.lbfgs(prob, th0, v, rho, 3, 10)
+    g2 = operator.gradient(th2, lay, Dh, Uh) + rho * (th2 - v)
+    real_two_loop = solver.two_loop
+    seen = []
+
+    def forced(g, S, Y):
+        seen.append(len(S))
+        d = real_two_loop(g, S, Y)
+        return g.copy() if len(seen) == 3 else d     # third call: an ascent direction
+
+    monkeypatch.setattr(solver, "two_loop", forced)
+    st = solver.SolveStats()
+    th3, _, _ = solver.lbfgs(prob, th0, v, rho, 3, 10, st)
+    assert seen == [0, 1, 2]              # pairs accumulated before the forced call
+    assert st.restarts == 1 and st.iters == 3 and st.alphas[2] > 0.0
+    assert not np.allclose(th3_plain, th3)
+    # the restart iteration's step is the exact minimiser of phi along -g2,
+    # found here by a grid and a bounded scalar search on the dense-literal objective
+    from scipy.optimize import minimize_scalar
+    phi = lambda a: _phi(th2 - a * g2, lay, Dh, Uh, rho, v)  # noqa: E731
+    amax = 10.0 * st.alphas[2]
+    grid = np.linspace(0.0, amax, 2001)
+    a0 = grid[int(np.argmin([phi(a) for a in grid]))]
+    res = minimize_scalar(phi, bounds=(max(0.0, a0 - amax / 1000), a0 + amax / 1000), method="bounded",
+                          options={"xatol": 1e-14 * amax})
+    step = th3 - th2
+    a_taken = float(np.vdot(-g2, step).real / np.vdot(g2, g2).real)
+    assert np.linalg.norm(step + a_taken * g2) <= 1e-12 * np.linalg.norm(step)   # along -g2
+    assert abs(a_taken - res.x) <= 1e-6 * res.x
+    # the memory was cleared: the next direction sees at most the restart's own pair
+    seen.clear()
+    solver.lbfgs(prob, th0, v, rho, 4, 10)
+    assert seen[:3] == [0, 1, 2] and seen[3] <= 1
+
+
+def test_no_minimiser_on_positive_steps_takes_no_step_and_clears_memory(monkeypatch):
+    prob, lay, Dh, Uh, th0, v = _restart_problem()
+    rho = 0.5
+    th2, _, _ = solver.lbfgs(prob, th0, v, rho, 2, 10)
+    real_coef = solver.Problem.coefficients
+    calls = []
+
+    def degenerate(self, theta, d, rho_, v_):
+        calls.append(1)
+        if len(calls) == 3:
+            # c1 < 0 (descent) but phi is linear: no stationary point on a > 0
+            return np.array([1.0, -1.0, 0.0, 0.0, 0.0])
+        return real_coef(self, theta, d, rho_, v_)
+
+    seen = []
+    real_two_loop = solver.two_loop
+
+    def spy(g, S, Y):
+        seen.append((len(S), g.copy()))
+        return real_two_loop(g, S, Y)
+
+    monkeypatch.setattr(solver.Problem, "coefficients", degenerate)
+    monkeypatch.setattr(solver, "two_loop", spy)
+    st = solver.SolveStats()
+    th3, _, _ = solver.lbfgs(prob, th0, v, rho, 3, 10, st)
+    assert np.array_equal(th3, th2)                      # no step in the third iteration
+    assert st.alphas[2] == 0.0 and st.restarts == 1 and st.iters == 3
+    assert st.f_hist[2] == st.f_hist[1]
+    seen.clear()
+    calls.clear()
+    st = solver.SolveStats()
+    solver.lbfgs(prob, th0, v, rho, 4, 10, st)
+    assert [n for n, _ in seen] == [0, 1, 2, 0]          # memory cleared: the fourth direction is -g
+    assert st.restarts == 1
+
+
+def test_stationary_start_restarts_every_iteration_without_a_step():
+    # theta = 0 with low-rank diagonals: every factor product is bilinear, so
+    # the gradient vanishes (a saddle): each iteration restarts, d = -g = 0,
+    # and no step is taken
+    prob, lay, Dh, Uh, _, v = _restart_problem()
+    th0 = np.zeros(lay.size, np.complex128)
+    st = solver.SolveStats()
+    th, f, gf = solver.lbfgs(prob, th0, np.zeros_like(th0), 1.0, 5, 10, st)
+    assert np.array_equal(th, th0) and st.restarts == 5 and st.iters == 5
+    assert np.all(np.asarray(st.alphas) == 0.0)
+    assert abs(f - 0.5 * float(np.vdot(Uh, Uh).real)) <= 1e-12 * f
+
+
+@pytest.mark.parametrize("c", [[1.0, -1.0, 0.0, 0.0, 0.0],     # linear, decreasing
+                               [0.0, -1.0, 0.0, -1.0, 0.0],    # cubic, phi' = -1 - 3a^2 < 0
+                               [0.0, 1.0, 1.0, 0.0, 1.0],      # phi' = 1 + 2a + 4a^3 > 0 on a > 0
+                               [2.0, 0.0, 0.0, 0.0, 0.0]])     # constant
+def test_quartic_without_positive_stationary_point(c):
+    assert solver.quartic_argmin(c) is None
