@@ -369,8 +369,10 @@ __global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) 
     for (int jj = 0; jj < kLbGroup; ++jj)
 #pragma unroll
         for (int t = 0; t < 5; ++t) acc[jj][t] = 0.f;
+    float gg = 0.f;   // <g, g> for the descent test (first group only)
     GRID_STRIDE(i, S.n2) {
         const float gi = S.g[i], sni = sn[i], yni = yn[i];
+        gg = fmaf(gi, gi, gg);
 #pragma unroll
         for (int jj = 0; jj < kLbGroup; ++jj) {
             if (jj < jc) {
@@ -394,6 +396,10 @@ __global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) 
             if (threadIdx.x == 0) out[jj * 5 + t] = r;
         }
     }
+    if (j0 == 0) {
+        const double r = block_sum((double)gg, sh);
+        if (threadIdx.x == 0) S.lbpart[kLbGGOff + blockIdx.x] = r;
+    }
 }
 
 // One block: finalise the partials (warp per value, fixed order), update the
@@ -406,24 +412,34 @@ __global__ void __launch_bounds__(kLbThreads, 4) k_lb_dots(SolverDev S, int j0) 
 constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) k_lb_solve(SolverDev S) {
-    __shared__ double val[32 * 5];
+    __shared__ double val[32 * 5 + 1];
     __shared__ double Rm[32 * 33];
     __shared__ double Ym[32 * 33];
     __shared__ double p[32], q[32], u[32], t[32];
     const int cnt = S.ints[SI_CNT];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int v = w; v < 5 * cnt; v += kFinThreads / 32) {
-        const int j = v / 5, kind = v % 5;
-        const double* base = S.lbpart + (long long)(j / kLbGroup) * kRedBlocks * (5 * kLbGroup) +
-                             (j % kLbGroup) * 5 + kind;
+    const int nval = cnt > 0 ? 5 * cnt + 1 : 0;   // the last value is <g, g>
+    for (int v = w; v < nval; v += kFinThreads / 32) {
+        const double* base;
+        long long stride;
+        if (v == 5 * cnt) {
+            base = S.lbpart + kLbGGOff;
+            stride = 1;
+        } else {
+            const int j = v / 5, kind = v % 5;
+            base = S.lbpart + (long long)(j / kLbGroup) * kRedBlocks * (5 * kLbGroup) + (j % kLbGroup) * 5 + kind;
+            stride = 5 * kLbGroup;
+        }
         double a = 0.0;
-        for (int b = l; b < kRedBlocks; b += 32) a += base[(long long)b * (5 * kLbGroup)];
+        for (int b = l; b < kRedBlocks; b += 32) a += base[(long long)b * stride];
         a = warp_sum(a);
         if (l == 0) val[v] = a;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    S.ints[SI_RFLAG] = 0;
     if (cnt == 0) {
+        // d = -g, a descent direction unless g = 0 (which the line search meets)
         S.sc[SC_GAMMA] = 1.0;
         return;
     }
@@ -466,6 +482,19 @@ __global__ void __launch_bounds__(kFinThreads) k_lb_solve(SolverDev S) {
         double a = t[i];
         for (int j = 0; j < i; ++j) a -= Rm[j * 33 + i] * t[j];
         t[i] = a / Rm[i * 33 + i];
+    }
+    // descent test: <g, d> = -(gamma <g,g> + sum_i a_i <s_i,g> - gamma sum_i u_i <y_i,g>)
+    double gd = gamma * val[5 * k];
+    for (int i = 0; i < k; ++i) gd += t[i] * p[i] - gamma * u[i] * q[i];
+    gd = -gd;
+    if (!(gd < 0.0)) {
+        // not a descent direction: clear the memory and take d = -g in this
+        // same iteration (the restart of L-BFGS)
+        S.ints[SI_CNT] = 0;
+        S.ints[SI_RESTARTS] += 1;
+        S.ints[SI_RFLAG] = 1;
+        S.sc[SC_GAMMA] = 1.0;
+        return;
     }
     for (int i = 0; i < k; ++i) {
         const int j = k - 1 - i;   // j-th newest
@@ -645,9 +674,11 @@ __global__ void __launch_bounds__(kFinThreads) k_line_search(SolverDev S, const 
     bool ok = false;
     if (c[1] < 0.0) ok = quartic_argmin(c, &a);
     if (!ok) {
+        // no minimiser on a > 0 along d: no step, memory cleared; counted as a
+        // restart unless the direction test already counted this iteration
         a = 0.0;
         S.ints[SI_CNT] = 0;
-        S.ints[SI_RESTARTS] += 1;
+        if (!S.ints[SI_RFLAG]) S.ints[SI_RESTARTS] += 1;
     }
     bool finite = isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(c[3]) && isfinite(c[4]);
     if (!finite) {
@@ -757,6 +788,7 @@ __global__ void k_admm_init(SolverDev S) {
         S.ints[SI_ITERS] = 0;
         S.ints[SI_RESTARTS] = 0;
         S.ints[SI_STATUS] = 0;
+        S.ints[SI_RFLAG] = 0;
     }
 }
 
@@ -769,6 +801,7 @@ __global__ void k_admm_resume(SolverDev S) {
         S.ints[SI_ITERS] = 0;
         S.ints[SI_RESTARTS] = 0;
         S.ints[SI_STATUS] = 0;
+        S.ints[SI_RFLAG] = 0;
     }
 }
 

@@ -9,12 +9,15 @@
 namespace tlr {
 
 enum ScalarSlot { SC_ALPHA = 0, SC_F, SC_F0, SC_C0, SC_C1, SC_C2, SC_C3, SC_C4, SC_GAMMA, SC_COUNT };
-enum IntSlot { SI_CNT = 0, SI_NEWEST, SI_ITERS, SI_RESTARTS, SI_STATUS, SI_COUNT };
+// SI_RFLAG: 1 when this iteration's direction failed the descent test and was
+// replaced by -g (the iteration already counts as a restart)
+enum IntSlot { SI_CNT = 0, SI_NEWEST, SI_ITERS, SI_RESTARTS, SI_STATUS, SI_RFLAG, SI_COUNT };
 
 // compact L-BFGS: pairs per inner-product pass, and the partial storage for
-// the largest memory (32 pairs)
+// the largest memory (32 pairs), followed by one slab of <g, g> partials
 constexpr int kLbGroup = 10;
-constexpr long long kLbPartDoubles = (long long)kRedBlocks * 5 * kLbGroup * ((32 + kLbGroup - 1) / kLbGroup);
+constexpr long long kLbGGOff = (long long)kRedBlocks * 5 * kLbGroup * ((32 + kLbGroup - 1) / kLbGroup);
+constexpr long long kLbPartDoubles = kLbGGOff + kRedBlocks;
 
 struct SolverDev {
     long long n2;        // floats per theta-space vector (2 * n_theta)

@@ -119,3 +119,20 @@ def test_async_graph_solves_on_two_streams_match_plain_solves(prec, monkeypatch)
             assert np.array_equal(th.cpu().numpy().astype(np.complex128), r)
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stationary_start_restarts_like_the_oracle(prec):
+    # theta = 0 with low-rank diagonals is a saddle (every product is bilinear
+    # in the factors, so g = 0 exactly): each of the 30 iterations restarts
+    # and takes no step, on both sides, and X stays 0
+    D, U, perm, lay, _ = problem(8, 8, 16, 3, "lowrank", ns=50, seed=6, snr_db=10)
+    th0 = np.zeros(lay.size, np.complex128)
+    tho, sto, alpha = _oracle_solve(D, U, perm, lay, th0)
+    g = Gpu(D, U, lay, nx=8, ny=8, alpha=alpha, precision=prec)
+    th, st = g.solve(th0)
+    g.close()
+    assert sto.restarts == 30 and st.restarts == sto.restarts
+    assert st.iters == 30 and st.status == 0
+    assert not np.any(th) and not np.any(tho)
+    np.testing.assert_allclose(np.array(st.f_hist[:st.n_hist]), sto.f_hist, rtol=1e-5)
