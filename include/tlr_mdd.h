@@ -355,13 +355,18 @@ void* tlr_mdd_stream(const tlr_mdd_t* h);
  * TLR_NOALLOC_SCRATCH_BYTES inside the library, held on every GPU that loads
  * the library until the process exits.  Sizes: nr * nr * 8 bytes must fit in
  * TLR_NOALLOC_SCRATCH_BYTES - 256 (nr <= 1448); larger nr returns
- * TLR_ERR_SHAPE before any work is enqueued.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  Every call
- * shares the one array and it keeps the last call's contents (each call
- * overwrites all it reads): calls that overlap on the GPU -- other streams,
- * other host threads -- race on it.  Synchronises the stream before
- * returning. */
+ * TLR_ERR_SHAPE before any work is enqueued.  V, Dt, G and the stream must
+ * belong to the current device (managed memory is accepted); a pointer on
+ * another device, or a host pointer, returns TLR_ERR_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use this entry point on a device
+ * after cudaDeviceReset (the kept address then belongs to a destroyed
+ * context).  Every call shares the one array and it keeps the last call's
+ * contents (each call overwrites all it reads): calls that overlap on the GPU
+ * -- other streams, other host threads -- race on it.  While diagnostics
+ * timing is on (tlr_mdd_timing_enable) the launch is timed in the "project"
+ * class like tlr_mdd_adjoint.  Synchronises the stream before returning. */
 #define TLR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int tlr_mdd_adjoint_noalloc(const void* V, const void* Dt, int64_t nr, int64_t ns, void* G, void* stream);
 
@@ -379,6 +384,16 @@ void tlr_mdd_timing_enable(int on);
 void tlr_mdd_timing_reset(void);
 int tlr_mdd_timing_read(double* ms, double* flops, int64_t* launches, int nclass);
 int64_t tlr_mdd_launch_count(void);
+
+/* Workspace pool (the paper has no counterpart).  Every handle's device
+ * workspace comes from one stream-ordered memory pool per device owned by the
+ * library, which keeps the memory of destroyed handles reserved for the next
+ * handle (creating and destroying handles per frequency or per request maps
+ * no fresh device memory).  tlr_mdd_trim_pool releases the current device's
+ * reserve down to keep_bytes (memory of live handles is never released) and
+ * writes the bytes still reserved to *reserved (HOST, may be NULL).  Call it
+ * once the device's memory is wanted elsewhere.  keep_bytes < 0: TLR_ERR_ARG. */
+int tlr_mdd_trim_pool(int64_t keep_bytes, int64_t* reserved);
 
 const char* tlr_mdd_last_error(const tlr_mdd_t* h);
 int tlr_mdd_destroy(tlr_mdd_t* h);

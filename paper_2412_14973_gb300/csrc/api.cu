@@ -36,6 +36,53 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// ---- workspace pool ----
+// Handles take their device workspace from one stream-ordered memory pool per
+// device owned by this library, created with no release threshold: memory a
+// destroyed handle gives back stays reserved for the next handle instead of
+// returning to the driver at the next synchronisation, so creating and
+// destroying a handle per frequency (or per served request) maps no fresh
+// device memory.  tlr_mdd_trim_pool() hands the reserve back.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+cudaError_t ws_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps pr;
+        memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.handleTypes = cudaMemHandleTypeNone;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        e = cudaMemPoolCreate(&p, &pr);
+        if (e != cudaSuccess) return e;
+        unsigned long long thr = ~0ULL;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// stream-ordered allocation of handle workspace from the library's pool
+cudaError_t ws_alloc(void** ptr, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = ws_pool(&p);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(ptr, bytes, p, st);
+}
+
 // environment switch set to "0"
 bool getenv_off(const char* name) {
     const char* e = getenv(name);
@@ -71,8 +118,10 @@ cudaEvent_t ev_get() {
 // re-recorded at every replay and read after each one.
 thread_local std::vector<TimedLaunch>* g_capture_sink = nullptr;
 
+}  // namespace
+
 // launch one grouped contraction, timed when diagnostics are on
-cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st) {
+cudaError_t tlr::run_gemm(const GemmLaunch& L, cudaStream_t st) {
     if (L.nprob == 0) return cudaSuccess;
     if (!g_timing) return gemm_any(L, st);
     std::lock_guard<std::mutex> lk(g_tmu);
@@ -89,6 +138,8 @@ cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st) {
         g_pending.push_back(t);
     return e;
 }
+
+namespace {
 
 // add the device times of a replayed graph's timed launches to the totals
 void account_replay(const std::vector<TimedLaunch>& v) {
@@ -939,7 +990,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
                 place(key_of(p.t[t], false, T.G->amode, T.G->bmode, p.N));
             }
     h->packed_size = total;
-    CK(h, cudaMallocAsync((void**)&h->packed, std::max<size_t>(total, 256), h->st));
+    CK(h, ws_alloc((void**)&h->packed, std::max<size_t>(total, 256), h->st));
     // padding rows and k-slots of every packed operand stay zero from here on
     CK(h, cudaMemsetAsync(h->packed, 0, std::max<size_t>(total, 256), h->st));
     auto job_of = [&](const PackKey& k, size_t off) {
@@ -1141,7 +1192,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
     bytes += (rowptr.size() * sizeof(char*) + 255) & ~size_t(255);
     const size_t rpo = bytes;
     bytes += (2 * (size_t)L.N * sizeof(char*) + 255) & ~size_t(255);
-    CK(h, cudaMallocAsync((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
+    CK(h, ws_alloc((void**)&h->tcp_tables, std::max<size_t>(bytes, 256), h->st));
     if (vpack) {
         char** d_rowptr = reinterpret_cast<char**>(h->tcp_tables + ro);
         CK(h, cudaMemcpyAsync(d_rowptr, rowptr.data(), rowptr.size() * sizeof(char*), cudaMemcpyHostToDevice, h->st));
@@ -1341,7 +1392,7 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         return code;
     };
     {
-        cudaError_t e = cudaMallocAsync((void**)&h->arena, h->arena_bytes, h->st);
+        cudaError_t e = ws_alloc((void**)&h->arena, h->arena_bytes, h->st);
         if (e != cudaSuccess) {
             h->arena = nullptr;
             h->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -2102,6 +2153,19 @@ void* tlr_mdd_stream(const tlr_mdd_t* h) { return h ? (void*)h->st : nullptr; }
 
 const char* tlr_mdd_last_error(const tlr_mdd_t* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
+int tlr_mdd_trim_pool(int64_t keep_bytes, int64_t* reserved) {
+    if (keep_bytes < 0) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "keep_bytes must be >= 0");
+    cudaMemPool_t p = nullptr;
+    CK((tlr_mdd_s*)nullptr, ws_pool(&p));
+    CK((tlr_mdd_s*)nullptr, cudaMemPoolTrimTo(p, (size_t)keep_bytes));
+    if (reserved) {
+        unsigned long long r = 0;
+        CK((tlr_mdd_s*)nullptr, cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &r));
+        *reserved = (int64_t)r;
+    }
+    return TLR_OK;
+}
+
 int tlr_mdd_destroy(tlr_mdd_t* h) {
     if (!h) return TLR_ERR_ARG;
     if (h->pending) cudaEventSynchronize(h->ev1);
@@ -2253,7 +2317,7 @@ static int enqueue_body(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
         if (h->ring) cudaFreeAsync(h->ring, h->st);
         h->ring = nullptr;
         h->ring_m = 0;
-        CK(h, cudaMallocAsync((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), h->st));
+        CK(h, ws_alloc((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), h->st));
         h->ring_m = o->memory;
     }
     h->pending_graph = false;

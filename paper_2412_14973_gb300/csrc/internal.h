@@ -224,6 +224,9 @@ inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
     if (e == cudaSuccess) e = pack_operands(L.d_jobs, L.njobs, L.max_items, st);
     return e == cudaSuccess ? gemm_tcp(L, st) : e;
 }
+// One grouped contraction through gemm_any, bracketed by CUDA events on its
+// stream while the diagnostics timing (tlr_mdd_timing_enable) is on (api.cu).
+cudaError_t run_gemm(const GemmLaunch& L, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // data kernels (k_data.cu)

@@ -45,6 +45,20 @@ cudaError_t scratch_address(void** out) {
     return cudaSuccess;
 }
 
+// A buffer of this call must live on the current device (or be managed
+// memory): the scratch array and the launch belong to that device.
+bool on_current_device(const void* p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 }  // namespace tlr
 
@@ -56,6 +70,7 @@ extern "C" int tlr_mdd_adjoint_noalloc(const void* V, const void* Dt, int64_t nr
     if (nr <= 0 || ns <= 0 || nr > (int64_t)1 << 30 || ns > (int64_t)1 << 30) return TLR_ERR_SHAPE;
     const size_t slab = (size_t)nr * (size_t)nr * sizeof(cf);
     if (slab > kScratchBytes - kProbBytes) return TLR_ERR_SHAPE;  // nr above the scratch limit
+    if (!on_current_device(V) || !on_current_device(Dt) || !on_current_device(G)) return TLR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return TLR_ERR_CUDA;
@@ -96,10 +111,12 @@ extern "C" int tlr_mdd_adjoint_noalloc(const void* V, const void* Dt, int64_t nr
     L.kchunk = (int)(((ns + nsplit - 1) / nsplit + 15) / 16 * 16);
     L.part_stride = nr * nr;
     L.epi = EPI_PARTIAL;
+    L.cls = 2;                                           // diagnostics class: project / adjoint
+    L.flops = 8.0 * (double)nr * (double)nr * (double)ns;
     // Every partial slab is written in full by the GEMM before the reduction
     // reads it, so no part of the array has to start at zero.
     if (cudaMemcpyAsync(base, &p, sizeof(GProb), cudaMemcpyHostToDevice, st) != cudaSuccess) return TLR_ERR_CUDA;
-    if (gemm_simt(L, st) != cudaSuccess) return TLR_ERR_CUDA;
+    if (run_gemm(L, st) != cudaSuccess) return TLR_ERR_CUDA;
     if (reduce_grad(part, nsplit, nr * nr, nr * nr, 0, 1, (cf*)G, st) != cudaSuccess) return TLR_ERR_CUDA;
     // p lives on this stack frame; the copy above was staged before return,
     // but wait for the stream so the caller may reuse V, Dt and G at once.

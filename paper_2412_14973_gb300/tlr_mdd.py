@@ -24,6 +24,7 @@ __all__ = [
     "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
     "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
     "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
+    "tlr_mdd_trim_pool",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -48,7 +49,7 @@ EXPORTED = [
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
     "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
     "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state", "tlr_mdd_time_to_freq",
-    "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
+    "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest", "tlr_mdd_trim_pool",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -165,6 +166,8 @@ def lib():
         L.tlr_mdd_stack_alpha.argtypes = [vp, C.c_int64, C.POINTER(C.c_double), vp]
         L.tlr_mdd_wait_selftest.argtypes = [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
         L.tlr_mdd_set_state.argtypes = [vp, vp, vp]
+        L.tlr_mdd_trim_pool.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
+        L.tlr_mdd_trim_pool.restype = i32
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
@@ -409,9 +412,47 @@ def tlr_mdd_wait_selftest(limit_ns, stream=None):
     return st.value, ms.value
 
 
+def _noalloc_args(V, Dt, nr, ns, G):
+    """Checks the buffers of tlr_mdd_adjoint_noalloc before the call: the entry
+    point has no handle that knows their sizes, so a short or misplaced buffer
+    would be read or written out of bounds on the device.  torch tensors must
+    be contiguous complex64 CUDA tensors on the current device holding at least
+    nr * ns (V, Dt) and nr * nr (G) values.  Raw integer pointers are passed
+    through unchecked (the C entry point still checks each pointer's device)."""
+    if V is None or Dt is None or G is None:
+        raise TLRError(TLR_ERR_ARG, "V, Dt and G must be given")
+    if int(nr) <= 0 or int(ns) <= 0:
+        raise TLRError(TLR_ERR_SHAPE, "nr and ns must be positive")
+    need = {"V": int(nr) * int(ns), "Dt": int(nr) * int(ns), "G": int(nr) * int(nr)}
+    tensors = [(n, t) for n, t in (("V", V), ("Dt", Dt), ("G", G)) if not isinstance(t, int)]
+    for name, t in tensors:
+        if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+            raise TLRError(TLR_ERR_ARG, f"{name} must be a torch tensor or a device pointer")
+        import torch
+        if t.dtype != torch.complex64:
+            raise TLRError(TLR_ERR_ARG, f"{name} must be complex64, not {t.dtype}")
+        if not t.is_contiguous():
+            raise TLRError(TLR_ERR_ARG, f"{name} must be contiguous")
+        if t.numel() < need[name]:
+            raise TLRError(TLR_ERR_SHAPE, f"{name} holds {t.numel()} values, needs {need[name]}")
+    for name, t in tensors:
+        import torch
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise TLRError(TLR_ERR_ARG, f"{name} must be on the current CUDA device")
+
+
 def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
     """G = V Dt^H without any device allocation (fixed in-library scratch)."""
+    _noalloc_args(V, Dt, nr, ns, G)
     _check(lib().tlr_mdd_adjoint_noalloc(_ptr(V), _ptr(Dt), nr, ns, _ptr(G), _stream(stream)))
+
+
+def tlr_mdd_trim_pool(keep_bytes=0) -> int:
+    """Release the library's reserved workspace memory on the current device
+    down to ``keep_bytes``; returns the bytes still reserved."""
+    r = C.c_int64()
+    _check(lib().tlr_mdd_trim_pool(int(keep_bytes), C.byref(r)))
+    return r.value
 
 
 def tlr_mdd_solve_async(h, theta, opts: SolveOpts | None = None):

@@ -183,3 +183,30 @@ def test_random_partitions_match_the_oracle_layout():
         assert (od, ol, orr, dn) == (lay.off_diag, lay.off_l, lay.off_r, lay.dense), (tiles, kd, kp, dense)
         assert T.tlr_mdd_theta_size(d) == lay.size
         assert T.tlr_mdd_workspace_bytes(d) > 0
+
+
+def test_noalloc_wrapper_rejects_bad_buffers_before_the_call():
+    # the allocation-free adjoint has no handle that knows the buffer sizes,
+    # so the binding checks dtype, contiguity, size and device before it calls
+    # into the library (no device work, no GPU needed to reach these checks)
+    torch = pytest.importorskip("torch")
+    nr, ns = 8, 5
+    ok_v = torch.zeros(nr * ns, dtype=torch.complex64)
+    ok_g = torch.zeros(nr * nr, dtype=torch.complex64)
+    short = torch.zeros(nr * ns - 1, dtype=torch.complex64)
+    cases = [
+        ((short, ok_v, ok_g), T.TLR_ERR_SHAPE),                        # V too short
+        ((ok_v, short, ok_g), T.TLR_ERR_SHAPE),                        # Dt too short
+        ((ok_v, ok_v, torch.zeros(nr * nr - 1, dtype=torch.complex64)), T.TLR_ERR_SHAPE),
+        ((ok_v.to(torch.complex128), ok_v, ok_g), T.TLR_ERR_ARG),      # wrong dtype
+        ((torch.zeros((ns, nr), dtype=torch.complex64).t(), ok_v, ok_g), T.TLR_ERR_ARG),  # not contiguous
+        ((ok_v, ok_v, ok_g), T.TLR_ERR_ARG),                           # host tensors, not on the device
+        ((None, ok_v, ok_g), T.TLR_ERR_ARG),
+    ]
+    for (V, Dt, G), code in cases:
+        with pytest.raises(T.TLRError) as ei:
+            T.tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G)
+        assert ei.value.code == code
+    with pytest.raises(T.TLRError) as ei:
+        T.tlr_mdd_adjoint_noalloc(ok_v, ok_v, 0, ns, ok_g)
+    assert ei.value.code == T.TLR_ERR_SHAPE
