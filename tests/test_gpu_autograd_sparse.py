@@ -23,9 +23,8 @@ B, K = 128, 12
 def test_autograd_gradient_vs_finite_differences_and_oracle(prec, tol):
     D, U, perm, lay, _ = problem(NX, NY, B, K, "lowrank", seed=31, snr_db=5, planted=False)
     th = (0.3 * synth.planted_theta(lay.nr, B, K, lay.dense, 32)).astype(np.complex64).astype(np.complex128)
-    g = Gpu(D, U, lay, nx=NX, ny=NY, precision=prec)
-    _, alpha, _, _ = g.data()
-    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    g = Gpu(D, U, lay, nx=NX, ny=NY, alpha=alpha, precision=prec)
     t = dev(th).requires_grad_(True)
     f = misfit(t, g.h)
     f.backward()

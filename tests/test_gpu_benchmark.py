@@ -1,7 +1,7 @@
 """Benchmark solver of eq. (4) on the GPU against the oracle's CG (FP64).
 
-Both sides solve from the handle's own normalised panels (Dfrak = D-hat^T,
-read back with tlr_mdd_get_data), so the comparison isolates the solver.
+The oracle normalises D, U itself (its own Hilbert order and alpha = max |D|)
+and passes that alpha to the library, so no oracle input comes from the GPU.
 """
 import numpy as np
 import pytest
@@ -9,7 +9,7 @@ import torch
 
 import paper_2412_14973_gb300 as T
 import tlr_synth as synth
-from oracle import benchmark, layout
+from oracle import benchmark, layout, operator
 
 from _cases import problem
 from _gpu import Gpu, dev, host, rel
@@ -19,21 +19,23 @@ pytestmark = pytest.mark.gpu
 PRECS = [(T.TLR_PREC_FP32, 1e-4), (T.TLR_PREC_BF16X3, 1e-3)]
 
 
-def _oracle(g, lam, maxit, tol):
-    _, _, Dt, Ut = g.data()
-    Dh = Dt.T.astype(np.complex128)
-    Uh = Ut.T.astype(np.complex128)
+def _oracle(D, U, perm, lam, maxit, tol):
+    Dh, Uh, _ = operator.normalise(D, U, perm)
     Z = benchmark.solve_eq4(Dh, Uh, lam, tol=tol, maxit=maxit)
     return 0.5 * (Z + Z.T)
+
+
+def _alpha(D):
+    return float(np.max(np.abs(D.astype(np.complex128))))
 
 
 @pytest.mark.parametrize("prec,tol", PRECS)
 def test_converged_solution_matches_oracle(prec, tol):
     # nr = 96 (12 x 8 grid), ns = 120: one ragged 128-row tile on the tensor cores
     D, U, perm, lay, _ = problem(12, 8, 16, 3, "lowrank", ns=120, seed=21, snr_db=10)
-    g = Gpu(D, U, lay, nx=12, ny=8, precision=prec)
+    g = Gpu(D, U, lay, nx=12, ny=8, alpha=_alpha(D), precision=prec)
     X, st = g.benchmark(0.3, 400, 1e-6)
-    Xo = _oracle(g, 0.3, 10000, 1e-13)
+    Xo = _oracle(D, U, perm, 0.3, 10000, 1e-13)
     err = rel(X, Xo)
     print(f"precision {prec}: iterations {st.iters}, rel. residual {st.rel_res:.2e}, |X - X_oracle| {err:.2e}")
     assert st.status == 0 and st.rel_res <= 1e-6 * 1.01
@@ -45,10 +47,10 @@ def test_fixed_iterations_follow_the_oracle_trajectory():
     # three CG iterations from Z = 0 on both sides: the iterates, not only the
     # fixed point, agree
     D, U, perm, lay, _ = problem(8, 8, 16, 2, "lowrank", ns=64, seed=22, snr_db=20)
-    g = Gpu(D, U, lay, nx=8, ny=8)
+    g = Gpu(D, U, lay, nx=8, ny=8, alpha=_alpha(D))
     for it in (1, 3):
         X, st = g.benchmark(0.05, it, 0.0)
-        Xo = _oracle(g, 0.05, it, 0.0)
+        Xo = _oracle(D, U, perm, 0.05, it, 0.0)
         assert st.iters == it
         assert rel(X, Xo) <= 1e-5
 
@@ -66,8 +68,10 @@ def test_unitary_data_converge_in_one_iteration_tensor_cores():
     g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=1.0, precision=T.TLR_PREC_BF16X3)
     lam = 0.25
     X, st = g.benchmark(lam, 5, 1e-5)
-    _, _, Dt, Ut = g.data()
-    B = Dt.astype(np.complex128).conj() @ Ut.T.astype(np.complex128)
+    from oracle import hilbert
+    p = hilbert.perm(nx, ny)
+    Dh, Uh = D[:, p].astype(np.complex128), U[:, p].astype(np.complex128)    # alpha = 1
+    B = Dh.conj().T @ Uh
     Xc = 0.5 * (B + B.T) / (1.0 + 2.0 * lam)
     print(f"iterations {st.iters}, rel. residual {st.rel_res:.2e}, |X - X_closed| {rel(X, Xc):.2e}")
     assert st.iters <= 2

@@ -22,9 +22,8 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(limit_ms):
     assert limit_ms <= waited < limit_ms + 500
     # a tensor-core product right after it runs and is correct
     D, U, perm, lay, _ = problem(8, 8, 16, 3, "lowrank", ns=70, seed=7, snr_db=10, planted=False)
-    g = Gpu(D, U, lay, nx=8, ny=8, precision=T.TLR_PREC_BF16X3)
-    _, alpha, _, _ = g.data()
-    Dh, _, _ = operator.normalise(D, U, perm, alpha=alpha)
+    Dh, _, alpha = operator.normalise(D, U, perm)
+    g = Gpu(D, U, lay, nx=8, ny=8, alpha=alpha, precision=T.TLR_PREC_BF16X3)
     th = (0.2 * synth.cn(synth.rng(8), lay.size)).astype(np.complex64).astype(np.complex128)
     assert rel(g.apply(th), operator.apply_y(th, lay, Dh)) <= 1e-3
     g.close()

@@ -1,23 +1,34 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
-The batched workload, nr = ns = 4096 (64 x 64 grid), tile 256, ranks 4 and 48, low-rank
-diagonals: sampled columns of Y = X_h Dfrak and the full gradient against the
-FP64 oracle's TLR-structured forms, on both paths.
-The large workload, nr = ns = 9216 (96 x 96 grid), tile 384, rank 64: sampled columns
-of Y on the tensor-core path, and the adjoint identity <X Dfrak, V> =
-<X, V Dfrak^H> with the GPU's own products at full size.
-Inputs: complex Gaussian D (the operator parity does not depend on D's
-spectrum) to keep the host-side generation fast; seeded."""
+The batched workload, nr = ns = 4096 (64 x 64 grid), tile 256, ranks 4 and 48,
+low-rank diagonals: sampled columns of Y = X_h Dfrak and the full gradient
+against the FP64 oracle's TLR-structured forms, on both paths; and a
+12-iteration solve (all three lambda stages, 2 ADMM x 2 L-BFGS iterations
+each) at rank 12 against the oracle's ADMM.
+The precision-form workload, nr = ns = 9216 (96 x 96 grid), tile 384: sampled
+columns of Y at rank 64 and the full gradient at rank 8 on the tensor-core
+path, and the adjoint identity <X Dfrak, V> = <X, V Dfrak^H> with the GPU's own
+products at full size.
+The oracle builds its panels itself from D, U, its own Hilbert order and
+alpha = max |D|, and passes that alpha to the library; nothing it compares
+against comes from the GPU.  Inputs: complex Gaussian D (the operator parity
+does not depend on D's spectrum) to keep the host-side generation fast; seeded.
+Tolerances: relative Frobenius error 1e-5 (FP32) / 1e-4 (tensor cores) per
+application at nr = 4096 and for Y at nr = 9216, 1e-3 (the tensor-core bound)
+for the nr = 9216 gradient, every element within 10x that of the reference's
+rms; solves: final X and the f history within 1e-3."""
+import functools
+
 import numpy as np
 import pytest
 import torch
 
 import tlr_synth as synth
-from oracle import hilbert, layout, operator, tlr
+from oracle import hilbert, layout, operator, solver, tlr
 
 pytestmark = pytest.mark.gpu
 T = pytest.importorskip("paper_2412_14973_gb300")
-from tests._gpu import Gpu, rel  # noqa: E402
+from tests._gpu import Gpu, elem, rel  # noqa: E402
 
 
 def _big(nx, ny, b, k, seed):
@@ -29,33 +40,82 @@ def _big(nx, ny, b, k, seed):
     return D, U, lay, th
 
 
+def _panels(D, U, nx, ny):
+    """The oracle's receiver-major panels (FP64) and its alpha."""
+    Dh, Uh, alpha = operator.normalise(D, U, hilbert.perm(nx, ny))
+    return np.ascontiguousarray(Dh.T), np.ascontiguousarray(Uh.T), alpha
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-4)])
 @pytest.mark.parametrize("k", [4, 48])
 def test_nr4096_tile256_columns_and_full_gradient(prec, tol, k):
     D, U, lay, th = _big(64, 64, 256, k, 100 + k)
-    g = Gpu(D, U, lay, nx=64, ny=64, precision=prec)
-    perm, alpha, Dt, Ut = g.data()
+    Dto, Uto, alpha = _panels(D, U, 64, 64)
+    g = Gpu(D, U, lay, nx=64, ny=64, alpha=alpha, precision=prec)
     Y = g.apply(th)
     cols = synth.rng(7).choice(lay.nr, 24, replace=False)
-    Dto, Uto = Dt.astype(np.complex128), Ut.astype(np.complex128)
     Yo = tlr.apply(th, lay, Dto[:, cols])
     assert rel(Y[:, cols], Yo) <= tol
+    assert elem(Y[:, cols], Yo) <= 10 * tol
     f, gr = g.grad(th)
     fo, go, _ = tlr.fgrad(th, lay, Dto, Uto)
     assert abs(f - fo) <= tol * fo
     assert rel(gr, go) <= tol
+    assert elem(gr, go) <= 10 * tol
     g.close()
+
+
+_SOLVE_KW = dict(stages=3, admm_iters=2, lbfgs_iters=2)
+
+
+@functools.lru_cache(maxsize=1)
+def _rank12_case():
+    """nr = ns = 4096, tile 256, rank 12, planted X at 10 dB, and the oracle's
+    12-iteration solve from a small planted start (shared by both precisions)."""
+    nx = ny = 64
+    nr, b, k = nx * ny, 256, 12
+    lay = layout.make_layout(nr, b, k, "rule")
+    perm = hilbert.perm(nx, ny)
+    D = (synth.cn(synth.rng(400), (nr, nr)) / np.sqrt(nr)).astype(np.complex64)
+    th_true = synth.planted_theta(nr, b, k, lay.dense, 401)
+    Y = D.astype(np.complex128) @ operator.unpermute(operator.assemble_xh(th_true, lay), perm)
+    nz = synth.noise(Y.shape, 402)
+    U = (Y + np.linalg.norm(Y) / np.linalg.norm(nz) * 10 ** (-10 / 20) * nz).astype(np.complex64)
+    del Y, nz
+    th0 = (0.1 * synth.planted_theta(nr, b, k, lay.dense, 403)).astype(np.complex64).astype(np.complex128)
+    Dto, Uto, alpha = _panels(D, U, nx, ny)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dto, Uto), th0, solver.SolveOpts(**_SOLVE_KW))
+    return D, U, lay, th0, alpha, tho, sto
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nr4096_tile256_rank12_solve_all_lambda_stages(prec):
+    nx = ny = 64
+    D, U, lay, th0, alpha, tho, sto = _rank12_case()
+    kw = _SOLVE_KW
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha, precision=prec)
+    th, st = g.solve(th0, **kw)
+    g.close()
+    assert st.iters == 12 and st.status == 0 and st.restarts == sto.restarts
+    e = rel(operator.assemble_xh(th, lay), operator.assemble_xh(tho, lay))
+    fh = np.array(st.f_hist[:st.n_hist])
+    print(f"nr 4096 rank 12 solve, precision {prec}: rel X {e:.2e}, "
+          f"max f-history error {np.max(np.abs(fh - sto.f_hist) / np.abs(sto.f_hist)):.2e}")
+    assert e <= 1e-3
+    np.testing.assert_allclose(fh, sto.f_hist, rtol=1e-3)
 
 
 def test_nr9216_tile384_columns_tensor_core():
     D, U, lay, th = _big(96, 96, 384, 64, 300)
-    g = Gpu(D, U, lay, nx=96, ny=96, precision=T.TLR_PREC_BF16X3)
-    perm, alpha, Dt, Ut = g.data()
+    Dto, _, alpha = _panels(D, U, 96, 96)
+    g = Gpu(D, U, lay, nx=96, ny=96, alpha=alpha, precision=T.TLR_PREC_BF16X3)
+    perm, _ = T.tlr_mdd_get_data(g.h, lay.nr)
     assert np.array_equal(perm, hilbert.perm(96, 96))
     Y = g.apply(th)
     cols = synth.rng(9).choice(lay.nr, 8, replace=False)
-    Yo = tlr.apply(th, lay, Dt.astype(np.complex128)[:, cols])
+    Yo = tlr.apply(th, lay, Dto[:, cols])
     assert rel(Y[:, cols], Yo) <= 1e-4
+    assert elem(Y[:, cols], Yo) <= 1e-3
     # adjoint identity with the GPU's own products: <Y, V> = <X_h, V Dfrak^H>
     V = synth.cn(synth.rng(10), (lay.nr, lay.nr)).astype(np.complex64)
     G = g.adjoint(V)
@@ -64,3 +124,18 @@ def test_nr9216_tile384_columns_tensor_core():
     rhs = torch.vdot(Xh.flatten().to(torch.complex128), torch.from_numpy(G).cuda().flatten()).item()
     assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
     g.close()
+
+
+def test_nr9216_tile384_full_gradient_tensor_core():
+    D, U, lay, th = _big(96, 96, 384, 8, 310)
+    Dto, Uto, alpha = _panels(D, U, 96, 96)
+    g = Gpu(D, U, lay, nx=96, ny=96, alpha=alpha, precision=T.TLR_PREC_BF16X3)
+    f, gr = g.grad(th)
+    g.close()
+    fo, go, _ = tlr.fgrad(th, lay, Dto, Uto)
+    print(f"nr 9216 rank 8 gradient: rel {rel(gr, go):.2e} elem {elem(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
+    # the tensor-core bound per application (1e-3; measured 1.3e-4: the
+    # projection sums 9216 products per entry), every element within 10x of it
+    assert abs(f - fo) <= 1e-4 * fo
+    assert rel(gr, go) <= 1e-3
+    assert elem(gr, go) <= 1e-2

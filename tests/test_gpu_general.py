@@ -14,7 +14,7 @@ import tlr_synth as synth
 from oracle import general, operator, solver
 
 from _cases import problem
-from _gpu import Gpu, dev, host, rel
+from _gpu import Gpu, dev, elem, host, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -34,11 +34,10 @@ def _setup(name, prec, seed=0):
     rl = ranks if isinstance(ranks, list) else [ranks] * (n + n * (n - 1))
     glay = general.make_general_layout(nr, b, rl, dense)
     D, U, perm, _, _ = problem(nx, ny, b, 1, "lowrank", ns=ns, seed=90 + seed, snr_db=10)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
     d = T.desc(nr, ns, b, ranks=rl, nx=nx, ny=ny, diag_mode=T.TLR_DIAG_PER_TILE, diag_dense=dense,
-               precision=prec, reciprocity=T.TLR_RECIP_NONE)
+               precision=prec, reciprocity=T.TLR_RECIP_NONE, alpha=alpha)
     g = Gpu(D, U, glay, desc=d)
-    _, alpha, _, _ = g.data()
-    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
     th = (0.2 * synth.cn(synth.rng(95 + seed), glay.size)).astype(np.complex64).astype(np.complex128)
     return g, glay, th, Dh, Uh, perm
 
@@ -57,6 +56,8 @@ def test_general_apply_grad_assemble(name, prec, tol):
     print(f"general {name} prec {prec}: apply {rel(Y, Yo):.2e} grad {rel(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
     assert rel(Y, Yo) <= tol
     assert rel(gr, go) <= tol and abs(f - fo) <= tol * fo
+    # elementwise: within max(1e-4, tol) of the reference's rms
+    assert elem(Y, Yo) <= max(1e-4, tol) and elem(gr, go) <= max(1e-4, tol)
     assert rel(X, Xo) <= 1e-5
     assert not np.allclose(X, X.T)
     g.close()

@@ -32,9 +32,10 @@ def _setup(name):
     nx, ny, b, ranks, mode, ns = CASES[name]
     D, U, perm, lay, _ = problem(nx, ny, b, ranks, mode, ns=ns, snr_db=10, planted=False)
     th = synth.cn(synth.rng(sorted(CASES).index(name)), lay.size) * 0.2
-    g = Gpu(D, U, lay, nx=nx, ny=ny)
-    _, alpha, _, _ = g.data()
-    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    # the oracle normalises by its own alpha (max |D|) and hands that value to
+    # the library explicitly: nothing on the oracle side comes from the GPU
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha)
     return g, lay, th, Dh, Uh, perm
 
 

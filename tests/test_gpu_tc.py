@@ -2,7 +2,9 @@
 
 Tolerance for the tensor-core path: relative Frobenius error <= 1e-3 per
 operator application (BF16x3 keeps about 16 significant bits of each operand;
-the measured error is printed with -s)."""
+the measured error is printed with -s), and every element within 1e-3 of the
+reference's rms value, so that an error confined to one tile block (which the
+Frobenius norm dilutes by the number of blocks) still fails."""
 import numpy as np
 import pytest
 
@@ -23,9 +25,8 @@ def _setup(name):
     D, U, perm, lay, _ = problem(nx, ny, b, ranks, mode, ns=ns, snr_db=10, planted=False)
     th = synth.cn(synth.rng(sorted(CASES).index(name)), lay.size) * 0.2
     th = th.astype(np.complex64).astype(np.complex128)
-    g = Gpu(D, U, lay, nx=nx, ny=ny, precision=T.TLR_PREC_BF16X3)
-    _, alpha, _, _ = g.data()
-    Dh, Uh, _ = operator.normalise(D, U, perm, alpha=alpha)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha, precision=T.TLR_PREC_BF16X3)
     return g, lay, th, Dh, Uh
 
 
@@ -37,6 +38,7 @@ def test_tc_apply(name):
     e = rel(Y, Yo)
     print(f"tc apply {name}: rel {e:.2e} elem {elem(Y, Yo):.2e}")
     assert e <= TC_TOL
+    assert elem(Y, Yo) <= TC_TOL
     g.close()
 
 
@@ -47,9 +49,10 @@ def test_tc_grad(name):
     fo = operator.misfit(th, lay, Dh, Uh)
     go = operator.gradient(th, lay, Dh, Uh)
     e = rel(gr, go)
-    print(f"tc grad {name}: rel {e:.2e} f {abs(f - fo) / fo:.2e}")
+    print(f"tc grad {name}: rel {e:.2e} elem {elem(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
     assert abs(f - fo) <= TC_TOL * fo
     assert e <= TC_TOL
+    assert elem(gr, go) <= TC_TOL
     g.close()
 
 
@@ -60,8 +63,9 @@ def test_tc_adjoint(name):
     G = g.adjoint(V)
     Go = operator.adjoint_g(V, Dh)
     e = rel(G, Go)
-    print(f"tc adjoint {name}: rel {e:.2e}")
+    print(f"tc adjoint {name}: rel {e:.2e} elem {elem(G, Go):.2e}")
     assert e <= TC_TOL
+    assert elem(G, Go) <= TC_TOL
     g.close()
 
 

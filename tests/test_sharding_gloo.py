@@ -1,13 +1,14 @@
-"""Multi-process path of the benchmark on CPU (gloo, world size 2): each rank
-takes its own frequencies, the shards cover everything once, and the step time
-is the maximum over the ranks."""
+"""Multi-process path of the benchmark on CPU (gloo, world size 2): the rank
+logic bench.py runs (frequency plan, steps, max-over-ranks timing, gather of
+the per-frequency results on rank 0) and its own start of N ranks."""
 import os
 import socket
+import sys
 
 import pytest
 import torch.multiprocessing as mp
 
-from paper_2412_14973_gb300.sharding import max_over_ranks, shard
+from paper_2412_14973_gb300.sharding import batches, frequency_plan, gather_results, max_over_ranks, shard
 
 
 def test_shards_partition_and_balance():
@@ -18,6 +19,33 @@ def test_shards_partition_and_balance():
         assert max(map(len, parts)) - min(map(len, parts)) <= 1
     with pytest.raises(ValueError):
         shard(4, 2, 2)
+
+
+@pytest.mark.parametrize("world", [1, 2, 4, 8])
+def test_weak_scaling_plan_gives_every_rank_the_same_rank_mix(world):
+    import bench
+    wl = bench.PRECISION_FORM
+    ranks = wl.ranks(wl.nfreq * world)
+    plans = [frequency_plan(wl.nfreq, r, world) for r in range(world)]
+    assert sorted(f for p in plans for f in p) == list(range(wl.nfreq * world))
+    assert all(len(p) == wl.nfreq for p in plans)
+    means = [sum(ranks[f] for f in p) / len(p) for p in plans]
+    assert max(means) - min(means) <= 1.0       # same work per GPU (weak scaling)
+    for p in plans:
+        steps = batches(p, wl.batch)
+        assert sorted(f for s in steps for f in s) == sorted(p)
+        assert all(len(s) == wl.batch for s in steps)
+        # every step spans the rank range: its lowest and highest ranks are
+        # within one step's stride of the plan's extremes
+        lo, hi = min(ranks[f] for f in p), max(ranks[f] for f in p)
+        for s in steps:
+            ks = [ranks[f] for f in s]
+            assert min(ks) - lo <= (hi - lo) / wl.batch + 1 and hi - max(ks) <= (hi - lo) / wl.batch + 1
+
+
+def test_batches_reject_a_ragged_split():
+    with pytest.raises(ValueError):
+        batches(list(range(10)), 4)
 
 
 def _free_port():
@@ -33,10 +61,14 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    mine = shard(64, rank, world)
+    mine = frequency_plan(16, rank, world)
+    steps = batches(mine, 4)
+    records = [{"freq": f, "rank": 8 + f, "iters": 30, "status": 0, "f_final": 1.0 / (1 + f), "f0": 1.0}
+               for s in steps for f in s]
     fake_ms = 100.0 + 10.0 * rank + len(mine)
     dist.barrier()
-    out[rank] = (mine, max_over_ranks(fake_ms, dist))
+    gathered = gather_results(records, dist)
+    out[rank] = (mine, max_over_ranks(fake_ms, dist), gathered)
     dist.destroy_process_group()
 
 
@@ -45,5 +77,42 @@ def test_gloo_world_size_two():
     mgr = mp.Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
-    assert sorted(out[0][0] + out[1][0]) == list(range(64))
-    assert out[0][1] == out[1][1] == 100.0 + 10.0 + 32
+    assert sorted(out[0][0] + out[1][0]) == list(range(32))
+    assert out[0][1] == out[1][1] == 100.0 + 10.0 + 16
+    got = out[0][2]
+    assert [r["freq"] for r in got] == list(range(32))      # every frequency once, on rank 0's host
+    assert out[1][2] is None
+
+
+def test_gather_without_a_process_group_returns_the_records_sorted():
+    recs = [{"freq": 3}, {"freq": 1}]
+    assert [r["freq"] for r in gather_results(recs)] == [1, 3]
+
+
+def test_bench_starts_its_own_ranks(monkeypatch):
+    # `bench.py --gpus N` outside torchrun starts N copies of itself with the
+    # rank environment and a 127.0.0.1 rendezvous
+    import bench
+    started = []
+
+    class FakeProc:
+        def __init__(self, cmd, env):
+            started.append((cmd, env))
+
+        def wait(self):
+            return 0
+
+    monkeypatch.setattr(bench.subprocess, "Popen", FakeProc)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--gpus", "3", "--steps", "2"])
+
+    class Args:
+        gpus = 3
+
+    assert bench.spawn_ranks(Args) == 0
+    assert len(started) == 3
+    ports = {e["MASTER_PORT"] for _, e in started}
+    assert len(ports) == 1
+    for r, (cmd, env) in enumerate(started):
+        assert env["RANK"] == str(r) and env["LOCAL_RANK"] == str(r) and env["WORLD_SIZE"] == "3"
+        assert env["MASTER_ADDR"] == "127.0.0.1"
+        assert cmd[1].endswith("bench.py") and cmd[2:] == ["--gpus", "3", "--steps", "2"]
