@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Frequency-solve throughput of reciprocity-aware TLR MDD on GB300.
 
-Workload (the plain-method batched-frequency configuration): nr = ns = 4096
-receivers / sources on a 64 x 64 grid (Hilbert-reordered), 64 frequencies,
-tile 256, off-diagonal rank rising linearly 4 -> 48 with frequency, low-rank
-diagonal tiles (rank < tile/4), D(w) = Q diag(sigma e^{i phi_w}) W^H with sigma
-decaying 1 -> 1e-3, U = D X + complex Gaussian noise at 10 dB SNR, X a planted
-symmetric TLR Green's function.  One step = one frequency solve (30 L-BFGS
-iterations: 3 lambda stages x 2 ADMM iterations x 5) for every frequency,
-inputs resident in HBM.
+Workload (the precision-form configuration, the largest that fits one GPU):
+nr = ns = 9216 receivers / sources on a 96 x 96 grid (Hilbert order on the
+128 x 128 square), 128 frequencies, tile 384 (24 x 24 tiles), off-diagonal rank
+rising linearly 8 -> 64 with frequency, low-rank diagonal tiles (rank < tile/4),
+complex contractions as BF16x3 on the tcgen05 tensor cores with FP32
+accumulation, FP64 reductions.  D(w) = Q diag(sigma e^{i phi_w}) W^H (sigma
+decaying 1 -> 1e-3, Q and W exactly unitary random-phase DFT products),
+U = D X + complex Gaussian noise at 10 dB SNR, X a planted symmetric TLR
+Green's function.  One frequency solve = 30 L-BFGS iterations (3 lambda stages
+x 2 ADMM iterations x 5).  One step = the solves of one batch of 8 of the 128
+frequencies (every 16th, so each batch spans the rank range; 16 batches cover
+all 128), each from its raw D, U (data step included: Hilbert reorder,
+normalisation, packing); inputs resident in HBM.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (the only place besides the cpu_baseline leg that runs it).
+``--gpus N`` without a torchrun environment starts the N ranks itself.
 """
 from __future__ import annotations
 
@@ -19,11 +25,13 @@ import argparse
 import json
 import math
 import os
+import socket
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -31,35 +39,54 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-NR = 4096
-GRID = (64, 64)
-NFREQ = 64
-TILE = 256
-RANK_LO, RANK_HI = 4, 48
-SNR_DB = 10.0
 ITERS_PER_SOLVE = 30
-FP32_LANES_PER_SM, SMS, SM_MAX_MHZ = 128, 152, 2070.0
 
 
-def rank_of(f, nfreq):
-    if nfreq == 1:
-        return RANK_LO
-    return RANK_LO + int(math.floor((RANK_HI - RANK_LO) * f / (nfreq - 1) + 0.5))
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nr: int
+    grid: tuple
+    tile: int
+    nfreq: int        # frequencies per GPU
+    rank_lo: int
+    rank_hi: int
+    snr_db: float
+    batch: int        # frequencies per step
+
+    def ranks(self, total: int) -> list:
+        """k_f = lo + floor((hi - lo) f / (F - 1) + 1/2) over the job's F frequencies."""
+        if total == 1:
+            return [self.rank_lo]
+        return [self.rank_lo + int(math.floor((self.rank_hi - self.rank_lo) * f / (total - 1) + 0.5))
+                for f in range(total)]
+
+
+PRECISION_FORM = Workload(
+    "precision form: nr=ns=9216 (96x96 grid, Hilbert order), 128 frequencies, tile 384, rank 8->64, "
+    "low-rank diagonal, 10 dB SNR, BF16x3 tensor cores", 9216, (96, 96), 384, 128, 8, 64, 10.0, 8)
+BATCHED = Workload(
+    "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), 64 frequencies, tile 256, "
+    "rank 4->48, low-rank diagonal, 10 dB SNR", 4096, (64, 64), 256, 64, 4, 48, 10.0, 64)
+
+
+def n_lr(nr, tile, k):
+    n = nr // tile
+    return n * n * tile * k
 
 
 def flops_per_iter(nr, ns, tile, k):
     """Algorithmic flops of one L-BFGS iteration (8 real flops per complex MAC):
     compress of the direction and of the residual (8 + 8), the two line-search
-    expands (16 + 8) and the gradient projection (16), all x ns x n_LR."""
-    n = nr // tile
-    n_lr = n * n * tile * k
-    return 56.0 * ns * n_lr
+    expands (16 + 8) and the gradient projection (16), all x ns x n_LR.  The
+    factor products T and the residual are carried between iterations and
+    updated in place, so an iteration has no fresh forward product (72 -> 56)."""
+    return 56.0 * ns * n_lr(nr, tile, k)
 
 
 def flops_per_solve(nr, ns, tile, k, iters=ITERS_PER_SOLVE):
-    n = nr // tile
-    n_lr = n * n * tile * k
-    return iters * flops_per_iter(nr, ns, tile, k) + 40.0 * ns * n_lr
+    """The iterations plus the solve's first forward product and gradient (40)."""
+    return iters * flops_per_iter(nr, ns, tile, k) + 40.0 * ns * n_lr(nr, tile, k)
 
 
 # ---------------------------------------------------------------------------
@@ -123,73 +150,18 @@ def clock_problem(clocks):
     return None
 
 
-# ---------------------------------------------------------------------------
-# synthetic workload on the device (input generation only)
-# ---------------------------------------------------------------------------
-def make_workload(T, torch, nfreq, seed, device):
-    """D, U stacks (paper layout, complex64) and start points theta0 per frequency."""
-    g = torch.Generator(device=device).manual_seed(seed)
-    n = NR
-
-    def cn(shape):
-        re = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
-        im = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
-        return torch.complex(re, im) * (1.0 / math.sqrt(2.0))
-
-    # exactly unitary random-phase DFT products (tlr_synth recipe), built on the host
-    import tlr_synth as synth
-    hg = synth.rng(seed)
-    Q = torch.from_numpy(synth.phase_dft_unitary(n, hg).astype(np.complex64)).to(device)
-    W = torch.from_numpy(synth.phase_dft_unitary(n, hg).astype(np.complex64)).to(device)
-    sig = torch.pow(10.0, -3.0 * torch.arange(n, device=device, dtype=torch.float32) / (n - 1))
-    perm = torch.empty(n, dtype=torch.int32, device=device)
-    T.tlr_mdd_hilbert_perm(GRID[0], GRID[1], perm)
-    inv = torch.empty_like(perm)
-    inv[perm.long()] = torch.arange(n, dtype=torch.int32, device=device)
-    D = torch.empty((nfreq, n, n), dtype=torch.complex64, device=device)
-    U = torch.empty_like(D)
-    thetas, descs, ranks = [], [], []
-    b = TILE
-    N = n // b
-    pairs = [(i, j) for j in range(N) for i in range(j + 1, N)]
-    for f in range(nfreq):
-        k = rank_of(f, nfreq)
-        ranks.append(k)
-        ph = torch.exp(2j * math.pi * torch.rand(n, generator=g, device=device)).to(torch.complex64)
-        D[f] = (Q * (sig * ph)[None, :]) @ W.conj().T
-        # planted X_h (Hilbert order) from random factors, then X = S X_h S^T
-        Xh = torch.zeros((n, n), dtype=torch.complex64, device=device)
-        for i in range(N):
-            Qi = cn((b, k)) / math.sqrt(b * k)
-            Xh[i * b:(i + 1) * b, i * b:(i + 1) * b] = Qi @ Qi.T
-        for (i, j) in pairs:
-            s = 1.0 / ((1 + abs(i - j)) * math.sqrt(b * k))
-            L, R = cn((b, k)) * s, cn((b, k)) * s
-            t = L @ R.T
-            Xh[i * b:(i + 1) * b, j * b:(j + 1) * b] = t
-            Xh[j * b:(j + 1) * b, i * b:(i + 1) * b] = t.T
-        X = Xh[inv.long()][:, inv.long()]
-        Y = D[f] @ X
-        nz = cn((n, n))
-        scale = Y.norm() / nz.norm() * 10 ** (-SNR_DB / 20)
-        U[f] = Y + scale * nz
-        d = T.desc(n, n, b, rank=k, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE)
-        descs.append(d)
-        nth = T.tlr_mdd_theta_size(d)
-        th0 = cn((nth,)) * (0.1 / math.sqrt(b * k))
-        thetas.append(th0)
-        del Xh, X, Y, nz
-    return D, U, thetas, descs, ranks
-
-
-def measured_bf16_sustained():
+def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as fh:
             j = json.load(fh)
-        return float(j["bf16_tflops_sustained"]), "measured sustained"
+        return float(j["bf16_tflops_sustained"]), float(j.get("hbm_gbs", 6794.1)), "measured"
     except (OSError, KeyError, ValueError):
-        return 1700.0, "fallback sustained"
+        return 1700.0, 6800.0, "fallback"
+
+
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def percentile(xs, p):
@@ -200,28 +172,6 @@ def percentile(xs, p):
     return xs[i]
 
 
-# ---------------------------------------------------------------------------
-# CPU oracle leg (bounded sample)
-# ---------------------------------------------------------------------------
-def oracle_sample(D0, U0, k, lbfgs_iters):
-    """Time the FP64 oracle's TLR-structured solve on one frequency for a few
-    L-BFGS iterations; returns (seconds, iterations, theta, threads)."""
-    from oracle import hilbert, layout, operator, solver
-    perm = hilbert.perm(*GRID)
-    lay = layout.make_layout(NR, TILE, k, "rule")
-    Dh, Uh, alpha = operator.normalise(D0, U0, perm)
-    prob = solver.Problem(lay, Dh.T, Uh.T)
-    return prob, lay, perm, alpha
-
-
-def run_oracle(prob, th0, iters):
-    from oracle import solver
-    opts = solver.SolveOpts(stages=1, admm_iters=1, lbfgs_iters=iters)
-    t0 = time.perf_counter()
-    th, z, u, st = solver.admm(prob, th0, opts)
-    return time.perf_counter() - t0, th, st
-
-
 def blas_threads():
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(k):
@@ -230,517 +180,702 @@ def blas_threads():
 
 
 # ---------------------------------------------------------------------------
+# synthetic workload on the device (input generation only, not timed)
+# ---------------------------------------------------------------------------
+def phase_dft_unitary_device(torch, n, g, device):
+    """tlr_synth.phase_dft_unitary's matrix F diag(phi) Pi F diag(psi) / n from
+    the same draws of g, with the two FFTs done on the device (complex64)."""
+    psi = np.exp(2j * np.pi * g.random(n))
+    phi = np.exp(2j * np.pi * g.random(n))
+    pi = g.permutation(n)
+    m = torch.fft.fft(torch.diag(torch.from_numpy(psi.astype(np.complex64)).to(device)), dim=0)
+    m = m[torch.from_numpy(pi).to(device), :] * torch.from_numpy(phi.astype(np.complex64)).to(device)[:, None]
+    return torch.fft.fft(m, dim=0) / n
+
+
+class Inputs:
+    """D, U (paper layout, complex64, device) and the start point theta0 of
+    each of a rank's frequencies, generated on the device from per-frequency
+    seeds, so any rank can regenerate any global frequency identically."""
+
+    def __init__(self, T, torch, wl: Workload, freqs, ranks, seed, device):
+        import tlr_synth as synth
+        self.wl, self.freqs, self.ranks = wl, list(freqs), ranks
+        n = wl.nr
+        self.dev = device
+        hg = synth.rng(seed)
+        Q = phase_dft_unitary_device(torch, n, hg, device)
+        W = phase_dft_unitary_device(torch, n, hg, device)
+        sig = torch.pow(10.0, -3.0 * torch.arange(n, device=device, dtype=torch.float32) / (n - 1))
+        perm = torch.empty(n, dtype=torch.int32, device=device)
+        T.tlr_mdd_hilbert_perm(wl.grid[0], wl.grid[1], perm)
+        inv = torch.empty_like(perm)
+        inv[perm.long()] = torch.arange(n, dtype=torch.int32, device=device)
+        inv = inv.long()
+        self.D = torch.empty((len(freqs), n, n), dtype=torch.complex64, device=device)
+        self.U = torch.empty_like(self.D)
+        self.th0, self.descs = [], []
+        b = wl.tile
+        N = n // b
+        pairs = [(i, j) for j in range(N) for i in range(j + 1, N)]
+        tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True   # generation only: far below the 10 dB noise
+        try:
+            for slot, f in enumerate(freqs):
+                k = ranks[f]
+                g = torch.Generator(device=device).manual_seed(seed * 1000003 + f)
+
+                def cn(shape):
+                    re = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+                    im = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+                    return torch.complex(re, im) * (1.0 / math.sqrt(2.0))
+
+                ph = torch.exp(2j * math.pi * torch.rand(n, generator=g, device=device)).to(torch.complex64)
+                Df = (Q * (sig * ph)[None, :]) @ W.conj().T
+                self.D[slot] = Df
+                Xh = torch.zeros((n, n), dtype=torch.complex64, device=device)
+                for i in range(N):
+                    Qi = cn((b, k)) / math.sqrt(b * k)
+                    Xh[i * b:(i + 1) * b, i * b:(i + 1) * b] = Qi @ Qi.T
+                for (i, j) in pairs:
+                    s = 1.0 / ((1 + abs(i - j)) * math.sqrt(b * k))
+                    t = (cn((b, k)) * s) @ (cn((b, k)) * s).T
+                    Xh[i * b:(i + 1) * b, j * b:(j + 1) * b] = t
+                    Xh[j * b:(j + 1) * b, i * b:(i + 1) * b] = t.T
+                X = Xh[inv][:, inv]
+                del Xh
+                Y = Df @ X
+                del X
+                nz = cn((n, n))
+                scale = Y.norm() / nz.norm() * 10 ** (-wl.snr_db / 20)
+                self.U[slot] = Y + scale * nz
+                del Y, nz, Df
+                d = T.desc(n, n, b, rank=k, nx=wl.grid[0], ny=wl.grid[1], diag_mode=T.TLR_DIAG_RULE,
+                           precision=T.TLR_PREC_BF16X3)
+                self.descs.append(d)
+                nth = T.tlr_mdd_theta_size(d)
+                self.th0.append(cn((nth,)) * (0.1 / math.sqrt(b * k)))
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+        del Q, W
+        self.slot_of = {f: s for s, f in enumerate(freqs)}
+
+    def desc(self, T, f, precision):
+        d = self.descs[self.slot_of[f]]
+        wl = self.wl
+        return T.desc(wl.nr, wl.nr, wl.tile, rank=d.rank, nx=wl.grid[0], ny=wl.grid[1],
+                      diag_mode=T.TLR_DIAG_RULE, precision=precision)
+
+
+class Runner:
+    """Solves frequencies on S streams.  Each stream slot takes its next
+    frequency, creates a handle for it from the raw D, U (receiver order,
+    alpha, normalised panels, packed operands, all in the library), enqueues
+    the solve, and destroys the handle when the solve has finished; the
+    library's workspace pool keeps the freed memory for the next handle."""
+
+    def __init__(self, T, torch, inp: Inputs, nstream, device, opts=None):
+        self.T, self.torch, self.inp = T, torch, inp
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(nstream)]
+        nmax = max(t.numel() for t in inp.th0)
+        self.bufs = [torch.empty(nmax, dtype=torch.complex64, device=device) for _ in range(nstream)]
+        self.opts = opts if opts is not None else T.solve_opts()
+        self.main = torch.cuda.current_stream(device)
+
+    def step(self, freqs, precision, host=None, records=None, lat=None):
+        """One pass over ``freqs``; returns the device ms between a start event
+        on the main stream and the join of the slot streams."""
+        T, torch = self.T, self.torch
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.main)
+        for s in self.streams:
+            s.wait_event(e0)
+        queue = list(freqs)
+        busy = [None] * len(self.streams)
+        while queue or any(b is not None for b in busy):
+            progressed = False
+            for si, st in enumerate(self.streams):
+                if busy[si] is None and queue:
+                    f = queue.pop(0)
+                    slot = self.inp.slot_of[f]
+                    d = self.inp.desc(T, f, precision)
+                    if host is None:
+                        h = T.tlr_mdd_create(d, self.inp.D[slot], self.inp.U[slot], st)
+                        buf = self.bufs[si][:self.inp.th0[slot].numel()]
+                        with torch.cuda.stream(st):
+                            buf.copy_(self.inp.th0[slot])
+                        T.tlr_mdd_solve_async(h, buf, self.opts)
+                    else:
+                        Dh, Uh, th_h, out_h, hopts = host     # pinned host tensors keyed by frequency
+                        d.input_memory = T.TLR_MEM_HOST
+                        h = T.tlr_mdd_create(d, Dh[f], Uh[f], st)
+                        out_h[f].copy_(th_h[f])
+                        T.tlr_mdd_solve_async(h, out_h[f], hopts)
+                        buf = out_h[f]
+                    busy[si] = (f, h, buf)
+                    progressed = True
+                elif busy[si] is not None and T.tlr_mdd_solve_query(busy[si][1]):
+                    f, h, buf = busy[si]
+                    stt = T.tlr_mdd_solve_wait(h)
+                    T.tlr_mdd_destroy(h)
+                    if lat is not None:
+                        lat.append(stt.gpu_ms)
+                    if records is not None:
+                        records.append({"freq": f, "rank": self.inp.ranks[f], "iters": stt.iters,
+                                        "restarts": stt.restarts, "status": stt.status,
+                                        "f_final": stt.f_hist[max(0, stt.n_hist - 1)], "f0": stt.f0,
+                                        "gpu_ms": round(stt.gpu_ms, 3)})
+                    busy[si] = None
+                    progressed = True
+            if not progressed:
+                time.sleep(2e-4)
+        for s in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            self.main.wait_event(ev)
+        e1.record(self.main)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+def oracle_problem(D0, U0, wl: Workload, k, cols=None):
+    """The oracle's own panels (its Hilbert order, alpha = max |D|) for one
+    frequency, optionally restricted to some source columns (rows of D, U)."""
+    from oracle import hilbert, layout, operator, solver
+    perm = hilbert.perm(*wl.grid)
+    lay = layout.make_layout(wl.nr, wl.tile, k, "rule")
+    alpha = float(np.max(np.abs(D0)))
+    Ds, Us = (D0, U0) if cols is None else (D0[cols], U0[cols])
+    Dh, Uh, _ = operator.normalise(Ds, Us, perm, alpha=alpha)
+    return solver.Problem(lay, Dh.T, Uh.T), lay, alpha
+
+
+def run_oracle_solve(prob, th0, iters):
+    from oracle import solver
+    opts = solver.SolveOpts(stages=1, admm_iters=1, lbfgs_iters=iters)
+    t0 = time.perf_counter()
+    th, z, u, st = solver.admm(prob, th0, opts)
+    return time.perf_counter() - t0, th, st
+
+
+# ---------------------------------------------------------------------------
+def spawn_ranks(args):
+    """``--gpus N`` without a torchrun environment: start N ranks (one process
+    per GPU, 127.0.0.1 rendezvous) and wait for them."""
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    procs = []
+    for r in range(args.gpus):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(args.gpus),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__)] + sys.argv[1:], env=env))
+    rc = 0
+    for p in procs:
+        rc = p.wait() or rc
+    return rc
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
-    ap.add_argument("--compare-fp32", type=int, default=8,
-                    help="frequencies (evenly spaced) re-solved with the FP32 SIMT path for the speedup")
-    ap.add_argument("--freqs", type=int, default=NFREQ)
+    ap.add_argument("--workload", default="precision", choices=["precision", "batched"])
     ap.add_argument("--seed", type=int, default=2412)
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the frequencies are spread over")
+    ap.add_argument("--streams", type=int, default=2, help="CUDA streams the frequencies of a step are spread over")
+    ap.add_argument("--e2e-steps", type=int, default=4, help="steps of the end-to-end leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--oracle-iters", type=int, default=3)
-    ap.add_argument("--bench-iters", type=int, default=20,
-                    help="CG iterations of the eq. (4) benchmark solver timed on frequency 0 (0: skip)")
-    ap.add_argument("--general-rank", type=int, default=26,
-                    help="rank of one timed solve of the general (non-reciprocal) form on frequency 0 (0: skip)")
-    ap.add_argument("--tiles-rank", type=int, default=26,
-                    help="rank of one timed solve on a non-uniform partition (tiles of 192 and 320 "
-                         "receivers alternating) of frequency 0 (0: skip)")
-    ap.add_argument("--serving", type=int, default=0,
-                    help="also serve this many per-frequency requests of the serving mix (nr 1024-8192)")
+    ap.add_argument("--oracle-cols", type=int, default=512,
+                    help="source columns per step of the reference arm's bounded sample")
+    ap.add_argument("--accuracy", type=int, default=4, help="frequencies of the precision table (0: skip)")
+    ap.add_argument("--freqs", type=int, default=0,
+                    help="frequencies per GPU (0: the workload's; a multiple of its batch)")
+    ap.add_argument("--secondary", type=int, default=2,
+                    help="timed steps of the nr=4096 batched workload reported beside the headline (0: skip)")
     args = ap.parse_args()
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = PRECISION_FORM if args.workload == "precision" else BATCHED
+    if args.freqs:
+        import dataclasses
+        wl = dataclasses.replace(wl, nfreq=args.freqs)
 
     if args.impl == "reference":
-        return reference_arm(args, world, rank)
+        return reference_arm(args, wl, world, rank)
 
     import torch
     import paper_2412_14973_gb300 as T
+    from paper_2412_14973_gb300 import sharding
 
+    os.environ["TLR_MDD_GRAPHS"] = "0" if wl.nr >= 8192 else "1"
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    nfreq = args.freqs
-    with torch.cuda.stream(stream):
-        D, U, th0, descs, ranks = make_workload(T, torch, nfreq, args.seed + 7919 * rank, dev)
-    torch.cuda.synchronize()
+    total = wl.nfreq * world
+    ranks = wl.ranks(total)
+    mine = sharding.frequency_plan(wl.nfreq, rank, world)
+    steps_of = sharding.batches(mine, wl.batch)
     prec = T.TLR_PREC_FP32 if args.precision == "fp32" else T.TLR_PREC_BF16X3
-    for d in descs:
-        d.precision = prec
-    theta = [t.clone() for t in th0]
-    opts = T.solve_opts()
-    lat_ms = []
-    # one handle per frequency, kept across steps (workspace and recorded
-    # solve); each step re-runs the data step (alpha, reorder, normalise)
-    nstream = max(1, min(args.streams, nfreq))
-    streams = [torch.cuda.Stream(device=dev) for _ in range(nstream)]
-    handles = [T.tlr_mdd_create(descs[f], D[f], U[f], streams[f % nstream]) for f in range(nfreq)]
-    main_stream = torch.cuda.current_stream(dev)
-
-    def step(record=False, host=None):
-        """One pass over every frequency; returns the device ms between the
-        start event (main stream) and the join of all worker streams."""
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(main_stream)
-        for s_ in streams:
-            s_.wait_event(e0)
-        for f in range(nfreq):
-            st_ = streams[f % nstream]
-            if host is None:
-                T.tlr_mdd_set_data(handles[f], D[f], U[f], T.TLR_MEM_DEVICE)
-                with torch.cuda.stream(st_):
-                    theta[f].copy_(th0[f])
-                T.tlr_mdd_solve_async(handles[f], theta[f], opts)
-            else:
-                Dh_, Uh_, th_h_, out_h_, hopts_ = host
-                T.tlr_mdd_set_data(handles[f], Dh_[f], Uh_[f], T.TLR_MEM_HOST)
-                out_h_[f].copy_(th_h_[f])
-                T.tlr_mdd_solve_async(handles[f], out_h_[f], hopts_)
-        for f in range(nfreq):
-            st = T.tlr_mdd_solve_wait(handles[f])
-            if record:
-                lat_ms.append(st.gpu_ms)
-        for s_ in streams:
-            ev = torch.cuda.Event()
-            ev.record(s_)
-            main_stream.wait_event(ev)
-        e1.record(main_stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    for _ in range(args.warmup):
-        step()
+    t_gen = time.perf_counter()
+    inp = Inputs(T, torch, wl, mine, ranks, args.seed, dev)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    t_gen = time.perf_counter() - t_gen
+    runner = Runner(T, torch, inp, max(1, args.streams), dev)
+    nstream = len(runner.streams)
+    lat_ms, records = [], []
+
+    for w in range(args.warmup):
+        runner.step(steps_of[w % len(steps_of)], prec)
     torch.cuda.synchronize()
-    T.tlr_mdd_timing_reset()
-    T.tlr_mdd_timing_enable(True)
-    step()   # records the solve graphs with the timing events (not timed)
+
     def timed_region():
-        T.tlr_mdd_timing_reset()
         lat_ms.clear()
+        records.clear()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        torch.cuda.synchronize()
         n0 = T.tlr_mdd_launch_count()
         clk = ClockSampler(local)
         clk.start()
         ms = 0.0
-        for _ in range(args.steps):
-            ms += step(record=True)
+        for s in range(args.steps):
+            ms += runner.step(steps_of[s % len(steps_of)], prec, records=records, lat=lat_ms)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        return ms, clk.stop(), T.tlr_mdd_launch_count() - n0, T.tlr_mdd_timing_read()
+        torch.cuda.synchronize()
+        return ms, clk.stop(), T.tlr_mdd_launch_count() - n0
 
-    ms, clocks, launches, timing = timed_region()
+    log(f"inputs generated in {t_gen:.1f} s; warm-up done")
+    ms, clocks, launches = timed_region()
+    log(f"timed region: {ms:.0f} ms for {args.steps} steps")
     # a timed region that saw a hardware or thermal slowdown, or SM clocks held
     # far below their maximum with no reason given (a clock lock), is measured
     # once more and that second measurement is reported
     bad = clock_problem(clocks)
     if bad:
-        ms, clocks, launches, timing = timed_region()
+        ms, clocks, launches = timed_region()
         clocks["remeasured_after"] = bad
         clocks["still_flagged"] = clock_problem(clocks)
-    T.tlr_mdd_timing_enable(False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    solves = nfreq * args.steps * world
+    ms = sharding.max_over_ranks(ms, dist, dev)
+    solved = [f for s in range(args.steps) for f in steps_of[s % len(steps_of)]]
+    solves = len(solved) * world
     value = solves / (ms / 1e3)
-    total_flops = sum(flops_per_solve(NR, NR, TILE, k) for k in ranks) * args.steps * world
+    my_flops = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, ranks[f]) for f in solved)
+    gathered = sharding.gather_results(records, dist)
 
-    # roofline of the dominant contraction kernel
+    # roofline of the dominant contraction class: one step's frequencies on
+    # ONE stream with CUDA events around every contraction launch (no overlap
+    # with other launches, so an event pair times that launch alone)
+    bf16, hbm, peak_src = measured_peaks()
     names = ["cgemm_compress", "cgemm_expand", "cgemm_project"]
-    dom = max(range(len(timing)), key=lambda c: timing[c][0])
-    dms, dfl, dnl = timing[dom]
-    achieved = (dfl / max(1, dnl)) / (dms / max(1, dnl) / 1e3) / 1e12 if dnl else 0.0
-    if args.precision == "fp32":
-        peak = FP32_LANES_PER_SM * SMS * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": names[dom], "achieved": round(achieved, 3),
-                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
-    else:
-        bf16, src = measured_bf16_sustained()
-        # 4M x BF16x3: 12 real BF16 products = 24 flops issued per complex MAC counted as 8
-        peak = bf16 * 8.0 / 24.0
-        roof = {"bound": "tensor", "kernel": names[dom], "achieved": round(achieved, 3),
-                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "bf16_issued_tflops": round(achieved * 24.0 / 8.0, 2),
-                "peak_source": f"{src} bf16 {bf16} TFLOP/s x 8/24 (complex flops per issued BF16 flop, 4M x BF16x3)"}
-    roof["per_class_ms"] = {names[c]: round(timing[c][0], 2) for c in range(len(timing))}
-    # launches of different frequencies overlap on the 4 streams, so a launch's
-    # event-timed duration includes time shared with other launches; the
-    # device-wide rate below is all contraction flops over the timed wall time
-    roof["aggregate_contraction_tflops"] = round(sum(t[1] for t in timing) / (ms / 1e3) / 1e12, 2)
-    roof["aggregate_frac"] = round(roof["aggregate_contraction_tflops"] / peak, 4)
+    roof = None
+    if rank == 0:
+        single = Runner(T, torch, inp, 1, dev)
+        T.tlr_mdd_timing_reset()
+        T.tlr_mdd_timing_enable(True)
+        ms1 = single.step(steps_of[0], prec)
+        timing = T.tlr_mdd_timing_read()
+        T.tlr_mdd_timing_enable(False)
+        del single
+        dom = max(range(len(timing)), key=lambda c: timing[c][0])
+        dms, dfl, dnl = timing[dom]
+        achieved = dfl / (dms / 1e3) / 1e12
+        step_flops = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, ranks[f]) for f in steps_of[0])
+        if prec == T.TLR_PREC_FP32:
+            peak = 152 * 128 * 2 * 2070e6 / 1e12
+            roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+        else:
+            # 4M x BF16x3: 12 real BF16 products (24 flops) issued per complex
+            # multiply-add counted as 8; the 3M form would issue 9 (18 flops)
+            peak = bf16 * 8.0 / 24.0
+            roof = {"bound": "tensor",
+                    "peak_source": (f"{peak_src} sustained bf16 {bf16} TFLOP/s x 8/24: the issue rate of the "
+                                    "4M BF16x3 form this kernel runs (12 BF16 products per complex MAC); "
+                                    f"against the 3M-effective peak (x 8/18 = {bf16 * 8 / 18:.1f}) the "
+                                    "fraction is frac x 0.75")}
+        roof.update({"kernel": names[dom], "achieved": round(achieved, 2), "peak": round(peak, 1),
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "launches": dnl, "ms": round(dms, 2),
+                     "flops_counted": "8 per complex MAC; per iteration 56 ns n_LR (T and the residual carried "
+                                      "between iterations; a fresh forward each iteration would be 72)",
+                     "single_stream_step_ms": round(ms1, 1),
+                     "single_stream_step_tflops": round(step_flops / (ms1 / 1e3) / 1e12, 1),
+                     "share_of_step": round(dms / ms1, 3),
+                     "per_class": {names[c]: {"ms": round(timing[c][0], 1), "launches": timing[c][2],
+                                              "tflops": round(timing[c][1] / max(1e-9, timing[c][0] / 1e3) / 1e12,
+                                                              1)}
+                                   for c in range(len(timing)) if timing[c][2]}})
 
-    # e2e through the C-ABI with HOST buffers: every step copies each
-    # frequency's D, U and start point from pinned host memory inside the
-    # timed region and reads the solved factors back
+    log("roofline pass done")
+    # e2e through the C ABI with HOST buffers: D, U and the start point copied
+    # from pinned host memory inside the timed region, the solved factors read back
     e2e = None
-    if not args.no_e2e:
-        Dh = torch.empty((nfreq, NR, NR), dtype=torch.complex64, pin_memory=True)
-        Uh = torch.empty_like(Dh, pin_memory=True)
-        Dh.copy_(D)
-        Uh.copy_(U)
-        th_h = [t.cpu().pin_memory() for t in th0]
-        out_h = [torch.empty_like(t).pin_memory() for t in th_h]
+    if args.e2e_steps > 0:
+        # the first two batches' D and U in pinned host memory (every batch has
+        # the same rank mix); e2e step i solves batch i % 2 from there
+        e2e_batches = steps_of[:min(2, len(steps_of))]
+        hf = [f for fs in e2e_batches for f in fs]
+        Dh = {f: inp.D[inp.slot_of[f]].cpu().pin_memory() for f in hf}
+        Uh = {f: inp.U[inp.slot_of[f]].cpu().pin_memory() for f in hf}
+        th_h = {f: inp.th0[inp.slot_of[f]].cpu().pin_memory() for f in hf}
+        out_h = {f: torch.empty_like(th_h[f]).pin_memory() for f in hf}
         hopts = T.solve_opts(theta_memory=T.TLR_MEM_HOST)
         host = (Dh, Uh, th_h, out_h, hopts)
-        step(host=host)  # records the host-theta graphs
+        runner.step(e2e_batches[0], prec, host=host)          # warm-up
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
-        step(host=host)
+        n_e2e = h2d = d2h = 0
+        for i in range(args.e2e_steps):
+            fs = e2e_batches[i % len(e2e_batches)]
+            runner.step(fs, prec, host=host)
+            n_e2e += len(fs)
+            h2d += sum(Dh[f].numel() * 8 + Uh[f].numel() * 8 + th_h[f].numel() * 8 for f in fs)
+            d2h += sum(out_h[f].numel() * 8 for f in fs)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        h2d = sum(2 * Dh[f].numel() * 8 + th_h[f].numel() * 8 for f in range(nfreq))
-        d2h = sum(out_h[f].numel() * 8 for f in range(nfreq))
-        e2e = {"value": round(nfreq * world / te, 4), "unit": "freq-solves/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-        del Dh, Uh
+        te = sharding.max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": round(n_e2e * world / te, 4), "unit": "freq-solves/s",
+               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "steps": args.e2e_steps,
+               "host_data": f"D, U and theta0 of {len(hf)} frequencies (two batches) in pinned host memory; "
+                            "every step copies its batch's inputs in and its solved factors out"}
+        del Dh, Uh, th_h, out_h, host
 
-    # the plain FP32 SIMT form on an evenly spaced subset, same subset on tensor cores
-    cmp = None
-    if args.precision != "fp32" and args.compare_fp32 > 0:
-        sub = sorted(set(int(round(i * (nfreq - 1) / max(1, args.compare_fp32 - 1)))
-                         for i in range(min(args.compare_fp32, nfreq))))
-
-        def run_subset(prec_):
-            hs = []
-            for f in sub:
-                d = T.desc(NR, NR, TILE, rank=ranks[f], nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
-                           precision=prec_)
-                hs.append(T.tlr_mdd_create(d, D[f], U[f], streams[0]))
-            ms_tot = 0.0
-            for rep in range(2):          # first pass records the graphs
-                if rep == 1 and prec_ == prec and prec != T.TLR_PREC_FP32:
-                    T.tlr_mdd_timing_reset()
-                    T.tlr_mdd_timing_enable(True)
-                t0_ = torch.cuda.Event(enable_timing=True)
-                t1_ = torch.cuda.Event(enable_timing=True)
-                t0_.record(streams[0])
-                for h_, f in zip(hs, sub):
-                    T.tlr_mdd_set_data(h_, D[f], U[f], T.TLR_MEM_DEVICE)
-                    with torch.cuda.stream(streams[0]):
-                        theta[f].copy_(th0[f])
-                    T.tlr_mdd_solve(h_, theta[f], opts)
-                t1_.record(streams[0])
-                torch.cuda.synchronize()
-                if rep == 1:
-                    ms_tot = t0_.elapsed_time(t1_)
-                    if T.tlr_mdd_timing_read and prec_ == prec and prec != T.TLR_PREC_FP32:
-                        single[:] = T.tlr_mdd_timing_read()
-                        T.tlr_mdd_timing_enable(False)
-            for h_ in hs:
-                T.tlr_mdd_destroy(h_)
-            return ms_tot
-
-        single = []
-        t_fp32 = run_subset(T.TLR_PREC_FP32)
-        t_tc = run_subset(prec)
-        if single:
-            # one stream, no overlap between launches: per-launch rates of each class
-            roof["single_stream_tflops_per_class"] = {
-                names[c]: round(single[c][1] / (single[c][0] / 1e3) / 1e12, 1) for c in range(len(single))
-                if single[c][0] > 0}
-            roof["single_stream_frac_per_class"] = {
-                k: round(v / roof["peak"], 4) for k, v in roof["single_stream_tflops_per_class"].items()}
-        cmp = {"frequencies": sub, "fp32_simt_freq_solves_per_s": round(len(sub) / (t_fp32 / 1e3), 4),
-               "tensor_core_freq_solves_per_s": round(len(sub) / (t_tc / 1e3), 4),
-               "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
-               "accuracy": "both paths within 1e-5 (FP32) / 1e-5 (BF16x3, measured) of the FP64 oracle per operator; see tests"}
-
-    # the eq. (4) benchmark solver (warm-start stage) on frequency 0's handle:
-    # G = D^H D and D^H U once, then one nr^3 complex product per CG iteration
-    bsolve = None
-    if args.bench_iters > 0 and rank == 0:
-        Xb = torch.empty((NR, NR), dtype=torch.complex64, device=dev)
-        T.tlr_mdd_set_data(handles[0], D[0], U[0], T.TLR_MEM_DEVICE)
-        T.tlr_mdd_benchmark_solve(handles[0], 0.1, 2, 0.0, Xb)          # warm-up
-        bst = T.tlr_mdd_benchmark_solve(handles[0], 0.1, args.bench_iters, 0.0, Xb)
-        fl = 2 * 8.0 * NR * NR * NR + bst.iters * 8.0 * NR ** 3
-        tf = fl / (bst.gpu_ms / 1e3) / 1e12
-        bsolve = {"nr": NR, "ns": NR, "lambda": 0.1, "iters": bst.iters, "ms": round(bst.gpu_ms, 2),
-                  "ms_per_iter": round(bst.gpu_ms / max(1, bst.iters + 2), 3),
-                  "tflops": round(tf, 1), "frac": round(tf / roof["peak"], 4) if args.precision != "fp32" else None,
-                  "rel_res": bst.rel_res,
-                  "flops": "8 nr^2 ns (D^H D) + 8 nr^2 ns (D^H U) + iters x 8 nr^3, complex-counted"}
-        del Xb
-
-    # the general (non-reciprocal) form: one solve of frequency 0's data at a
-    # given rank (same contraction flops per iteration as the reciprocal form
-    # at that rank, twice the unknowns)
-    gsolve = None
-    if args.general_rank > 0 and rank == 0:
-        kg = args.general_rank
-        dg = T.desc(NR, NR, TILE, rank=kg, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
-                    precision=prec, reciprocity=T.TLR_RECIP_NONE)
-        hg = T.tlr_mdd_create(dg, D[0], U[0], streams[0])
-        gen = torch.Generator(device=dev).manual_seed(args.seed + 5)
-        ntg = T.tlr_mdd_theta_size(dg)
-        th_g0 = 0.01 * torch.randn(ntg, dtype=torch.complex64, device=dev, generator=gen)
-        th_g = th_g0.clone()
-        torch.cuda.synchronize()
-        T.tlr_mdd_solve(hg, th_g, opts)                                   # records the graph
-        th_g.copy_(th_g0)
-        torch.cuda.synchronize()
-        gst = T.tlr_mdd_solve(hg, th_g, opts)
-        gf = flops_per_solve(NR, NR, TILE, kg)
-        gsolve = {"rank": kg, "n_theta": ntg, "ms": round(gst.gpu_ms, 2),
-                  "tflops": round(gf / (gst.gpu_ms / 1e3) / 1e12, 1), "iters": gst.iters,
-                  "note": "one solve, one stream; flops as for the reciprocal form at this rank"}
-        T.tlr_mdd_destroy(hg)
-
-    # a non-uniform partition: 16 tiles of 192 and 320 receivers alternating
-    # (sum 4096), the same rank on every tile; with N tiles and rank k the
-    # low-rank entries are N k nr, as for equal tiles
-    tsolve = None
-    if args.tiles_rank > 0 and rank == 0 and NR == 4096:
-        kt = args.tiles_rank
-        tiles = [192, 320] * 8
-        dt = T.desc(NR, NR, 0, rank=kt, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE,
-                    precision=prec, tiles=tiles)
-        ht = T.tlr_mdd_create(dt, D[0], U[0], streams[0])
-        gen = torch.Generator(device=dev).manual_seed(args.seed + 6)
-        ntt = T.tlr_mdd_theta_size(dt)
-        th_t0 = 0.01 * torch.randn(ntt, dtype=torch.complex64, device=dev, generator=gen)
-        th_t = th_t0.clone()
-        torch.cuda.synchronize()
-        T.tlr_mdd_solve(ht, th_t, opts)                                   # records the graph
-        th_t.copy_(th_t0)
-        torch.cuda.synchronize()
-        tst = T.tlr_mdd_solve(ht, th_t, opts)
-        T.tlr_mdd_destroy(ht)
-        # the same rank on 16 equal tiles, for comparison
-        du = T.desc(NR, NR, NR // 16, rank=kt, nx=GRID[0], ny=GRID[1], diag_mode=T.TLR_DIAG_RULE, precision=prec)
-        hu = T.tlr_mdd_create(du, D[0], U[0], streams[0])
-        th_u0 = 0.01 * torch.randn(T.tlr_mdd_theta_size(du), dtype=torch.complex64, device=dev, generator=gen)
-        th_u = th_u0.clone()
-        torch.cuda.synchronize()
-        T.tlr_mdd_solve(hu, th_u, opts)
-        th_u.copy_(th_u0)
-        torch.cuda.synchronize()
-        ust = T.tlr_mdd_solve(hu, th_u, opts)
-        T.tlr_mdd_destroy(hu)
-        tf = (ITERS_PER_SOLVE * 56.0 + 40.0) * NR * ntt
-        tsolve = {"tiles": "192,320 alternating x8", "rank": kt, "n_theta": ntt, "ms": round(tst.gpu_ms, 2),
-                  "tflops": round(tf / (tst.gpu_ms / 1e3) / 1e12, 1), "iters": tst.iters,
-                  "equal_tiles_ms": round(ust.gpu_ms, 2),
-                  "note": "one solve, one stream; equal_tiles_ms: 16 tiles of 256 at the same rank "
-                          "(same flops); 192- and 320-row blocks fill 75% and 83% of their 128-row MMA tiles"}
-
-    # CPU oracle baseline (rank 0 only, N = 1 only) + accuracy at the sample
-    cpu = None
+    # precision table: on frequencies spread over the rank range, the error
+    # of one operator application (seeded theta0) against the FP64 oracle on
+    # sampled source columns, for both paths, and 30-iteration solves on both
+    # paths (time, and the difference of their X and final misfit)
+    log("e2e leg done")
     acc = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        f0 = 0
-        k0 = ranks[f0]
-        D0 = D[f0].cpu().numpy()
-        U0 = U[f0].cpu().numpy()
-        prob, lay, perm, alpha = oracle_sample(D0, U0, k0, args.oracle_iters)
-        th_start = th0[f0].cpu().numpy().astype(np.complex128)
-        secs, th_or, st_or = run_oracle(prob, th_start, args.oracle_iters)
-        # GPU with the same short schedule for the accuracy check
-        h = T.tlr_mdd_create(descs[f0], D[f0], U[f0], stream)
-        thg = th0[f0].clone()
-        T.tlr_mdd_solve(h, thg, T.solve_opts(stages=1, admm_iters=1, lbfgs_iters=args.oracle_iters))
-        T.tlr_mdd_destroy(h)
-        from oracle import operator
-        Xo = operator.assemble_xh(th_or, lay)
-        Xg = operator.assemble_xh(thg.cpu().numpy().astype(np.complex128), lay)
-        rel = float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo))
-        kmean = sum(ranks) / len(ranks)
-        per_solve = secs * (ITERS_PER_SOLVE / args.oracle_iters) * (kmean / k0)
-        cpu = {"value": round(1.0 / per_solve, 6), "unit": "freq-solves/s", "cores": blas_threads(),
-               "kind": "oracle",
-               "sample": (f"frequency {f0} (rank {k0}), {args.oracle_iters} L-BFGS iterations of the FP64 "
-                          f"TLR-structured oracle in {secs:.1f} s, scaled to a {ITERS_PER_SOLVE}-iteration "
-                          f"solve at the mean rank {kmean:.1f} (work grows linearly with rank)")}
-        acc = {"frequency": f0, "iters": args.oracle_iters, "rel_err_X_vs_fp64_oracle": rel,
-               "within_1e-3": rel <= 1e-3}
+    cmp = None
+    if rank == 0 and args.accuracy > 0 and not args.no_cpu:
+        acc, cmp = precision_table(T, torch, inp, wl, mine, args, dev)
 
-    for h_ in handles:
-        T.tlr_mdd_destroy(h_)
-    serve = None
-    if args.serving > 0 and rank == 0:
-        del D, U
+    # CPU oracle baseline: one full L-BFGS iteration (the solve's first forward
+    # product and gradient, the line-search products, the gradient at the new
+    # point) of the FP64 oracle at the mean rank, on the host cores, and the
+    # same iteration on the GPU for the error of X and f
+    log("precision table done")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, solve_acc = cpu_leg(T, torch, inp, wl, mine, ranks, dev)
+        if acc is not None:
+            acc["oracle_solve"] = solve_acc
+
+    log("cpu leg done")
+    secondary = None
+    if rank == 0 and args.secondary > 0 and wl.nr == PRECISION_FORM.nr:
+        del runner, inp
+        torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        serve = serving_leg(T, torch, args.serving, args.seed, dev)
+        T.tlr_mdd_trim_pool(0)
+        secondary = secondary_leg(T, torch, args, dev)
+
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return
     line = {
         "metric": "freq-solves/s", "value": round(value, 4), "unit": "freq-solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
-        "streams": nstream,
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+        "vs_baseline": None, "dtype": "f32" if prec == T.TLR_PREC_FP32 else "bf16x3",
         "data": "synthetic",
-        "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "
-                               "64 frequencies, tile 256, rank 4->48, low-rank diagonal, 10 dB SNR",
-                   "nr": NR, "ns": NR, "frequencies_per_gpu": nfreq, "tile": TILE,
-                   "ranks": f"{RANK_LO}->{RANK_HI} linear", "iters_per_solve": ITERS_PER_SOLVE,
-                   "precision": args.precision,
-                   "l2": "inputs larger than L2 (each 4096x4096 complex64 panel is 134 MB; 64 frequencies cycled)",
-                   "parallelism": f"frequency sharding x{world}"},
-        "gflops": round(total_flops / (ms / 1e3) / 1e9, 1),
+        "config": {"workload": wl.name, "nr": wl.nr, "ns": wl.nr, "grid": list(wl.grid),
+                   "frequencies_per_gpu": wl.nfreq, "frequencies_per_step": wl.batch,
+                   "tile": wl.tile, "ranks": f"{wl.rank_lo}->{wl.rank_hi} linear",
+                   "iters_per_solve": ITERS_PER_SOLVE, "precision": args.precision, "streams": nstream,
+                   "step": "one batch of frequencies (every nfreq/batch-th), each solved from its raw D, U "
+                           "through a handle created for it (data step, packing, solve)",
+                   "l2": "inputs larger than L2 (each 9216x9216 complex64 panel is 679 MB; every step reads "
+                         "8 frequencies' D and U, 10.9 GB)" if wl.nr == PRECISION_FORM.nr else
+                         "inputs larger than L2 (134 MB panels)",
+                   "parallelism": f"frequency sharding x{world}", "launches": "plain (no CUDA graph) at nr >= 8192",
+                   "generation_s": round(t_gen, 1)},
+        "gflops": round(my_flops * world / (ms / 1e3) / 1e9, 1),
         "latency_ms": {"p50": percentile(lat_ms, 50), "p99": percentile(lat_ms, 99)},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "accuracy": acc, "fp32_comparison": cmp,
+        "results": {"frequencies": len(gathered or []), "ranks_gathered": world,
+                    "all_ok": all(r["status"] == 0 and r["iters"] == ITERS_PER_SOLVE for r in gathered or []),
+                    "f_final_over_f0_median": statistics.median(r["f_final"] / r["f0"] for r in gathered)
+                    if gathered else None},
     }
-    if bsolve is not None:
-        line["benchmark_solver"] = bsolve
-    if gsolve is not None:
-        line["general_form"] = gsolve
-    if tsolve is not None:
-        line["nonuniform_tiles"] = tsolve
-    if serve is not None:
-        line["serving"] = serve
+    if secondary is not None:
+        line["secondary"] = secondary
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def serving_leg(T, torch, n, seed, dev):
-    """The serving mix: per-frequency solve requests with nr = ns uniform over
-    {1024, 2048, 4096, 8192}, tile over {128, 256, 512}, rank log-uniform 2-64,
-    Poisson arrivals.  Measures one-at-a-time throughput on the FP32 and the
-    tensor-core paths, then serves the stream with continuous batching (4
-    slots, HBM budget 200 GB) at 90% of the tensor-core one-at-a-time capacity
-    and at 0.7x and 1.3x the FP32 one-at-a-time capacity, and reports p50 /
-    p99 latency.  One seeded D, U per problem size is shared
-    by the requests of that size (work does not depend on the values)."""
+def precision_table(T, torch, inp, wl, mine, args, dev):
+    """Per frequency: relative error of Y = X_h Dfrak and of the column misfit
+    at the seeded start point against the FP64 oracle (sampled source columns,
+    both paths), and 30-iteration solves on both paths from that start point:
+    the relative difference of their X and final misfit, and their times."""
+    from oracle import tlr
     import tlr_synth as synth
-    from paper_2412_14973_gb300 import serving
-    reqs = synth.request_stream(n, 1.0, seed + 17)
-    g = torch.Generator(device=dev).manual_seed(seed + 18)
-    pool = {}
-    for r in reqs:
-        if r.nr not in pool:
-            re = torch.randn((r.nr, r.nr), generator=g, device=dev)
-            im = torch.randn((r.nr, r.nr), generator=g, device=dev)
-            Dm = (torch.complex(re, im) / math.sqrt(2 * r.nr)).to(torch.complex64)
-            re = torch.randn((r.nr, r.nr), generator=g, device=dev)
-            im = torch.randn((r.nr, r.nr), generator=g, device=dev)
-            Um = (torch.complex(re, im) / math.sqrt(2 * r.nr)).to(torch.complex64)
-            pool[r.nr] = (Dm, Um)
+    pick = sorted({mine[int(round(i * (len(mine) - 1) / max(1, args.accuracy - 1)))]
+                   for i in range(args.accuracy)})
+    rows = []
+    t_fp32 = t_tc = 0.0
+    st = torch.cuda.current_stream(dev)
+    for f in pick:
+        sl = inp.slot_of[f]
+        k = inp.ranks[f]
+        D0 = inp.D[sl].cpu().numpy()
+        U0 = inp.U[sl].cpu().numpy()
+        cols = np.sort(synth.rng(f + 1).choice(wl.nr, 32, replace=False))
+        prob, lay, alpha = oracle_problem(D0, U0, wl, k, cols=cols)
+        th0 = inp.th0[sl]
+        th0n = th0.cpu().numpy().astype(np.complex128)
+        Yo = tlr.apply(th0n, lay, prob.Dt)
+        Ro = Yo - prob.Ut
+        fo = 0.5 * float(np.vdot(Ro, Ro).real)
+        row = {"freq": f, "rank": k}
+        X = {}
+        for name, p in (("bf16x3", T.TLR_PREC_BF16X3), ("fp32", T.TLR_PREC_FP32)):
+            d = inp.desc(T, f, p)
+            d.alpha = alpha
+            h = T.tlr_mdd_create(d, inp.D[sl], inp.U[sl], st)
+            Y = torch.empty((wl.nr, wl.nr), dtype=torch.complex64, device=dev)
+            T.tlr_mdd_apply(h, th0, Y)
+            Yc = Y[:, torch.from_numpy(cols).to(dev)].cpu().numpy().astype(np.complex128)
+            del Y
+            Rc = Yc - prob.Ut
+            fc = 0.5 * float(np.vdot(Rc, Rc).real)
+            row[f"apply_rel_err_{name}"] = float(np.linalg.norm(Yc - Yo) / np.linalg.norm(Yo))
+            row[f"column_misfit_rel_err_{name}"] = abs(fc - fo) / fo
+            th = th0.clone()
+            torch.cuda.synchronize()
+            s = T.tlr_mdd_solve(h, th, T.solve_opts())
+            row[f"solve_ms_{name}"] = round(s.gpu_ms, 1)
+            row[f"f_final_{name}"] = s.f_hist[s.n_hist - 1]
+            if name == "bf16x3":
+                t_tc += s.gpu_ms
+            else:
+                t_fp32 += s.gpu_ms
+            Xd = torch.empty((wl.nr, wl.nr), dtype=torch.complex64, device=dev)
+            T.tlr_mdd_unpermute_dense(h, th, Xd)
+            X[name] = Xd
+            T.tlr_mdd_destroy(h)
+        row["solve_X_rel_diff_tc_vs_fp32"] = float((X["bf16x3"] - X["fp32"]).norm() / X["fp32"].norm())
+        row["solve_misfit_rel_diff_tc_vs_fp32"] = abs(row["f_final_bf16x3"] - row["f_final_fp32"]) / \
+            row["f_final_fp32"]
+        del X
+        rows.append(row)
+    worst = lambda key: max(r[key] for r in rows)  # noqa: E731
+    acc = {"per_frequency": rows,
+           "bounds": "per application: 1e-5 (FP32), 1e-3 (tensor cores) relative; final X: 1e-3",
+           "worst_apply_rel_err_bf16x3": worst("apply_rel_err_bf16x3"),
+           "worst_apply_rel_err_fp32": worst("apply_rel_err_fp32"),
+           "worst_solve_X_rel_diff_tc_vs_fp32": worst("solve_X_rel_diff_tc_vs_fp32"),
+           "within_bounds": worst("apply_rel_err_bf16x3") <= 1e-3 and worst("apply_rel_err_fp32") <= 1e-5
+           and worst("solve_X_rel_diff_tc_vs_fp32") <= 1e-3,
+           "sample": "32 seeded source columns per frequency for the oracle (its work is per column)"}
+    cmp = {"frequencies": pick, "fp32_simt_freq_solves_per_s": round(len(pick) / (t_fp32 / 1e3), 4),
+           "tensor_core_freq_solves_per_s": round(len(pick) / (t_tc / 1e3), 4),
+           "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
+           "accuracy": {"worst_apply_rel_err_fp32": acc["worst_apply_rel_err_fp32"],
+                        "worst_apply_rel_err_bf16x3": acc["worst_apply_rel_err_bf16x3"],
+                        "worst_solve_X_rel_diff": acc["worst_solve_X_rel_diff_tc_vs_fp32"]},
+           "note": "one solve at a time on one stream, device time; equal accuracy: both within the bounds"}
+    return acc, cmp
 
-    def make(prec, arrivals):
-        out = []
-        for r, t in zip(reqs, arrivals):
-            d = T.desc(r.nr, r.nr, r.tile, rank=r.rank, nx=r.nx, ny=r.ny, diag_mode=T.TLR_DIAG_RULE,
-                       precision=prec)
-            nth = T.tlr_mdd_theta_size(d)
-            gg = torch.Generator(device=dev).manual_seed(r.seed)
-            th = (torch.randn(nth, generator=gg, device=dev) + 1j * torch.randn(nth, generator=gg, device=dev))
-            th = (th * (0.1 / math.sqrt(r.tile * max(1, r.rank)))).to(torch.complex64)
-            out.append(serving.SolveRequest(r.rid, t, d, pool[r.nr][0], pool[r.nr][1], th, T.solve_opts()))
-        return out
 
-    budget = 200 << 30
-    zero = [0.0] * n
-    t0 = time.perf_counter()
-    res_fp32 = serving.Server(budget, max_active=1).run(make(T.TLR_PREC_FP32, zero), realtime=False)
-    t_fp32 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    res_tc1 = serving.Server(budget, max_active=1).run(make(T.TLR_PREC_BF16X3, zero), realtime=False)
-    t_tc1 = time.perf_counter() - t0
-    rate = 0.9 * n / t_tc1
-    gg = np.random.default_rng(seed + 19)
-    arrivals = list(np.cumsum(gg.exponential(1.0 / rate, n)))
-    srv = serving.Server(budget, max_active=4)
-    t0 = time.perf_counter()
-    res = srv.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
-    t_srv = time.perf_counter() - t0
-    ok = [r for r in res if r.status == 0]
-    pc = serving.percentiles(res)
-    same = all(torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, res) if a.status == 0 and b.status == 0)
-    # the tensor-core server at 0.7x and 1.3x the FP32 path's one-at-a-time
-    # capacity (the FP32 path alone would keep up with the first and not the second)
-    loads = []
-    for x in (0.7, 1.3):
-        rx = x * n / t_fp32
-        ax = list(np.cumsum(np.random.default_rng(seed + 20).exponential(1.0 / rx, n)))
-        sx = serving.Server(budget, max_active=4)
+def cpu_leg(T, torch, inp, wl, mine, ranks, dev):
+    """One full L-BFGS iteration of the FP64 oracle at the frequency nearest
+    the mean rank, timed on the host cores and scaled to a 30-iteration solve
+    (every iteration does the same work); the same iteration on the GPU gives
+    the relative error of X and of f against the oracle."""
+    from oracle import operator
+    kmean = sum(ranks[f] for f in mine) / len(mine)
+    f = min(mine, key=lambda x: (abs(ranks[x] - kmean), x))
+    sl = inp.slot_of[f]
+    k = ranks[f]
+    D0 = inp.D[sl].cpu().numpy()
+    U0 = inp.U[sl].cpu().numpy()
+    prob, lay, alpha = oracle_problem(D0, U0, wl, k)
+    del D0, U0
+    th0 = inp.th0[sl].cpu().numpy().astype(np.complex128)
+    # the oracle's own first forward product and gradient are timed apart from
+    # the iteration (line-search products + gradient at the new point), so the
+    # 30-iteration figure is first + 30 x iteration, both measured
+    calls = []
+    fgrad = prob.fgrad
+
+    def timed_fgrad(theta):
         t0 = time.perf_counter()
-        rs = sx.run(make(T.TLR_PREC_BF16X3, ax), realtime=True)
-        tx = time.perf_counter() - t0
-        px = serving.percentiles(rs)
-        loads.append({"x_fp32_capacity": x, "arrival_rate_hz": round(rx, 3),
-                      "completed": sum(1 for r in rs if r.status == 0), "served_solves_per_s": round(n / tx, 3),
-                      "p50_ms": round(1e3 * px[50], 1) if px[50] else None,
-                      "p99_ms": round(1e3 * px[99], 1) if px[99] else None})
-    return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
-            "fp32_one_at_a_time_solves_per_s": round(n / t_fp32, 3),
-            "tc_one_at_a_time_solves_per_s": round(n / t_tc1, 3),
-            "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
-            "p50_ms": round(1e3 * pc[50], 1) if pc[50] else None,
-            "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,
-            "peak_active": srv.peak_active, "peak_budget_gb": round(srv.peak_used / 2**30, 1),
-            "results_identical_alone_and_in_mix": bool(same),
-            "fp32_capacity_load_points": loads,
-            "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson"}
+        r = fgrad(theta)
+        calls.append(time.perf_counter() - t0)
+        return r
+
+    prob.fgrad = timed_fgrad
+    secs, th_or, st_or = run_oracle_solve(prob, th0, 1)
+    t_first = calls[0]
+    t_iter = secs - t_first
+    per_solve = t_first + ITERS_PER_SOLVE * t_iter
+    cpu = {"value": round(1.0 / per_solve, 7), "unit": "freq-solves/s", "cores": blas_threads(),
+           "kind": "oracle",
+           "sample": (f"frequency {f} (rank {k}, the mean rank {kmean:.1f}): one full L-BFGS iteration of the "
+                      f"FP64 TLR-structured oracle in {secs:.1f} s (first forward product and gradient "
+                      f"{t_first:.1f} s, then the iteration {t_iter:.1f} s: line-search products and the "
+                      f"gradient at the new point); a {ITERS_PER_SOLVE}-iteration solve = first + "
+                      f"{ITERS_PER_SOLVE} x iteration = {per_solve:.0f} s")}
+    d = inp.desc(T, f, T.TLR_PREC_BF16X3)
+    d.alpha = alpha
+    h = T.tlr_mdd_create(d, inp.D[sl], inp.U[sl], torch.cuda.current_stream(dev))
+    thg = inp.th0[sl].clone()
+    sg = T.tlr_mdd_solve(h, thg, T.solve_opts(stages=1, admm_iters=1, lbfgs_iters=1))
+    T.tlr_mdd_destroy(h)
+    Xo = operator.assemble_xh(th_or, lay)
+    Xg = operator.assemble_xh(thg.cpu().numpy().astype(np.complex128), lay)
+    acc = {"frequency": f, "rank": k, "iters": 1, "path": "bf16x3",
+           "rel_err_X_vs_fp64_oracle": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
+           "rel_err_f_vs_fp64_oracle": abs(sg.f_hist[0] - st_or.f_hist[0]) / st_or.f_hist[0]}
+    return cpu, acc
 
 
-def reference_arm(args, world, rank):
-    """The FP64 CPU oracle on this workload's config, a bounded sample per step."""
+def secondary_leg(T, torch, args, dev):
+    """The nr = 4096 batched workload (64 frequencies, rank 4 -> 48), reported
+    beside the headline: one handle per frequency kept across steps (its solve
+    recorded once as a CUDA graph), every step re-running each frequency's data
+    step and solve on 4 streams."""
+    os.environ["TLR_MDD_GRAPHS"] = "1"
+    wl = BATCHED
+    ranks = wl.ranks(wl.nfreq)
+    freqs = list(range(wl.nfreq))
+    inp = Inputs(T, torch, wl, freqs, ranks, args.seed + 1, dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+    main = torch.cuda.current_stream(dev)
+    hs = [T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_BF16X3), inp.D[f], inp.U[f], streams[f % 4]) for f in freqs]
+    theta = [t.clone() for t in inp.th0]
+    opts = T.solve_opts()
+
+    def step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for s_ in streams:
+            s_.wait_event(e0)
+        for f in freqs:
+            T.tlr_mdd_set_data(hs[f], inp.D[f], inp.U[f], T.TLR_MEM_DEVICE)
+            with torch.cuda.stream(streams[f % 4]):
+                theta[f].copy_(inp.th0[f])
+            T.tlr_mdd_solve_async(hs[f], theta[f], opts)
+        for f in freqs:
+            T.tlr_mdd_solve_wait(hs[f])
+        for s_ in streams:
+            ev = torch.cuda.Event()
+            ev.record(s_)
+            main.wait_event(ev)
+        e1.record(main)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    step()          # records the solve graphs
+    ms = sum(step() for _ in range(args.secondary))
+    for h in hs:
+        T.tlr_mdd_destroy(h)
+    fl = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, k) for k in ranks) * args.secondary
+    return {"workload": wl.name, "value": round(wl.nfreq * args.secondary / (ms / 1e3), 3),
+            "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
+            "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": 4,
+            "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency"}
+
+
+def reference_arm(args, wl, world, rank):
+    """The FP64 CPU oracle on this workload's config: each step is a bounded
+    sample, the forward product and gradient of one frequency at the mean rank
+    restricted to a subset of the source columns (the oracle's work is the
+    same for every column), scaled to a 30-iteration solve of the whole
+    frequency."""
     if rank != 0:
         return
     import tlr_synth as synth
-    from oracle import hilbert
-    k0 = rank_of(0, args.freqs)
-    # one frequency of the same recipe, generated on the host
-    D0 = synth.make_d(NR, NR, 1, args.seed, haar_max=1024)[0]
-    lay_perm = hilbert.perm(*GRID)
-    from oracle import layout, operator
-    lay = layout.make_layout(NR, TILE, k0, "rule")
-    th_true = synth.planted_theta(NR, TILE, k0, lay.dense, args.seed + 1)
-    X = operator.unpermute(operator.assemble_xh(th_true, lay), lay_perm)
-    Y = D0.astype(np.complex128) @ X
-    nz = synth.noise(Y.shape, args.seed + 2)
-    U0 = (Y + np.linalg.norm(Y) / np.linalg.norm(nz) * 10 ** (-SNR_DB / 20) * nz).astype(np.complex64)
-    prob, lay, perm, alpha = oracle_sample(D0, U0, k0, args.oracle_iters)
-    th0 = 0.1 * synth.planted_theta(NR, TILE, k0, lay.dense, args.seed + 3)
-    for _ in range(args.warmup):
-        run_oracle(prob, th0, args.oracle_iters)
-    t = 0.0
-    for _ in range(args.steps):
-        s, _, _ = run_oracle(prob, th0, args.oracle_iters)
-        t += s
-    ranks = [rank_of(f, args.freqs) for f in range(args.freqs)]
+    from oracle import hilbert, layout, operator, tlr
+    ranks = wl.ranks(wl.nfreq)
     kmean = sum(ranks) / len(ranks)
-    per_solve = (t / args.steps) * (ITERS_PER_SOLVE / args.oracle_iters) * (kmean / k0)
+    k0 = min(ranks, key=lambda k: abs(k - kmean))
+    n = wl.nr
+    cols = args.oracle_cols
+    g = synth.rng(args.seed)
+    # one frequency of the same recipe on the host, restricted to `cols` sources:
+    # those rows of D = Q diag(sigma e^{i phi}) W^H and of U = D X + noise
+    Q = synth.phase_dft_unitary(n, g)[:cols]
+    W = synth.phase_dft_unitary(n, g)
+    sig = synth.singular_decay(n)
+    ph = np.exp(2j * np.pi * g.random(n))
+    Ds = (Q * (sig * ph)[None, :]) @ W.conj().T
+    del Q, W
+    lay = layout.make_layout(n, wl.tile, k0, "rule")
+    perm = hilbert.perm(*wl.grid)
+    th_true = synth.planted_theta(n, wl.tile, k0, lay.dense, args.seed + 1)
+    X = operator.unpermute(operator.assemble_xh(th_true, lay), perm)
+    Ys = Ds @ X
+    del X
+    nz = synth.noise(Ys.shape, args.seed + 2)
+    Us = (Ys + np.linalg.norm(Ys) / np.linalg.norm(nz) * 10 ** (-wl.snr_db / 20) * nz).astype(np.complex64)
+    Ds = Ds.astype(np.complex64)
+    Dh, Uh, _ = operator.normalise(Ds, Us, perm)
+    Dt, Ut = Dh.T.copy(), Uh.T.copy()
+    th0 = 0.1 * synth.planted_theta(n, wl.tile, k0, lay.dense, args.seed + 3)
+
+    from oracle import solver
+    prob = solver.Problem(lay, Dt, Ut)
+    d = 0.01 * synth.cn(synth.rng(args.seed + 4), lay.size)
+
+    def one():
+        t0 = time.perf_counter()
+        prob.fgrad(th0)
+        t1 = time.perf_counter()
+        prob.coefficients(th0, d, 1.0, th0)
+        return t1 - t0, time.perf_counter() - t1
+
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    t_f = sum(a for a, _ in ts) / len(ts)
+    t_c = sum(b for _, b in ts) / len(ts)
+    per_step = t_f + t_c
+    # the oracle's solve: a first forward product and gradient, then per
+    # iteration the line-search products and the gradient at the new point
+    scale = n / cols
+    per_solve = scale * (t_f + ITERS_PER_SOLVE * (t_f + t_c))
     v = 1.0 / per_solve
-    sample = (f"per step: frequency 0 (rank {k0}), {args.oracle_iters} L-BFGS iterations of the FP64 "
-              f"TLR-structured oracle, scaled to a {ITERS_PER_SOLVE}-iteration solve at mean rank {kmean:.1f}")
-    line = {"impl": "reference", "metric": "freq-solves/s", "value": round(v, 6), "unit": "freq-solves/s",
+    sample = (f"per step: the FP64 TLR-structured oracle's forward product and gradient ({t_f:.2f} s) and "
+              f"line-search products ({t_c:.2f} s) at rank {k0} (the mean rank) on {cols} of the {n} source "
+              f"columns (its work is the same for every column); a {ITERS_PER_SOLVE}-iteration solve of the "
+              f"whole frequency = {n}/{cols} x (first + {ITERS_PER_SOLVE} x iteration)")
+    line = {"impl": "reference", "metric": "freq-solves/s", "value": round(v, 7), "unit": "freq-solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * t / args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": round(1e3 * per_step, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "plain-method batched frequencies: nr=ns=4096 (64x64 grid, Hilbert order), "
-                                   "64 frequencies, tile 256, rank 4->48, low-rank diagonal, 10 dB SNR",
-                       "nr": NR, "ns": NR, "frequencies_per_gpu": args.freqs, "tile": TILE,
-                       "ranks": f"{RANK_LO}->{RANK_HI} linear", "iters_per_solve": ITERS_PER_SOLVE,
+            "config": {"workload": wl.name, "nr": wl.nr, "ns": wl.nr, "grid": list(wl.grid),
+                       "frequencies_per_gpu": wl.nfreq, "frequencies_per_step": wl.batch, "tile": wl.tile,
+                       "ranks": f"{wl.rank_lo}->{wl.rank_hi} linear", "iters_per_solve": ITERS_PER_SOLVE,
                        "precision": "fp64 (oracle)", "parallelism": f"frequency sharding x{world}"},
-            "cpu_baseline": {"value": round(v, 6), "unit": "freq-solves/s", "cores": blas_threads(),
+            "cpu_baseline": {"value": round(v, 7), "unit": "freq-solves/s", "cores": blas_threads(),
                              "kind": "oracle", "sample": sample},
-            "e2e": {"value": round(v, 6), "unit": "freq-solves/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": round(v, 7), "unit": "freq-solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
