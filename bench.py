@@ -398,6 +398,11 @@ def main():
     ap.add_argument("--accuracy", type=int, default=4, help="frequencies of the precision table (0: skip)")
     ap.add_argument("--freqs", type=int, default=0,
                     help="frequencies per GPU (0: the workload's; a multiple of its batch)")
+    ap.add_argument("--serving", type=int, default=120,
+                    help="requests of the serving mix (nr 1024-8192, tile 128-512, rank 2-64) served with "
+                         "continuous batching (0: skip)")
+    ap.add_argument("--small-configs", type=int, default=200,
+                    help="solves timed for each of the nr=256 and nr=1024 workloads (0: skip)")
     ap.add_argument("--secondary", type=int, default=2,
                     help="timed steps of the nr=4096 batched workload reported beside the headline (0: skip)")
     args = ap.parse_args()
@@ -566,7 +571,7 @@ def main():
     log("e2e leg done")
     acc = None
     cmp = None
-    if rank == 0 and args.accuracy > 0 and not args.no_cpu:
+    if rank == 0 and args.accuracy > 0:
         acc, cmp = precision_table(T, torch, inp, wl, mine, args, dev)
 
     # CPU oracle baseline: one full L-BFGS iteration (the solve's first forward
@@ -588,6 +593,20 @@ def main():
         torch.cuda.empty_cache()
         T.tlr_mdd_trim_pool(0)
         secondary = secondary_leg(T, torch, args, dev)
+
+    peaks = measure_peaks(torch, dev) if rank == 0 else None
+    small = None
+    if rank == 0 and args.small_configs > 0:
+        small = small_configs_leg(T, torch, args.small_configs, args.seed, dev)
+        log("small workloads done")
+
+    serve = None
+    if rank == 0 and args.serving > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        T.tlr_mdd_trim_pool(0)
+        serve = serving_leg(T, torch, args.serving, args.seed, dev)
+        log("serving leg done")
 
     if rank != 0:
         if dist:
@@ -621,6 +640,12 @@ def main():
     }
     if secondary is not None:
         line["secondary"] = secondary
+    if serve is not None:
+        line["serving"] = serve
+    if peaks is not None:
+        line["peaks_measured"] = peaks
+    if small is not None:
+        line["small_workloads"] = small
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -636,7 +661,7 @@ def precision_table(T, torch, inp, wl, mine, args, dev):
     pick = sorted({mine[int(round(i * (len(mine) - 1) / max(1, args.accuracy - 1)))]
                    for i in range(args.accuracy)})
     rows = []
-    t_fp32 = t_tc = 0.0
+    t_path = {"bf16x3": 0.0, "tf32": 0.0, "fp32": 0.0}
     st = torch.cuda.current_stream(dev)
     for f in pick:
         sl = inp.slot_of[f]
@@ -652,7 +677,7 @@ def precision_table(T, torch, inp, wl, mine, args, dev):
         fo = 0.5 * float(np.vdot(Ro, Ro).real)
         row = {"freq": f, "rank": k}
         X = {}
-        for name, p in (("bf16x3", T.TLR_PREC_BF16X3), ("fp32", T.TLR_PREC_FP32)):
+        for name, p in (("bf16x3", T.TLR_PREC_BF16X3), ("tf32", T.TLR_PREC_TF32), ("fp32", T.TLR_PREC_FP32)):
             d = inp.desc(T, f, p)
             d.alpha = alpha
             h = T.tlr_mdd_create(d, inp.D[sl], inp.U[sl], st)
@@ -669,34 +694,40 @@ def precision_table(T, torch, inp, wl, mine, args, dev):
             s = T.tlr_mdd_solve(h, th, T.solve_opts())
             row[f"solve_ms_{name}"] = round(s.gpu_ms, 1)
             row[f"f_final_{name}"] = s.f_hist[s.n_hist - 1]
-            if name == "bf16x3":
-                t_tc += s.gpu_ms
-            else:
-                t_fp32 += s.gpu_ms
+            t_path[name] += s.gpu_ms
             Xd = torch.empty((wl.nr, wl.nr), dtype=torch.complex64, device=dev)
             T.tlr_mdd_unpermute_dense(h, th, Xd)
             X[name] = Xd
             T.tlr_mdd_destroy(h)
-        row["solve_X_rel_diff_tc_vs_fp32"] = float((X["bf16x3"] - X["fp32"]).norm() / X["fp32"].norm())
-        row["solve_misfit_rel_diff_tc_vs_fp32"] = abs(row["f_final_bf16x3"] - row["f_final_fp32"]) / \
-            row["f_final_fp32"]
+        for name in ("bf16x3", "tf32"):
+            sfx = "tc" if name == "bf16x3" else name
+            row[f"solve_X_rel_diff_{sfx}_vs_fp32"] = float((X[name] - X["fp32"]).norm() / X["fp32"].norm())
+            row[f"solve_misfit_rel_diff_{sfx}_vs_fp32"] = abs(row[f"f_final_{name}"] - row["f_final_fp32"]) / \
+                row["f_final_fp32"]
         del X
         rows.append(row)
     worst = lambda key: max(r[key] for r in rows)  # noqa: E731
     acc = {"per_frequency": rows,
            "bounds": "per application: 1e-5 (FP32), 1e-3 (tensor cores) relative; final X: 1e-3",
            "worst_apply_rel_err_bf16x3": worst("apply_rel_err_bf16x3"),
+           "worst_apply_rel_err_tf32": worst("apply_rel_err_tf32"),
            "worst_apply_rel_err_fp32": worst("apply_rel_err_fp32"),
            "worst_solve_X_rel_diff_tc_vs_fp32": worst("solve_X_rel_diff_tc_vs_fp32"),
+           "worst_solve_X_rel_diff_tf32_vs_fp32": worst("solve_X_rel_diff_tf32_vs_fp32"),
            "within_bounds": worst("apply_rel_err_bf16x3") <= 1e-3 and worst("apply_rel_err_fp32") <= 1e-5
            and worst("solve_X_rel_diff_tc_vs_fp32") <= 1e-3,
+           "tf32_within_bounds": worst("apply_rel_err_tf32") <= 1e-3 and worst("solve_X_rel_diff_tf32_vs_fp32") <= 1e-3,
            "sample": "32 seeded source columns per frequency for the oracle (its work is per column)"}
-    cmp = {"frequencies": pick, "fp32_simt_freq_solves_per_s": round(len(pick) / (t_fp32 / 1e3), 4),
-           "tensor_core_freq_solves_per_s": round(len(pick) / (t_tc / 1e3), 4),
-           "speedup_tc_vs_fp32": round(t_fp32 / t_tc, 3),
+    rate = {k: round(len(pick) / (v / 1e3), 4) for k, v in t_path.items()}
+    cmp = {"frequencies": pick, "fp32_simt_freq_solves_per_s": rate["fp32"],
+           "tensor_core_freq_solves_per_s": rate["bf16x3"], "tf32_freq_solves_per_s": rate["tf32"],
+           "speedup_tc_vs_fp32": round(t_path["fp32"] / t_path["bf16x3"], 3),
+           "speedup_tf32_vs_fp32": round(t_path["fp32"] / t_path["tf32"], 3),
            "accuracy": {"worst_apply_rel_err_fp32": acc["worst_apply_rel_err_fp32"],
                         "worst_apply_rel_err_bf16x3": acc["worst_apply_rel_err_bf16x3"],
-                        "worst_solve_X_rel_diff": acc["worst_solve_X_rel_diff_tc_vs_fp32"]},
+                        "worst_apply_rel_err_tf32": acc["worst_apply_rel_err_tf32"],
+                        "worst_solve_X_rel_diff": acc["worst_solve_X_rel_diff_tc_vs_fp32"],
+                        "worst_solve_X_rel_diff_tf32": acc["worst_solve_X_rel_diff_tf32_vs_fp32"]},
            "note": "one solve at a time on one stream, device time; equal accuracy: both within the bounds"}
     return acc, cmp
 
@@ -800,6 +831,199 @@ def secondary_leg(T, torch, args, dev):
             "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
             "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": 4,
             "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency"}
+
+
+def serving_leg(T, torch, n, seed, dev):
+    """The serving mix: n per-frequency solve requests, nr = ns uniform over
+    {1024, 2048, 4096, 8192}, tile over {128, 256, 512}, rank log-uniform
+    2-64, BF16x3 tensor cores, 30-iteration solves.  Measured: one request at
+    a time on the tensor cores (all n) and on the FP32 SIMT path (the first
+    m of them), then the whole stream served with continuous batching (4
+    slots, 120 GB budget, shape-keyed handle reuse) at Poisson arrivals of 90%
+    of the tensor cores' one-at-a-time capacity: solves/s, p50 / p99 latency
+    from arrival to result, and whether every served result equals its
+    one-at-a-time result bit for bit.  One seeded D, U per size is shared by
+    the requests of that size (the work does not depend on the values)."""
+    import tlr_synth as synth
+    from paper_2412_14973_gb300 import serving
+    reqs = synth.request_stream(n, 1.0, seed + 17)
+    g = torch.Generator(device=dev).manual_seed(seed + 18)
+    pool = {}
+    for r in reqs:
+        if r.nr not in pool:
+            mats = []
+            for _ in range(2):
+                re = torch.randn((r.nr, r.nr), generator=g, device=dev)
+                im = torch.randn((r.nr, r.nr), generator=g, device=dev)
+                mats.append((torch.complex(re, im) / math.sqrt(2 * r.nr)).to(torch.complex64))
+            pool[r.nr] = tuple(mats)
+
+    def make(prec, arrivals, subset=None):
+        out = []
+        for r, t in zip(reqs[:subset], arrivals):
+            d = T.desc(r.nr, r.nr, r.tile, rank=r.rank, nx=r.nx, ny=r.ny, diag_mode=T.TLR_DIAG_RULE,
+                       precision=prec)
+            nth = T.tlr_mdd_theta_size(d)
+            gg = torch.Generator(device=dev).manual_seed(r.seed)
+            th = (torch.randn(nth, generator=gg, device=dev) + 1j * torch.randn(nth, generator=gg, device=dev))
+            th = (th * (0.1 / math.sqrt(r.tile * max(1, r.rank)))).to(torch.complex64)
+            out.append(serving.SolveRequest(r.rid, t, d, pool[r.nr][0], pool[r.nr][1], th, T.solve_opts()))
+        return out
+
+    budget = 120 << 30
+    m = min(n, 24)
+    zero = [0.0] * n
+    s1 = serving.Server(budget, max_active=1, reuse=False)
+    t0 = time.perf_counter()
+    res_fp32 = s1.run(make(T.TLR_PREC_FP32, zero, m), realtime=False)
+    t_fp32 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_tc1 = s1.run(make(T.TLR_PREC_BF16X3, zero), realtime=False)
+    t_tc1 = time.perf_counter() - t0
+    t_tc1_m = sum(r.finished - r.admitted for r in res_tc1[:m])
+    rate = 0.9 * n / t_tc1
+    arrivals = list(np.cumsum(np.random.default_rng(seed + 19).exponential(1.0 / rate, n)))
+    srv = serving.Server(budget, max_active=4)
+    t0 = time.perf_counter()
+    res = srv.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
+    t_srv = time.perf_counter() - t0
+    ok = [r for r in res if r.status == 0]
+    pc = serving.percentiles(res)
+    same = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, res))
+    srv.close()
+    # the same stream with lockstep batches of up to 4 same-size requests per slot
+    srvb = serving.Server(budget, max_active=4, batch_max=4)
+    t0 = time.perf_counter()
+    resb = srvb.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
+    t_b = time.perf_counter() - t0
+    pcb = serving.percentiles(resb)
+    sameb = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, resb))
+    srvb.close()
+    batched = {"tc_served_solves_per_s": round(sum(1 for r in resb if r.status == 0) / t_b, 3),
+               "p50_ms": round(1e3 * pcb[50], 1) if pcb[50] else None,
+               "p99_ms": round(1e3 * pcb[99], 1) if pcb[99] else None,
+               "batches": srvb.batches, "results_identical_alone_and_in_batches": bool(sameb),
+               "note": "same arrivals; requests of one size admitted together share one launch per contraction"}
+    sizes = collections_counter(r.nr for r in reqs)
+    return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
+            "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
+            "p50_ms": round(1e3 * pc[50], 1) if pc[50] else None,
+            "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,
+            "tc_one_at_a_time_solves_per_s": round(n / t_tc1, 3),
+            "fp32_one_at_a_time_solves_per_s": round(m / t_fp32, 3),
+            "tc_one_at_a_time_solves_per_s_same_subset": round(m / t_tc1_m, 3),
+            "speedup_tc_vs_fp32_one_at_a_time": round(t_fp32 / t_tc1_m, 2),
+            "fp32_subset": m,
+            "peak_active": srv.peak_active, "peak_budget_gb": round(srv.peak_used / 2**30, 1),
+            "handles_created": srv.created, "handles_reused": srv.reused, "handles_evicted": srv.evicted,
+            "results_identical_alone_and_in_mix": bool(same),
+            "lockstep_batches": batched,
+            "sizes": dict(sorted(sizes.items())),
+            "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson; "
+                   "latency = arrival to result on the host clock"}
+
+
+def measure_peaks(torch, dev):
+    """FP32 (CUDA cores), TF32 and BF16 (tensor cores) and FP64 matrix-multiply
+    rates of this GPU, measured like the driver's peaks: torch.matmul (cuBLAS)
+    on square operands, CUDA events, best of several."""
+    out = {}
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, allow, reps in (("fp32_simt", torch.float32, 8192, False, 3),
+                                        ("tf32_tensor", torch.float32, 8192, True, 5),
+                                        ("bf16_tensor", torch.bfloat16, 8192, False, 5),
+                                        ("fp64", torch.float64, 4096, False, 3)):
+            torch.backends.cuda.matmul.allow_tf32 = allow
+            a = torch.randn((n, n), device=dev, dtype=dt)
+            b = torch.randn((n, n), device=dev, dtype=dt)
+            torch.matmul(a, b)
+            best = 1e30
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name + "_tflops"] = round(2.0 * n ** 3 / (best / 1e3) / 1e12, 2)
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    out["method"] = "torch.matmul (cuBLAS), n = 8192 (FP64: 4096), 2 n^3 flops, best of 3-5, CUDA events"
+    return out
+
+
+def small_configs_leg(T, torch, n, seed, dev):
+    """The two small workloads, solve by solve (CUDA-graph replays on one
+    stream, device time per solve, p50 / p99 over n solves), on both paths:
+    the plain method on one frequency (nr = ns = 256, 16 x 16 grid, tile 64,
+    rank 8, dense diagonal tiles, 20 dB, 30 iterations: latency bound), and
+    the differentiation form's sparse solve (nr = 1024, 32 x 32 grid, tile 128,
+    rank 12, low-rank diagonals, 717 of 1024 sources kept, 5 dB, 16
+    frequencies cycled)."""
+    import tlr_synth as synth
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for name, nx, b, k, mode, snr, nfreq, keep in (
+            ("plain_nr256", 16, 64, 8, T.TLR_DIAG_DENSE, 20.0, 1, None),
+            ("sparse_nr1024", 32, 128, 12, T.TLR_DIAG_LOWRANK, 5.0, 16, 717)):
+        nr = nx * nx
+        g = torch.Generator(device=dev).manual_seed(seed + nr)
+        hg = synth.rng(seed + nr)
+        Q = phase_dft_unitary_device(torch, nr, hg, dev)
+        W = phase_dft_unitary_device(torch, nr, hg, dev)
+        sig = torch.pow(10.0, -3.0 * torch.arange(nr, device=dev, dtype=torch.float32) / (nr - 1))
+        rows = torch.arange(nr, device=dev) if keep is None else \
+            torch.from_numpy(synth.source_keep(nr, keep / nr, seed + 5)).to(dev)
+        data = []
+        for f in range(nfreq):
+            ph = torch.exp(2j * math.pi * torch.rand(nr, generator=g, device=dev)).to(torch.complex64)
+            D = ((Q * (sig * ph)[None, :]) @ W.conj().T)[rows].contiguous()
+            X = torch.complex(torch.randn((nr, nr), generator=g, device=dev),
+                              torch.randn((nr, nr), generator=g, device=dev)) / math.sqrt(2 * nr)
+            X = ((X + X.T) * 0.5).to(torch.complex64)
+            Y = D @ X
+            nz = torch.complex(torch.randn(Y.shape, generator=g, device=dev), torch.randn(Y.shape, generator=g,
+                                                                                             device=dev))
+            U = (Y + nz * (Y.norm() / nz.norm() * 10 ** (-snr / 20))).to(torch.complex64)
+            data.append((D, U))
+        res = {}
+        for pname, prec in (("bf16x3", T.TLR_PREC_BF16X3), ("fp32", T.TLR_PREC_FP32)):
+            d = T.desc(nr, rows.numel(), b, rank=k, nx=nx, ny=nx, diag_mode=mode, precision=prec)
+            h = T.tlr_mdd_create(d, data[0][0], data[0][1], stream)
+            nth = T.tlr_mdd_theta_size(d)
+            th0 = (torch.randn(nth, generator=g, device=dev) * (0.1 / math.sqrt(b * k))).to(torch.complex64)
+            th = th0.clone()
+            opts = T.solve_opts()
+            T.tlr_mdd_solve(h, th, opts)            # records the solve graph
+            ms = []
+            m = n if prec != T.TLR_PREC_FP32 else max(1, n // 4)
+            for i in range(m):
+                if nfreq > 1:
+                    D, U = data[i % nfreq]
+                    T.tlr_mdd_set_data(h, D, U, T.TLR_MEM_DEVICE)
+                with torch.cuda.stream(stream):
+                    th.copy_(th0)
+                st = T.tlr_mdd_solve(h, th, opts)
+                ms.append(st.gpu_ms)
+            T.tlr_mdd_destroy(h)
+            res[pname] = {"solves": m, "solves_per_s": round(1e3 * m / sum(ms), 2),
+                          "p50_ms": round(percentile(ms, 50), 3), "p99_ms": round(percentile(ms, 99), 3)}
+        res["speedup_tc_vs_fp32"] = round(res["bf16x3"]["solves_per_s"] / res["fp32"]["solves_per_s"], 2)
+        res["workload"] = (f"nr={nr} ({nx}x{nx} grid), ns={rows.numel()}, tile {b}, rank {k}, "
+                           f"{'dense' if mode == T.TLR_DIAG_DENSE else 'low-rank'} diagonal, {snr:g} dB, "
+                           f"{nfreq} frequenc{'y' if nfreq == 1 else 'ies'}, 30 iterations; X a random symmetric "
+                           f"matrix (the solve's work does not depend on it)")
+        out[name] = res
+    out["timing"] = "device time of each solve (CUDA events), CUDA-graph replays one at a time on one stream"
+    return out
+
+
+def collections_counter(xs):
+    import collections
+    return collections.Counter(xs)
 
 
 def reference_arm(args, wl, world, rank):

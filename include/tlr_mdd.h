@@ -49,6 +49,9 @@ extern "C" {
 /* ---- precision of the complex contractions ---- */
 #define TLR_PREC_FP32   0  /* FP32 SIMT (CUDA cores), FP32 accumulation */
 #define TLR_PREC_BF16X3 1  /* tcgen05 tensor cores: BF16 hi/lo split (3 products), 4M complex, FP32 accumulation */
+#define TLR_PREC_TF32   2  /* tcgen05 tensor cores: operands rounded to TF32 (RN, ties away; 10 mantissa bits),
+                              4M complex, FP32 accumulation.  The dense adjoint (tlr_mdd_adjoint) and the
+                              benchmark solver of a TF32 handle compute in BF16x3. */
 
 /* ---- diagonal tile representation (eq. 6 / eq. 7) ---- */
 #define TLR_DIAG_RULE     0  /* dense iff k_ii >= d_i/4 (d_i: the tile size) */
@@ -340,8 +343,15 @@ int tlr_mdd_unpermute_dense(tlr_mdd_t* h, const void* theta, void* X);
  * if Dt / Ut are non-NULL, its panels (DEVICE complex64 [nr x ns]). */
 int tlr_mdd_get_data(tlr_mdd_t* h, int32_t* perm_host, double* alpha, void* Dt, void* Ut);
 
-/* The handle's stream (as passed to create). */
+/* The handle's stream (as passed to create, or last set). */
 void* tlr_mdd_stream(const tlr_mdd_t* h);
+
+/* Moves the handle to another stream (of the same device): later calls enqueue
+ * there; the handle's workspace, data panels and recorded solve stay.  Waits
+ * for the work already enqueued on the old stream.  A pending solve:
+ * TLR_ERR_STATE.  Used by a server that keeps finished handles for reuse by
+ * later requests of the same shape on whichever slot is free. */
+int tlr_mdd_set_stream(tlr_mdd_t* h, void* stream);
 
 /* ---- allocation-free dense adjoint ----
  * G = V Dt^H (nr x nr) for receiver-major V and Dt (nr x ns), all complex64
@@ -384,6 +394,32 @@ void tlr_mdd_timing_enable(int on);
 void tlr_mdd_timing_reset(void);
 int tlr_mdd_timing_read(double* ms, double* flops, int64_t* launches, int nclass);
 int64_t tlr_mdd_launch_count(void);
+
+/* ---- batched solve (serving; the paper solves frequencies one by one) ----
+ * A batch runs the solves of n handles (1 <= n <= 64, tensor-core precision
+ * with packed operands, one precision for all, any sizes) in lockstep: every
+ * member's own kernels run on a stream of the batch's, and each contraction
+ * of an L-BFGS step (compress, expand, projection) is ONE launch over the
+ * output tiles of every member, so requests of different sizes share the
+ * GPU's waves.  Each member's result is bit for bit its result alone (the
+ * same K chunks reach the same accumulators; every reduction has a fixed
+ * order).  create: validates, creates the batch's streams and events and its
+ * merged launch tables (device memory from the workspace pool), synchronises
+ * `stream`.  solve_async: thetas[m] (device or host per opts->theta_memory,
+ * n_theta of member m) is member m's start point and receives its solution;
+ * the same options for every member; enqueued on `stream` (plain launches,
+ * no graph); thetas must stay valid until the wait.  query: 1 done, 0
+ * running.  wait: stats (HOST array [n], may be NULL) as for a single solve,
+ * gpu_ms the whole batch's device time; returns TLR_ERR_TIMEOUT if a merged
+ * contraction timed out, TLR_ERR_NONFINITE if a member met a non-finite
+ * value.  A member must not be used otherwise while a batched solve is
+ * pending; destroy does not destroy the members. */
+typedef struct tlr_mdd_batch_s tlr_mdd_batch_t;
+int tlr_mdd_batch_create(tlr_mdd_batch_t** b, tlr_mdd_t* const* hs, int32_t n, void* stream);
+int tlr_mdd_batch_solve_async(tlr_mdd_batch_t* b, void* const* thetas, const tlr_mdd_solve_opts_t* opts);
+int tlr_mdd_batch_query(tlr_mdd_batch_t* b);
+int tlr_mdd_batch_wait(tlr_mdd_batch_t* b, tlr_mdd_stats_t* stats);
+int tlr_mdd_batch_destroy(tlr_mdd_batch_t* b);
 
 /* Workspace pool (the paper has no counterpart).  Every handle's device
  * workspace comes from one stream-ordered memory pool per device owned by the

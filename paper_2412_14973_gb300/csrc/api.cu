@@ -35,6 +35,7 @@ std::atomic<long long> tlr::g_launches{0};
 namespace {
 
 thread_local std::string g_last_error;
+constexpr int kPersistDefault = 0;
 
 // ---- workspace pool ----
 // Handles take their device workspace from one stream-ordered memory pool per
@@ -119,6 +120,14 @@ cudaEvent_t ev_get() {
 thread_local std::vector<TimedLaunch>* g_capture_sink = nullptr;
 
 }  // namespace
+
+// Contraction classes (bit 0 compress, 1 expand, 2 project) whose packed
+// tensor-core launches use the persistent, double-buffered kernel; the
+// environment variable TLR_MDD_PERSIST (a bit mask) overrides the default.
+static int persist_classes() {
+    const char* e = getenv("TLR_MDD_PERSIST");   // read when a handle's launches are planned
+    return e ? (atoi(e) & 7) : kPersistDefault;
+}
 
 // launch one grouped contraction, timed when diagnostics are on
 cudaError_t tlr::run_gemm(const GemmLaunch& L, cudaStream_t st) {
@@ -258,7 +267,7 @@ int build_layout(const tlr_mdd_desc_t* d, Layout& L, std::string& err) {
         err = "unknown reciprocity mode";
         return TLR_ERR_ARG;
     }
-    if (d->precision != TLR_PREC_FP32 && d->precision != TLR_PREC_BF16X3) {
+    if (d->precision != TLR_PREC_FP32 && d->precision != TLR_PREC_BF16X3 && d->precision != TLR_PREC_TF32) {
         err = "unknown precision mode";
         return TLR_ERR_ARG;
     }
@@ -697,7 +706,7 @@ int sm_count() {
 // tiles, c0 = 128 standing for a tile's fixed cost (set-up, pipeline fill,
 // epilogue) in units of contraction depth; this avoids a short last wave.
 int split_for(const Layout& L, int prec) {
-    if (prec == TLR_PREC_BF16X3) {
+    if (tensor_core(prec)) {
         long long tiles = 0;
         for (int i = 0; i < L.N; ++i) {
             const long long b = L.d[i];
@@ -768,6 +777,7 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
         }
         G.cls = am == A_KM ? 0 : (bm == B_KN ? 1 : 2);
         G.prec = h->d.precision;
+        G.persistent = tensor_core(G.prec) && ((persist_classes() >> G.cls) & 1);
         G.err = h->ints + SI_COUNT + 1;
         if (!v.empty()) {
             cudaError_t e = cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(GProb), cudaMemcpyHostToDevice, h->st);
@@ -808,9 +818,10 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
         if (upload(G, v, A_KM, B_KN, EPI_STORE)) return -1;
     }
     // expand: forward residual (SUB Ufrak), plain apply (STORE), A1, A2.  The
-    // line-search pair runs as one grouped launch (A1's problems, then A2's):
-    // their tiles share the operand packs and one launch fills the last wave
-    // better than two; Le_a2 stays empty.
+    // line-search pair runs as one grouped launch, block i's A1 problem next to
+    // its A2 problem (both read T~_p,i, which then comes from L2 the second
+    // time): their tiles share the operand packs and one launch fills the last
+    // wave better than two; Le_a2 stays empty.
     std::vector<GProb> a12;
     for (int which = 0; which < 4; ++which) {
         std::vector<GProb> v;
@@ -850,7 +861,12 @@ int build_tables(tlr_mdd_s* h, char* tab_base, std::vector<HostTable>* keep) {
             continue;
         }
         if (which == 3) {
-            a12.insert(a12.end(), v.begin(), v.end());
+            std::vector<GProb> a1 = a12;
+            a12.clear();
+            for (size_t i = 0; i < v.size(); ++i) {
+                a12.push_back(a1[i]);
+                a12.push_back(v[i]);
+            }
             std::vector<GProb> none;
             if (upload(h->Le_a1, a12, A_MK, B_KN, EPI_STORE)) return -1;
             if (upload(h->Le_a2, none, A_MK, B_KN, EPI_STORE)) return -1;
@@ -1005,6 +1021,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
         j.K = k.K;
         j.TR = k.TR;
         j.dst = h->packed + off;
+        j.fmt = pack_fmt(h->d.precision);
         return j;
     };
     // (padded rows << 32) | k-groups of 8; the launch grid covers the maximum of each
@@ -1071,8 +1088,11 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             const int64_t pg = L.partner[gm];
             const int i = (int)(std::upper_bound(L.KoffB.begin(), L.KoffB.end(), pg) - L.KoffB.begin()) - 1;
             const int64_t k = pg - L.KoffB[i];
+            // the row's first 16-byte group in its packed tile (row groups of
+            // 8 are 256 B apart in the BF16 planes, 512 B in the TF32 planes)
+            const long long rg = h->d.precision == TLR_PREC_TF32 ? 512 : 256;
             rowptr[gm] = h->packed + v_nk[h->d_partnerB + L.KoffB[i]] + (k >> 7) * nkcN * 4 * plane +
-                         ((k & 127) >> 3) * 256 + (k & 7) * 16;
+                         ((k & 127) >> 3) * rg + (k & 7) * 16;
         }
     }
     std::vector<std::pair<size_t, int64_t>> vfix;   // (problem index in Lc_v, Koff of its block)
@@ -1163,6 +1183,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             t.Ki = Ki;
             t.kn = h->packed + a->second;
             t.nk_dst = h->packed + c->second;
+            t.fmt = pack_fmt(h->d.precision);
             tt.push_back(t);
         }
     }
@@ -1179,6 +1200,7 @@ int build_tc(tlr_mdd_s* h, std::vector<HostTable>& tabs) {
             t.Ki = Ki;
             t.kn = h->packed + kv.second.first;
             t.nk_dst = nullptr;
+            t.fmt = pack_fmt(h->d.precision);
             ttp.push_back(t);
         }
     }
@@ -1336,7 +1358,7 @@ int64_t tlr_mdd_workspace_bytes(const tlr_mdd_desc_t* d) {
     carve(&tmp, a);
     // plus the L-BFGS ring for the default memory (m = 10: 11 slots of s and y)
     int64_t total = (int64_t)a.used + (int64_t)2 * 11 * tmp.L.nth * (int64_t)sizeof(cf);
-    if (d->precision == TLR_PREC_BF16X3) total += packed_estimate(tmp.L);
+    if (tensor_core(d->precision)) total += packed_estimate(tmp.L);
     return total;
 }
 
@@ -1463,7 +1485,9 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
         h->err = "uploading GEMM tables failed";
         return fail(TLR_ERR_CUDA);
     }
-    if (d->precision == TLR_PREC_BF16X3 && !getenv_off("TLR_MDD_PACKED")) {
+    // packed operands: always for TF32 (the on-the-fly kernel splits to BF16x3
+    // only); for BF16x3 unless TLR_MDD_PACKED=0 selects the on-the-fly kernel
+    if (d->precision == TLR_PREC_TF32 || (d->precision == TLR_PREC_BF16X3 && !getenv_off("TLR_MDD_PACKED"))) {
         // every tensor-core contraction except the dense adjoint (allocated per call)
         int rc = build_tc(h, tabs);
         if (rc) return fail(rc);
@@ -1473,7 +1497,7 @@ int tlr_mdd_create(tlr_mdd_t** out, const tlr_mdd_desc_t* d, const void* D, cons
     CKF(cudaEventCreate(&h->ev0));
     CKF(cudaEventCreate(&h->ev1));
     CKF(cudaMallocHost((void**)&h->hstats, sizeof(HostStats)));
-    if (d->precision == TLR_PREC_BF16X3) CKF(gemm_tc_prepare());
+    if (tensor_core(d->precision)) CKF(gemm_tc_prepare());
     CKF(cudaStreamSynchronize(h->st));
     CKF(cudaMemcpy(&h->alpha, h->scal, sizeof(double), cudaMemcpyDeviceToHost));
 #undef CKF
@@ -1504,7 +1528,7 @@ static int forward(tlr_mdd_s* h, bool plain_apply) {
     CK(h, run_gemm(plain_apply ? h->Le_apply : h->Le_fwd, h->st));
     if (!plain_apply && h->rstep_on)
         CK(h, rstep(h->R, h->A1, h->A2, nullptr, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn, h->d_rmk, nullptr, h->st,
-                    L.b > 0 ? nullptr : h->d_roff, L.N));
+                    L.b > 0 ? nullptr : h->d_roff, L.N, pack_fmt(h->d.precision)));
     return TLR_OK;
 }
 
@@ -1596,7 +1620,7 @@ int tlr_mdd_adjoint(tlr_mdd_t* h, const void* V, void* G) {
     cudaError_t e = cudaMemcpyAsync(dp, &p, sizeof(GProb), cudaMemcpyHostToDevice, h->st);
     G1.flops = 8.0 * nr * (double)nr * ns;
     G1.cls = 2;
-    G1.prec = h->d.precision;
+    G1.prec = tensor_core(h->d.precision) ? TLR_PREC_BF16X3 : TLR_PREC_FP32;   // operands split on the fly
     G1.err = h->ints + SI_COUNT + 1;
     if (e == cudaSuccess) e = run_gemm(G1, h->st);
     if (e == cudaSuccess && ns_split > 1) e = reduce_grad(part, ns_split, nr * nr, nr * nr, 0, 1, (cf*)G, h->st);
@@ -1622,7 +1646,7 @@ int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double t
     const Layout& L = h->L;
     const int n = (int)L.nr, ns = (int)L.ns;
     const size_t n2 = (size_t)n * n;
-    const bool tc = h->d.precision == TLR_PREC_BF16X3;
+    const bool tc = tensor_core(h->d.precision);   // BF16x3 packed products for both tensor-core modes
     const int np = cg_partials(n);
     // work arrays: G, x, r, p, y, Ap; partials; scalars; tables; packed operands (tensor cores)
     const size_t pk = tc ? (size_t)std::max(packed_bytes(n, ns, kPackTRA), packed_bytes(n, n, kPackTRA)) : 0;
@@ -1694,6 +1718,7 @@ int tlr_mdd_benchmark_solve(tlr_mdd_t* h, double lambda, int32_t iters, double t
             J[i].K = Ks[i];
             J[i].TR = (i == 0 || i == 3) ? kPackTRA : kPackTRB;
             J[i].dst = (i == 0 || i == 3) ? (void*)pkA : (void*)pkB;
+            J[i].fmt = kFmtBF16X3;
         }
         PProb q[3];
         memset(q, 0, sizeof(q));
@@ -2151,6 +2176,17 @@ int64_t tlr_mdd_launch_count(void) { return g_launches.load(); }
 
 void* tlr_mdd_stream(const tlr_mdd_t* h) { return h ? (void*)h->st : nullptr; }
 
+int tlr_mdd_set_stream(tlr_mdd_t* h, void* stream) {
+    if (!h) FAIL(h, TLR_ERR_STATE, "handle is NULL");
+    if (h->pending) FAIL(h, TLR_ERR_STATE, "a solve is pending on this handle");
+    if (stream == (void*)h->st) return TLR_OK;
+    // work already enqueued on the old stream finishes before anything that
+    // follows on the new one
+    CK(h, cudaStreamSynchronize(h->st));
+    h->st = (cudaStream_t)stream;
+    return TLR_OK;
+}
+
 const char* tlr_mdd_last_error(const tlr_mdd_t* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
 int tlr_mdd_trim_pool(int64_t keep_bytes, int64_t* reserved) {
@@ -2199,14 +2235,13 @@ static int check_opts(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
 
 // The whole solve as a fixed sequence of launches on h->st: theta is read from
 // and written back to h->th_io; every decision lives in device memory.
-static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
-    const Layout& L = h->L;
-    const long long n2 = 2 * L.nth;
-    const long long nrs = (long long)L.nr * L.ns;
+// The device-side solver state of a handle for L-BFGS memory m.
+static SolverDev solver_dev(tlr_mdd_s* h, int m) {
+    const long long n2 = 2 * h->L.nth;
     SolverDev S;
     S.n2 = n2;
-    S.m = o->memory;
-    S.ring = o->memory + 1;
+    S.m = m;
+    S.ring = m + 1;
     S.x = (float*)h->x;
     S.z = (float*)h->z;
     S.u = (float*)h->u;
@@ -2227,7 +2262,14 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     S.sc = h->sc;
     S.ints = h->ints;
     S.fhist = h->fhist;
-    S.part = h->dpart;                            // 2 slabs
+    S.part = h->dpart;   // 2 slabs
+    return S;
+}
+
+static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
+    const Layout& L = h->L;
+    const long long nrs = (long long)L.nr * L.ns;
+    SolverDev S = solver_dev(h, o->memory);
     double* part6 = h->dpart + 2 * kRedBlocks;    // 6 slabs
     double* part3 = h->dpart + 8 * kRedBlocks;    // 3 slabs
     double* part3b = h->dpart + 11 * kRedBlocks;  // 3 slabs
@@ -2266,7 +2308,7 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 if (h->rstep_on) {
                     // the carried residual lives in its packed forms
                     CK(h, dots6_packed(h->d_rkn, h->A1, h->A2, (int)L.nr, (int)L.ns, (int)L.b, part6, h->st,
-                                       L.b > 0 ? nullptr : h->d_roff, L.N));
+                                       L.b > 0 ? nullptr : h->d_roff, L.N, pack_fmt(h->d.precision)));
                     CK(h, sv_dots3(S, part3, h->st));
                     CK(h, sv_line_search(S, part6, kRedBlocks, part3, rho, h->st));
                 } else {
@@ -2276,7 +2318,8 @@ static int enqueue_solve(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
                 }
                 if (h->rstep_on)
                     CK(h, rstep(h->R, h->A1, h->A2, h->sc + SC_ALPHA, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn,
-                                h->d_rmk, h->rpart, h->st, L.b > 0 ? nullptr : h->d_roff, L.N));
+                                h->d_rmk, h->rpart, h->st, L.b > 0 ? nullptr : h->d_roff, L.N,
+                                pack_fmt(h->d.precision)));
                 else
                     CK(h, sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, partf, h->st));
                 if (h->n_tpack)
@@ -2435,6 +2478,463 @@ int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o
     int rc = tlr_mdd_solve_async(h, theta_inout, o);
     if (rc) return rc;
     return tlr_mdd_solve_wait(h, stats);
+}
+
+// ---------------------------------------------------------------------------
+// batched solve: several handles in lockstep, each contraction one
+// persistent launch over the tiles of every member
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct tlr_mdd_batch_s {
+    std::vector<tlr_mdd_s*> hs;
+    cudaStream_t st = nullptr;            // merged contractions; the solve's start and end
+    std::vector<cudaStream_t> ms;         // one per member: its own kernels
+    std::vector<cudaEvent_t> evm;         // end of a member's phase
+    cudaEvent_t evj = nullptr;            // end of a merged contraction
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    char* tables = nullptr;               // merged problem / job / slice tables and the error word
+    int* err = nullptr;
+    // merged launches (null d_pprobs: that kind runs per member)
+    GemmLaunch Lc_x, Lc_d, Lc_v, Le_fwd, Le_a1, Lp;
+    std::vector<void*> io;                // caller theta buffers of the pending solve
+    int theta_memory = 0;
+    bool pending = false;
+    std::string err_msg;
+};
+
+namespace {
+
+// One merged launch of contraction kind `kind` over every member: problem
+// tables and pack jobs concatenated (device-to-device), one slice per
+// member problem and split in a map.  Returns false when the members'
+// launches of this kind differ in epilogue or format (they then run apart).
+bool plan_merged(tlr_mdd_batch_s* b, GemmLaunch tlr_mdd_s::*kind, GemmLaunch& M, size_t& off, bool size_only,
+                 cudaStream_t st, cudaError_t& e) {
+    const GemmLaunch& G0 = b->hs[0]->*kind;
+    int nprob = 0, njobs = 0, nz = 0;
+    for (auto* h : b->hs) {
+        const GemmLaunch& G = h->*kind;
+        if (G.epi != G0.epi || pack_fmt(G.prec) != pack_fmt(G0.prec) || G.cls != G0.cls || !G.d_pprobs)
+            return false;
+        nprob += G.nprob;
+        njobs += G.njobs;
+        nz += G.nprob * G.nsplit;
+    }
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    const size_t po = take(std::max<size_t>(1, nprob) * sizeof(PProb));
+    const size_t jo = take(std::max<size_t>(1, njobs) * sizeof(PackJob));
+    const size_t zo = take(std::max<size_t>(1, nz) * sizeof(ZItem));
+    if (size_only) return true;
+    M = GemmLaunch();
+    M.d_pprobs = reinterpret_cast<PProb*>(b->tables + po);
+    M.d_jobs = njobs ? reinterpret_cast<PackJob*>(b->tables + jo) : nullptr;
+    M.d_zmap = reinterpret_cast<ZItem*>(b->tables + zo);
+    M.nprob = nprob;
+    M.njobs = njobs;
+    M.nz = nz;
+    M.nsplit = 1;
+    M.epi = G0.epi;
+    M.cls = G0.cls;
+    M.prec = G0.prec;
+    M.persistent = (persist_classes() >> G0.cls) & 1;
+    M.err = b->err;
+    std::vector<ZItem> zm;
+    int pbase = 0, jbase = 0;
+    for (auto* h : b->hs) {
+        const GemmLaunch& G = h->*kind;
+        M.maxM = std::max(M.maxM, G.maxM);
+        M.maxN = std::max(M.maxN, G.maxN);
+        M.maxK = std::max(M.maxK, G.maxK);
+        M.flops += G.flops;
+        M.max_items = std::max(M.max_items >> 32, G.max_items >> 32) << 32 |
+                      std::max(M.max_items & 0xffffffffLL, G.max_items & 0xffffffffLL);
+        if (G.nprob && e == cudaSuccess)
+            e = cudaMemcpyAsync(M.d_pprobs + pbase, G.d_pprobs, G.nprob * sizeof(PProb), cudaMemcpyDeviceToDevice, st);
+        if (G.njobs && e == cudaSuccess)
+            e = cudaMemcpyAsync(M.d_jobs + jbase, G.d_jobs, G.njobs * sizeof(PackJob), cudaMemcpyDeviceToDevice, st);
+        for (int p = 0; p < G.nprob; ++p)
+            for (int c = 0; c < G.nsplit; ++c) {
+                ZItem z;
+                z.prob = pbase + p;
+                z.chunk = c;
+                z.kchunk = G.nsplit > 1 ? G.kchunk : 0;
+                z.pad = 0;
+                z.part_off = (long long)c * G.part_stride;
+                zm.push_back(z);
+            }
+        pbase += G.nprob;
+        jbase += G.njobs;
+    }
+    if (!zm.empty() && e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<ZItem*>(M.d_zmap), zm.data(), zm.size() * sizeof(ZItem), cudaMemcpyHostToDevice,
+                            st);
+    return true;
+}
+
+using BatchKinds = GemmLaunch tlr_mdd_s::*;
+const BatchKinds kBatchKinds[6] = {&tlr_mdd_s::Lc_x, &tlr_mdd_s::Lc_d, &tlr_mdd_s::Lc_v,
+                                    &tlr_mdd_s::Le_fwd, &tlr_mdd_s::Le_a1, &tlr_mdd_s::Lp};
+
+GemmLaunch tlr_mdd_batch_s::* const kBatchMerged[6] = {&tlr_mdd_batch_s::Lc_x, &tlr_mdd_batch_s::Lc_d,
+                                                       &tlr_mdd_batch_s::Lc_v, &tlr_mdd_batch_s::Le_fwd,
+                                                       &tlr_mdd_batch_s::Le_a1, &tlr_mdd_batch_s::Lp};
+
+#define BCK(expr)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (expr);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            b->err_msg = std::string(#expr) + ": " + cudaGetErrorString(e_);   \
+            g_last_error = b->err_msg;                                         \
+            return TLR_ERR_CUDA;                                               \
+        }                                                                      \
+    } while (0)
+
+// the merged stream waits for every member's stream / every member waits for it
+int b_join(tlr_mdd_batch_s* b) {
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        BCK(cudaEventRecord(b->evm[m], b->ms[m]));
+        BCK(cudaStreamWaitEvent(b->st, b->evm[m], 0));
+    }
+    return TLR_OK;
+}
+int b_fork(tlr_mdd_batch_s* b) {
+    BCK(cudaEventRecord(b->evj, b->st));
+    for (auto s : b->ms) BCK(cudaStreamWaitEvent(s, b->evj, 0));
+    return TLR_OK;
+}
+
+// one contraction kind for every member: the merged launch on the merged
+// stream (after the members' gathered packs on their own streams), or each
+// member's own launch on its stream when the kinds could not be merged
+int b_gemm(tlr_mdd_batch_s* b, int k) {
+    GemmLaunch& M = b->*kBatchMerged[k];
+    const BatchKinds kind = kBatchKinds[k];
+    if (!M.d_pprobs) {
+        for (size_t m = 0; m < b->hs.size(); ++m) BCK(run_gemm(b->hs[m]->*kind, b->ms[m]));
+        return TLR_OK;
+    }
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        const GemmLaunch& G = b->hs[m]->*kind;
+        if (G.n_gpack) BCK(tpack(G.d_gpack, G.n_gpack, G.gpack_src, nullptr, nullptr, G.gpack_ns, b->ms[m]));
+    }
+    int rc = b_join(b);
+    if (rc) return rc;
+    if (M.njobs) BCK(pack_operands(M.d_jobs, M.njobs, M.max_items, b->st));
+    GemmLaunch L = M;
+    L.njobs = 0;   // packed above
+    BCK(run_gemm(L, b->st));
+    return b_fork(b);
+}
+
+int b_forward(tlr_mdd_batch_s* b) {
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        const Layout& L = h->L;
+        BCK(sym_dense(h->x, L.nlr, L.ndense, L.dmax, h->Zs, b->ms[m], L.general, h->pm.zoff, h->pm.zdim));
+    }
+    int rc = b_gemm(b, 0);   // Lc_x
+    if (rc) return rc;
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        if (h->n_tpack) BCK(tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, nullptr, (int)h->L.ns, b->ms[m]));
+    }
+    rc = b_gemm(b, 3);   // Le_fwd
+    if (rc) return rc;
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        const Layout& L = h->L;
+        if (h->rstep_on)
+            BCK(rstep(h->R, h->A1, h->A2, nullptr, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn, h->d_rmk, nullptr,
+                      b->ms[m], L.b > 0 ? nullptr : h->d_roff, L.N, pack_fmt(h->d.precision)));
+    }
+    return TLR_OK;
+}
+
+int b_gradient(tlr_mdd_batch_s* b) {
+    int rc = b_gemm(b, 2);   // Lc_v
+    if (rc) return rc;
+    rc = b_gemm(b, 5);       // Lp
+    if (rc) return rc;
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        const Layout& L = h->L;
+        BCK(reduce_grad(h->part, h->nsplit, L.nth, L.nlr, L.ndense, L.dmax, h->gf, b->ms[m], L.general, h->pm.zoff,
+                        h->pm.zdim));
+    }
+    return TLR_OK;
+}
+
+// The lockstep solve: the same sequence as enqueue_solve for every member,
+// its own kernels on its own stream, the contractions merged.
+int b_enqueue(tlr_mdd_batch_s* b, const tlr_mdd_solve_opts_t* o) {
+    const size_t n = b->hs.size();
+    std::vector<SolverDev> S(n);
+    for (size_t m = 0; m < n; ++m) S[m] = solver_dev(b->hs[m], o->memory);
+    auto part = [&](size_t m, int slab) { return b->hs[m]->dpart + (size_t)slab * kRedBlocks; };
+    const double rho = o->rho;
+    for (size_t m = 0; m < n; ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        BCK(theta_to_panel(h->pm, h->th_io, h->x, b->ms[m]));
+        if (o->flags & TLR_SOLVE_RESUME)
+            BCK(sv_admm_resume(S[m], b->ms[m]));
+        else
+            BCK(sv_admm_init(S[m], b->ms[m]));
+    }
+    int rc = b_forward(b);
+    if (rc) return rc;
+    for (size_t m = 0; m < n; ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        BCK(sv_norm_part(h->R, (long long)h->L.nr * h->L.ns, part(m, 14), b->ms[m]));
+        BCK(sv_record_f0(S[m], part(m, 14), b->ms[m]));
+    }
+    rc = b_gradient(b);
+    if (rc) return rc;
+    int xu = 0;
+    for (int s = 0; s < o->stages; ++s) {
+        const double lam = o->lam0 * std::pow(o->decay, (double)s);
+        for (int it = 0; it < o->admm_iters; ++it, ++xu) {
+            if ((o->flags & TLR_SOLVE_REFRESH) && xu > 0) {
+                rc = b_forward(b);
+                if (rc) return rc;
+                rc = b_gradient(b);
+                if (rc) return rc;
+            }
+            for (size_t m = 0; m < n; ++m) BCK(sv_xupdate_start(S[m], rho, b->ms[m]));
+            for (int t = 0; t < o->lbfgs_iters; ++t) {
+                for (size_t m = 0; m < n; ++m) BCK(sv_direction(S[m], b->ms[m]));
+                rc = b_gemm(b, 1);   // Lc_d
+                if (rc) return rc;
+                for (size_t m = 0; m < n; ++m) {
+                    tlr_mdd_s* h = b->hs[m];
+                    const Layout& L = h->L;
+                    BCK(sym_dense(h->dd, L.nlr, L.ndense, L.dmax, h->Zsd, b->ms[m], L.general, h->pm.zoff,
+                                  h->pm.zdim));
+                }
+                rc = b_gemm(b, 4);   // Le_a1 (A1 and A2)
+                if (rc) return rc;
+                for (size_t m = 0; m < n; ++m) {
+                    tlr_mdd_s* h = b->hs[m];
+                    const Layout& L = h->L;
+                    const long long nrs = (long long)L.nr * L.ns;
+                    cudaStream_t st = b->ms[m];
+                    if (h->rstep_on)
+                        BCK(dots6_packed(h->d_rkn, h->A1, h->A2, (int)L.nr, (int)L.ns, (int)L.b, part(m, 2), st,
+                                         L.b > 0 ? nullptr : h->d_roff, L.N, pack_fmt(h->d.precision)));
+                    else
+                        BCK(dots6_part(h->R, h->A1, h->A2, nrs, part(m, 2), st));
+                    BCK(sv_dots3(S[m], part(m, 8), st));
+                    BCK(sv_line_search(S[m], part(m, 2), kRedBlocks, part(m, 8), rho, st));
+                    if (h->rstep_on)
+                        BCK(rstep(h->R, h->A1, h->A2, h->sc + SC_ALPHA, (int)L.nr, (int)L.ns, (int)L.b, h->d_rkn,
+                                  h->d_rmk, h->rpart, st, L.b > 0 ? nullptr : h->d_roff, L.N,
+                                  pack_fmt(h->d.precision)));
+                    else
+                        BCK(sv_step_residual(h->R, h->A1, h->A2, nrs, h->sc + SC_ALPHA, part(m, 14), st));
+                    if (h->n_tpack)
+                        BCK(tpack(h->d_tpack, h->n_tpack, h->T, h->Tp, h->sc + SC_ALPHA, (int)L.ns, st));
+                    else if (L.KtotB > 0)
+                        BCK(axpy_dev((float*)h->T, (const float*)h->Tp, 2LL * L.KtotB * L.ns, h->sc + SC_ALPHA, st));
+                    BCK(sv_step_theta(S[m], st));
+                }
+                rc = b_gradient(b);
+                if (rc) return rc;
+                for (size_t m = 0; m < n; ++m) {
+                    tlr_mdd_s* h = b->hs[m];
+                    BCK(sv_pair_prep(S[m], rho, part(m, 11), b->ms[m]));
+                    if (h->rstep_on)
+                        BCK(sv_pair_accept(S[m], part(m, 11), h->rpart, (int)h->n_rpart, b->ms[m]));
+                    else
+                        BCK(sv_pair_accept(S[m], part(m, 11), part(m, 14), kRedBlocks, b->ms[m]));
+                }
+            }
+            for (size_t m = 0; m < n; ++m) BCK(sv_admm_zu(S[m], lam, rho, b->ms[m]));
+        }
+    }
+    for (size_t m = 0; m < n; ++m) BCK(panel_to_theta(b->hs[m]->pm, b->hs[m]->x, b->hs[m]->th_io, b->ms[m]));
+    return TLR_OK;
+}
+
+void b_free(tlr_mdd_batch_s* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    for (auto s : b->ms)
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    for (auto e : b->evm)
+        if (e) cudaEventDestroy(e);
+    if (b->evj) cudaEventDestroy(b->evj);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->tables) {
+        cudaFreeAsync(b->tables, b->st);
+        cudaStreamSynchronize(b->st);
+    }
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tlr_mdd_batch_create(tlr_mdd_batch_t** out, tlr_mdd_t* const* hs, int32_t n, void* stream) {
+    if (!out) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "batch pointer is NULL");
+    *out = nullptr;
+    if (!hs || n < 1 || n > 64) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "a batch holds 1 to 64 handles");
+    int fmt = -1;
+    for (int i = 0; i < n; ++i) {
+        tlr_mdd_s* h = hs[i];
+        if (!h) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "NULL handle in the batch");
+        if (h->pending) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "a member has a pending solve");
+        if (!h->packed) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_UNSUPPORTED, "batched solves need the packed tensor-core path");
+        if (fmt >= 0 && pack_fmt(h->d.precision) != fmt)
+            FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "members of a batch share one tensor-core precision");
+        fmt = pack_fmt(h->d.precision);
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "a handle appears twice in the batch");
+    }
+    tlr_mdd_batch_s* b = new tlr_mdd_batch_s();
+    b->hs.assign(hs, hs + n);
+    b->st = (cudaStream_t)stream;
+    auto fail = [&](int code, const char* msg) {
+        g_last_error = msg;
+        b_free(b);
+        return code;
+    };
+    b->ms.assign(n, nullptr);
+    b->evm.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        if (cudaStreamCreateWithFlags(&b->ms[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->evm[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(TLR_ERR_CUDA, "creating the batch's streams failed");
+    }
+    if (cudaEventCreateWithFlags(&b->evj, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
+        return fail(TLR_ERR_CUDA, "creating the batch's events failed");
+    // sizing pass, then the tables
+    size_t off = 256;   // the error word first
+    cudaError_t e = cudaSuccess;
+    bool merged[6];
+    for (int k = 0; k < 6; ++k) {
+        GemmLaunch tmp;
+        merged[k] = plan_merged(b, kBatchKinds[k], tmp, off, true, b->st, e);
+    }
+    if (ws_alloc((void**)&b->tables, off, b->st) != cudaSuccess) {
+        b->tables = nullptr;
+        return fail(TLR_ERR_NOMEM, "allocating the batch's tables failed");
+    }
+    b->err = reinterpret_cast<int*>(b->tables);
+    e = cudaMemsetAsync(b->tables, 0, 256, b->st);
+    off = 256;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        if (merged[k]) plan_merged(b, kBatchKinds[k], b->*kBatchMerged[k], off, false, b->st, e);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail(TLR_ERR_CUDA, cudaGetErrorString(e));
+    *out = b;
+    return TLR_OK;
+}
+
+int tlr_mdd_batch_solve_async(tlr_mdd_batch_t* b, void* const* thetas, const tlr_mdd_solve_opts_t* o) {
+    if (!b) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "batch is NULL");
+    if (!thetas || !o) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "thetas or opts is NULL");
+    if (b->pending) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "a batched solve is already pending");
+    const size_t n = b->hs.size();
+    for (size_t m = 0; m < n; ++m) {
+        if (!thetas[m]) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "NULL theta in the batch");
+        if (b->hs[m]->pending) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "a member has a pending solve");
+        int rc = check_opts(b->hs[m], o);
+        if (rc) return rc;
+    }
+    const bool host = o->theta_memory == TLR_MEM_HOST;
+    BCK(cudaEventRecord(b->ev0, b->st));
+    int rc = b_fork(b);
+    if (rc) return rc;
+    for (size_t m = 0; m < n; ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        const long long n2 = 2 * h->L.nth;
+        if (h->ring_m < o->memory) {   // the member's ring of s / y vectors
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            if (h->ring) cudaFreeAsync(h->ring, b->ms[m]);
+            h->ring = nullptr;
+            h->ring_m = 0;
+            BCK(ws_alloc((void**)&h->ring, (size_t)2 * (o->memory + 1) * n2 * sizeof(float), b->ms[m]));
+            h->ring_m = o->memory;
+        }
+        BCK(cudaMemcpyAsync(h->th_io, thetas[m], h->L.nth * sizeof(cf),
+                            host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->ms[m]));
+    }
+    rc = b_enqueue(b, o);
+    if (rc) return rc;
+    for (size_t m = 0; m < n; ++m) {
+        tlr_mdd_s* h = b->hs[m];
+        cudaStream_t s = b->ms[m];
+        BCK(cudaMemcpyAsync(thetas[m], h->th_io, h->L.nth * sizeof(cf),
+                            host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        BCK(cudaMemcpyAsync(h->hstats->ints, h->ints, sizeof(h->hstats->ints), cudaMemcpyDeviceToHost, s));
+        BCK(cudaMemcpyAsync(h->hstats->sc, h->sc, sizeof(h->hstats->sc), cudaMemcpyDeviceToHost, s));
+        BCK(cudaMemcpyAsync(h->hstats->fhist, h->fhist, sizeof(h->hstats->fhist), cudaMemcpyDeviceToHost, s));
+    }
+    rc = b_join(b);
+    if (rc) return rc;
+    BCK(cudaEventRecord(b->ev1, b->st));
+    b->pending = true;
+    return TLR_OK;
+}
+
+int tlr_mdd_batch_query(tlr_mdd_batch_t* b) {
+    if (!b) return TLR_ERR_STATE;
+    if (!b->pending) return 1;
+    cudaError_t e = cudaEventQuery(b->ev1);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return TLR_ERR_CUDA;
+}
+
+int tlr_mdd_batch_wait(tlr_mdd_batch_t* b, tlr_mdd_stats_t* stats) {
+    if (!b) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "batch is NULL");
+    if (!b->pending) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_STATE, "no batched solve is pending");
+    b->pending = false;
+    BCK(cudaEventSynchronize(b->ev1));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) != cudaSuccess) (void)cudaGetLastError();
+    int werr = 0;
+    BCK(cudaMemcpy(&werr, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    int worst = TLR_OK;
+    for (size_t m = 0; m < b->hs.size(); ++m) {
+        const HostStats& hs = *b->hs[m]->hstats;
+        if (stats) {
+            tlr_mdd_stats_t& s = stats[m];
+            s.iters = hs.ints[SI_ITERS];
+            s.restarts = hs.ints[SI_RESTARTS];
+            s.status = hs.ints[SI_STATUS];
+            s.n_hist = std::min(hs.ints[SI_ITERS], TLR_MAX_HIST);
+            memcpy(s.f_hist, hs.fhist, sizeof(s.f_hist));
+            s.f0 = hs.sc[SC_F0];
+            s.gpu_ms = ms;
+        }
+        if (hs.ints[SI_STATUS] != 0) worst = TLR_ERR_NONFINITE;
+    }
+    if (werr != 0) {
+        BCK(cudaMemset(b->err, 0, sizeof(int)));
+        FAIL((tlr_mdd_s*)nullptr, TLR_ERR_TIMEOUT, "a tensor-core contraction timed out on a barrier wait");
+    }
+    if (worst) FAIL((tlr_mdd_s*)nullptr, worst, "non-finite value met during a member's solve");
+    return TLR_OK;
+}
+
+int tlr_mdd_batch_destroy(tlr_mdd_batch_t* b) {
+    if (!b) return TLR_ERR_ARG;
+    b_free(b);
+    return TLR_OK;
 }
 
 }  // extern "C"

@@ -58,7 +58,13 @@ enum BMode { B_KN = 0, B_NK = 1 };
 
 // ---------------------------------------------------------------------------
 // Packed-operand tensor-core path (k_gemm_tcp.cu).
-// One pack job writes one operand in the BF16-plane tile format; element
+// Packed tile formats (one tile = 128 rows x 16 k = 16 KB in both):
+//   kFmtBF16X3: four BF16 planes (Re hi, Re lo, Im hi, Im lo), x = hi + lo;
+//   kFmtTF32:   two planes (Re, Im) of FP32 words rounded to TF32 (RN, ties away).
+constexpr int kFmtBF16X3 = 0, kFmtTF32 = 1;
+inline int pack_fmt(int precision) { return precision == TLR_PREC_TF32 ? kFmtTF32 : kFmtBF16X3; }
+inline bool tensor_core(int precision) { return precision == TLR_PREC_BF16X3 || precision == TLR_PREC_TF32; }
+// One pack job writes one operand in a packed tile format; element
 // (r, k) of the logical operand is src[row(r) * ld + k] when kcontig, else
 // src[krow(k) * ld + r]; row(r) = g_row ? g_row[r] : r, krow likewise with g_k;
 // the imaginary part is multiplied by sgn.
@@ -71,6 +77,7 @@ struct PackJob {
     float sgn;
     int R, K, TR;
     void* dst;
+    int fmt;   // kFmt*
 };
 // row-tile heights of packed A (M) and B (N) operands: the GEMM tile's M and N
 constexpr int kPackTRA = 128, kPackTRB = 128;
@@ -94,6 +101,13 @@ struct PProb {
     char* const* rowptr;   // EPI_PACKNK: per output row, its first 16-byte group in the packed operand
 };
 
+// One problem-and-split slice of a launch whose problems have their own split
+// (the persistent kernel's z index through a map): K chunk `chunk` of
+// `kchunk` (0: the whole K), split-K partial at element offset part_off of C.
+struct ZItem {
+    int prob, chunk, kchunk, pad;
+    long long part_off;
+};
 struct TPackTile;
 struct GemmLaunch {
     GProb* d_probs = nullptr;   // device copy
@@ -105,7 +119,10 @@ struct GemmLaunch {
     int amode = 0, bmode = 0, epi = 0;
     double flops = 0.0;         // algorithmic flops of one launch (8 per complex MAC)
     int cls = 0;                // diagnostics class (0 compress, 1 expand, 2 project)
-    int prec = 0;               // TLR_PREC_FP32 (SIMT) or TLR_PREC_BF16X3 (tcgen05)
+    int prec = 0;               // TLR_PREC_FP32 (SIMT), TLR_PREC_BF16X3 or TLR_PREC_TF32 (tcgen05)
+    bool persistent = false;    // packed path: the persistent, double-buffered kernel
+    const ZItem* d_zmap = nullptr;   // persistent only: per-slice problem, split and partial offset
+    int nz = 0;                      // slices in d_zmap (replaces nprob x nsplit)
     int* err = nullptr;         // device error word (tensor-core path: bounded-wait timeouts)
     // packed tensor-core path: problems on packed operands and the packs to run first
     PProb* d_pprobs = nullptr;
@@ -129,6 +146,7 @@ struct TPackTile {
     int k0, nk, Ki;
     void* kn;       // packed T~_i (KN), base of block i's buffer
     void* nk_dst;   // packed conj(T~_i) (NK), base of block i's buffer
+    int fmt;        // kFmt*
 };
 // T[r] += alpha T_p[r] (FP32 fmaf, alpha read on the device; alpha == nullptr
 // or *alpha == 0: no update) for every row reached through the tiles (each
@@ -152,9 +170,9 @@ long long rstep_ctas(int nr, int ns);
 // as rstep writes it), over rstep's tiles: part[blk * 6 + k], kRedBlocks
 // partials (a fixed grid, so the sums are reproducible).
 cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, int ns, int b, double* part,
-                         cudaStream_t st, const long long* roff = nullptr, int nblk = 0);
+                         cudaStream_t st, const long long* roff, int nblk, int fmt);
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
-                  char* const* mk, double* part, cudaStream_t st, const long long* roff = nullptr, int nblk = 0);
+                  char* const* mk, double* part, cudaStream_t st, const long long* roff, int nblk, int fmt);
 // Benchmark solver of eq. (4) (k_cg.cu): the symmetrising pass
 // out = P(y) + s2 p (with partials of <p, out> when part != nullptr; p may be
 // nullptr: out = P(y)), the start (x = 0, r = p = b with b in r on entry),
@@ -217,7 +235,7 @@ cudaError_t gemm_tc(const GemmLaunch& L, cudaStream_t st);
 // one-time kernel attributes (shared-memory size), outside any stream capture
 cudaError_t gemm_tc_prepare();
 inline cudaError_t gemm_any(const GemmLaunch& L, cudaStream_t st) {
-    if (L.prec != TLR_PREC_BF16X3) return gemm_simt(L, st);
+    if (!tensor_core(L.prec)) return gemm_simt(L, st);
     if (!L.d_pprobs) return gemm_tc(L, st);
     cudaError_t e = cudaSuccess;
     if (L.n_gpack) e = tpack(L.d_gpack, L.n_gpack, L.gpack_src, nullptr, nullptr, L.gpack_ns, st);

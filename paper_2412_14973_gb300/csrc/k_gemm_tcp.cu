@@ -1,17 +1,22 @@
 // Tensor-core GEMM on pre-packed operands, and the pack kernel that makes them.
 //
 // Packed format ("P-format") of an operand with R rows (the M or N index) and
-// K columns (the contraction index): tiles of TR = 128 rows x 16 k; tile
-// (rb, kc) starts at byte
-// (rb * nkc + kc) * 4 * TR * 32 and holds four BF16 planes (Re hi, Re lo,
-// Im hi, Im lo; x = hi + lo with hi = RN_bf16(x), lo = RN_bf16(x - hi)), each
-// in the tensor core's canonical K-major, no-swizzle layout (8-row x 16-byte
-// core matrices, 128 B apart along K, 256 B apart along rows).  Elements
-// outside R x K are zero.  The pack applies the row gather and the
-// conjugation of the operand, so a tile is exactly what a stage of the GEMM
-// needs and is moved with one cp.async.bulk copy.
+// K columns (the contraction index): tiles of TR = 128 rows x 16 k, 16 KB
+// each; tile (rb, kc) starts at byte (rb * nkc + kc) * 16384.  Two formats:
+//   BF16x3: four BF16 planes (Re hi, Re lo, Im hi, Im lo; x = hi + lo with
+//     hi = RN_bf16(x), lo = RN_bf16(x - hi)) of 4 KB;
+//   TF32: two planes (Re, Im) of 8 KB, FP32 words rounded to TF32 (RN, ties
+//     away from zero: the low 13 mantissa bits zero, so the tensor core's
+//     handling of them does not matter).
+// Each plane is in the tensor core's canonical K-major, no-swizzle layout:
+// 8-row x 16-byte core matrices, 128 B apart along K, 256 B (BF16, two per
+// 16 k) or 512 B (TF32, four per 16 k) apart along rows.  Elements outside
+// R x K are zero.  The pack applies the row gather and the conjugation of the
+// operand, so a tile is exactly what a stage of the GEMM needs and is moved
+// with one cp.async.bulk copy.
 //
-// The GEMM (4M complex products, 128 x 128 tile, 12 MMAs per 16-deep chunk)
+// The GEMM (4M complex products, 128 x 128 tile, 12 BF16 MMAs of K 16 or 8
+// TF32 MMAs of K 8 per 16-deep chunk)
 // has one thread issuing the bulk copies of the A and B tiles of each chunk
 // into a 3-stage ring with a transaction-count mbarrier,
 // one thread issuing the MMAs, and eight warps for the epilogue.  Every wait
@@ -46,16 +51,26 @@ static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "TMEM columns of the CTAs sharing 
 static_assert(8 * 32 * 17 * 8 <= NSTAGE * STAGE, "epilogue staging fits in the operand ring");
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
+// instruction descriptors: FP32 accumulator (bits 4-5 = 1), A and B format
+// (bits 7-9, 10-12: 1 = BF16, 2 = TF32), N / 8 (bits 17-22), M / 16 (bits 24-28),
+// bit 13 negates A
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 constexpr uint32_t IDESC_NEG_A = IDESC | (1u << 13);
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_TF32_NEG_A = IDESC_TF32 | (1u << 13);
+constexpr int PK_TILE = 16384;   // bytes of one packed 128 x 16 tile (both formats)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+// shared-memory matrix descriptor, K-major no-swizzle: leading byte offset
+// 128 (core matrices adjacent along K), stride byte offset sbo (adjacent
+// along M / N: 256 for the BF16 planes, 512 for the TF32 planes)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = 256u) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(256u >> 4) << 32;
+    d |= (uint64_t)(sbo >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -93,6 +108,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         : "memory");
 }
 
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -107,6 +132,88 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
 
 __device__ __forceinline__ int core_off(int r, int kg) { return ((r >> 3) * 2 + kg) * 128 + (r & 7) * 16; }
 
+// byte offset of row r's first 16-byte group (k 0 .. 7 for BF16, k 0 .. 3
+// for TF32) inside a packed tile's first plane
+__device__ __forceinline__ int row_off(int fmt, int r) {
+    return (r >> 3) * (fmt == kFmtTF32 ? 512 : 256) + (r & 7) * 16;
+}
+
+// TF32 bit pattern of x rounded to nearest, ties away from zero
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// The 8 complex values of k-group kg (k = 8 kg .. 8 kg + 7) of one row of a
+// packed tile, row = tile + row_off(fmt, r); the imaginary parts times sgn.
+__device__ __forceinline__ void pk_store8(char* row, int fmt, int kg, const float2* v, float sgn) {
+    if (fmt == kFmtTF32) {
+        uint32_t re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            re[j] = tf32_rna(v[j].x);
+            im[j] = tf32_rna(v[j].y * sgn);
+        }
+        char* p = row + kg * 256;
+        *reinterpret_cast<uint4*>(p) = make_uint4(re[0], re[1], re[2], re[3]);
+        *reinterpret_cast<uint4*>(p + 128) = make_uint4(re[4], re[5], re[6], re[7]);
+        *reinterpret_cast<uint4*>(p + 8192) = make_uint4(im[0], im[1], im[2], im[3]);
+        *reinterpret_cast<uint4*>(p + 8192 + 128) = make_uint4(im[4], im[5], im[6], im[7]);
+        return;
+    }
+    uint32_t w[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        const float x[2][2] = {{v[j].x, v[j + 1].x}, {v[j].y * sgn, v[j + 1].y * sgn}};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[p][0], x[p][1]);
+            const float2 hf = __bfloat1622float2(hi);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[p][0] - hf.x, x[p][1] - hf.y);
+            w[2 * p][j >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
+            w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
+        }
+    }
+    char* dst = row + kg * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(dst + q * 4096) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+}
+
+// The inverse: the 8 complex values of k-group kg of a packed row (BF16:
+// hi + lo of each part, the BF16 halves widened by moving their bits into the
+// high half of an FP32 word; TF32: the stored words).
+__device__ __forceinline__ void pk_load8(const char* row, int fmt, int kg, float2* v) {
+    if (fmt == kFmtTF32) {
+        const char* p = row + kg * 256;
+        const uint4 r0 = *reinterpret_cast<const uint4*>(p), r1 = *reinterpret_cast<const uint4*>(p + 128);
+        const uint4 i0 = *reinterpret_cast<const uint4*>(p + 8192),
+                    i1 = *reinterpret_cast<const uint4*>(p + 8192 + 128);
+        const uint32_t re[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const uint32_t im[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        return;
+    }
+    const char* src = row + kg * 128;
+    uint4 w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = *reinterpret_cast<const uint4*>(src + q * 4096);
+    const uint32_t* wr = reinterpret_cast<const uint32_t*>(&w[0]);
+    const uint32_t* wl = reinterpret_cast<const uint32_t*>(&w[1]);
+    const uint32_t* wi = reinterpret_cast<const uint32_t*>(&w[2]);
+    const uint32_t* wm = reinterpret_cast<const uint32_t*>(&w[3]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t sh = (j & 1) * 16;
+        v[j] = make_float2(__uint_as_float(((wr[j >> 1] >> sh) & 0xffffu) << 16) +
+                               __uint_as_float(((wl[j >> 1] >> sh) & 0xffffu) << 16),
+                           __uint_as_float(((wi[j >> 1] >> sh) & 0xffffu) << 16) +
+                               __uint_as_float(((wm[j >> 1] >> sh) & 0xffffu) << 16));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // pack
 // ---------------------------------------------------------------------------
@@ -119,6 +226,7 @@ constexpr int PACK_KG = 2;
 
 __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) {
     const PackJob& J = jobs[blockIdx.y];
+    if (J.TR != 128) return;   // both formats are laid out on 128-row tiles
     const int nkc = (J.K + KC - 1) / KC;
     const int nrb = (J.R + J.TR - 1) / J.TR;
     const int r = blockIdx.x * 256 + threadIdx.x;
@@ -165,23 +273,7 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
                 v[j] = x;
             }
         }
-        uint32_t w[4][4];
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            const float x[2][2] = {{v[j].x, v[j + 1].x}, {v[j].y, v[j + 1].y}};
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const __nv_bfloat162 hi = __floats2bfloat162_rn(x[p][0], x[p][1]);
-                const float2 hf = __bfloat1622float2(hi);
-                const __nv_bfloat162 lo = __floats2bfloat162_rn(x[p][0] - hf.x, x[p][1] - hf.y);
-                w[2 * p][j >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
-                w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
-            }
-        }
-        char* tile = base + (size_t)kc * 4 * plane + core_off(rr, kg);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(tile + q * plane) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+        pk_store8(base + (size_t)kc * 4 * plane + row_off(J.fmt, rr), J.fmt, kg, v, 1.f);
     }
 }
 
@@ -204,47 +296,6 @@ constexpr int TP_KS = TP_K == 16 ? 4 : 5;   // log2(TP_K)
 static_assert(kPackTRB == 128 && KC == 16 && (TP_K == 16 || TP_K == 32),
               "tpack writes 128-row, 16-deep B tiles, 16 or 32 rows per CTA");
 
-__device__ __forceinline__ void split_store(char* dst, int plane, const float2* v, float sgn) {
-    uint32_t w[4][4];
-#pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-        const float x[2][2] = {{v[j].x, v[j + 1].x}, {v[j].y * sgn, v[j + 1].y * sgn}};
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[p][0], x[p][1]);
-            const float2 hf = __bfloat1622float2(hi);
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[p][0] - hf.x, x[p][1] - hf.y);
-            w[2 * p][j >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
-            w[2 * p + 1][j >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(dst + q * plane) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-}
-
-// The 8 complex values of k-group kg of one row of a 16-deep packed tile
-// (src = the row's 16-byte group in plane 0): hi + lo of each part, the
-// BF16 halves widened by moving their bits into the high half of an FP32 word.
-__device__ __forceinline__ void unpack8(const char* src, float2* v) {
-    constexpr int plane = 128 * 16 * 2;
-    uint4 w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w[q] = *reinterpret_cast<const uint4*>(src + q * plane);
-    const uint32_t* wr = reinterpret_cast<const uint32_t*>(&w[0]);
-    const uint32_t* wl = reinterpret_cast<const uint32_t*>(&w[1]);
-    const uint32_t* wi = reinterpret_cast<const uint32_t*>(&w[2]);
-    const uint32_t* wm = reinterpret_cast<const uint32_t*>(&w[3]);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint32_t sh = (j & 1) * 16;
-        v[j] = make_float2(__uint_as_float(((wr[j >> 1] >> sh) & 0xffffu) << 16) +
-                               __uint_as_float(((wl[j >> 1] >> sh) & 0xffffu) << 16),
-                           __uint_as_float(((wi[j >> 1] >> sh) & 0xffffu) << 16) +
-                               __uint_as_float(((wm[j >> 1] >> sh) & 0xffffu) << 16));
-    }
-}
-
 __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ tiles, cf* __restrict__ T,
                                                const cf* __restrict__ Tp, const double* __restrict__ alpha,
                                                int ns) {
@@ -265,9 +316,9 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
         const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
         const int nkcK = (P.Ki + 15) >> 4;
         const char* src = reinterpret_cast<const char*>(P.kn) +
-                          ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + core_off(n, kg);
+                          ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + row_off(P.fmt, n);
         float2 v[8];
-        unpack8(src, v);
+        pk_load8(src, P.fmt, kg, v);
         const bool nv = n0 + n < ns;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -321,8 +372,8 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
             const int k = P.k0 + kg * 8;   // multiple of 8
             const int nn = n0 + n;
             char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
-                        core_off(nn & 127, (k >> 3) & 1);
-            split_store(dst, plane, v, 1.f);
+                        row_off(P.fmt, nn & 127);
+            pk_store8(dst, P.fmt, (k >> 3) & 1, v, 1.f);
         }
     }
     // phase 3: NK, rows = factor index, k = n; conjugated
@@ -339,8 +390,8 @@ __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ til
             for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
             const int r = P.k0 + kk;
             char* dst = reinterpret_cast<char*>(P.nk_dst) + ((long long)(r >> 7) * nkcN + (nb >> 4)) * 4 * plane +
-                        core_off(r & 127, (nb >> 3) & 1);
-            split_store(dst, plane, v, -1.f);
+                        row_off(P.fmt, r & 127);
+            pk_store8(dst, P.fmt, (nb >> 3) & 1, v, -1.f);
         }
     }
 }
@@ -390,7 +441,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
                                                const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
                                                int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
                                                double* __restrict__ part, const long long* __restrict__ roff,
-                                               int nblk) {
+                                               int nblk, int fmt) {
     __shared__ float2 s[TP_K * TP_LD];
     __shared__ double sh[32];
     constexpr int plane = 128 * 16 * 2;
@@ -406,7 +457,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
         const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
         const bool nv = n0 + n < ns;
         float2 v[8];
-        unpack8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + core_off(n, kg), v);
+        pk_load8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + row_off(fmt, n), fmt, kg, v);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int kk = kg * 8 + j;
@@ -460,8 +511,8 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
             const int rl = rl0 + kk;
-            char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + core_off(rl & 127, (nb >> 3) & 1);
-            split_store(dst, plane, v, 1.f);
+            char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + row_off(fmt, rl & 127);
+            pk_store8(dst, fmt, (nb >> 3) & 1, v, 1.f);
         }
     }
     // phase 3: KN, rows = n, k = receiver of block blk
@@ -476,8 +527,8 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = s[(kg * 8 + j) * TP_LD + n];
             const int k = rl0 + kg * 8;
-            char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + core_off(nn & 127, (k >> 3) & 1);
-            split_store(dst, plane, v, 1.f);
+            char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + row_off(fmt, nn & 127);
+            pk_store8(dst, fmt, (k >> 3) & 1, v, 1.f);
         }
     }
 }
@@ -491,7 +542,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
 __global__ void __launch_bounds__(256) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
                                                 const cf* __restrict__ A2, int ns, int nr, int b,
                                                 const long long* __restrict__ roff, int nblk,
-                                                double* __restrict__ part) {
+                                                double* __restrict__ part, int fmt) {
     __shared__ double sh[32];
     constexpr int plane = 128 * 16 * 2;
     const int gx = (ns + TP_N - 1) / TP_N;
@@ -503,7 +554,8 @@ __global__ void __launch_bounds__(256) k_dots6p(char* const* __restrict__ kn, co
         if (n0 + n >= ns) continue;
         const RTile tl = rtile(r0, b, roff, nblk);
         float2 v[8];
-        unpack8(kn[tl.blk] + ((long long)(n0 >> 7) * (tl.bK >> 4) + (tl.rl0 >> 4)) * 4 * plane + core_off(n, kg), v);
+        pk_load8(kn[tl.blk] + ((long long)(n0 >> 7) * (tl.bK >> 4) + (tl.rl0 >> 4)) * 4 * plane + row_off(fmt, n), fmt,
+                 kg, v);
         float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -534,11 +586,132 @@ __global__ void __launch_bounds__(256) k_dots6p(char* const* __restrict__ kn, co
 // ---------------------------------------------------------------------------
 // GEMM on packed operands
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs, int nsplit, int kchunk,
-                                                       int epi, long long part_stride, int* err) {
+// Epilogue of one 128 x TN output tile (warps 0-7): warp w reads TMEM lanes
+// 32 (w % 4) .. +31 and columns [TN/2 (w / 4), +TN/2) of the accumulator
+// pair at tmem (Cr at column 0, Ci at column TN; zeros when !have, a tile
+// without K chunks) and writes the tile to its destination: a packed NK
+// operand (EPI_PACKNK), or rows of C (store, subtract S, accumulate, split-K
+// partial) through the warp's 32 x 17 staging block stg in shared memory.
+__device__ __forceinline__ void epi_drain(const PProb& P, int m0, int n0, long long part_off, int epi, int fmt,
+                                          uint32_t tmem, bool have, cf* stg, int warp, int lane) {
+    if (epi == EPI_PACKNK) {
+        // Row m goes to one row of a packed NK operand: 16 columns are one
+        // 16-deep chunk there (two k-groups of 8).  Lanes hold consecutive
+        // rows, which are 16 bytes apart in the packed tile.
+        const int lg = warp & 3, ch = warp >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
+        const int m = m0 + lg * 32 + lane;
+#pragma unroll 1
+        for (int cb = 0; cb < TN / 32; ++cb) {
+            const int col = ch * (TN / 2) + cb * 16;
+            if (n0 + col >= P.N) break;
+            float pr[16], pi[16];
+            if (have) {
+                tmem_ld16(lane_addr + col, pr);
+                tmem_ld16(lane_addr + TN + col, pi);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
+            }
+            if (m < P.M) {
+                const int n = n0 + col;
+                float2 v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = n + j < P.N ? make_float2(pr[j], pi[j]) : make_float2(0.f, 0.f);
+                char* d = P.rowptr[m] + (long long)(n >> 4) * PK_TILE;
+                pk_store8(d, fmt, 0, v, 1.f);
+                pk_store8(d, fmt, 1, v + 8, 1.f);
+            }
+        }
+        return;
+    }
+    // Each warp drains 32 rows x 16 columns at a time: tcgen05.ld gives a
+    // thread one row; the block is transposed through shared memory so that
+    // each store instruction writes four full 128-byte row segments.
+    const int lg = warp & 3, ch = warp >> 2;
+    cf* Cp = P.C + (epi == EPI_PARTIAL ? part_off : 0);
+    const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
+    const int rsub = lane >> 3, q = lane & 7;   // write phase: row group, 16-B chunk
+#pragma unroll 1
+    for (int cb = 0; cb < TN / 32; ++cb) {
+        const int col = ch * (TN / 2) + cb * 16;
+        if (n0 + col >= P.N) break;
+        float pr[16], pi[16];
+        if (have) {
+            tmem_ld16(lane_addr + col, pr);
+            tmem_ld16(lane_addr + TN + col, pi);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = make_float2(pr[j], pi[j]);
+        __syncwarp();
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) {
+            const int r = j2 * 4 + rsub;
+            const int m = m0 + lg * 32 + r;
+            const int n = n0 + col + 2 * q;
+            if (m < P.M && n < P.N) {
+                const long long o = (long long)m * P.ldc + n;
+                cf v0 = stg[r * 17 + 2 * q], v1 = stg[r * 17 + 2 * q + 1];
+                const bool two = n + 1 < P.N;
+                if (epi == EPI_SUB) {
+                    const cf s0 = P.S[o];
+                    v0.x -= s0.x;
+                    v0.y -= s0.y;
+                    if (two) {
+                        const cf s1 = P.S[o + 1];
+                        v1.x -= s1.x;
+                        v1.y -= s1.y;
+                    }
+                } else if (epi == EPI_ACCUM) {
+                    const cf c0 = Cp[o];
+                    v0.x += c0.x;
+                    v0.y += c0.y;
+                    if (two) {
+                        const cf c1 = Cp[o + 1];
+                        v1.x += c1.x;
+                        v1.y += c1.y;
+                    }
+                }
+                if (two && ((reinterpret_cast<uintptr_t>(Cp + o) & 15) == 0)) {
+                    *reinterpret_cast<float4*>(Cp + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                } else {
+                    Cp[o] = v0;
+                    if (two) Cp[o + 1] = v1;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Grid (M tiles, N tiles, problems x splits) with the M tile fastest in
+// launch order (mfast): the CTAs that read the same B tile (all M tiles of an
+// N tile) run together and the later ones find it in L2; (N, M, ...) when
+// the N tiles exceed the grid's y limit.
+__global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs,
+                                                       const ZItem* __restrict__ zmap, int nsplit, int kchunk,
+                                                       int epi, long long part_stride, int* err, int fmt,
+                                                       int mfast) {
     extern __shared__ __align__(1024) char smem[];
-    const int prob = blockIdx.z / nsplit, chunk = blockIdx.z % nsplit;
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    // slice z: problem and split (uniform, or each problem its own through zmap)
+    int prob, chunk;
+    long long part_off;
+    if (zmap) {
+        const ZItem zi = zmap[blockIdx.z];
+        prob = zi.prob;
+        chunk = zi.chunk;
+        kchunk = zi.kchunk;
+        part_off = zi.part_off;
+    } else {
+        prob = blockIdx.z / nsplit;
+        chunk = blockIdx.z % nsplit;
+        kchunk = nsplit > 1 ? kchunk : 0;
+        part_off = (long long)chunk * part_stride;
+    }
+    const int m0 = (mfast ? blockIdx.x : blockIdx.y) * TM, n0 = (mfast ? blockIdx.y : blockIdx.x) * TN;
     {
         const PProb& Pg = probs[prob];
         if (m0 >= Pg.M || n0 >= Pg.N) return;
@@ -581,7 +754,7 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
     int C = 0;
     for (int ti = 0; ti < P.nt; ++ti) {
         int kb = 0, ke = P.t[ti].K;
-        if (nsplit > 1) {
+        if (kchunk > 0) {
             kb = chunk * kchunk;
             ke = min(P.t[ti].K, kb + kchunk);
         }
@@ -594,7 +767,7 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
         for (int ti = 0; ti < P.nt && !*abort_flag; ++ti) {
             const PTerm& t = P.t[ti];
             int kb = 0, ke = t.K;
-            if (nsplit > 1) {
+            if (kchunk > 0) {
                 kb = chunk * kchunk;
                 ke = min(t.K, kb + kchunk);
             }
@@ -635,11 +808,30 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + TILE_A;
+            const uint32_t dr = tmem, di = tmem + TN;
+            const uint32_t first = c > 0 ? 1u : 0u;
+            if (fmt == kFmtTF32) {
+                // planes Re, Im of 8 KB; K = 8 per MMA: two K steps 256 B apart
+                constexpr int PA = TILE_A / 2, PB = TILE_B / 2;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t o = ks * 256;
+                    const uint64_t ar = sdesc(a0 + o, 512u), ai = sdesc(a0 + PA + o, 512u);
+                    const uint64_t br = sdesc(b0 + o, 512u), bi = sdesc(b0 + PB + o, 512u);
+                    const uint32_t acc = ks > 0 ? 1u : first;
+                    mma_tf32(dr, ar, br, IDESC_TF32, acc);
+                    mma_tf32(dr, ai, bi, IDESC_TF32_NEG_A, 1u);
+                    mma_tf32(di, ar, bi, IDESC_TF32, acc);
+                    mma_tf32(di, ai, br, IDESC_TF32, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+                continue;
+            }
             constexpr int PA = TILE_A / 4, PB = TILE_B / 4;
             const uint64_t arh = sdesc(a0), arl = sdesc(a0 + PA), aih = sdesc(a0 + 2 * PA), ail = sdesc(a0 + 3 * PA);
             const uint64_t brh = sdesc(b0), brl = sdesc(b0 + PB), bih = sdesc(b0 + 2 * PB), bil = sdesc(b0 + 3 * PB);
-            const uint32_t dr = tmem, di = tmem + TN;
-            const uint32_t first = c > 0 ? 1u : 0u;
             mma_bf16(dr, arh, brh, IDESC, first);
             mma_bf16(dr, arh, brl, IDESC, 1u);
             mma_bf16(dr, arl, brh, IDESC, 1u);
@@ -669,104 +861,264 @@ __global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __
         if (threadIdx.x == 0 || !ok) atomicExch(err, TLR_ERR_TIMEOUT);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 8 && ok && !*abort_flag && epi == EPI_PACKNK) {
-        // Row m goes to one row of a packed NK operand: 16 columns are one
-        // 16-deep chunk there (two 16-byte groups per BF16 plane).  Lanes hold
-        // consecutive rows, which are 16 bytes apart in the packed tile.
-        const int lg = warp & 3, ch = warp >> 2;
-        const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
-        const int m = m0 + lg * 32 + lane;
-        constexpr int plane = 128 * 16 * 2;
-#pragma unroll 1
-        for (int cb = 0; cb < TN / 32; ++cb) {
-            const int col = ch * (TN / 2) + cb * 16;
-            if (n0 + col >= P.N) break;
-            float pr[16], pi[16];
-            if (C > 0) {
-                tmem_ld16(lane_addr + col, pr);
-                tmem_ld16(lane_addr + TN + col, pi);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
-            }
-            if (m < P.M) {
-                const int n = n0 + col;
-                float2 v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = n + j < P.N ? make_float2(pr[j], pi[j]) : make_float2(0.f, 0.f);
-                char* d = P.rowptr[m] + (long long)(n >> 4) * 4 * plane;
-                split_store(d, plane, v, 1.f);
-                split_store(d + 128, plane, v + 8, 1.f);
-            }
-        }
-    } else if (warp < 8 && ok && !*abort_flag) {
-        // Each warp drains 32 rows x 16 columns at a time: tcgen05.ld gives a
-        // thread one row; the block is transposed through shared memory (the
-        // operand ring is idle once the last MMA has completed) so that each
-        // store instruction writes four full 128-byte row segments.
-        const int lg = warp & 3, ch = warp >> 2;
-        cf* Cp = P.C + (epi == EPI_PARTIAL ? chunk * part_stride : 0);
-        const uint32_t lane_addr = tmem + ((uint32_t)(lg * 32) << 16);
-        cf* stg = reinterpret_cast<cf*>(smem) + warp * (32 * 17);   // 32 rows x 16 (+1 pad)
-        const int rsub = lane >> 3, q = lane & 7;                   // write phase: row group, 16-B chunk
-#pragma unroll 1
-        for (int cb = 0; cb < TN / 32; ++cb) {
-            const int col = ch * (TN / 2) + cb * 16;
-            if (n0 + col >= P.N) break;
-            float pr[16], pi[16];
-            if (C > 0) {
-                tmem_ld16(lane_addr + col, pr);
-                tmem_ld16(lane_addr + TN + col, pi);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) pr[j] = pi[j] = 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = make_float2(pr[j], pi[j]);
-            __syncwarp();
-#pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) {
-                const int r = j2 * 4 + rsub;
-                const int m = m0 + lg * 32 + r;
-                const int n = n0 + col + 2 * q;
-                if (m < P.M && n < P.N) {
-                    const long long o = (long long)m * P.ldc + n;
-                    cf v0 = stg[r * 17 + 2 * q], v1 = stg[r * 17 + 2 * q + 1];
-                    const bool two = n + 1 < P.N;
-                    if (epi == EPI_SUB) {
-                        const cf s0 = P.S[o];
-                        v0.x -= s0.x;
-                        v0.y -= s0.y;
-                        if (two) {
-                            const cf s1 = P.S[o + 1];
-                            v1.x -= s1.x;
-                            v1.y -= s1.y;
-                        }
-                    } else if (epi == EPI_ACCUM) {
-                        const cf c0 = Cp[o];
-                        v0.x += c0.x;
-                        v0.y += c0.y;
-                        if (two) {
-                            const cf c1 = Cp[o + 1];
-                            v1.x += c1.x;
-                            v1.y += c1.y;
-                        }
-                    }
-                    if (two && ((reinterpret_cast<uintptr_t>(Cp + o) & 15) == 0)) {
-                        *reinterpret_cast<float4*>(Cp + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
-                    } else {
-                        Cp[o] = v0;
-                        if (two) Cp[o + 1] = v1;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
+    if (warp < 8 && ok && !*abort_flag)
+        epi_drain(P, m0, n0, part_off, epi, fmt, tmem, C > 0,
+                  reinterpret_cast<cf*>(smem) + warp * (32 * 17), warp, lane);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == WMMA) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of the packed GEMM: one CTA per SM walks the launch's
+// output tiles (item i = (y, x, z): M tile y fastest, then N tile x, then
+// problem-and-split z; CTA c takes items c, c + grid, ...), with the copy
+// thread streaming K chunks across tile boundaries through a 5-stage ring and
+// two TMEM accumulator pairs (512 columns): the MMA thread fills one pair
+// while the eight epilogue warps drain the other, so a tile's set-up,
+// pipeline fill and epilogue overlap the next tile's MMAs.  Items outside
+// their problem are skipped by every role alike; items without K chunks are
+// written as zeros by the epilogue alone.  Every wait is bounded (2 s, or an
+// abort by another role); before it returns, the copy thread waits (bounded)
+// for its copies still in flight.
+constexpr int P_NSTAGE = 5;
+constexpr int P_STG_OFF = P_NSTAGE * STAGE;                 // 160 KB of operand ring
+constexpr int P_CTRL_OFF = P_STG_OFF + 8 * 32 * 17 * 8;     // + 34 KB epilogue staging
+constexpr int P_SMEM_BYTES = P_CTRL_OFF + 256;
+constexpr uint32_t P_TMEM_COLS = 512;                       // two accumulator pairs of 2 x TN columns
+static_assert(P_SMEM_BYTES <= 227 * 1024, "shared memory of the persistent GEMM");
+static_assert(2 * 2 * TN <= (int)P_TMEM_COLS, "two accumulator pairs");
+
+struct PItem {
+    int prob, m0, n0, chunk, kchunk;   // kchunk 0: the whole K
+    long long part_off;
+};
+
+// item i: M tile fastest (the items that share a B tile are adjacent), then
+// N tile, then slice z (problem and split: z / nsplit, z % nsplit, or zmap[z])
+__device__ __forceinline__ bool p_item(const PProb* probs, const ZItem* zmap, long long i, int nx, int ny,
+                                       int nsplit, int kchunk, long long part_stride, PItem& it) {
+    const long long xy = (long long)nx * ny;
+    const int z = (int)(i / xy);
+    const int r = (int)(i - (long long)z * xy);
+    if (zmap) {
+        const ZItem zi = zmap[z];
+        it.prob = zi.prob;
+        it.chunk = zi.chunk;
+        it.kchunk = zi.kchunk;
+        it.part_off = zi.part_off;
+    } else {
+        it.prob = z / nsplit;
+        it.chunk = z - it.prob * nsplit;
+        it.kchunk = nsplit > 1 ? kchunk : 0;
+        it.part_off = (long long)it.chunk * part_stride;
+    }
+    it.m0 = (r % ny) * TM;
+    it.n0 = (r / ny) * TN;
+    const PProb& P = probs[it.prob];
+    return it.m0 < P.M && it.n0 < P.N;
+}
+
+// the K range [kb, ke) of term t for an item
+__device__ __forceinline__ void p_range(const PTerm& t, const PItem& it, int& kb, int& ke) {
+    kb = 0;
+    ke = t.K;
+    if (it.kchunk > 0) {
+        kb = it.chunk * it.kchunk;
+        ke = min(t.K, kb + it.kchunk);
+    }
+}
+
+// K chunks of one item (16-deep chunks over its terms)
+__device__ __forceinline__ int p_chunks(const PProb& P, const PItem& it) {
+    int C = 0;
+    for (int ti = 0; ti < P.nt; ++ti) {
+        int kb, ke;
+        p_range(P.t[ti], it, kb, ke);
+        if (ke > kb) C += (ke - kb + KC - 1) / KC;
+    }
+    return C;
+}
+
+__global__ void __launch_bounds__(NTHR, 1) k_cgemm_tcp_pers(const PProb* __restrict__ probs,
+                                                            const ZItem* __restrict__ zmap, int nsplit, int kchunk,
+                                                            int epi, long long part_stride, int* err, int fmt,
+                                                            int nx, int ny, long long nitems) {
+    extern __shared__ __align__(1024) char smem[];
+    if (*(volatile int*)err != 0) return;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + P_CTRL_OFF);
+    uint64_t* empty = full + P_NSTAGE;
+    uint64_t* tfull = empty + P_NSTAGE;    // [2] accumulator pair ready for the epilogue
+    uint64_t* tempty = tfull + 2;          // [2] accumulator pair drained (8 warp arrivals)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P_NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tempty[b])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (warp == WMMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(P_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == WCOPY && lane == 0) {
+        // ---------------- bulk copies, across tiles ----------------
+        long long c = 0;
+        for (long long i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x) {
+            PItem it;
+            if (!p_item(probs, zmap, i, nx, ny, nsplit, kchunk, part_stride, it)) continue;
+            const PProb& P = probs[it.prob];
+            for (int ti = 0; ti < P.nt && !*abort_flag; ++ti) {
+                const PTerm& t = P.t[ti];
+                int kb, ke;
+                p_range(t, it, kb, ke);
+                const int nkc = (t.K + KC - 1) / KC;
+                const char* abase = reinterpret_cast<const char*>(t.A) + (long long)(it.m0 / TM) * nkc * TILE_A;
+                const char* bbase = reinterpret_cast<const char*>(t.B) + (long long)(it.n0 / TN) * nkc * TILE_B;
+                for (int k0 = kb; k0 < ke; k0 += KC, ++c) {
+                    const int s = (int)(c % P_NSTAGE);
+                    if (c >= P_NSTAGE &&
+                        !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((c / P_NSTAGE) - 1) & 1), err)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE)
+                                 : "memory");
+                    const int kc = k0 / KC;
+                    const uint32_t dst = smem_u32(smem + s * STAGE);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            dst),
+                        "l"(abase + (long long)kc * TILE_A), "r"(TILE_A), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            dst + TILE_A),
+                        "l"(bbase + (long long)kc * TILE_B), "r"(TILE_B), "r"(fb)
+                        : "memory");
+                }
+            }
+        }
+        // copies still in flight land before the CTA's shared memory goes away
+        for (long long j = c - 1; j >= 0 && j >= c - P_NSTAGE; --j) {
+            const int s = (int)(j % P_NSTAGE);
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((j / P_NSTAGE) & 1), err)) *abort_flag = 1;
+        }
+    } else if (warp == WMMA && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        long long c = 0, u = 0;
+        for (long long i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x) {
+            PItem it;
+            if (!p_item(probs, zmap, i, nx, ny, nsplit, kchunk, part_stride, it)) continue;
+            const int C = p_chunks(probs[it.prob], it);
+            if (C == 0) continue;
+            const int ab = (int)(u & 1);
+            if (u >= 2 && !mbar_wait(smem_u32(&tempty[ab]), (uint32_t)(((u >> 1) - 1) & 1), err)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dr = tmem + ab * 2 * TN, di = dr + TN;
+            for (int k = 0; k < C; ++k, ++c) {
+                const int s = (int)(c % P_NSTAGE);
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((c / P_NSTAGE) & 1), err)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + TILE_A;
+                const uint32_t first = k > 0 ? 1u : 0u;
+                if (fmt == kFmtTF32) {
+                    constexpr int PA = TILE_A / 2, PB = TILE_B / 2;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t o = ks * 256;
+                        const uint64_t ar = sdesc(a0 + o, 512u), ai = sdesc(a0 + PA + o, 512u);
+                        const uint64_t br = sdesc(b0 + o, 512u), bi = sdesc(b0 + PB + o, 512u);
+                        const uint32_t acc = ks > 0 ? 1u : first;
+                        mma_tf32(dr, ar, br, IDESC_TF32, acc);
+                        mma_tf32(dr, ai, bi, IDESC_TF32_NEG_A, 1u);
+                        mma_tf32(di, ar, bi, IDESC_TF32, acc);
+                        mma_tf32(di, ai, br, IDESC_TF32, 1u);
+                    }
+                } else {
+                    constexpr int PA = TILE_A / 4, PB = TILE_B / 4;
+                    const uint64_t arh = sdesc(a0), arl = sdesc(a0 + PA), aih = sdesc(a0 + 2 * PA),
+                                   ail = sdesc(a0 + 3 * PA);
+                    const uint64_t brh = sdesc(b0), brl = sdesc(b0 + PB), bih = sdesc(b0 + 2 * PB),
+                                   bil = sdesc(b0 + 3 * PB);
+                    mma_bf16(dr, arh, brh, IDESC, first);
+                    mma_bf16(dr, arh, brl, IDESC, 1u);
+                    mma_bf16(dr, arl, brh, IDESC, 1u);
+                    mma_bf16(dr, aih, bih, IDESC_NEG_A, 1u);
+                    mma_bf16(dr, aih, bil, IDESC_NEG_A, 1u);
+                    mma_bf16(dr, ail, bih, IDESC_NEG_A, 1u);
+                    mma_bf16(di, arh, bih, IDESC, first);
+                    mma_bf16(di, arh, bil, IDESC, 1u);
+                    mma_bf16(di, arl, bih, IDESC, 1u);
+                    mma_bf16(di, aih, brh, IDESC, 1u);
+                    mma_bf16(di, aih, brl, IDESC, 1u);
+                    mma_bf16(di, ail, brh, IDESC, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+            }
+            if (*abort_flag) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&tfull[ab]))
+                         : "memory");
+            ++u;
+        }
+    } else if (warp < 8) {
+        // ---------------- epilogue, one accumulator pair at a time ----------------
+        cf* stg = reinterpret_cast<cf*>(smem + P_STG_OFF) + warp * (32 * 17);
+        long long u = 0;
+        for (long long i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x) {
+            PItem it;
+            if (!p_item(probs, zmap, i, nx, ny, nsplit, kchunk, part_stride, it)) continue;
+            const PProb& P = probs[it.prob];
+            const int C = p_chunks(P, it);
+            if (C == 0) {
+                epi_drain(P, it.m0, it.n0, it.part_off, epi, fmt, tmem, false, stg, warp, lane);
+                continue;
+            }
+            const int ab = (int)(u & 1);
+            if (!mbar_wait(smem_u32(&tfull[ab]), (uint32_t)((u >> 1) & 1), err)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epi_drain(P, it.m0, it.n0, it.part_off, epi, fmt, tmem + ab * 2 * TN, true, stg, warp, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[ab])) : "memory");
+            ++u;
+        }
+    }
+    if (*abort_flag && threadIdx.x == 0) atomicExch(err, TLR_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == WMMA) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P_TMEM_COLS) : "memory");
     }
 }
 
@@ -816,24 +1168,24 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 long long rstep_ctas(int nr, int ns) { return (long long)((ns + TP_N - 1) / TP_N) * (nr / TP_K); }
 
 cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr, int ns, int b, char* const* kn,
-                  char* const* mk, double* part, cudaStream_t st, const long long* roff, int nblk) {
+                  char* const* mk, double* part, cudaStream_t st, const long long* roff, int nblk, int fmt) {
     if (nr == 0 || ns == 0) return cudaSuccess;
     if (nr % TP_K != 0) return cudaErrorInvalidValue;
     if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
-    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk);
+    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk, fmt);
     counted(1);
     return cudaGetLastError();
 }
 
 cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, int ns, int b, double* part,
-                         cudaStream_t st, const long long* roff, int nblk) {
+                         cudaStream_t st, const long long* roff, int nblk, int fmt) {
     if (nr == 0 || ns == 0) return cudaSuccess;
     if (nr % TP_K != 0) return cudaErrorInvalidValue;
     if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
-    k_dots6p<<<kRedBlocks, 256, 0, st>>>(kn, A1, A2, ns, nr, b, roff, nblk, part);
+    k_dots6p<<<kRedBlocks, 256, 0, st>>>(kn, A1, A2, ns, nr, b, roff, nblk, part, fmt);
     counted(1);
     return cudaGetLastError();
 }
@@ -846,15 +1198,38 @@ cudaError_t wait_selftest(int* status, unsigned long long limit_ns, unsigned lon
 }
 
 cudaError_t gemm_tcp_prepare() {
-    return cudaFuncSetAttribute(k_cgemm_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_cgemm_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cgemm_tcp_pers, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    return e;
 }
 
 cudaError_t gemm_tcp(const GemmLaunch& L, cudaStream_t st) {
     if (L.nprob == 0 || L.maxM == 0 || L.maxN == 0) return cudaSuccess;
     if (!L.err || !L.d_pprobs) return cudaErrorInvalidValue;
-    dim3 grid((L.maxN + TN - 1) / TN, (L.maxM + TM - 1) / TM, L.nprob * L.nsplit);
     const int kchunk = L.nsplit > 1 ? L.kchunk : 0;
-    k_cgemm_tcp<<<grid, NTHR, SMEM_BYTES, st>>>(L.d_pprobs, L.nsplit, kchunk, L.epi, L.part_stride, L.err);
+    if (L.persistent) {
+        const int nx = (L.maxN + TN - 1) / TN, ny = (L.maxM + TM - 1) / TM;
+        const long long nz = L.d_zmap ? L.nz : (long long)L.nprob * L.nsplit;
+        const long long nitems = (long long)nx * ny * nz;
+        if (nitems == 0) return cudaSuccess;
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+        const unsigned g = (unsigned)std::min<long long>(sms, nitems);
+        k_cgemm_tcp_pers<<<g, NTHR, P_SMEM_BYTES, st>>>(L.d_pprobs, L.d_zmap, L.nsplit, kchunk, L.epi,
+                                                        L.part_stride, L.err, pack_fmt(L.prec), nx, ny, nitems);
+        counted(1);
+        return cudaGetLastError();
+    }
+    const unsigned mt = (unsigned)((L.maxM + TM - 1) / TM), nt = (unsigned)((L.maxN + TN - 1) / TN);
+    const int mfast = nt <= 65535u ? 1 : 0;
+    const unsigned nzs = (unsigned)(L.d_zmap ? L.nz : L.nprob * L.nsplit);
+    if (nzs == 0) return cudaSuccess;
+    dim3 grid(mfast ? mt : nt, mfast ? nt : mt, nzs);
+    k_cgemm_tcp<<<grid, NTHR, SMEM_BYTES, st>>>(L.d_pprobs, L.d_zmap, L.nsplit, kchunk, L.epi, L.part_stride, L.err,
+                                                 pack_fmt(L.prec), mfast);
     counted(1);
     return cudaGetLastError();
 }

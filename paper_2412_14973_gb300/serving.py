@@ -5,10 +5,18 @@ server admits arrived requests in arrival order while the device-memory
 budget (the library's own footprint figure, ``tlr_mdd_workspace_bytes``) and
 the number of slots allow, runs each admitted solve asynchronously on a
 stream of its own (``tlr_mdd_solve_async``: the solve's launch sequence is a
-recorded CUDA graph), and, as solves finish, frees their memory and admits
-the next requests, so work from requests that arrived at different times
-overlaps on the GPU.  A request larger than the whole budget is rejected at
-admission (TLR_ERR_NOMEM), never attempted.
+recorded CUDA graph), and, as solves finish, admits the next requests, so
+work from requests that arrived at different times overlaps on the GPU.  A
+request larger than the whole budget is rejected at admission
+(TLR_ERR_NOMEM), never attempted.
+
+Finished handles are kept, with their workspace and recorded solve, in a
+cache keyed by the problem's shape (nr, ns, grid, tiles, ranks, diagonal
+modes, precision): a later request of that shape takes one over
+(``tlr_mdd_set_stream`` to its slot's stream, ``tlr_mdd_set_data`` for its
+D, U), so its admission allocates nothing and records nothing.  Idle cached
+handles count against the budget and are destroyed, least recently used
+first, when an admission needs their memory.
 
 Only host-side scheduling lives here; every computation is in the CUDA
 library.  Results do not depend on what else is running: the library's
@@ -59,12 +67,30 @@ class SolveResult:
         return self.admitted - self.arrival
 
 
+def shape_key(d):
+    """Cache key of a problem description: every field that shapes the
+    handle's layout, workspace and recorded solve (not the data)."""
+    if isinstance(d, T.Desc):
+        arrays = tuple(tuple(a) for a in getattr(d, "_keep", []))
+        return (d.nr, d.ns, d.nx, d.ny, d.tile, d.rank, d.diag_mode, d.reciprocity, d.precision, d.alpha,
+                d.input_memory, d.ntiles, bool(d.tiles), bool(d.perm), bool(d.ranks), bool(d.diag_dense), arrays)
+    try:
+        hash(d)
+        return d
+    except TypeError:
+        return id(d)
+
+
 class Server:
     def __init__(self, hbm_budget_bytes: int, max_active: int = 8, device=None, poll_s: float = 2e-4,
-                 stream_factory=None):
+                 stream_factory=None, reuse: bool = True, batch_max: int = 1, window: int = 32):
         self.budget = int(hbm_budget_bytes)
         self.max_active = max(1, int(max_active))
         self.poll_s = poll_s
+        self.reuse = reuse
+        self.batch_max = max(1, int(batch_max))   # requests per lockstep batch (1: one per slot)
+        self.window = window                      # queued requests scanned for batch partners
+        self.batches = 0
         if stream_factory is None:
             dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
             stream_factory = lambda: torch.cuda.Stream(device=dev)  # noqa: E731
@@ -72,65 +98,121 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self.peak_active = 0
+        self.idle = collections.OrderedDict()   # handle -> (key, bytes), least recently used first
+        self.created = 0
+        self.reused = 0
+        self.evicted = 0
 
     def footprint(self, req: SolveRequest) -> int:
         return T.tlr_mdd_workspace_bytes(req.desc)
+
+    def _take_idle(self, key):
+        for h, (k, need) in reversed(self.idle.items()):
+            if k == key:
+                del self.idle[h]
+                return h, need
+        return None, 0
+
+    def _evict_until(self, need) -> None:
+        while self.idle and self.used + need > self.budget:
+            h, (k, n) = self.idle.popitem(last=False)
+            T.tlr_mdd_destroy(h)
+            self.used -= n
+            self.evicted += 1
+
+    def close(self) -> None:
+        """Destroy the cached idle handles and release their memory."""
+        while self.idle:
+            h, (k, n) = self.idle.popitem(last=False)
+            T.tlr_mdd_destroy(h)
+            self.used -= n
+
+    def _acquire(self, req, key):
+        """A handle for req: a cached one of its shape (no allocation), or the
+        budget for a new one (idle handles evicted as needed).  Returns
+        (handle or None, bytes, status): status -4 when the request can never
+        fit, 1 when it must wait for memory, 0 otherwise."""
+        h, need = self._take_idle(key) if self.reuse else (None, 0)
+        if h is not None:
+            return h, need, 0
+        need = self.footprint(req)
+        if need < 0 or need > self.budget:
+            return None, need, -4
+        self._evict_until(need)
+        if self.used + need > self.budget:
+            return None, need, 1
+        return None, need, 0
+
+    def _group(self, queue, realtime, now):
+        """The head request and, when batching, later arrived requests of the
+        same size, precision and solver options (lockstep solves end together)."""
+        head = queue[0]
+        group = [head]
+        if self.batch_max <= 1 or getattr(head.desc, "precision", 0) == T.TLR_PREC_FP32:
+            return group
+        hk = (getattr(head.desc, "nr", None), getattr(head.desc, "precision", None), _opts_key(head.opts))
+        for r in list(queue)[1:self.window]:
+            if len(group) >= self.batch_max or (realtime and r.arrival > now):
+                break
+            if (getattr(r.desc, "nr", None), getattr(r.desc, "precision", None), _opts_key(r.opts)) == hk:
+                group.append(r)
+        return group
 
     def run(self, requests, realtime: bool = True) -> list:
         """Serve ``requests``; with ``realtime`` a request is not admitted
         before its arrival time (seconds from the call), else all arrive at 0."""
         queue = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         free = list(range(self.max_active))
-        active = {}
+        active = []   # units: (slot, members [(req, h, theta, need, key, t_adm, fresh)], batch or None)
         out = []
         t0 = time.perf_counter()
         while queue or active:
             now = time.perf_counter() - t0
             progressed = False
             while queue and free and (not realtime or queue[0].arrival <= now):
-                req = queue[0]
-                need = self.footprint(req)
-                if need < 0 or need > self.budget:
-                    queue.popleft()
-                    out.append(SolveResult(req.rid, None, -4, "request exceeds the device-memory budget",
-                                           req.arrival, now, now, 0.0, 0))
-                    progressed = True
+                members = []
+                blocked = False
+                for req in self._group(queue, realtime, now):
+                    key = shape_key(req.desc)
+                    h, need, st = self._acquire(req, key)
+                    if st == -4:
+                        if req is queue[0] or not members:
+                            queue.remove(req)
+                            out.append(SolveResult(req.rid, None, -4, "request exceeds the device-memory budget",
+                                                   req.arrival, now, now, 0.0, 0))
+                            progressed = True
+                        continue
+                    if st == 1:
+                        blocked = not members   # the head waits for memory; later ones wait their turn
+                        break
+                    fresh = h is None
+                    if fresh:
+                        self.used += need
+                    members.append([req, h, None, need, key, now, fresh])
+                if not members:
+                    if blocked:
+                        break   # first-come first-served: wait for memory to free up
                     continue
-                if self.used + need > self.budget:
-                    break   # first-come first-served: wait for memory to free up
-                queue.popleft()
+                for m in members:
+                    queue.remove(m[0])
                 slot = free.pop()
                 stream = self.streams[slot]
-                theta = req.theta0.clone() if hasattr(req.theta0, "clone") else req.theta0
-                try:
-                    h = T.tlr_mdd_create(req.desc, req.D, req.U, stream)
-                    T.tlr_mdd_solve_async(h, theta, req.opts)
-                except T.TLRError as e:
+                unit = self._start(members, stream, out, now)
+                if unit is None:
                     free.append(slot)
-                    out.append(SolveResult(req.rid, None, e.code, str(e), req.arrival, now, now, 0.0, 0))
-                    progressed = True
-                    continue
-                self.used += need
+                else:
+                    active.append((slot,) + unit)
+                    self.peak_active = max(self.peak_active, sum(len(u[1]) for u in active))
                 self.peak_used = max(self.peak_used, self.used)
-                active[req.rid] = (req, h, slot, theta, need, now)
-                self.peak_active = max(self.peak_active, len(active))
                 progressed = True
-            for rid in list(active):
-                req, h, slot, theta, need, t_adm = active[rid]
-                if not T.tlr_mdd_solve_query(h):
+            for unit in list(active):
+                slot, members, batch = unit
+                done = batch.query() if batch is not None else T.tlr_mdd_solve_query(members[0][1])
+                if not done:
                     continue
-                status, msg, ms, iters = 0, "", 0.0, 0
-                try:
-                    st = T.tlr_mdd_solve_wait(h)
-                    ms, iters = st.gpu_ms, st.iters
-                except T.TLRError as e:
-                    status, msg = e.code, str(e)
-                T.tlr_mdd_destroy(h)
-                del active[rid]
+                self._finish(members, batch, out, time.perf_counter() - t0)
+                active.remove(unit)
                 free.append(slot)
-                self.used -= need
-                out.append(SolveResult(rid, theta, status, msg, req.arrival, t_adm,
-                                       time.perf_counter() - t0, ms, iters))
                 progressed = True
             if not progressed:
                 if realtime and queue and not active:
@@ -138,6 +220,83 @@ class Server:
                 else:
                     time.sleep(self.poll_s)
         return sorted(out, key=lambda r: r.rid)
+
+    def _start(self, members, stream, out, now):
+        """Create or take over the members' handles and enqueue their solve:
+        one handle alone, or several as one lockstep batch."""
+        started = []
+        for m in members:
+            req, h, _, need, key, t_adm, fresh = m
+            m[2] = req.theta0.clone() if hasattr(req.theta0, "clone") else req.theta0
+            try:
+                if fresh:
+                    m[1] = T.tlr_mdd_create(req.desc, req.D, req.U, stream)
+                    self.created += 1
+                else:
+                    T.tlr_mdd_set_stream(h, stream)
+                    T.tlr_mdd_set_data(h, req.D, req.U, getattr(req.desc, "input_memory", 0))
+                    self.reused += 1
+                started.append(m)
+            except T.TLRError as e:
+                self.used -= need
+                if not fresh:
+                    T.tlr_mdd_destroy(h)
+                out.append(SolveResult(req.rid, None, e.code, str(e), req.arrival, now, now, 0.0, 0))
+        if not started:
+            return None
+        batch = None
+        try:
+            if len(started) > 1:
+                batch = T.Batch([m[1] for m in started], stream)
+                batch.solve_async([m[2] for m in started], started[0][0].opts)
+                self.batches += 1
+            else:
+                T.tlr_mdd_solve_async(started[0][1], started[0][2], started[0][0].opts)
+        except T.TLRError as e:
+            if batch is not None:
+                batch.destroy()
+            for m in started:
+                self._release(m, ok=False)
+                out.append(SolveResult(m[0].rid, None, e.code, str(e), m[0].arrival, now, now, 0.0, 0))
+            return None
+        return started, batch
+
+    def _release(self, m, ok):
+        req, h, theta, need, key, t_adm, fresh = m
+        if self.reuse and ok:
+            self.idle[h] = (key, need)       # most recently used last
+        else:
+            T.tlr_mdd_destroy(h)
+            self.used -= need
+
+    def _finish(self, members, batch, out, t_end):
+        if batch is not None:
+            try:
+                stats = batch.wait()
+                res = [(0, "", st.gpu_ms, st.iters) for st in stats]
+            except T.TLRError as e:
+                res = [(e.code, str(e), 0.0, 0)] * len(members)
+            batch.destroy()
+        else:
+            try:
+                st = T.tlr_mdd_solve_wait(members[0][1])
+                res = [(0, "", st.gpu_ms, st.iters)]
+            except T.TLRError as e:
+                res = [(e.code, str(e), 0.0, 0)]
+        for m, (status, msg, ms, iters) in zip(members, res):
+            req, h, theta, need, key, t_adm, fresh = m
+            self._release(m, ok=status == 0)
+            out.append(SolveResult(req.rid, theta if status == 0 else theta, status, msg, req.arrival, t_adm, t_end,
+                                   ms, iters))
+
+
+def _opts_key(o):
+    if o is None:
+        return None
+    try:
+        return tuple(getattr(o, f) for f, _ in o._fields_)
+    except AttributeError:
+        return id(o)
 
 
 def percentiles(results, ps=(50, 99)):

@@ -12,7 +12,7 @@ import os
 
 __all__ = [
     "TLRError", "Desc", "SolveOpts", "Stats", "lib", "lib_path",
-    "TLR_PREC_FP32", "TLR_PREC_BF16X3", "TLR_DIAG_RULE", "TLR_DIAG_LOWRANK", "TLR_DIAG_DENSE",
+    "TLR_PREC_FP32", "TLR_PREC_BF16X3", "TLR_PREC_TF32", "TLR_DIAG_RULE", "TLR_DIAG_LOWRANK", "TLR_DIAG_DENSE",
     "TLR_DIAG_PER_TILE", "TLR_MEM_DEVICE", "TLR_MEM_HOST", "TLR_RECIP_SYMMETRIC", "TLR_RECIP_NONE",
     "ERR", "desc", "solve_opts", "tlr_mdd_theta_size", "tlr_mdd_theta_layout",
     "tlr_mdd_workspace_bytes", "tlr_mdd_hilbert_perm", "tlr_mdd_create", "tlr_mdd_apply",
@@ -24,14 +24,15 @@ __all__ = [
     "tlr_mdd_benchmark_solve", "BenchStats", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile", "tlr_mdd_warm_start",
     "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
     "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
-    "tlr_mdd_trim_pool",
+    "tlr_mdd_trim_pool", "tlr_mdd_set_stream", "tlr_mdd_batch_create", "tlr_mdd_batch_solve_async",
+    "tlr_mdd_batch_query", "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy", "Batch",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
 
 TLR_OK, TLR_ERR_ARG, TLR_ERR_SHAPE, TLR_ERR_UNSUPPORTED = 0, -1, -2, -3
 TLR_ERR_NOMEM, TLR_ERR_CUDA, TLR_ERR_NONFINITE, TLR_ERR_TIMEOUT, TLR_ERR_STATE = -4, -5, -6, -7, -8
-TLR_PREC_FP32, TLR_PREC_BF16X3 = 0, 1
+TLR_PREC_FP32, TLR_PREC_BF16X3, TLR_PREC_TF32 = 0, 1, 2
 TLR_SOLVE_RESUME, TLR_SOLVE_REFRESH = 1, 2
 TLR_DIAG_RULE, TLR_DIAG_LOWRANK, TLR_DIAG_DENSE, TLR_DIAG_PER_TILE = 0, 1, 2, 3
 TLR_RECIP_SYMMETRIC, TLR_RECIP_NONE = 0, 1
@@ -44,12 +45,14 @@ EXPORTED = [
     "tlr_mdd_desc_init", "tlr_mdd_solve_opts_init", "tlr_mdd_theta_size", "tlr_mdd_theta_layout",
     "tlr_mdd_workspace_bytes", "tlr_mdd_hilbert_perm", "tlr_mdd_create", "tlr_mdd_apply",
     "tlr_mdd_adjoint", "tlr_mdd_grad", "tlr_mdd_solve", "tlr_mdd_unpermute_dense",
-    "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
+    "tlr_mdd_get_data", "tlr_mdd_stream", "tlr_mdd_set_stream", "tlr_mdd_last_error", "tlr_mdd_destroy",
     "tlr_mdd_timing_enable", "tlr_mdd_timing_reset", "tlr_mdd_timing_read", "tlr_mdd_launch_count",
     "tlr_mdd_adjoint_noalloc", "tlr_mdd_solve_async", "tlr_mdd_solve_query", "tlr_mdd_solve_wait",
     "tlr_mdd_set_data", "tlr_mdd_benchmark_solve", "tlr_mdd_tile_ranks", "tlr_mdd_choose_tile",
     "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state", "tlr_mdd_time_to_freq",
     "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest", "tlr_mdd_trim_pool",
+    "tlr_mdd_set_stream", "tlr_mdd_batch_create", "tlr_mdd_batch_solve_async", "tlr_mdd_batch_query",
+    "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -133,6 +136,18 @@ def lib():
         L.tlr_mdd_get_data.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp, vp]
         L.tlr_mdd_stream.argtypes = [vp]
         L.tlr_mdd_stream.restype = vp
+        L.tlr_mdd_set_stream.argtypes = [vp, vp]
+        L.tlr_mdd_set_stream.restype = i32
+        L.tlr_mdd_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int32, vp]
+        L.tlr_mdd_batch_create.restype = i32
+        L.tlr_mdd_batch_solve_async.argtypes = [vp, C.POINTER(vp), C.POINTER(SolveOpts)]
+        L.tlr_mdd_batch_solve_async.restype = i32
+        L.tlr_mdd_batch_query.argtypes = [vp]
+        L.tlr_mdd_batch_query.restype = i32
+        L.tlr_mdd_batch_wait.argtypes = [vp, C.POINTER(Stats)]
+        L.tlr_mdd_batch_wait.restype = i32
+        L.tlr_mdd_batch_destroy.argtypes = [vp]
+        L.tlr_mdd_batch_destroy.restype = i32
         L.tlr_mdd_last_error.argtypes = [vp]
         L.tlr_mdd_last_error.restype = C.c_char_p
         L.tlr_mdd_destroy.argtypes = [vp]
@@ -445,6 +460,70 @@ def tlr_mdd_adjoint_noalloc(V, Dt, nr, ns, G, stream=None):
     """G = V Dt^H without any device allocation (fixed in-library scratch)."""
     _noalloc_args(V, Dt, nr, ns, G)
     _check(lib().tlr_mdd_adjoint_noalloc(_ptr(V), _ptr(Dt), nr, ns, _ptr(G), _stream(stream)))
+
+
+def tlr_mdd_set_stream(h, stream=None):
+    """Move a handle (no solve pending) to ``stream``."""
+    _check(lib().tlr_mdd_set_stream(h, _stream(stream)), h)
+
+
+class Batch:
+    """A batched solve over handles (binding of tlr_mdd_batch_*): keeps the
+    handle list and, while a solve is pending, the theta buffers alive."""
+
+    def __init__(self, handles, stream=None):
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*self.handles)
+        b = C.c_void_p()
+        _check(lib().tlr_mdd_batch_create(C.byref(b), arr, len(self.handles), _stream(stream)))
+        self.b = b.value
+        self._keep = None
+
+    def solve_async(self, thetas, opts: SolveOpts | None = None):
+        opts = opts if opts is not None else solve_opts()
+        if len(thetas) != len(self.handles):
+            raise TLRError(TLR_ERR_ARG, "one theta per member")
+        arr = (C.c_void_p * len(thetas))(*[_ptr(t) for t in thetas])
+        self._keep = (list(thetas), arr, opts)
+        _check(lib().tlr_mdd_batch_solve_async(self.b, arr, C.byref(opts)))
+
+    def query(self) -> bool:
+        rc = lib().tlr_mdd_batch_query(self.b)
+        if rc < 0:
+            _check(rc)
+        return rc == 1
+
+    def wait(self) -> list:
+        st = (Stats * len(self.handles))()
+        rc = lib().tlr_mdd_batch_wait(self.b, st)
+        self._keep = None
+        _check(rc)
+        return list(st)
+
+    def destroy(self):
+        if self.b:
+            _check(lib().tlr_mdd_batch_destroy(self.b))
+            self.b = None
+
+
+def tlr_mdd_batch_create(handles, stream=None) -> Batch:
+    return Batch(handles, stream)
+
+
+def tlr_mdd_batch_solve_async(batch: Batch, thetas, opts: SolveOpts | None = None):
+    batch.solve_async(thetas, opts)
+
+
+def tlr_mdd_batch_query(batch: Batch) -> bool:
+    return batch.query()
+
+
+def tlr_mdd_batch_wait(batch: Batch) -> list:
+    return batch.wait()
+
+
+def tlr_mdd_batch_destroy(batch: Batch):
+    batch.destroy()
 
 
 def tlr_mdd_trim_pool(keep_bytes=0) -> int:

@@ -25,6 +25,10 @@ CASES = {
     "ragged": (12, 8, 32, 4, [False, True, False], 203),
 }
 PRECS = [(T.TLR_PREC_FP32, 1e-5), (T.TLR_PREC_BF16X3, 1e-3)]
+# per-application bounds of the apply / gradient tests, TF32 included; every
+# element within ETOL of the reference's rms
+APPLY_PRECS = PRECS + [(T.TLR_PREC_TF32, 1e-3)]
+ETOL = {T.TLR_PREC_FP32: 1e-4, T.TLR_PREC_BF16X3: 1e-3, T.TLR_PREC_TF32: 1e-2}
 
 
 def _setup(name, prec, seed=0):
@@ -42,7 +46,7 @@ def _setup(name, prec, seed=0):
     return g, glay, th, Dh, Uh, perm
 
 
-@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("prec,tol", APPLY_PRECS)
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_general_apply_grad_assemble(name, prec, tol):
     g, glay, th, Dh, Uh, perm = _setup(name, prec)
@@ -56,8 +60,7 @@ def test_general_apply_grad_assemble(name, prec, tol):
     print(f"general {name} prec {prec}: apply {rel(Y, Yo):.2e} grad {rel(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
     assert rel(Y, Yo) <= tol
     assert rel(gr, go) <= tol and abs(f - fo) <= tol * fo
-    # elementwise: within max(1e-4, tol) of the reference's rms
-    assert elem(Y, Yo) <= max(1e-4, tol) and elem(gr, go) <= max(1e-4, tol)
+    assert elem(Y, Yo) <= ETOL[prec] and elem(gr, go) <= ETOL[prec]
     assert rel(X, Xo) <= 1e-5
     assert not np.allclose(X, X.T)
     g.close()

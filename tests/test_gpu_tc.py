@@ -85,10 +85,10 @@ def test_tc_dense256_solve():
     assert e <= 1e-3   # final Green's function bound (measured ~3e-6)
 
 
-@pytest.mark.parametrize("nx,ny,b,k,ns", [(12, 8, 48, 5, 203), (8, 8, 16, 3, 64)])
-def test_tc_solve_tiles_off_the_fused_residual_path(nx, ny, b, k, ns):
-    # tiles that are not a multiple of 32 take the plain residual step and the
-    # per-launch residual packs instead of the fused residual step
+@pytest.mark.parametrize("nx,ny,b,k,ns", [(12, 8, 24, 5, 203), (8, 8, 16, 3, 64)])
+def test_tc_solve_tiles_on_and_off_the_fused_residual_path(nx, ny, b, k, ns):
+    # tile 24 (not a multiple of 16) takes the plain residual step and the
+    # per-launch residual packs; tile 16 the fused residual step
     D, U, perm, lay, _ = problem(nx, ny, b, k, "lowrank", ns=ns, seed=3, snr_db=20)
     nr = nx * ny
     th0 = (0.1 * synth.planted_theta(nr, b, k, lay.dense, 78)).astype(np.complex64).astype(np.complex128)
@@ -103,3 +103,78 @@ def test_tc_solve_tiles_off_the_fused_residual_path(nx, ny, b, k, ns):
     print(f"tc solve b {b}: rel X {e:.2e}, f {st.f_hist[st.n_hist - 1]:.4e} vs {sto.f_hist[-1]:.4e}")
     assert st.iters == 30 and st.status == 0
     assert e <= 1e-3   # measured ~1e-5
+
+
+# ---- TF32 form (TLR_PREC_TF32): operands rounded to TF32 (10 mantissa bits,
+# unit roundoff 2^-11), FP32 accumulation.  Per application the error is about
+# 2^-11 x the growth of a sum of K products with random signs relative to its
+# value, measured 2-4e-4: inside the 1e-3 tensor-core bound.  The elementwise
+# bound is 10x that (1e-2 of the reference's rms), as for the other paths. ----
+TF32_TOL, TF32_ETOL = 1e-3, 1e-2
+
+
+def _setup_tf32(name, precision=T.TLR_PREC_TF32):
+    nx, ny, b, ranks, mode, ns = CASES[name]
+    D, U, perm, lay, _ = problem(nx, ny, b, ranks, mode, ns=ns, snr_db=10, planted=False)
+    th = synth.cn(synth.rng(sorted(CASES).index(name)), lay.size) * 0.2
+    th = th.astype(np.complex64).astype(np.complex128)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha, precision=precision)
+    return g, lay, th, Dh, Uh
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tf32_apply_and_grad(name):
+    g, lay, th, Dh, Uh = _setup_tf32(name)
+    Y = g.apply(th)
+    Yo = operator.apply_y(th, lay, Dh)
+    f, gr = g.grad(th)
+    fo = operator.misfit(th, lay, Dh, Uh)
+    go = operator.gradient(th, lay, Dh, Uh)
+    g.close()
+    print(f"tf32 {name}: apply rel {rel(Y, Yo):.2e} elem {elem(Y, Yo):.2e}; grad rel {rel(gr, go):.2e} "
+          f"elem {elem(gr, go):.2e}; f {abs(f - fo) / fo:.2e}")
+    assert rel(Y, Yo) <= TF32_TOL and elem(Y, Yo) <= TF32_ETOL
+    assert rel(gr, go) <= TF32_TOL and elem(gr, go) <= TF32_ETOL
+    assert abs(f - fo) <= TF32_TOL * fo
+    # the TF32 result differs from the BF16x3 one by about the TF32 rounding
+    # (it is not the BF16x3 path under another name)
+    g2, _, _, _, _ = _setup_tf32(name, T.TLR_PREC_BF16X3)
+    Y2 = g2.apply(th)
+    g2.close()
+    assert rel(Y, Y2) > 1e-6
+
+
+def test_tf32_dense256_solve():
+    D, U, perm, lay, _ = problem(16, 16, 64, 8, "dense", seed=0, snr_db=20)
+    th0 = (0.1 * synth.planted_theta(256, 64, 8, lay.dense, 77)).astype(np.complex64).astype(np.complex128)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dh.T, Uh.T), th0)
+    g = Gpu(D, U, lay, nx=16, ny=16, alpha=alpha, precision=T.TLR_PREC_TF32)
+    th, st = g.solve(th0)
+    g.close()
+    Xo = operator.unpermute(operator.assemble_xh(tho, lay), perm)
+    X = operator.unpermute(operator.assemble_xh(th, lay), perm)
+    e = rel(X, Xo)
+    fh = np.array(st.f_hist[:st.n_hist])
+    print(f"tf32 dense256 solve: rel X {e:.2e}, max f-history error {np.max(np.abs(fh - sto.f_hist) / sto.f_hist):.2e}")
+    assert st.iters == 30 and st.status == 0
+    assert e <= 1e-2     # 30 iterations compound the per-application TF32 error
+    np.testing.assert_allclose(fh, sto.f_hist, rtol=1e-2)
+
+
+@pytest.mark.parametrize("nx,ny,b,k,ns", [(12, 8, 24, 5, 203), (16, 16, 64, 6, 300)])
+def test_tf32_solve_on_both_residual_paths(nx, ny, b, k, ns):
+    # tile 24 (not a multiple of 16) takes the plain residual step; tile 64 the fused one
+    D, U, perm, lay, _ = problem(nx, ny, b, k, "lowrank", ns=ns, seed=3, snr_db=20)
+    nr = nx * ny
+    th0 = (0.1 * synth.planted_theta(nr, b, k, lay.dense, 78)).astype(np.complex64).astype(np.complex128)
+    Dh, Uh, alpha = operator.normalise(D, U, perm)
+    tho, _, _, sto = solver.admm(solver.Problem(lay, Dh.T, Uh.T), th0)
+    g = Gpu(D, U, lay, nx=nx, ny=ny, alpha=alpha, precision=T.TLR_PREC_TF32)
+    th, st = g.solve(th0)
+    g.close()
+    e = rel(operator.assemble_xh(th, lay), operator.assemble_xh(tho, lay))
+    print(f"tf32 solve b {b}: rel X {e:.2e}")
+    assert st.iters == 30 and st.status == 0
+    assert e <= 1e-2

@@ -27,6 +27,10 @@ CASES = {
     "unit_tile": (4, 4, [1, 9, 1, 5], [1, 3, 1, 2] + [1, 0, 1, 0, 3, 1], [False, False, True, False], 37),
 }
 PRECS = [(T.TLR_PREC_FP32, 1e-5), (T.TLR_PREC_BF16X3, 1e-3)]
+# per-application bounds of the apply / gradient tests, TF32 included; every
+# element within ETOL of the reference's rms
+APPLY_PRECS = PRECS + [(T.TLR_PREC_TF32, 1e-3)]
+ETOL = {T.TLR_PREC_FP32: 1e-4, T.TLR_PREC_BF16X3: 1e-3, T.TLR_PREC_TF32: 1e-2}
 
 
 def _setup(name, prec, seed=0):
@@ -39,7 +43,7 @@ def _setup(name, prec, seed=0):
     return g, lay, th, Dh, Uh, perm
 
 
-@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("prec,tol", APPLY_PRECS)
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_apply_grad_unpermute(name, prec, tol):
     g, lay, th, Dh, Uh, perm = _setup(name, prec)
@@ -53,8 +57,7 @@ def test_apply_grad_unpermute(name, prec, tol):
     print(f"tiles {name} prec {prec}: apply {rel(Y, Yo):.2e} grad {rel(gr, go):.2e} f {abs(f - fo) / fo:.2e}")
     assert rel(Y, Yo) <= tol
     assert rel(gr, go) <= tol and abs(f - fo) <= tol * fo
-    # elementwise: within max(1e-4, tol) of the reference's rms
-    assert elem(Y, Yo) <= max(1e-4, tol) and elem(gr, go) <= max(1e-4, tol)
+    assert elem(Y, Yo) <= ETOL[prec] and elem(gr, go) <= ETOL[prec]
     assert rel(X, Xo) <= 1e-5
     assert np.array_equal(X, X.T)
     g.close()
