@@ -390,14 +390,18 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--workload", default="precision", choices=["precision", "batched"])
     ap.add_argument("--seed", type=int, default=2412)
-    ap.add_argument("--streams", type=int, default=2, help="CUDA streams the frequencies of a step are spread over")
+    ap.add_argument("--streams", type=int, default=3, help="CUDA streams the frequencies of a step are spread over")
     ap.add_argument("--e2e-steps", type=int, default=4, help="steps of the end-to-end leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-cols", type=int, default=512,
                     help="source columns per step of the reference arm's bounded sample")
     ap.add_argument("--accuracy", type=int, default=4, help="frequencies of the precision table (0: skip)")
     ap.add_argument("--freqs", type=int, default=0,
-                    help="frequencies per GPU (0: the workload's; a multiple of its batch)")
+                    help="frequencies per GPU (0: the workload's); fewer than a batch make one step")
+    ap.add_argument("--rank", type=int, default=0, help="one rank for every frequency (profiling runs; 0: the schedule)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="with --freqs n: take every (schedule/n)-th rank of a schedule over this many frequencies "
+                         "(a profiling run then sees the ranks of one headline step)")
     ap.add_argument("--serving", type=int, default=120,
                     help="requests of the serving mix (nr 1024-8192, tile 128-512, rank 2-64) served with "
                          "continuous batching (0: skip)")
@@ -413,9 +417,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = PRECISION_FORM if args.workload == "precision" else BATCHED
-    if args.freqs:
+    if args.freqs or args.rank:
         import dataclasses
-        wl = dataclasses.replace(wl, nfreq=args.freqs)
+        if args.freqs:
+            wl = dataclasses.replace(wl, nfreq=args.freqs, batch=min(wl.batch, args.freqs))
+        if args.rank:
+            wl = dataclasses.replace(wl, rank_lo=args.rank, rank_hi=args.rank)
 
     if args.impl == "reference":
         return reference_arm(args, wl, world, rank)
@@ -433,6 +440,10 @@ def main():
     dev = torch.device("cuda", local)
     total = wl.nfreq * world
     ranks = wl.ranks(total)
+    if args.schedule and args.freqs and args.schedule % args.freqs == 0:
+        full = wl.ranks(args.schedule * world)
+        stride = args.schedule // args.freqs
+        ranks = [full[g * stride] for g in range(total)]
     mine = sharding.frequency_plan(wl.nfreq, rank, world)
     steps_of = sharding.batches(mine, wl.batch)
     prec = T.TLR_PREC_FP32 if args.precision == "fp32" else T.TLR_PREC_BF16X3
@@ -822,15 +833,45 @@ def secondary_leg(T, torch, args, dev):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
+    step()          # plain launches (a handle's first solve)
     step()          # records the solve graphs
     ms = sum(step() for _ in range(args.secondary))
     for h in hs:
         T.tlr_mdd_destroy(h)
     fl = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, k) for k in ranks) * args.secondary
+
+    def one_solve(d, seed_):
+        # one timed solve (device time) of frequency 0's data in a given form
+        h = T.tlr_mdd_create(d, inp.D[0], inp.U[0], streams[0])
+        gen = torch.Generator(device=dev).manual_seed(seed_)
+        nth = T.tlr_mdd_theta_size(d)
+        th0 = 0.01 * torch.randn(nth, dtype=torch.complex64, device=dev, generator=gen)
+        th = th0.clone()
+        torch.cuda.synchronize()
+        T.tlr_mdd_solve(h, th, opts)
+        th.copy_(th0)
+        torch.cuda.synchronize()
+        st = T.tlr_mdd_solve(h, th, opts)
+        T.tlr_mdd_destroy(h)
+        return st, nth
+
+    kx = 26
+    common = dict(rank=kx, nx=wl.grid[0], ny=wl.grid[1], diag_mode=T.TLR_DIAG_RULE, precision=T.TLR_PREC_BF16X3)
+    gst, gn = one_solve(T.desc(wl.nr, wl.nr, wl.tile, reciprocity=T.TLR_RECIP_NONE, **common), args.seed + 5)
+    tst, tn = one_solve(T.desc(wl.nr, wl.nr, 0, tiles=[192, 320] * 8, **common), args.seed + 6)
+    ust, un = one_solve(T.desc(wl.nr, wl.nr, wl.nr // 16, **common), args.seed + 6)
+    f_eq = flops_per_solve(wl.nr, wl.nr, wl.tile, kx)
     return {"workload": wl.name, "value": round(wl.nfreq * args.secondary / (ms / 1e3), 3),
             "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
             "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": 4,
-            "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency"}
+            "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency",
+            "general_form": {"rank": kx, "n_theta": gn, "ms": round(gst.gpu_ms, 2),
+                             "tflops": round(f_eq / (gst.gpu_ms / 1e3) / 1e12, 1),
+                             "note": "one solve, one stream; the same contraction flops as the reciprocal form"},
+            "nonuniform_tiles": {"tiles": "192,320 alternating x8", "rank": kx, "n_theta": tn,
+                                 "ms": round(tst.gpu_ms, 2), "equal_tiles_ms": round(ust.gpu_ms, 2),
+                                 "note": "one solve, one stream; 16 equal tiles of 256 at the same rank "
+                                         "(the same flops) beside it"}}
 
 
 def serving_leg(T, torch, n, seed, dev):
@@ -997,6 +1038,7 @@ def small_configs_leg(T, torch, n, seed, dev):
             th0 = (torch.randn(nth, generator=g, device=dev) * (0.1 / math.sqrt(b * k))).to(torch.complex64)
             th = th0.clone()
             opts = T.solve_opts()
+            T.tlr_mdd_solve(h, th, opts)            # plain launches (the handle's first solve)
             T.tlr_mdd_solve(h, th, opts)            # records the solve graph
             ms = []
             m = n if prec != T.TLR_PREC_FP32 else max(1, n // 4)

@@ -221,8 +221,10 @@ int tlr_mdd_solve(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* o
  * handle's stream and returns.  theta_inout (device or host per
  * opts->theta_memory) must stay valid and untouched until the solve has
  * finished.  The launch sequence is recorded once into a CUDA graph per
- * handle and solver options and replayed afterwards (set the environment
- * variable TLR_MDD_GRAPHS=0, or use the NULL stream, for plain launches).
+ * handle and solver options and replayed afterwards: a handle's first solve
+ * with given options runs as plain launches, the second records the graph,
+ * later ones replay it (TLR_MDD_LAZY_GRAPH=0 records on the first; set
+ * TLR_MDD_GRAPHS=0, or use the NULL stream, for plain launches only).
  * One solve may be pending per handle; handles on different streams run
  * concurrently. */
 int tlr_mdd_solve_async(tlr_mdd_t* h, void* theta_inout, const tlr_mdd_solve_opts_t* opts);

@@ -575,6 +575,7 @@ struct tlr_mdd_s {
     HostStats* hstats = nullptr;       // pinned
     cudaGraphExec_t gexec = nullptr;
     long long graph_kernels = 0;       // kernel launches recorded in gexec
+    int plain_solves = 0;              // solves enqueued as plain launches since the last recording
     GraphKey gkey;
     std::vector<TimedLaunch> gtimed;
     bool pending = false;
@@ -2365,6 +2366,29 @@ static int enqueue_body(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
     }
     h->pending_graph = false;
     if (!graphs_enabled(h)) return enqueue_solve(h, o);
+    // A handle's first solve with given options runs as plain launches (a
+    // recording and instantiation cost more host time than one enqueue, and a
+    // handle used once, as most served requests are, never needs the graph);
+    // the second records the graph that every later solve replays.
+    const bool same = h->gexec && [&] {
+        GraphKey k;
+        k.lam0 = o->lam0;
+        k.decay = o->decay;
+        k.rho = o->rho;
+        k.stages = o->stages;
+        k.admm = o->admm_iters;
+        k.lbfgs = o->lbfgs_iters;
+        k.mem = o->memory;
+        k.flags = o->flags;
+        std::lock_guard<std::mutex> lk(g_tmu);
+        k.timing = g_timing ? 1 : 0;
+        return k == h->gkey;
+    }();
+    if (!same && h->plain_solves == 0 && !getenv_off("TLR_MDD_LAZY_GRAPH")) {
+        h->plain_solves = 1;
+        return enqueue_solve(h, o);
+    }
+    h->plain_solves = 0;
     GraphKey k;
     k.lam0 = o->lam0;
     k.decay = o->decay;

@@ -736,11 +736,26 @@ __global__ void __launch_bounds__(kFinThreads) k_pair_accept(SolverDev S, const 
                                                              int nf) {
     __shared__ double sh[32];
     double v[4];
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         double a = 0.0;
-        const int nb = k < 3 ? kRedBlocks : nf;
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) a += k < 3 ? part3[i * 3 + k] : partf[i];
+        for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) a += part3[i * 3 + k];
         v[k] = block_sum(a, sh);
+    }
+    {
+        // the residual-norm partials can number tens of thousands (one per
+        // fused residual-step CTA): four independent sums per thread in a
+        // fixed order keep the loads in flight
+        const int bd = blockDim.x;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int i = threadIdx.x;
+        for (; i + 3 * bd < nf; i += 4 * bd) {
+            a0 += partf[i];
+            a1 += partf[i + bd];
+            a2 += partf[i + 2 * bd];
+            a3 += partf[i + 3 * bd];
+        }
+        for (; i < nf; i += bd) a0 += partf[i];
+        v[3] = block_sum((a0 + a1) + (a2 + a3), sh);
     }
     if (threadIdx.x != 0) return;
     const double ss = v[0], sy = v[1], yy = v[2], rr = v[3];
