@@ -160,6 +160,30 @@ def measured_peaks():
         return 1700.0, 6800.0, "fallback"
 
 
+# DRAM bytes per contraction launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the 992 contraction launches of one step of the nr = 9216 workload:
+# the 8 frequencies of ranks 8, 15, ..., 57 solved on one stream), from one ncu
+# capture of the sources whose SHA-256 is GEMM_TRAFFIC_SHA.  A change to any of
+# those sources, another rank mix or another tile voids the figures (traffic null).
+GEMM_TRAFFIC_SOURCES = ("k_gemm_tcp.cu", "api.cu", "internal.h")
+GEMM_TRAFFIC_SHA = "73f137d417fd710870b5ac661923966c92143908757e8fcc9e1e17c164099a05"
+GEMM_TRAFFIC_CASE = {"nr": 9216, "tile": 384, "ranks": [8, 15, 22, 29, 36, 43, 50, 57], "precision": "bf16x3"}
+GEMM_TRAFFIC_BYTES = {"cgemm_compress": 2091883834, "cgemm_expand": 4452802642, "cgemm_project": 4727283401}
+
+
+def gemm_traffic(kernel, nr, tile, step_ranks, precision):
+    """Measured DRAM bytes per launch of `kernel`, or None when the capture does not apply."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in GEMM_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2412_14973_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    case = {"nr": nr, "tile": tile, "ranks": list(step_ranks), "precision": precision}
+    if h.hexdigest() != GEMM_TRAFFIC_SHA or case != GEMM_TRAFFIC_CASE:
+        return None
+    return GEMM_TRAFFIC_BYTES.get(kernel)
+
+
 def log(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -354,6 +378,28 @@ def oracle_problem(D0, U0, wl: Workload, k, cols=None):
     return solver.Problem(lay, Dh.T, Uh.T), lay, alpha
 
 
+def oracle_solve_rate(prob, th0):
+    """Seconds of a 30-iteration oracle solve from one measured iteration:
+    the first forward product and gradient are timed apart from the
+    iteration (line-search products and the gradient at the new point), so
+    the figure is first + 30 x iteration, both measured."""
+    calls = []
+    fgrad = prob.fgrad
+
+    def timed_fgrad(theta):
+        t0 = time.perf_counter()
+        r = fgrad(theta)
+        calls.append(time.perf_counter() - t0)
+        return r
+
+    prob.fgrad = timed_fgrad
+    secs, th, st = run_oracle_solve(prob, th0, 1)
+    prob.fgrad = fgrad
+    t_first = calls[0]
+    t_iter = secs - t_first
+    return t_first + ITERS_PER_SOLVE * t_iter, secs, t_first, t_iter
+
+
 def run_oracle_solve(prob, th0, iters):
     from oracle import solver
     opts = solver.SolveOpts(stages=1, admm_iters=1, lbfgs_iters=iters)
@@ -527,7 +573,12 @@ def main():
                                     f"against the 3M-effective peak (x 8/18 = {bf16 * 8 / 18:.1f}) the "
                                     "fraction is frac x 0.75")}
         roof.update({"kernel": names[dom], "achieved": round(achieved, 2), "peak": round(peak, 1),
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": gemm_traffic(names[dom], wl.nr, wl.tile, [ranks[f] for f in steps_of[0]],
+                                             args.precision),
+                     "traffic_note": ("DRAM read + write bytes per launch of this class, mean over one step's "
+                                      "launches, from the ncu capture of these GEMM sources (null when the "
+                                      "sources or the step's shapes differ from the capture's)"),
                      "launches": dnl, "ms": round(dms, 2),
                      "flops_counted": "8 per complex MAC; per iteration 56 ns n_LR (T and the residual carried "
                                       "between iterations; a fresh forward each iteration would be 72)",
@@ -608,7 +659,7 @@ def main():
     peaks = measure_peaks(torch, dev) if rank == 0 else None
     small = None
     if rank == 0 and args.small_configs > 0:
-        small = small_configs_leg(T, torch, args.small_configs, args.seed, dev)
+        small = small_configs_leg(T, torch, args.small_configs, args.seed, dev, cpu=not args.no_cpu)
         log("small workloads done")
 
     serve = None
@@ -812,18 +863,18 @@ def secondary_leg(T, torch, args, dev):
     theta = [t.clone() for t in inp.th0]
     opts = T.solve_opts()
 
-    def step():
+    def step(hs=hs, fs=freqs):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(main)
         for s_ in streams:
             s_.wait_event(e0)
-        for f in freqs:
+        for f in fs:
             T.tlr_mdd_set_data(hs[f], inp.D[f], inp.U[f], T.TLR_MEM_DEVICE)
             with torch.cuda.stream(streams[f % 4]):
                 theta[f].copy_(inp.th0[f])
             T.tlr_mdd_solve_async(hs[f], theta[f], opts)
-        for f in freqs:
+        for f in fs:
             T.tlr_mdd_solve_wait(hs[f])
         for s_ in streams:
             ev = torch.cuda.Event()
@@ -836,9 +887,28 @@ def secondary_leg(T, torch, args, dev):
     step()          # plain launches (a handle's first solve)
     step()          # records the solve graphs
     ms = sum(step() for _ in range(args.secondary))
-    for h in hs:
+    # the same step on every 8th frequency, tensor cores and the FP32 SIMT path
+    sub = freqs[::8]
+    ms_tc_sub = step(fs=sub)
+    hs32 = {f: T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_FP32), inp.D[f], inp.U[f], streams[f % 4]) for f in sub}
+    step(hs32, sub)
+    step(hs32, sub)
+    ms_fp32_sub = step(hs32, sub)
+    for h in list(hs) + list(hs32.values()):
         T.tlr_mdd_destroy(h)
     fl = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, k) for k in ranks) * args.secondary
+    oracle_cpu = None
+    if not args.no_cpu:
+        kmean = sum(ranks) / len(ranks)
+        f = min(freqs, key=lambda x: (abs(ranks[x] - kmean), x))
+        prob, _, _ = oracle_problem(inp.D[f].cpu().numpy(), inp.U[f].cpu().numpy(), wl, ranks[f])
+        per_solve, secs, t_first, t_iter = oracle_solve_rate(prob, inp.th0[f].cpu().numpy().astype(np.complex128))
+        oracle_cpu = {"value": round(1.0 / per_solve, 6), "unit": "freq-solves/s", "cores": blas_threads(),
+                      "kind": "oracle",
+                      "sample": (f"frequency {f} (rank {ranks[f]}, the mean rank {kmean:.1f}): one full L-BFGS "
+                                 f"iteration of the FP64 oracle in {secs:.1f} s (first forward product and "
+                                 f"gradient {t_first:.1f} s, the iteration {t_iter:.1f} s); a "
+                                 f"{ITERS_PER_SOLVE}-iteration solve = {per_solve:.0f} s")}
 
     def one_solve(d, seed_):
         # one timed solve (device time) of frequency 0's data in a given form
@@ -865,6 +935,12 @@ def secondary_leg(T, torch, args, dev):
             "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
             "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": 4,
             "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency",
+            "fp32_comparison": {"frequencies": sub, "fp32_simt_freq_solves_per_s":
+                                round(len(sub) / (ms_fp32_sub / 1e3), 3),
+                                "tensor_core_freq_solves_per_s": round(len(sub) / (ms_tc_sub / 1e3), 3),
+                                "speedup_tc_vs_fp32": round(ms_fp32_sub / ms_tc_sub, 2),
+                                "note": "one step over every 8th frequency (the same rank mix), 4 streams"},
+            "cpu_oracle": oracle_cpu,
             "general_form": {"rank": kx, "n_theta": gn, "ms": round(gst.gpu_ms, 2),
                              "tflops": round(f_eq / (gst.gpu_ms / 1e3) / 1e12, 1),
                              "note": "one solve, one stream; the same contraction flops as the reciprocal form"},
@@ -930,6 +1006,7 @@ def serving_leg(T, torch, n, seed, dev):
     t_srv = time.perf_counter() - t0
     ok = [r for r in res if r.status == 0]
     pc = serving.percentiles(res)
+    svc = [1e3 * (r.finished - r.admitted) for r in ok]   # admission to result: the solve without queueing
     same = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, res))
     srv.close()
     # the same stream with lockstep batches of up to 4 same-size requests per slot
@@ -950,6 +1027,8 @@ def serving_leg(T, torch, n, seed, dev):
             "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
             "p50_ms": round(1e3 * pc[50], 1) if pc[50] else None,
             "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,
+            "service_p50_ms": round(percentile(svc, 50), 1) if svc else None,
+            "service_p99_ms": round(percentile(svc, 99), 1) if svc else None,
             "tc_one_at_a_time_solves_per_s": round(n / t_tc1, 3),
             "fp32_one_at_a_time_solves_per_s": round(m / t_fp32, 3),
             "tc_one_at_a_time_solves_per_s_same_subset": round(m / t_tc1_m, 3),
@@ -961,7 +1040,8 @@ def serving_leg(T, torch, n, seed, dev):
             "lockstep_batches": batched,
             "sizes": dict(sorted(sizes.items())),
             "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson; "
-                   "latency = arrival to result on the host clock"}
+                   "latency = arrival to result on the host clock (queueing included), service = admission to "
+                   "result"}
 
 
 def measure_peaks(torch, dev):
@@ -996,7 +1076,7 @@ def measure_peaks(torch, dev):
     return out
 
 
-def small_configs_leg(T, torch, n, seed, dev):
+def small_configs_leg(T, torch, n, seed, dev, cpu=True):
     """The two small workloads, solve by solve (CUDA-graph replays on one
     stream, device time per solve, p50 / p99 over n solves), on both paths:
     the plain method on one frequency (nr = ns = 256, 16 x 16 grid, tile 64,
@@ -1054,6 +1134,19 @@ def small_configs_leg(T, torch, n, seed, dev):
             res[pname] = {"solves": m, "solves_per_s": round(1e3 * m / sum(ms), 2),
                           "p50_ms": round(percentile(ms, 50), 3), "p99_ms": round(percentile(ms, 99), 3)}
         res["speedup_tc_vs_fp32"] = round(res["bf16x3"]["solves_per_s"] / res["fp32"]["solves_per_s"], 2)
+        if cpu:
+            # the FP64 oracle's full solve (3 lambda stages x 2 ADMM x 5 L-BFGS)
+            # of the first frequency, from its own panels, on the host cores
+            from oracle import hilbert, layout, operator, solver
+            lay = layout.make_layout(nr, b, k, "dense" if mode == T.TLR_DIAG_DENSE else "lowrank")
+            Dh, Uh, _ = operator.normalise(data[0][0].cpu().numpy(), data[0][1].cpu().numpy(),
+                                           hilbert.perm(nx, nx))
+            prob = solver.Problem(lay, Dh.T, Uh.T)
+            t0 = time.perf_counter()
+            solver.admm(prob, th0.cpu().numpy().astype(np.complex128), solver.SolveOpts())
+            secs = time.perf_counter() - t0
+            res["oracle"] = {"solves_per_s": round(1.0 / secs, 4), "cores": blas_threads(),
+                             "sample": f"one full 30-iteration FP64 solve of the first frequency in {secs:.2f} s"}
         res["workload"] = (f"nr={nr} ({nx}x{nx} grid), ns={rows.numel()}, tile {b}, rank {k}, "
                            f"{'dense' if mode == T.TLR_DIAG_DENSE else 'low-rank'} diagonal, {snr:g} dB, "
                            f"{nfreq} frequenc{'y' if nfreq == 1 else 'ies'}, 30 iterations; X a random symmetric "
