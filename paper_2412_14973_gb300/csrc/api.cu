@@ -2426,7 +2426,9 @@ static int enqueue_body(tlr_mdd_s* h, const tlr_mdd_solve_opts_t* o) {
             return rc;
         }
         CK(h, e);
-        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        // node priorities kept: the memory-bound passes run ahead of other
+        // streams' pending contraction CTAs, as in plain launches
+        e = cudaGraphInstantiate(&h->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         CK(h, e);
         h->gkey = k;

@@ -18,6 +18,29 @@ typedef float2 cf;  // complex64, interleaved
 extern std::atomic<long long> g_launches;
 inline void counted(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Launch priority of the memory-bound passes (operand packs, the fused
+// update-and-pack kernels): the device's greatest stream priority, so that
+// where solves on several streams share the GPU, their CTAs are dispatched
+// ahead of pending contraction CTAs as an SM's resources free up and run
+// beside the contraction CTAs already there.  The environment variable
+// TLR_MDD_PASS_PRIORITY=0 launches them at their stream's priority.
+int pass_priority();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pass(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = pass_priority();
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Grouped complex GEMM descriptors (FP32 SIMT and tensor-core paths).
 //
@@ -158,13 +181,14 @@ cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, con
 // same arithmetic as the plain residual step; a read on the device), with R
 // read from and written back to its packed forms only (the FP32 R of the
 // forward product is read when alpha == nullptr: packing, no update); the
-// per-CTA partial of ||R||^2 (two-sum per thread, FP64 across the CTA) into
-// part[cta] when part != nullptr, and R in both packed forms: block i's rows
+// per-tile partial of ||R||^2 (16 x 128 tiles; two-sum per thread, FP64
+// across the CTA) into part[tile] when part != nullptr, whatever the grid,
+// and R in both packed forms: block i's rows
 // as an A operand with k = ns (MK, mk[i]) and as a B operand with rows = ns
 // and k = the receiver (KN, kn[i]).  Blocks of
 // b rows (roff == nullptr) or block i = rows roff[i] .. roff[i+1]-1 (DEVICE
 // [nblk + 1]); every block size a multiple of kFuseRows.  rstep_ctas gives the
-// number of CTAs (and partials).
+// number of tiles (and partials).
 long long rstep_ctas(int nr, int ns);
 // The six line-search inner products with R read from its KN packing (kn[i],
 // as rstep writes it), over rstep's tiles: part[blk * 6 + k], kRedBlocks

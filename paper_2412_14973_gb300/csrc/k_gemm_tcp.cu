@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.h"
 #include "reduce.h"
@@ -129,8 +130,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-__device__ __forceinline__ int core_off(int r, int kg) { return ((r >> 3) * 2 + kg) * 128 + (r & 7) * 16; }
 
 // byte offset of row r's first 16-byte group (k 0 .. 7 for BF16, k 0 .. 3
 // for TF32) inside a packed tile's first plane
@@ -298,101 +297,102 @@ static_assert(kPackTRB == 128 && KC == 16 && (TP_K == 16 || TP_K == 32),
 
 __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ tiles, cf* __restrict__ T,
                                                const cf* __restrict__ Tp, const double* __restrict__ alpha,
-                                               int ns) {
+                                               int ns, int gx, long long ntiles) {
     __shared__ float2 s[TP_K * TP_LD];
-    const TPackTile& P = tiles[blockIdx.y];
-    const int n0 = blockIdx.x * TP_N;
-    const int nk = P.nk;
+    __shared__ long long srow[TP_K];
     const float a = alpha ? (float)alpha[0] : 0.f;
     constexpr int plane = 128 * 16 * 2;   // bytes of one BF16 plane of a 128 x 16 tile
-    // phase 1 (source row indices staged first; four rows per thread in flight)
-    __shared__ long long srow[TP_K];
-    if (threadIdx.x < nk) srow[threadIdx.x] = (long long)P.g[P.k0 + threadIdx.x] * ns;
-    __syncthreads();
-    if (alpha) {
-        // thread = (n, k-group of 8): four 16-byte loads (one per BF16 plane)
-        // give 8 complex values of the tile, then the 8 rows of T_p at n
-        static_assert(TP_K == 16, "the update reads one 16-deep packed tile");
-        const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
-        const int nkcK = (P.Ki + 15) >> 4;
-        const char* src = reinterpret_cast<const char*>(P.kn) +
-                          ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + row_off(P.fmt, n);
-        float2 v[8];
-        pk_load8(src, P.fmt, kg, v);
-        const bool nv = n0 + n < ns;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int kk = kg * 8 + j;
-            float2 t = v[j];
-            if (kk < nk && nv && a != 0.f) {
-                const float2 d = Tp[srow[kk] + n0 + n];
-                t.x = fmaf(a, d.x, t.x);
-                t.y = fmaf(a, d.y, t.y);
-            }
-            s[kk * TP_LD + n] = kk < nk ? t : make_float2(0.f, 0.f);
-        }
-    } else {
-        const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
-        const bool nv = n0 + n < ns;
-#pragma unroll 1
-        for (int kb = kq; kb < TP_K; kb += 8) {
-            float2 t[4], d[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int kk = kb + 2 * u;
-                t[u] = d[u] = make_float2(0.f, 0.f);
-                if (kk < nk && nv) {
-                    const long long o = srow[kk] + n0 + n;
-                    t[u] = T[o];
-                    if (a != 0.f) d[u] = Tp[o];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int kk = kb + 2 * u;
-                if (kk >= nk) continue;
-                s[kk * TP_LD + n] = t[u];
-            }
-        }
-    }
-    __syncthreads();
-    // phase 2: KN, rows n, k = factor index; nk rows of this tile in k-groups of 8
-    {
-        const int nkcK = (P.Ki + 15) >> 4;
-        const int ngrp = (nk + 7) >> 3;
-        for (int it = threadIdx.x; it < TP_N * ngrp; it += blockDim.x) {
-            const int n = it & (TP_N - 1), kg = it >> 7;
-            if (n0 + n >= ns) continue;
+    // tile tt = (row tile tt / gx, columns (tt % gx) * 128 ..): a capped grid
+    // walks them in launch order
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TPackTile& P = tiles[tt / gx];
+        const int n0 = (int)(tt % gx) * TP_N;
+        const int nk = P.nk;
+        // phase 1 (source row indices staged first; four rows per thread in flight)
+        if (threadIdx.x < nk) srow[threadIdx.x] = (long long)P.g[P.k0 + threadIdx.x] * ns;
+        __syncthreads();
+        if (alpha) {
+            // thread = (n, k-group of 8): four 16-byte loads (one per BF16 plane)
+            // give 8 complex values of the tile, then the 8 rows of T_p at n
+            static_assert(TP_K == 16, "the update reads one 16-deep packed tile");
+            const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+            const int nkcK = (P.Ki + 15) >> 4;
+            const char* src = reinterpret_cast<const char*>(P.kn) +
+                              ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + row_off(P.fmt, n);
             float2 v[8];
+            pk_load8(src, P.fmt, kg, v);
+            const bool nv = n0 + n < ns;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int kk = kg * 8 + j;
-                v[j] = kk < nk ? s[kk * TP_LD + n] : make_float2(0.f, 0.f);
+                float2 t = v[j];
+                if (kk < nk && nv && a != 0.f) {
+                    const float2 d = Tp[srow[kk] + n0 + n];
+                    t.x = fmaf(a, d.x, t.x);
+                    t.y = fmaf(a, d.y, t.y);
+                }
+                s[kk * TP_LD + n] = kk < nk ? t : make_float2(0.f, 0.f);
             }
-            const int k = P.k0 + kg * 8;   // multiple of 8
-            const int nn = n0 + n;
-            char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
-                        row_off(P.fmt, nn & 127);
-            pk_store8(dst, P.fmt, (k >> 3) & 1, v, 1.f);
-        }
-    }
-    // phase 3: NK, rows = factor index, k = n; conjugated
-    if (P.nk_dst) {
-        const int nkcN = (ns + 15) >> 4;
-        // lanes take consecutive rows: conflict-free shared reads, and 16-byte
-        // stores 16 bytes apart in the packed tile
-        for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-            const int kk = it & (TP_K - 1), ng = it >> TP_KS;
-            const int nb = n0 + ng * 8;
-            if (kk >= nk || nb >= ns) continue;
-            float2 v[8];
+        } else {
+            const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
+            const bool nv = n0 + n < ns;
+#pragma unroll 1
+            for (int kb = kq; kb < TP_K; kb += 8) {
+                float2 t[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
-            const int r = P.k0 + kk;
-            char* dst = reinterpret_cast<char*>(P.nk_dst) + ((long long)(r >> 7) * nkcN + (nb >> 4)) * 4 * plane +
-                        row_off(P.fmt, r & 127);
-            pk_store8(dst, P.fmt, (nb >> 3) & 1, v, -1.f);
+                for (int u = 0; u < 4; ++u) {
+                    const int kk = kb + 2 * u;
+                    t[u] = make_float2(0.f, 0.f);
+                    if (kk < nk && nv) t[u] = T[srow[kk] + n0 + n];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int kk = kb + 2 * u;
+                    if (kk >= nk) continue;
+                    s[kk * TP_LD + n] = t[u];
+                }
+            }
         }
+        __syncthreads();
+        // phase 2: KN, rows n, k = factor index; nk rows of this tile in k-groups of 8
+        {
+            const int nkcK = (P.Ki + 15) >> 4;
+            const int ngrp = (nk + 7) >> 3;
+            for (int it = threadIdx.x; it < TP_N * ngrp; it += blockDim.x) {
+                const int n = it & (TP_N - 1), kg = it >> 7;
+                if (n0 + n >= ns) continue;
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int kk = kg * 8 + j;
+                    v[j] = kk < nk ? s[kk * TP_LD + n] : make_float2(0.f, 0.f);
+                }
+                const int k = P.k0 + kg * 8;   // multiple of 8
+                const int nn = n0 + n;
+                char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
+                            row_off(P.fmt, nn & 127);
+                pk_store8(dst, P.fmt, (k >> 3) & 1, v, 1.f);
+            }
+        }
+        // phase 3: NK, rows = factor index, k = n; conjugated
+        if (P.nk_dst) {
+            const int nkcN = (ns + 15) >> 4;
+            // lanes take consecutive rows: conflict-free shared reads, and 16-byte
+            // stores 16 bytes apart in the packed tile
+            for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
+                const int kk = it & (TP_K - 1), ng = it >> TP_KS;
+                const int nb = n0 + ng * 8;
+                if (kk >= nk || nb >= ns) continue;
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
+                const int r = P.k0 + kk;
+                char* dst = reinterpret_cast<char*>(P.nk_dst) + ((long long)(r >> 7) * nkcN + (nb >> 4)) * 4 * plane +
+                            row_off(P.fmt, r & 127);
+                pk_store8(dst, P.fmt, (nb >> 3) & 1, v, -1.f);
+            }
+        }
+        __syncthreads();   // s and srow are rewritten for the next tile
     }
 }
 
@@ -441,95 +441,101 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
                                                const cf* __restrict__ A2, const double* __restrict__ alpha, int ns,
                                                int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
                                                double* __restrict__ part, const long long* __restrict__ roff,
-                                               int nblk, int fmt) {
+                                               int nblk, int fmt, int gx, long long ntiles) {
     __shared__ float2 s[TP_K * TP_LD];
     __shared__ double sh[32];
     constexpr int plane = 128 * 16 * 2;
-    const int n0 = blockIdx.x * TP_N, r0 = blockIdx.y * TP_K;
-    const RTile tl = rtile(r0, b, roff, nblk);
-    const int blk = tl.blk, rl0 = tl.rl0, bK = tl.bK;
     const float a = alpha ? (float)alpha[0] : 0.f;
     const float a2 = alpha ? (float)(alpha[0] * alpha[0]) : 0.f;
-    Acc acc;
-    if (alpha) {
-        // the step: the tile's current values from its own KN packing (one
-        // 16-deep packed tile; thread = (n, k-group of 8)), then A1, A2
-        const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
-        const bool nv = n0 + n < ns;
-        float2 v[8];
-        pk_load8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + row_off(fmt, n), fmt, kg, v);
+    // tile tt = (rows (tt / gx) * 16 .., columns (tt % gx) * 128 ..): a capped
+    // grid walks them in launch order; tile tt's partial of ||R||^2 is part[tt]
+    for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int n0 = (int)(tt % gx) * TP_N, r0 = (int)(tt / gx) * TP_K;
+        const RTile tl = rtile(r0, b, roff, nblk);
+        const int blk = tl.blk, rl0 = tl.rl0, bK = tl.bK;
+        Acc acc;
+        if (alpha) {
+            // the step: the tile's current values from its own KN packing (one
+            // 16-deep packed tile; thread = (n, k-group of 8)), then A1, A2
+            const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+            const bool nv = n0 + n < ns;
+            float2 v[8];
+            pk_load8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + row_off(fmt, n), fmt,
+                     kg, v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int kk = kg * 8 + j;
-            float2 r = v[j];
-            if (nv) {
-                if (a != 0.f) {
-                    const long long o = (long long)(r0 + kk) * ns + n0 + n;
-                    const float2 u = A1[o], w = A2[o];
-                    r.x = fmaf(a2, w.x, fmaf(a, u.x, r.x));
-                    r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
+            for (int j = 0; j < 8; ++j) {
+                const int kk = kg * 8 + j;
+                float2 r = v[j];
+                if (nv) {
+                    if (a != 0.f) {
+                        const long long o = (long long)(r0 + kk) * ns + n0 + n;
+                        const float2 u = A1[o], w = A2[o];
+                        r.x = fmaf(a2, w.x, fmaf(a, u.x, r.x));
+                        r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
+                    }
+                    acc.add(fmaf(r.x, r.x, r.y * r.y));
                 }
-                acc.add(fmaf(r.x, r.x, r.y * r.y));
+                s[kk * TP_LD + n] = r;
             }
-            s[kk * TP_LD + n] = r;
-        }
-    } else {
-        // packing only (after a forward product): the FP32 rows of R
-        const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
-        const bool nv = n0 + n < ns;
+        } else {
+            // packing only (after a forward product): the FP32 rows of R
+            const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
+            const bool nv = n0 + n < ns;
 #pragma unroll 1
-        for (int kb = kq; kb < TP_K; kb += 8) {
-            float2 r[4];
+            for (int kb = kq; kb < TP_K; kb += 8) {
+                float2 r[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                r[q] = make_float2(0.f, 0.f);
-                if (nv) r[q] = R[(long long)(r0 + kb + 2 * q) * ns + n0 + n];
+                for (int q = 0; q < 4; ++q) {
+                    r[q] = make_float2(0.f, 0.f);
+                    if (nv) r[q] = R[(long long)(r0 + kb + 2 * q) * ns + n0 + n];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = kb + 2 * q;
+                    if (nv) acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
+                    s[kk * TP_LD + n] = r[q];
+                }
             }
+        }
+        if (part) {
+            const double t = block_sum(acc.val(), sh);   // includes the __syncthreads phase 2 needs
+            if (threadIdx.x == 0) part[tt] = t;
+        } else {
+            __syncthreads();
+        }
+        // phase 2: MK, rows = receivers of block blk, k = n
+        {
+            const int nkcN = (ns + 15) >> 4;
+            char* const base = mk[blk];
+            for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
+                const int kk = it & (TP_K - 1), ng = it >> TP_KS;
+                const int nb = n0 + ng * 8;
+                if (nb >= ns) continue;
+                float2 v[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kk = kb + 2 * q;
-                if (nv) acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
-                s[kk * TP_LD + n] = r[q];
+                for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
+                const int rl = rl0 + kk;
+                char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + row_off(fmt, rl & 127);
+                pk_store8(dst, fmt, (nb >> 3) & 1, v, 1.f);
             }
         }
-    }
-    if (part) {
-        const double t = block_sum(acc.val(), sh);   // includes the __syncthreads phase 2 needs
-        if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-    } else {
-        __syncthreads();
-    }
-    // phase 2: MK, rows = receivers of block blk, k = n
-    {
-        const int nkcN = (ns + 15) >> 4;
-        char* const base = mk[blk];
-        for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-            const int kk = it & (TP_K - 1), ng = it >> TP_KS;
-            const int nb = n0 + ng * 8;
-            if (nb >= ns) continue;
-            float2 v[8];
+        // phase 3: KN, rows = n, k = receiver of block blk
+        {
+            const int nkcK = bK >> 4;
+            char* const base = kn[blk];
+            for (int it = threadIdx.x; it < TP_N * (TP_K / 8); it += blockDim.x) {
+                const int n = it & (TP_N - 1), kg = it >> 7;
+                const int nn = n0 + n;
+                if (nn >= ns) continue;
+                float2 v[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
-            const int rl = rl0 + kk;
-            char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + row_off(fmt, rl & 127);
-            pk_store8(dst, fmt, (nb >> 3) & 1, v, 1.f);
+                for (int j = 0; j < 8; ++j) v[j] = s[(kg * 8 + j) * TP_LD + n];
+                const int k = rl0 + kg * 8;
+                char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + row_off(fmt, nn & 127);
+                pk_store8(dst, fmt, (k >> 3) & 1, v, 1.f);
+            }
         }
-    }
-    // phase 3: KN, rows = n, k = receiver of block blk
-    {
-        const int nkcK = bK >> 4;
-        char* const base = kn[blk];
-        for (int it = threadIdx.x; it < TP_N * (TP_K / 8); it += blockDim.x) {
-            const int n = it & (TP_N - 1), kg = it >> 7;
-            const int nn = n0 + n;
-            if (nn >= ns) continue;
-            float2 v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = s[(kg * 8 + j) * TP_LD + n];
-            const int k = rl0 + kg * 8;
-            char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + row_off(fmt, nn & 127);
-            pk_store8(dst, fmt, (k >> 3) & 1, v, 1.f);
-        }
+        __syncthreads();   // s is rewritten for the next tile
     }
 }
 
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
 // and A1, A2 in FP32; products of four elements summed in FP32 before each
 // compensated add.  A fixed grid walks the tiles in a fixed order and leaves
 // one partial per dot and CTA (few partials for the one-block finaliser).
-__global__ void __launch_bounds__(256) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
+__global__ void __maxnreg__(56) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
                                                 const cf* __restrict__ A2, int ns, int nr, int b,
                                                 const long long* __restrict__ roff, int nblk,
                                                 double* __restrict__ part, int fmt) {
@@ -1141,6 +1147,31 @@ __global__ void k_wait_selftest(int* status, unsigned long long limit_ns, unsign
 
 }  // namespace
 
+int pass_priority() {
+    static const int prio = [] {
+        const char* e = getenv("TLR_MDD_PASS_PRIORITY");   // read once, at the first pass launched
+        if (e && atoi(e) == 0) return 0;
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        return greatest;
+    }();
+    return prio;
+}
+
+// CTAs of a fused update-and-pack launch over nt tiles: all of them, or at
+// most TLR_MDD_PASS_CTAS (a tile loop walks the rest), so that beside
+// contractions of other streams the pass holds a bounded share of the SMs
+long long pass_grid(long long nt) {
+    static const long long cap = [] {
+        const char* e = getenv("TLR_MDD_PASS_CTAS");   // read once
+        return e ? atoll(e) : 0LL;
+    }();
+    return cap > 0 ? std::min(nt, cap) : nt;
+}
+
 long long packed_bytes(long long R, long long K, int TR) {
     const long long nkc = (K + KC - 1) / KC, nrb = (R + TR - 1) / TR;
     return nrb * nkc * 4LL * TR * KC * 2;
@@ -1151,18 +1182,20 @@ cudaError_t pack_operands(const PackJob* jobs, int njobs, long long max_items, c
     if (njobs == 0 || max_items == 0) return cudaSuccess;
     const long long rows = max_items >> 32, kgs = max_items & 0xffffffffLL;
     dim3 grid((unsigned)((rows + 255) / 256), (unsigned)njobs, (unsigned)((kgs + PACK_KG - 1) / PACK_KG));
-    k_pack<<<grid, 256, 0, st>>>(jobs);
+    const cudaError_t e = launch_pass(k_pack, grid, dim3(256), st, jobs);
     counted(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t tpack(const TPackTile* d_tiles, int ntiles, cf* T, const cf* Tp, const double* alpha, int ns,
                   cudaStream_t st) {
     if (ntiles == 0 || ns == 0) return cudaSuccess;
-    dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)ntiles);
-    k_tpack<<<grid, 256, 0, st>>>(d_tiles, T, Tp, alpha, ns);
+    const int gx = (ns + TP_N - 1) / TP_N;
+    const long long nt = (long long)gx * ntiles;
+    const cudaError_t e = launch_pass(k_tpack, dim3((unsigned)pass_grid(nt)), dim3(256), st, d_tiles, T, Tp, alpha, ns,
+                                      gx, nt);
     counted(1);
-    return cudaGetLastError();
+    return e;
 }
 
 long long rstep_ctas(int nr, int ns) { return (long long)((ns + TP_N - 1) / TP_N) * (nr / TP_K); }
@@ -1173,10 +1206,12 @@ cudaError_t rstep(cf* R, const cf* A1, const cf* A2, const double* alpha, int nr
     if (nr % TP_K != 0) return cudaErrorInvalidValue;
     if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((ns + TP_N - 1) / TP_N), (unsigned)(nr / TP_K));
-    k_rstep<<<grid, 256, 0, st>>>(R, A1, A2, alpha, ns, b, kn, mk, part, roff, nblk, fmt);
+    const int gx = (ns + TP_N - 1) / TP_N;
+    const long long nt = (long long)gx * (nr / TP_K);
+    const cudaError_t e = launch_pass(k_rstep, dim3((unsigned)pass_grid(nt)), dim3(256), st, R, A1, A2, alpha, ns, b, kn,
+                                      mk, part, roff, nblk, fmt, gx, nt);
     counted(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, int ns, int b, double* part,
@@ -1185,9 +1220,10 @@ cudaError_t dots6_packed(char* const* kn, const cf* A1, const cf* A2, int nr, in
     if (nr % TP_K != 0) return cudaErrorInvalidValue;
     if (!roff && (b <= 0 || b % TP_K != 0 || nr % b != 0)) return cudaErrorInvalidValue;
     if (roff && nblk <= 0) return cudaErrorInvalidValue;
-    k_dots6p<<<kRedBlocks, 256, 0, st>>>(kn, A1, A2, ns, nr, b, roff, nblk, part, fmt);
+    const cudaError_t e = launch_pass(k_dots6p, dim3(kRedBlocks), dim3(256), st, kn, A1, A2, ns, nr, b, roff, nblk,
+                                      part, fmt);
     counted(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t wait_selftest(int* status, unsigned long long limit_ns, unsigned long long* waited_ns,

@@ -63,12 +63,12 @@ __global__ void k_panel_to_theta(PanelMap m, const cf* __restrict__ pan, cf* __r
 }
 
 cudaError_t theta_to_panel(const PanelMap& m, const cf* theta, cf* pan, cudaStream_t st) {
-    k_theta_to_panel<<<1024, 256, 0, st>>>(m, theta, pan);
+    (void)launch_pass(k_theta_to_panel, dim3(1024), dim3(256), st, m, theta, pan);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t panel_to_theta(const PanelMap& m, const cf* pan, cf* theta, cudaStream_t st) {
-    k_panel_to_theta<<<1024, 256, 0, st>>>(m, pan, theta);
+    (void)launch_pass(k_panel_to_theta, dim3(1024), dim3(256), st, m, pan, theta);
     counted(1);
     return cudaGetLastError();
 }
@@ -108,7 +108,7 @@ __global__ void k_sym_dense(const cf* __restrict__ pan, long long zbase, long lo
 cudaError_t sym_dense(const cf* pan, long long zbase, long long ndense, long long b, cf* Zs, cudaStream_t st,
                       int general, const long long* zoff, const int* zdim) {
     if (ndense == 0) return cudaSuccess;
-    k_sym_dense<<<512, 256, 0, st>>>(pan, zbase, ndense, b, Zs, general, zoff, zdim);
+    (void)launch_pass(k_sym_dense, dim3(512), dim3(256), st, pan, zbase, ndense, b, Zs, general, zoff, zdim);
     counted(1);
     return cudaGetLastError();
 }
@@ -150,7 +150,8 @@ __global__ void k_reduce_grad(const cf* __restrict__ part, int nsplit, long long
 cudaError_t reduce_grad(const cf* part, int nsplit, long long stride, long long nlr, long long ndense,
                         long long b, cf* grad, cudaStream_t st, int general, const long long* zoff,
                         const int* zdim) {
-    k_reduce_grad<<<1024, 256, 0, st>>>(part, nsplit, stride, nlr, ndense, b, grad, general, zoff, zdim);
+    (void)launch_pass(k_reduce_grad, dim3(1024), dim3(256), st, part, nsplit, stride, nlr, ndense, b, grad, general,
+                      zoff, zdim);
     counted(1);
     return cudaGetLastError();
 }
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const float* __restric
 }
 
 cudaError_t dot_part(const float* a, const float* b, long long n2, double* part, cudaStream_t st) {
-    k_dot_part<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n2, part);
+    (void)launch_pass(k_dot_part, dim3(kRedBlocks), dim3(kRedThreads), st, a, b, n2, part);
     counted(1);
     return cudaGetLastError();
 }
@@ -182,7 +183,7 @@ __global__ void k_finalize(const double* part, int nblk, int stride, int cnt, do
 }
 
 cudaError_t finalize(const double* part, int nblk, int stride, int cnt, double* out, cudaStream_t st) {
-    k_finalize<<<1, 32, 0, st>>>(part, nblk, stride, cnt, out);
+    (void)launch_pass(k_finalize, dim3(1), dim3(32), st, part, nblk, stride, cnt, out);
     counted(1);
     return cudaGetLastError();
 }
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dots6(const cf* __restrict__ R,
 }
 
 cudaError_t dots6_part(const cf* R, const cf* A1, const cf* A2, long long n, double* part, cudaStream_t st) {
-    k_dots6<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, part);
+    (void)launch_pass(k_dots6, dim3(kRedBlocks), dim3(kRedThreads), st, R, A1, A2, n, part);
     counted(1);
     return cudaGetLastError();
 }
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(kRedThreads) k_step_residual(cf* __restrict__ 
 }
 
 cudaError_t step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha, cudaStream_t st) {
-    k_step_residual<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, alpha, nullptr);
+    (void)launch_pass(k_step_residual, dim3(kRedBlocks), dim3(kRedThreads), st, R, A1, A2, n, alpha, nullptr);
     counted(1);
     return cudaGetLastError();
 }
@@ -295,7 +296,7 @@ __global__ void k_axpy_dev(float* __restrict__ x, const float* __restrict__ y, l
 }
 
 cudaError_t axpy_dev(float* x, const float* y, long long n2, const double* alpha, cudaStream_t st) {
-    k_axpy_dev<<<1024, 256, 0, st>>>(x, y, n2, alpha);
+    (void)launch_pass(k_axpy_dev, dim3(1024), dim3(256), st, x, y, n2, alpha);
     counted(1);
     return cudaGetLastError();
 }
@@ -833,75 +834,75 @@ __global__ void k_record_f0(SolverDev S, const double* partf) {
 // host wrappers
 // ---------------------------------------------------------------------------
 cudaError_t sv_norm_part(const cf* R, long long n, double* part, cudaStream_t st) {
-    k_norm_part<<<kRedBlocks, kRedThreads, 0, st>>>(R, n, part);
+    (void)launch_pass(k_norm_part, dim3(kRedBlocks), dim3(kRedThreads), st, R, n, part);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_record_f0(const SolverDev& S, const double* partf, cudaStream_t st) {
-    k_record_f0<<<1, 32, 0, st>>>(S, partf);
+    (void)launch_pass(k_record_f0, dim3(1), dim3(32), st, S, partf);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_admm_init(const SolverDev& S, cudaStream_t st) {
-    k_admm_init<<<1024, 256, 0, st>>>(S);
+    (void)launch_pass(k_admm_init, dim3(1024), dim3(256), st, S);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_admm_resume(const SolverDev& S, cudaStream_t st) {
-    k_admm_resume<<<1024, 256, 0, st>>>(S);
+    (void)launch_pass(k_admm_resume, dim3(1024), dim3(256), st, S);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_xupdate_start(const SolverDev& S, double rho, cudaStream_t st) {
-    k_xupdate_start<<<1024, 256, 0, st>>>(S, rho);
+    (void)launch_pass(k_xupdate_start, dim3(1024), dim3(256), st, S, rho);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_direction(const SolverDev& S, cudaStream_t st) {
     for (int j0 = 0; j0 < S.m; j0 += kLbGroup) {
-        k_lb_dots<<<kRedBlocks, kLbThreads, 0, st>>>(S, j0);
+        (void)launch_pass(k_lb_dots, dim3(kRedBlocks), dim3(kLbThreads), st, S, j0);
         counted(1);
     }
-    k_lb_solve<<<1, kFinThreads, 0, st>>>(S);
+    (void)launch_pass(k_lb_solve, dim3(1), dim3(kFinThreads), st, S);
     counted(1);
-    k_lb_dir<<<1024, 256, 0, st>>>(S);
+    (void)launch_pass(k_lb_dir, dim3(1024), dim3(256), st, S);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_dots3(const SolverDev& S, double* part, cudaStream_t st) {
-    k_dots3<<<kRedBlocks, kRedThreads, 0, st>>>(S, part);
+    (void)launch_pass(k_dots3, dim3(kRedBlocks), dim3(kRedThreads), st, S, part);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_line_search(const SolverDev& S, const double* part6, int nb6, const double* part3, double rho,
                            cudaStream_t st) {
-    k_line_search<<<1, kFinThreads, 0, st>>>(S, part6, nb6, part3, rho);
+    (void)launch_pass(k_line_search, dim3(1), dim3(kFinThreads), st, S, part6, nb6, part3, rho);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_step_residual(cf* R, const cf* A1, const cf* A2, long long n, const double* alpha,
                              double* partf, cudaStream_t st) {
-    k_step_residual<<<kRedBlocks, kRedThreads, 0, st>>>(R, A1, A2, n, alpha, partf);
+    (void)launch_pass(k_step_residual, dim3(kRedBlocks), dim3(kRedThreads), st, R, A1, A2, n, alpha, partf);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_step_theta(const SolverDev& S, cudaStream_t st) {
-    k_step_theta<<<1024, 256, 0, st>>>(S);
+    (void)launch_pass(k_step_theta, dim3(1024), dim3(256), st, S);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_pair_prep(const SolverDev& S, double rho, double* part, cudaStream_t st) {
-    k_pair_prep<<<kRedBlocks, kRedThreads, 0, st>>>(S, rho, part);
+    (void)launch_pass(k_pair_prep, dim3(kRedBlocks), dim3(kRedThreads), st, S, rho, part);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_pair_accept(const SolverDev& S, const double* part3, const double* partf, int nf, cudaStream_t st) {
-    k_pair_accept<<<1, kFinThreads, 0, st>>>(S, part3, partf, nf);
+    (void)launch_pass(k_pair_accept, dim3(1), dim3(kFinThreads), st, S, part3, partf, nf);
     counted(1);
     return cudaGetLastError();
 }
 cudaError_t sv_admm_zu(const SolverDev& S, double lam, double rho, cudaStream_t st) {
-    k_admm_zu<<<1024, 256, 0, st>>>(S, lam, rho);
+    (void)launch_pass(k_admm_zu, dim3(1024), dim3(256), st, S, lam, rho);
     counted(1);
     return cudaGetLastError();
 }
