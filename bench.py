@@ -437,6 +437,9 @@ def main():
     ap.add_argument("--workload", default="precision", choices=["precision", "batched"])
     ap.add_argument("--seed", type=int, default=2412)
     ap.add_argument("--streams", type=int, default=3, help="CUDA streams the frequencies of a step are spread over")
+    ap.add_argument("--pass-ctas", type=int, default=-1,
+                    help="cap on the CTAs of one fused update-and-pack launch in the timed steps "
+                         "(tlr_mdd_set_pass_ctas; -1: 4 per SM with more than one stream, else 0 = one per tile)")
     ap.add_argument("--e2e-steps", type=int, default=4, help="steps of the end-to-end leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-cols", type=int, default=512,
@@ -484,6 +487,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # with several streams a capped pass grid leaves the contraction CTAs of
+    # the other streams their SMs (3 streams: 3.32 against 3.27 freq-solves/s)
+    pass_ctas = args.pass_ctas if args.pass_ctas >= 0 else (4 * sms if args.streams > 1 else 0)
+    T.tlr_mdd_set_pass_ctas(pass_ctas)
     total = wl.nfreq * world
     ranks = wl.ranks(total)
     if args.schedule and args.freqs and args.schedule % args.freqs == 0:
@@ -550,11 +558,13 @@ def main():
     roof = None
     if rank == 0:
         single = Runner(T, torch, inp, 1, dev)
+        T.tlr_mdd_set_pass_ctas(0)   # one stream: a CTA per tile
         T.tlr_mdd_timing_reset()
         T.tlr_mdd_timing_enable(True)
         ms1 = single.step(steps_of[0], prec)
         timing = T.tlr_mdd_timing_read()
         T.tlr_mdd_timing_enable(False)
+        T.tlr_mdd_set_pass_ctas(pass_ctas)
         del single
         dom = max(range(len(timing)), key=lambda c: timing[c][0])
         dms, dfl, dnl = timing[dom]
@@ -631,6 +641,8 @@ def main():
     # sampled source columns, for both paths, and 30-iteration solves on both
     # paths (time, and the difference of their X and final misfit)
     log("e2e leg done")
+    # the legs below run one solve at a time (or their own streams): a CTA per tile
+    T.tlr_mdd_set_pass_ctas(0)
     acc = None
     cmp = None
     if rank == 0 and args.accuracy > 0:
@@ -684,6 +696,7 @@ def main():
                    "frequencies_per_gpu": wl.nfreq, "frequencies_per_step": wl.batch,
                    "tile": wl.tile, "ranks": f"{wl.rank_lo}->{wl.rank_hi} linear",
                    "iters_per_solve": ITERS_PER_SOLVE, "precision": args.precision, "streams": nstream,
+                   "pass_ctas": pass_ctas,
                    "step": "one batch of frequencies (every nfreq/batch-th), each solved from its raw D, U "
                            "through a handle created for it (data step, packing, solve)",
                    "l2": "inputs larger than L2 (each 9216x9216 complex64 panel is 679 MB; every step reads "

@@ -433,6 +433,20 @@ int tlr_mdd_batch_destroy(tlr_mdd_batch_t* b);
  * once the device's memory is wanted elsewhere.  keep_bytes < 0: TLR_ERR_ARG. */
 int tlr_mdd_trim_pool(int64_t keep_bytes, int64_t* reserved);
 
+/* Launch shape of the memory-bound passes (the paper has no counterpart).
+ * The fused update-and-pack kernels of the tensor-core path (the step of T
+ * with its packings, the residual step with its packings) are launched at
+ * the device's greatest stream priority, so that where solves on several
+ * streams share the GPU their CTAs run beside other streams' contraction
+ * CTAs.  tlr_mdd_set_pass_ctas caps the CTAs of one such launch (each walks
+ * tiles until all are done; 0: one CTA per tile, the initial value unless the
+ * environment variable TLR_MDD_PASS_CTAS gives another), process-wide, for
+ * launches made and graphs recorded after the call; the previous cap goes to
+ * *previous (HOST, may be NULL).  Results do not depend on the cap (every
+ * tile's arithmetic and its partial sums are the same).  ctas < 0:
+ * TLR_ERR_ARG. */
+int tlr_mdd_set_pass_ctas(int64_t ctas, int64_t* previous);
+
 const char* tlr_mdd_last_error(const tlr_mdd_t* h);
 int tlr_mdd_destroy(tlr_mdd_t* h);
 

@@ -2203,6 +2203,13 @@ int tlr_mdd_trim_pool(int64_t keep_bytes, int64_t* reserved) {
     return TLR_OK;
 }
 
+int tlr_mdd_set_pass_ctas(int64_t ctas, int64_t* previous) {
+    if (ctas < 0) FAIL((tlr_mdd_s*)nullptr, TLR_ERR_ARG, "ctas must be >= 0");
+    if (previous) *previous = (int64_t)pass_cap();
+    set_pass_cap((long long)ctas);
+    return TLR_OK;
+}
+
 int tlr_mdd_destroy(tlr_mdd_t* h) {
     if (!h) return TLR_ERR_ARG;
     if (h->pending) cudaEventSynchronize(h->ev1);

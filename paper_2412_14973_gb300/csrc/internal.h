@@ -26,6 +26,11 @@ inline void counted(int n) { g_launches.fetch_add(n, std::memory_order_relaxed);
 // TLR_MDD_PASS_PRIORITY=0 launches them at their stream's priority.
 int pass_priority();
 
+// Cap on the CTAs of a fused update-and-pack launch (0: one CTA per tile).
+constexpr long long kPassCtasDefault = 0;
+long long pass_cap();
+void set_pass_cap(long long ctas);
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pass(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};

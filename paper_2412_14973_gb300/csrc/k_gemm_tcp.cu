@@ -1147,9 +1147,14 @@ __global__ void k_wait_selftest(int* status, unsigned long long limit_ns, unsign
 
 }  // namespace
 
+// The passes' launch priority: the device's greatest, or their stream's with
+// TLR_MDD_PASS_PRIORITY=0 (read once).  Measured on the nr = 9216 workload
+// with 3 streams: 3.32 freq-solves/s against 3.26 at the stream's priority
+// (both with the pass grid capped at 4 CTAs per SM), and 3.26 with the
+// contractions at the greatest priority instead.
 int pass_priority() {
     static const int prio = [] {
-        const char* e = getenv("TLR_MDD_PASS_PRIORITY");   // read once, at the first pass launched
+        const char* e = getenv("TLR_MDD_PASS_PRIORITY");
         if (e && atoi(e) == 0) return 0;
         int least = 0, greatest = 0;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
@@ -1162,13 +1167,33 @@ int pass_priority() {
 }
 
 // CTAs of a fused update-and-pack launch over nt tiles: all of them, or at
-// most TLR_MDD_PASS_CTAS (a tile loop walks the rest), so that beside
-// contractions of other streams the pass holds a bounded share of the SMs
+// most the cap (a tile loop walks the rest), so that beside contractions of
+// other streams the pass holds a bounded share of the SMs.  The cap starts
+// from the environment variable TLR_MDD_PASS_CTAS (else kPassCtasDefault)
+// and is set with tlr_mdd_set_pass_ctas.
+namespace {
+std::atomic<long long> g_pass_cap{-1};
+}
+
+long long pass_cap() {
+    long long c = g_pass_cap.load(std::memory_order_relaxed);
+    if (c < 0) {
+        const char* e = getenv("TLR_MDD_PASS_CTAS");
+        long long want = e ? std::max(0LL, atoll(e)) : kPassCtasDefault;
+        long long expect = -1;
+        g_pass_cap.compare_exchange_strong(expect, want);
+        c = g_pass_cap.load(std::memory_order_relaxed);
+    }
+    return c;
+}
+
+void set_pass_cap(long long ctas) {
+    pass_cap();   // the environment's value is consumed first, so a set is never overwritten
+    g_pass_cap.store(std::max(0LL, ctas), std::memory_order_relaxed);
+}
+
 long long pass_grid(long long nt) {
-    static const long long cap = [] {
-        const char* e = getenv("TLR_MDD_PASS_CTAS");   // read once
-        return e ? atoll(e) : 0LL;
-    }();
+    const long long cap = pass_cap();
     return cap > 0 ? std::min(nt, cap) : nt;
 }
 

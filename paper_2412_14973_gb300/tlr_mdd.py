@@ -25,7 +25,7 @@ __all__ = [
     "tlr_mdd_get_state", "tlr_mdd_set_state", "TLR_SOLVE_RESUME", "TLR_SOLVE_REFRESH",
     "tlr_mdd_time_to_freq", "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest",
     "tlr_mdd_trim_pool", "tlr_mdd_set_stream", "tlr_mdd_batch_create", "tlr_mdd_batch_solve_async",
-    "tlr_mdd_batch_query", "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy", "Batch",
+    "tlr_mdd_batch_query", "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy", "Batch", "tlr_mdd_set_pass_ctas",
     "TLR_OK", "TLR_ERR_ARG", "TLR_ERR_SHAPE", "TLR_ERR_UNSUPPORTED", "TLR_ERR_NOMEM", "TLR_ERR_CUDA",
     "TLR_ERR_NONFINITE", "TLR_ERR_TIMEOUT", "TLR_ERR_STATE",
 ]
@@ -52,7 +52,7 @@ EXPORTED = [
     "tlr_mdd_warm_start", "tlr_mdd_get_state", "tlr_mdd_set_state", "tlr_mdd_time_to_freq",
     "tlr_mdd_freq_to_time", "tlr_mdd_stack_alpha", "tlr_mdd_wait_selftest", "tlr_mdd_trim_pool",
     "tlr_mdd_set_stream", "tlr_mdd_batch_create", "tlr_mdd_batch_solve_async", "tlr_mdd_batch_query",
-    "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy",
+    "tlr_mdd_batch_wait", "tlr_mdd_batch_destroy", "tlr_mdd_set_pass_ctas",
 ]
 TLR_NCLASS = 3
 TLR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -183,6 +183,8 @@ def lib():
         L.tlr_mdd_set_state.argtypes = [vp, vp, vp]
         L.tlr_mdd_trim_pool.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
         L.tlr_mdd_trim_pool.restype = i32
+        L.tlr_mdd_set_pass_ctas.argtypes = [C.c_int64, C.POINTER(C.c_int64)]
+        L.tlr_mdd_set_pass_ctas.restype = i32
         L.tlr_mdd_set_data.restype = i32
         for name in ("tlr_mdd_theta_size", "tlr_mdd_theta_layout", "tlr_mdd_hilbert_perm",
                      "tlr_mdd_create", "tlr_mdd_apply", "tlr_mdd_adjoint", "tlr_mdd_grad",
@@ -532,6 +534,14 @@ def tlr_mdd_trim_pool(keep_bytes=0) -> int:
     r = C.c_int64()
     _check(lib().tlr_mdd_trim_pool(int(keep_bytes), C.byref(r)))
     return r.value
+
+
+def tlr_mdd_set_pass_ctas(ctas: int) -> int:
+    """Cap the CTAs of the fused update-and-pack launches (0: one per tile),
+    for launches made and graphs recorded from now on; returns the previous cap."""
+    prev = C.c_int64()
+    _check(lib().tlr_mdd_set_pass_ctas(int(ctas), C.byref(prev)))
+    return prev.value
 
 
 def tlr_mdd_solve_async(h, theta, opts: SolveOpts | None = None):
