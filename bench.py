@@ -166,9 +166,9 @@ def measured_peaks():
 # capture of the sources whose SHA-256 is GEMM_TRAFFIC_SHA.  A change to any of
 # those sources, another rank mix or another tile voids the figures (traffic null).
 GEMM_TRAFFIC_SOURCES = ("k_gemm_tcp.cu", "api.cu", "internal.h")
-GEMM_TRAFFIC_SHA = "73f137d417fd710870b5ac661923966c92143908757e8fcc9e1e17c164099a05"
+GEMM_TRAFFIC_SHA = "5f1c2b0b86e5f57b4183064acb2e466fe940878e713d56325270af06c9a5d0ef"
 GEMM_TRAFFIC_CASE = {"nr": 9216, "tile": 384, "ranks": [8, 15, 22, 29, 36, 43, 50, 57], "precision": "bf16x3"}
-GEMM_TRAFFIC_BYTES = {"cgemm_compress": 2091883834, "cgemm_expand": 4452802642, "cgemm_project": 4727283401}
+GEMM_TRAFFIC_BYTES = {"cgemm_compress": 2098328847, "cgemm_expand": 4448126664, "cgemm_project": 4657551388}
 
 
 def gemm_traffic(kernel, nr, tile, step_ranks, precision):
@@ -454,6 +454,9 @@ def main():
     ap.add_argument("--serving", type=int, default=120,
                     help="requests of the serving mix (nr 1024-8192, tile 128-512, rank 2-64) served with "
                          "continuous batching (0: skip)")
+    ap.add_argument("--serving-fp32-loads", default="",
+                    help="comma-separated arrival rates as fractions of the FP32 path's one-at-a-time capacity "
+                         "(e.g. 0.7,1.3): the serving mix served on the tensor cores at each, Poisson")
     ap.add_argument("--small-configs", type=int, default=200,
                     help="solves timed for each of the nr=256 and nr=1024 workloads (0: skip)")
     ap.add_argument("--secondary", type=int, default=2,
@@ -679,7 +682,8 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         T.tlr_mdd_trim_pool(0)
-        serve = serving_leg(T, torch, args.serving, args.seed, dev)
+        loads = [float(x) for x in args.serving_fp32_loads.split(",") if x.strip()]
+        serve = serving_leg(T, torch, args.serving, args.seed, dev, loads)
         log("serving leg done")
 
     if rank != 0:
@@ -963,7 +967,7 @@ def secondary_leg(T, torch, args, dev):
                                          "(the same flops) beside it"}}
 
 
-def serving_leg(T, torch, n, seed, dev):
+def serving_leg(T, torch, n, seed, dev, fp32_loads=()):
     """The serving mix: n per-frequency solve requests, nr = ns uniform over
     {1024, 2048, 4096, 8192}, tile over {128, 256, 512}, rank log-uniform
     2-64, BF16x3 tensor cores, 30-iteration solves.  Measured: one request at
@@ -1035,6 +1039,29 @@ def serving_leg(T, torch, n, seed, dev):
                "p99_ms": round(1e3 * pcb[99], 1) if pcb[99] else None,
                "batches": srvb.batches, "results_identical_alone_and_in_batches": bool(sameb),
                "note": "same arrivals; requests of one size admitted together share one launch per contraction"}
+    # the stream at loads relative to the FP32 path's one-at-a-time capacity
+    # (a load above 1 is one the FP32 path alone cannot carry)
+    at_fp32_loads = []
+    for li, load in enumerate(fp32_loads):
+        rate_l = load * m / t_fp32
+        arr = list(np.cumsum(np.random.default_rng(seed + 23 + li).exponential(1.0 / rate_l, n)))
+        srvl = serving.Server(budget, max_active=4)
+        t0 = time.perf_counter()
+        resl = srvl.run(make(T.TLR_PREC_BF16X3, arr), realtime=True)
+        t_l = time.perf_counter() - t0
+        pcl = serving.percentiles(resl)
+        okl = [r for r in resl if r.status == 0]
+        svl = [1e3 * (r.finished - r.admitted) for r in okl]
+        samel = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta)
+                    for a, b in zip(res_tc1, resl))
+        srvl.close()
+        at_fp32_loads.append({"load_of_fp32_capacity": load, "arrival_rate_hz": round(rate_l, 3),
+                              "tc_served_solves_per_s": round(len(okl) / t_l, 3),
+                              "p50_ms": round(1e3 * pcl[50], 1) if pcl[50] else None,
+                              "p99_ms": round(1e3 * pcl[99], 1) if pcl[99] else None,
+                              "service_p50_ms": round(percentile(svl, 50), 1) if svl else None,
+                              "service_p99_ms": round(percentile(svl, 99), 1) if svl else None,
+                              "results_identical_alone_and_in_mix": bool(samel)})
     sizes = collections_counter(r.nr for r in reqs)
     return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
             "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
@@ -1051,6 +1078,7 @@ def serving_leg(T, torch, n, seed, dev):
             "handles_created": srv.created, "handles_reused": srv.reused, "handles_evicted": srv.evicted,
             "results_identical_alone_and_in_mix": bool(same),
             "lockstep_batches": batched,
+            "at_fp32_loads": at_fp32_loads,
             "sizes": dict(sorted(sizes.items())),
             "mix": "nr=ns in {1024,2048,4096,8192}, tile in {128,256,512}, rank log-uniform 2-64, Poisson; "
                    "latency = arrival to result on the host clock (queueing included), service = admission to "
