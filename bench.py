@@ -184,6 +184,13 @@ def gemm_traffic(kernel, nr, tile, step_ranks, precision):
     return GEMM_TRAFFIC_BYTES.get(kernel)
 
 
+# CTAs per SM of a fused update-and-pack launch when several streams share
+# the GPU (beside two contraction CTAs an SM has registers for two; one per
+# SM measured best: 4 streams 3.45 freq-solves/s against 3.43 with two and
+# 3.32 uncapped)
+PASS_CTAS_PER_SM = 1
+
+
 def log(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -436,10 +443,12 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--workload", default="precision", choices=["precision", "batched"])
     ap.add_argument("--seed", type=int, default=2412)
-    ap.add_argument("--streams", type=int, default=3, help="CUDA streams the frequencies of a step are spread over")
+    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the frequencies of a step are spread over")
     ap.add_argument("--pass-ctas", type=int, default=-1,
                     help="cap on the CTAs of one fused update-and-pack launch in the timed steps "
-                         "(tlr_mdd_set_pass_ctas; -1: 4 per SM with more than one stream, else 0 = one per tile)")
+                         "and the other multi-stream legs (tlr_mdd_set_pass_ctas; -1: PASS_CTAS_PER_SM per SM with "
+                         "more than one stream, else 0 = one per tile)")
+    ap.add_argument("--secondary-streams", type=int, default=4, help="streams of the nr=4096 workload's steps")
     ap.add_argument("--e2e-steps", type=int, default=4, help="steps of the end-to-end leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--oracle-cols", type=int, default=512,
@@ -492,8 +501,9 @@ def main():
     dev = torch.device("cuda", local)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # with several streams a capped pass grid leaves the contraction CTAs of
-    # the other streams their SMs (3 streams: 3.32 against 3.27 freq-solves/s)
-    pass_ctas = args.pass_ctas if args.pass_ctas >= 0 else (4 * sms if args.streams > 1 else 0)
+    # the other streams their SMs
+    multi_ctas = args.pass_ctas if args.pass_ctas >= 0 else PASS_CTAS_PER_SM * sms
+    pass_ctas = multi_ctas if args.streams > 1 else (args.pass_ctas if args.pass_ctas >= 0 else 0)
     T.tlr_mdd_set_pass_ctas(pass_ctas)
     total = wl.nfreq * world
     ranks = wl.ranks(total)
@@ -669,7 +679,9 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         T.tlr_mdd_trim_pool(0)
+        T.tlr_mdd_set_pass_ctas(multi_ctas)       # several streams
         secondary = secondary_leg(T, torch, args, dev)
+        T.tlr_mdd_set_pass_ctas(0)
 
     peaks = measure_peaks(torch, dev) if rank == 0 else None
     small = None
@@ -683,7 +695,7 @@ def main():
         torch.cuda.empty_cache()
         T.tlr_mdd_trim_pool(0)
         loads = [float(x) for x in args.serving_fp32_loads.split(",") if x.strip()]
-        serve = serving_leg(T, torch, args.serving, args.seed, dev, loads)
+        serve = serving_leg(T, torch, args.serving, args.seed, dev, loads, multi_ctas)
         log("serving leg done")
 
     if rank != 0:
@@ -700,7 +712,7 @@ def main():
                    "frequencies_per_gpu": wl.nfreq, "frequencies_per_step": wl.batch,
                    "tile": wl.tile, "ranks": f"{wl.rank_lo}->{wl.rank_hi} linear",
                    "iters_per_solve": ITERS_PER_SOLVE, "precision": args.precision, "streams": nstream,
-                   "pass_ctas": pass_ctas,
+                   "pass_ctas": pass_ctas, "pass_ctas_other_multi_stream_legs": multi_ctas,
                    "step": "one batch of frequencies (every nfreq/batch-th), each solved from its raw D, U "
                            "through a handle created for it (data step, packing, solve)",
                    "l2": "inputs larger than L2 (each 9216x9216 complex64 panel is 679 MB; every step reads "
@@ -874,9 +886,10 @@ def secondary_leg(T, torch, args, dev):
     ranks = wl.ranks(wl.nfreq)
     freqs = list(range(wl.nfreq))
     inp = Inputs(T, torch, wl, freqs, ranks, args.seed + 1, dev)
-    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+    nst = max(1, args.secondary_streams)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nst)]
     main = torch.cuda.current_stream(dev)
-    hs = [T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_BF16X3), inp.D[f], inp.U[f], streams[f % 4]) for f in freqs]
+    hs = [T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_BF16X3), inp.D[f], inp.U[f], streams[f % nst]) for f in freqs]
     theta = [t.clone() for t in inp.th0]
     opts = T.solve_opts()
 
@@ -888,7 +901,7 @@ def secondary_leg(T, torch, args, dev):
             s_.wait_event(e0)
         for f in fs:
             T.tlr_mdd_set_data(hs[f], inp.D[f], inp.U[f], T.TLR_MEM_DEVICE)
-            with torch.cuda.stream(streams[f % 4]):
+            with torch.cuda.stream(streams[f % nst]):
                 theta[f].copy_(inp.th0[f])
             T.tlr_mdd_solve_async(hs[f], theta[f], opts)
         for f in fs:
@@ -907,7 +920,7 @@ def secondary_leg(T, torch, args, dev):
     # the same step on every 8th frequency, tensor cores and the FP32 SIMT path
     sub = freqs[::8]
     ms_tc_sub = step(fs=sub)
-    hs32 = {f: T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_FP32), inp.D[f], inp.U[f], streams[f % 4]) for f in sub}
+    hs32 = {f: T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_FP32), inp.D[f], inp.U[f], streams[f % nst]) for f in sub}
     step(hs32, sub)
     step(hs32, sub)
     ms_fp32_sub = step(hs32, sub)
@@ -950,13 +963,13 @@ def secondary_leg(T, torch, args, dev):
     f_eq = flops_per_solve(wl.nr, wl.nr, wl.tile, kx)
     return {"workload": wl.name, "value": round(wl.nfreq * args.secondary / (ms / 1e3), 3),
             "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
-            "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": 4,
+            "tflops": round(fl / (ms / 1e3) / 1e12, 1), "streams": nst,
             "step": "all 64 frequencies; handles kept across steps, data step and CUDA-graph solve per frequency",
             "fp32_comparison": {"frequencies": sub, "fp32_simt_freq_solves_per_s":
                                 round(len(sub) / (ms_fp32_sub / 1e3), 3),
                                 "tensor_core_freq_solves_per_s": round(len(sub) / (ms_tc_sub / 1e3), 3),
                                 "speedup_tc_vs_fp32": round(ms_fp32_sub / ms_tc_sub, 2),
-                                "note": "one step over every 8th frequency (the same rank mix), 4 streams"},
+                                "note": f"one step over every 8th frequency (the same rank mix), {nst} streams"},
             "cpu_oracle": oracle_cpu,
             "general_form": {"rank": kx, "n_theta": gn, "ms": round(gst.gpu_ms, 2),
                              "tflops": round(f_eq / (gst.gpu_ms / 1e3) / 1e12, 1),
@@ -967,7 +980,7 @@ def secondary_leg(T, torch, args, dev):
                                          "(the same flops) beside it"}}
 
 
-def serving_leg(T, torch, n, seed, dev, fp32_loads=()):
+def serving_leg(T, torch, n, seed, dev, fp32_loads=(), multi_ctas=0):
     """The serving mix: n per-frequency solve requests, nr = ns uniform over
     {1024, 2048, 4096, 8192}, tile over {128, 256, 512}, rank log-uniform
     2-64, BF16x3 tensor cores, 30-iteration solves.  Measured: one request at
@@ -1017,6 +1030,9 @@ def serving_leg(T, torch, n, seed, dev, fp32_loads=()):
     t_tc1_m = sum(r.finished - r.admitted for r in res_tc1[:m])
     rate = 0.9 * n / t_tc1
     arrivals = list(np.cumsum(np.random.default_rng(seed + 19).exponential(1.0 / rate, n)))
+    # served: several slots share the GPU, so the pass grid is capped (the
+    # one-at-a-time runs above use one CTA per tile)
+    T.tlr_mdd_set_pass_ctas(multi_ctas)
     srv = serving.Server(budget, max_active=4)
     t0 = time.perf_counter()
     res = srv.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
@@ -1062,8 +1078,10 @@ def serving_leg(T, torch, n, seed, dev, fp32_loads=()):
                               "service_p50_ms": round(percentile(svl, 50), 1) if svl else None,
                               "service_p99_ms": round(percentile(svl, 99), 1) if svl else None,
                               "results_identical_alone_and_in_mix": bool(samel)})
+    T.tlr_mdd_set_pass_ctas(0)
     sizes = collections_counter(r.nr for r in reqs)
     return {"requests": n, "completed": len(ok), "arrival_rate_hz": round(rate, 3),
+            "pass_ctas_served": multi_ctas,
             "tc_served_solves_per_s": round(len(ok) / t_srv, 3),
             "p50_ms": round(1e3 * pc[50], 1) if pc[50] else None,
             "p99_ms": round(1e3 * pc[99], 1) if pc[99] else None,

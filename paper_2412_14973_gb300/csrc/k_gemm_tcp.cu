@@ -279,134 +279,123 @@ __global__ void __launch_bounds__(256) k_pack(const PackJob* __restrict__ jobs) 
 // ---------------------------------------------------------------------------
 // tpack: fused update of the factor products and both of their packings
 // ---------------------------------------------------------------------------
-// A CTA takes one row tile (TP_K rows of one block's gathered T~_i) and 128
-// columns (n).  Phase 1 either reads the TP_K source rows of T coalesced
-// along n (packing only: alpha == nullptr), or, for the update, reads the
-// tile's current values from its own KN packing (one 16 KB packed tile: the
-// carried products live in packed form between forward products, each
-// update re-rounding them to the hi + lo pair) and the rows of T_p, applies
-// T += alpha T_p; it keeps the tile in shared memory; phase 2 writes the KN
-// packing (thread = (n, k-group of 8)); phase 3 the conjugated NK packing
-// (thread = (k, n-group of 8), lanes along k).  Padding of the packed buffers
-// (k >= K_i, rows >= ns) is zero from the buffer's creation and is never
-// written.
-constexpr int TP_K = kFuseRows, TP_N = 128, TP_LD = TP_N + 1;
-constexpr int TP_KS = TP_K == 16 ? 4 : 5;   // log2(TP_K)
-static_assert(kPackTRB == 128 && KC == 16 && (TP_K == 16 || TP_K == 32),
-              "tpack writes 128-row, 16-deep B tiles, 16 or 32 rows per CTA");
+// A tile is TP_K = 16 rows of one block's gathered T~_i by 128 columns (n);
+// thread = (n, k-group of 8).  A thread reads its 8 values either from the
+// rows of T (packing only: alpha == nullptr; coalesced along n) or, for the
+// update, from the tile's own KN packing (the carried products live in packed
+// form between forward products, each update re-rounding them to the hi + lo
+// pair) plus the rows of T_p, applying T += alpha T_p; it writes them back to
+// the KN packing as they are (the same 8 k of row n), then an 8 x 8 transpose
+// across each group of 8 lanes (warp shuffles) gives every lane 8
+// consecutive n of one row k for the conjugated NK packing.  No shared
+// memory: beside two contraction CTAs an SM then has room for as many pass
+// CTAs as registers allow.  Padding of the packed buffers (k >= K_i, rows >=
+// ns) is zero from the buffer's creation; whole padding groups are never
+// written, and the padding inside a written group is written as zeros.
+constexpr int TP_K = kFuseRows, TP_N = 128;
+static_assert(kPackTRB == 128 && KC == 16 && TP_K == 16,
+              "the passes take 16-deep, 128-row packed tiles with two k-groups of 8");
+
+// 8 x 8 transpose across the 8 lanes of each aligned lane group: lane i holds
+// a[j] = M[i][j] before and M[j][i] after (three butterfly exchanges).
+__device__ __forceinline__ void transpose8(float2* a) {
+    const int i = threadIdx.x & 7;
+#pragma unroll
+    for (int s = 4; s >= 1; s >>= 1) {
+        const bool upper = (i & s) != 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j & s) continue;
+            const float2 send = upper ? a[j] : a[j + s];
+            float2 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, s);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, s);
+            if (upper)
+                a[j] = recv;
+            else
+                a[j + s] = recv;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(256) k_tpack(const TPackTile* __restrict__ tiles, cf* __restrict__ T,
                                                const cf* __restrict__ Tp, const double* __restrict__ alpha,
                                                int ns, int gx, long long ntiles) {
-    __shared__ float2 s[TP_K * TP_LD];
-    __shared__ long long srow[TP_K];
     const float a = alpha ? (float)alpha[0] : 0.f;
     constexpr int plane = 128 * 16 * 2;   // bytes of one BF16 plane of a 128 x 16 tile
+    const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
     // tile tt = (row tile tt / gx, columns (tt % gx) * 128 ..): a capped grid
     // walks them in launch order
     for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const TPackTile& P = tiles[tt / gx];
         const int n0 = (int)(tt % gx) * TP_N;
         const int nk = P.nk;
-        // phase 1 (source row indices staged first; four rows per thread in flight)
-        if (threadIdx.x < nk) srow[threadIdx.x] = (long long)P.g[P.k0 + threadIdx.x] * ns;
-        __syncthreads();
+        const int nkcK = (P.Ki + 15) >> 4;
+        const bool nv = n0 + n < ns;
+        float2 t[8];
         if (alpha) {
-            // thread = (n, k-group of 8): four 16-byte loads (one per BF16 plane)
-            // give 8 complex values of the tile, then the 8 rows of T_p at n
-            static_assert(TP_K == 16, "the update reads one 16-deep packed tile");
-            const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
-            const int nkcK = (P.Ki + 15) >> 4;
+            // four 16-byte loads (one per BF16 plane) give the thread's 8
+            // values of the tile, then the 8 rows of T_p at n
             const char* src = reinterpret_cast<const char*>(P.kn) +
                               ((long long)(n0 >> 7) * nkcK + (P.k0 >> 4)) * 4 * plane + row_off(P.fmt, n);
-            float2 v[8];
-            pk_load8(src, P.fmt, kg, v);
-            const bool nv = n0 + n < ns;
+            pk_load8(src, P.fmt, kg, t);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int kk = kg * 8 + j;
-                float2 t = v[j];
                 if (kk < nk && nv && a != 0.f) {
-                    const float2 d = Tp[srow[kk] + n0 + n];
-                    t.x = fmaf(a, d.x, t.x);
-                    t.y = fmaf(a, d.y, t.y);
+                    const float2 d = Tp[(long long)P.g[P.k0 + kk] * ns + n0 + n];
+                    t[j].x = fmaf(a, d.x, t[j].x);
+                    t[j].y = fmaf(a, d.y, t[j].y);
                 }
-                s[kk * TP_LD + n] = kk < nk ? t : make_float2(0.f, 0.f);
             }
         } else {
-            const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
-            const bool nv = n0 + n < ns;
-#pragma unroll 1
-            for (int kb = kq; kb < TP_K; kb += 8) {
-                float2 t[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int kk = kb + 2 * u;
-                    t[u] = make_float2(0.f, 0.f);
-                    if (kk < nk && nv) t[u] = T[srow[kk] + n0 + n];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int kk = kb + 2 * u;
-                    if (kk >= nk) continue;
-                    s[kk * TP_LD + n] = t[u];
-                }
+            for (int j = 0; j < 8; ++j) {
+                const int kk = kg * 8 + j;
+                t[j] = (kk < nk && nv) ? T[(long long)P.g[P.k0 + kk] * ns + n0 + n] : make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
-        // phase 2: KN, rows n, k = factor index; nk rows of this tile in k-groups of 8
-        {
-            const int nkcK = (P.Ki + 15) >> 4;
-            const int ngrp = (nk + 7) >> 3;
-            for (int it = threadIdx.x; it < TP_N * ngrp; it += blockDim.x) {
-                const int n = it & (TP_N - 1), kg = it >> 7;
-                if (n0 + n >= ns) continue;
-                float2 v[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int kk = kg * 8 + j;
-                    v[j] = kk < nk ? s[kk * TP_LD + n] : make_float2(0.f, 0.f);
-                }
-                const int k = P.k0 + kg * 8;   // multiple of 8
-                const int nn = n0 + n;
-                char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
-                            row_off(P.fmt, nn & 127);
-                pk_store8(dst, P.fmt, (k >> 3) & 1, v, 1.f);
-            }
+        for (int j = 0; j < 8; ++j)
+            if (kg * 8 + j >= nk || !nv) t[j] = make_float2(0.f, 0.f);
+        // KN: rows n, k = factor index (this thread's own 8 values)
+        if (kg * 8 < nk && nv) {
+            const int k = P.k0 + kg * 8;   // multiple of 8
+            const int nn = n0 + n;
+            char* dst = reinterpret_cast<char*>(P.kn) + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane +
+                        row_off(P.fmt, nn & 127);
+            pk_store8(dst, P.fmt, (k >> 3) & 1, t, 1.f);
         }
-        // phase 3: NK, rows = factor index, k = n; conjugated
+        // NK: rows = factor index, k = n; conjugated.  After the transpose
+        // lane i of a group holds row kg * 8 + i at the group's 8 columns.
         if (P.nk_dst) {
-            const int nkcN = (ns + 15) >> 4;
-            // lanes take consecutive rows: conflict-free shared reads, and 16-byte
-            // stores 16 bytes apart in the packed tile
-            for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-                const int kk = it & (TP_K - 1), ng = it >> TP_KS;
-                const int nb = n0 + ng * 8;
-                if (kk >= nk || nb >= ns) continue;
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
+            transpose8(t);
+            const int kk = kg * 8 + (threadIdx.x & 7);
+            const int nb = n0 + (n & ~7);
+            if (kk < nk && nb < ns) {
+                const int nkcN = (ns + 15) >> 4;
                 const int r = P.k0 + kk;
                 char* dst = reinterpret_cast<char*>(P.nk_dst) + ((long long)(r >> 7) * nkcN + (nb >> 4)) * 4 * plane +
                             row_off(P.fmt, r & 127);
-                pk_store8(dst, P.fmt, (nb >> 3) & 1, v, -1.f);
+                pk_store8(dst, P.fmt, (nb >> 3) & 1, t, -1.f);
             }
         }
-        __syncthreads();   // s and srow are rewritten for the next tile
     }
 }
 
 // ---------------------------------------------------------------------------
 // rstep: fused residual step and both packings of the residual
 // ---------------------------------------------------------------------------
-// A CTA takes TP_K receiver rows (inside one block, every block a multiple of
-// TP_K) and 128 columns: phase 1 either reads the FP32 rows of R left by a
-// forward product (packing only), or, for the step, reads the tile from R's
-// own KN packing (the residual is carried in packed form between forward
-// products) with A1, A2 coalesced along n and applies it; it accumulates
-// ||R||^2 and keeps the tile in shared memory; phase 2 writes the MK packing
-// (rows = receivers, lanes along rows); phase 3 the KN packing (rows = n,
-// k = receiver, lanes along n).
+// A tile is TP_K = 16 receiver rows (inside one block, every block a
+// multiple of TP_K) by 128 columns; thread = (n, k-group of 8 rows).  A
+// thread reads its 8 values either from the FP32 rows of R left by a forward
+// product (packing only), or, for the step, from R's own KN packing (the
+// residual is carried in packed form between forward products) with A1, A2
+// coalesced along n, and applies the step; it accumulates ||R||^2, writes its
+// 8 values to the KN packing (rows = n, k = receiver) as they are, and after
+// an 8 x 8 transpose across each group of 8 lanes, 8 consecutive n of one
+// receiver row to the MK packing (rows = receivers, k = n).  No shared
+// memory besides the block sum.
 
 // Block of the 16-row residual tile starting at row r0: r0 / b for equal
 // tiles, else the largest i with roff[i] <= r0 (every roff[i] is a multiple
@@ -442,100 +431,69 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
                                                int b, char* const* __restrict__ kn, char* const* __restrict__ mk,
                                                double* __restrict__ part, const long long* __restrict__ roff,
                                                int nblk, int fmt, int gx, long long ntiles) {
-    __shared__ float2 s[TP_K * TP_LD];
     __shared__ double sh[32];
     constexpr int plane = 128 * 16 * 2;
     const float a = alpha ? (float)alpha[0] : 0.f;
     const float a2 = alpha ? (float)(alpha[0] * alpha[0]) : 0.f;
+    const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
+    const int nkcN = (ns + 15) >> 4;
     // tile tt = (rows (tt / gx) * 16 .., columns (tt % gx) * 128 ..): a capped
     // grid walks them in launch order; tile tt's partial of ||R||^2 is part[tt]
     for (long long tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const int n0 = (int)(tt % gx) * TP_N, r0 = (int)(tt / gx) * TP_K;
         const RTile tl = rtile(r0, b, roff, nblk);
         const int blk = tl.blk, rl0 = tl.rl0, bK = tl.bK;
+        const bool nv = n0 + n < ns;
         Acc acc;
+        float2 r[8];
         if (alpha) {
-            // the step: the tile's current values from its own KN packing (one
-            // 16-deep packed tile; thread = (n, k-group of 8)), then A1, A2
-            const int n = threadIdx.x & (TP_N - 1), kg = threadIdx.x >> 7;
-            const bool nv = n0 + n < ns;
-            float2 v[8];
+            // the step: the thread's 8 values from the tile's KN packing (one
+            // 16-deep packed tile), then A1, A2
             pk_load8(kn[blk] + ((long long)(n0 >> 7) * (bK >> 4) + (rl0 >> 4)) * 4 * plane + row_off(fmt, n), fmt,
-                     kg, v);
+                     kg, r);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int kk = kg * 8 + j;
-                float2 r = v[j];
                 if (nv) {
                     if (a != 0.f) {
-                        const long long o = (long long)(r0 + kk) * ns + n0 + n;
+                        const long long o = (long long)(r0 + kg * 8 + j) * ns + n0 + n;
                         const float2 u = A1[o], w = A2[o];
-                        r.x = fmaf(a2, w.x, fmaf(a, u.x, r.x));
-                        r.y = fmaf(a2, w.y, fmaf(a, u.y, r.y));
+                        r[j].x = fmaf(a2, w.x, fmaf(a, u.x, r[j].x));
+                        r[j].y = fmaf(a2, w.y, fmaf(a, u.y, r[j].y));
                     }
-                    acc.add(fmaf(r.x, r.x, r.y * r.y));
+                    acc.add(fmaf(r[j].x, r[j].x, r[j].y * r[j].y));
                 }
-                s[kk * TP_LD + n] = r;
             }
         } else {
             // packing only (after a forward product): the FP32 rows of R
-            const int n = threadIdx.x & (TP_N - 1), kq = threadIdx.x >> 7;
-            const bool nv = n0 + n < ns;
-#pragma unroll 1
-            for (int kb = kq; kb < TP_K; kb += 8) {
-                float2 r[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    r[q] = make_float2(0.f, 0.f);
-                    if (nv) r[q] = R[(long long)(r0 + kb + 2 * q) * ns + n0 + n];
-                }
+            for (int j = 0; j < 8; ++j)
+                r[j] = nv ? R[(long long)(r0 + kg * 8 + j) * ns + n0 + n] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int kk = kb + 2 * q;
-                    if (nv) acc.add(fmaf(r[q].x, r[q].x, r[q].y * r[q].y));
-                    s[kk * TP_LD + n] = r[q];
-                }
-            }
+            for (int j = 0; j < 8; ++j)
+                if (nv) acc.add(fmaf(r[j].x, r[j].x, r[j].y * r[j].y));
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!nv) r[j] = make_float2(0.f, 0.f);
         if (part) {
-            const double t = block_sum(acc.val(), sh);   // includes the __syncthreads phase 2 needs
+            const double t = block_sum(acc.val(), sh);
             if (threadIdx.x == 0) part[tt] = t;
-        } else {
-            __syncthreads();
         }
-        // phase 2: MK, rows = receivers of block blk, k = n
-        {
-            const int nkcN = (ns + 15) >> 4;
-            char* const base = mk[blk];
-            for (int it = threadIdx.x; it < TP_K * (TP_N / 8); it += blockDim.x) {
-                const int kk = it & (TP_K - 1), ng = it >> TP_KS;
-                const int nb = n0 + ng * 8;
-                if (nb >= ns) continue;
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = nb + j < ns ? s[kk * TP_LD + ng * 8 + j] : make_float2(0.f, 0.f);
-                const int rl = rl0 + kk;
-                char* dst = base + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + row_off(fmt, rl & 127);
-                pk_store8(dst, fmt, (nb >> 3) & 1, v, 1.f);
-            }
+        // KN: rows = n, k = receiver of block blk (this thread's own 8 values)
+        if (nv) {
+            const int nn = n0 + n, k = rl0 + kg * 8;
+            char* dst = kn[blk] + ((long long)(nn >> 7) * (bK >> 4) + (k >> 4)) * 4 * plane + row_off(fmt, nn & 127);
+            pk_store8(dst, fmt, (k >> 3) & 1, r, 1.f);
         }
-        // phase 3: KN, rows = n, k = receiver of block blk
-        {
-            const int nkcK = bK >> 4;
-            char* const base = kn[blk];
-            for (int it = threadIdx.x; it < TP_N * (TP_K / 8); it += blockDim.x) {
-                const int n = it & (TP_N - 1), kg = it >> 7;
-                const int nn = n0 + n;
-                if (nn >= ns) continue;
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = s[(kg * 8 + j) * TP_LD + n];
-                const int k = rl0 + kg * 8;
-                char* dst = base + ((long long)(nn >> 7) * nkcK + (k >> 4)) * 4 * plane + row_off(fmt, nn & 127);
-                pk_store8(dst, fmt, (k >> 3) & 1, v, 1.f);
-            }
+        // MK: rows = receivers of block blk, k = n.  After the transpose lane
+        // i of a group holds receiver row kg * 8 + i at the group's 8 columns.
+        transpose8(r);
+        const int nb = n0 + (n & ~7);
+        if (nb < ns) {
+            const int rl = rl0 + kg * 8 + (threadIdx.x & 7);
+            char* dst = mk[blk] + ((long long)(rl >> 7) * nkcN + (nb >> 4)) * 4 * plane + row_off(fmt, rl & 127);
+            pk_store8(dst, fmt, (nb >> 3) & 1, r, 1.f);
         }
-        __syncthreads();   // s is rewritten for the next tile
     }
 }
 
@@ -545,7 +503,7 @@ __global__ void __launch_bounds__(256) k_rstep(cf* __restrict__ R, const cf* __r
 // and A1, A2 in FP32; products of four elements summed in FP32 before each
 // compensated add.  A fixed grid walks the tiles in a fixed order and leaves
 // one partial per dot and CTA (few partials for the one-block finaliser).
-__global__ void __maxnreg__(56) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
+__global__ void __maxnreg__(48) k_dots6p(char* const* __restrict__ kn, const cf* __restrict__ A1,
                                                 const cf* __restrict__ A2, int ns, int nr, int b,
                                                 const long long* __restrict__ roff, int nblk,
                                                 double* __restrict__ part, int fmt) {
@@ -697,7 +655,7 @@ __device__ __forceinline__ void epi_drain(const PProb& P, int m0, int n0, long l
 // launch order (mfast): the CTAs that read the same B tile (all M tiles of an
 // N tile) run together and the later ones find it in L2; (N, M, ...) when
 // the N tiles exceed the grid's y limit.
-__global__ void __launch_bounds__(NTHR, CTAS_PER_SM) k_cgemm_tcp(const PProb* __restrict__ probs,
+__global__ void __launch_bounds__(NTHR, CTAS_PER_SM + 1) k_cgemm_tcp(const PProb* __restrict__ probs,
                                                        const ZItem* __restrict__ zmap, int nsplit, int kchunk,
                                                        int epi, long long part_stride, int* err, int fmt,
                                                        int mfast) {
