@@ -166,9 +166,9 @@ def measured_peaks():
 # capture of the sources whose SHA-256 is GEMM_TRAFFIC_SHA.  A change to any of
 # those sources, another rank mix or another tile voids the figures (traffic null).
 GEMM_TRAFFIC_SOURCES = ("k_gemm_tcp.cu", "api.cu", "internal.h")
-GEMM_TRAFFIC_SHA = "5f1c2b0b86e5f57b4183064acb2e466fe940878e713d56325270af06c9a5d0ef"
+GEMM_TRAFFIC_SHA = "e581fcb16358b17cf51da7bbe9389e1ba4ced8619b74d2b3ae55e566bada001a"
 GEMM_TRAFFIC_CASE = {"nr": 9216, "tile": 384, "ranks": [8, 15, 22, 29, 36, 43, 50, 57], "precision": "bf16x3"}
-GEMM_TRAFFIC_BYTES = {"cgemm_compress": 2098328847, "cgemm_expand": 4448126664, "cgemm_project": 4657551388}
+GEMM_TRAFFIC_BYTES = {"cgemm_compress": 2098697744, "cgemm_expand": 4456706142, "cgemm_project": 4685540407}
 
 
 def gemm_traffic(kernel, nr, tile, step_ranks, precision):
@@ -695,7 +695,9 @@ def main():
         torch.cuda.empty_cache()
         T.tlr_mdd_trim_pool(0)
         loads = [float(x) for x in args.serving_fp32_loads.split(",") if x.strip()]
-        serve = serving_leg(T, torch, args.serving, args.seed, dev, loads, multi_ctas)
+        # the server's slots run the passes uncapped: with one CTA per SM the
+        # served rate fell (9.9 against 11.5 solves/s at the same arrivals)
+        serve = serving_leg(T, torch, args.serving, args.seed, dev, loads, 0)
         log("serving leg done")
 
     if rank != 0:
@@ -917,14 +919,21 @@ def secondary_leg(T, torch, args, dev):
     step()          # plain launches (a handle's first solve)
     step()          # records the solve graphs
     ms = sum(step() for _ in range(args.secondary))
-    # the same step on every 8th frequency, tensor cores and the FP32 SIMT path
+    # the same step on every 8th frequency, tensor cores and the FP32 SIMT
+    # path, on handles of their own (8 solves on the streams overlap little:
+    # the pass grid is left uncapped; a recorded graph keeps the grid it was
+    # recorded with)
     sub = freqs[::8]
-    ms_tc_sub = step(fs=sub)
-    hs32 = {f: T.tlr_mdd_create(inp.desc(T, f, T.TLR_PREC_FP32), inp.D[f], inp.U[f], streams[f % nst]) for f in sub}
-    step(hs32, sub)
-    step(hs32, sub)
-    ms_fp32_sub = step(hs32, sub)
-    for h in list(hs) + list(hs32.values()):
+    prev_cap = T.tlr_mdd_set_pass_ctas(0)
+    hs_sub = {}
+    for prec in (T.TLR_PREC_BF16X3, T.TLR_PREC_FP32):
+        hs_sub[prec] = {f: T.tlr_mdd_create(inp.desc(T, f, prec), inp.D[f], inp.U[f], streams[f % nst]) for f in sub}
+        step(hs_sub[prec], sub)     # plain launches
+        step(hs_sub[prec], sub)     # records the graphs
+    ms_tc_sub = step(hs_sub[T.TLR_PREC_BF16X3], sub)
+    ms_fp32_sub = step(hs_sub[T.TLR_PREC_FP32], sub)
+    T.tlr_mdd_set_pass_ctas(prev_cap)
+    for h in list(hs) + [h for d in hs_sub.values() for h in d.values()]:
         T.tlr_mdd_destroy(h)
     fl = sum(flops_per_solve(wl.nr, wl.nr, wl.tile, k) for k in ranks) * args.secondary
     oracle_cpu = None
