@@ -210,3 +210,14 @@ def test_noalloc_wrapper_rejects_bad_buffers_before_the_call():
     with pytest.raises(T.TLRError) as ei:
         T.tlr_mdd_adjoint_noalloc(ok_v, ok_v, 0, ns, ok_g)
     assert ei.value.code == T.TLR_ERR_SHAPE
+
+
+def test_pass_cta_cap_is_set_and_restored_without_a_gpu():
+    # the cap is host state: setting it launches nothing
+    _lib()
+    prev = T.tlr_mdd_set_pass_ctas(37)
+    assert prev >= 0
+    assert T.tlr_mdd_set_pass_ctas(0) == 37
+    with pytest.raises(T.TLRError):
+        T.tlr_mdd_set_pass_ctas(-1)
+    assert T.tlr_mdd_set_pass_ctas(prev) == 0
