@@ -966,9 +966,11 @@ def secondary_leg(T, torch, args, dev):
 
     kx = 26
     common = dict(rank=kx, nx=wl.grid[0], ny=wl.grid[1], diag_mode=T.TLR_DIAG_RULE, precision=T.TLR_PREC_BF16X3)
+    prev_cap = T.tlr_mdd_set_pass_ctas(0)   # one solve on one stream: a CTA per tile
     gst, gn = one_solve(T.desc(wl.nr, wl.nr, wl.tile, reciprocity=T.TLR_RECIP_NONE, **common), args.seed + 5)
     tst, tn = one_solve(T.desc(wl.nr, wl.nr, 0, tiles=[192, 320] * 8, **common), args.seed + 6)
     ust, un = one_solve(T.desc(wl.nr, wl.nr, wl.nr // 16, **common), args.seed + 6)
+    T.tlr_mdd_set_pass_ctas(prev_cap)
     f_eq = flops_per_solve(wl.nr, wl.nr, wl.tile, kx)
     return {"workload": wl.name, "value": round(wl.nfreq * args.secondary / (ms / 1e3), 3),
             "unit": "freq-solves/s", "ms_per_step": round(ms / args.secondary, 1), "steps": args.secondary,
