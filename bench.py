@@ -1061,11 +1061,23 @@ def serving_leg(T, torch, n, seed, dev, fp32_loads=(), multi_ctas=0):
     pcb = serving.percentiles(resb)
     sameb = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, resb))
     srvb.close()
+    # and with batch partners of any size
+    srvm = serving.Server(budget, max_active=4, batch_max=4, mix_sizes=True)
+    t0 = time.perf_counter()
+    resm = srvm.run(make(T.TLR_PREC_BF16X3, arrivals), realtime=True)
+    t_m = time.perf_counter() - t0
+    pcm = serving.percentiles(resm)
+    samem = all(a.status == 0 and b.status == 0 and torch.equal(a.theta, b.theta) for a, b in zip(res_tc1, resm))
+    srvm.close()
     batched = {"tc_served_solves_per_s": round(sum(1 for r in resb if r.status == 0) / t_b, 3),
                "p50_ms": round(1e3 * pcb[50], 1) if pcb[50] else None,
                "p99_ms": round(1e3 * pcb[99], 1) if pcb[99] else None,
                "batches": srvb.batches, "results_identical_alone_and_in_batches": bool(sameb),
-               "note": "same arrivals; requests of one size admitted together share one launch per contraction"}
+               "note": "same arrivals; requests of one size admitted together share one launch per contraction",
+               "any_size": {"tc_served_solves_per_s": round(sum(1 for r in resm if r.status == 0) / t_m, 3),
+                            "p50_ms": round(1e3 * pcm[50], 1) if pcm[50] else None,
+                            "p99_ms": round(1e3 * pcm[99], 1) if pcm[99] else None,
+                            "batches": srvm.batches, "results_identical_alone_and_in_batches": bool(samem)}}
     # the stream at loads relative to the FP32 path's one-at-a-time capacity
     # (a load above 1 is one the FP32 path alone cannot carry)
     at_fp32_loads = []

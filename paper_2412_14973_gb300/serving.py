@@ -83,13 +83,17 @@ def shape_key(d):
 
 class Server:
     def __init__(self, hbm_budget_bytes: int, max_active: int = 8, device=None, poll_s: float = 2e-4,
-                 stream_factory=None, reuse: bool = True, batch_max: int = 1, window: int = 32):
+                 stream_factory=None, reuse: bool = True, batch_max: int = 1, window: int = 32,
+                 mix_sizes: bool = False):
         self.budget = int(hbm_budget_bytes)
         self.max_active = max(1, int(max_active))
         self.poll_s = poll_s
         self.reuse = reuse
         self.batch_max = max(1, int(batch_max))   # requests per lockstep batch (1: one per slot)
         self.window = window                      # queued requests scanned for batch partners
+        # batch partners of any size (each contraction launch then walks the
+        # tiles of problems of several sizes) instead of the head's size only
+        self.mix_sizes = bool(mix_sizes)
         self.batches = 0
         if stream_factory is None:
             dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -145,16 +149,22 @@ class Server:
 
     def _group(self, queue, realtime, now):
         """The head request and, when batching, later arrived requests of the
-        same size, precision and solver options (lockstep solves end together)."""
+        same precision and solver options (lockstep solves end together) and,
+        unless ``mix_sizes``, the same size."""
         head = queue[0]
         group = [head]
         if self.batch_max <= 1 or getattr(head.desc, "precision", 0) == T.TLR_PREC_FP32:
             return group
-        hk = (getattr(head.desc, "nr", None), getattr(head.desc, "precision", None), _opts_key(head.opts))
+
+        def key(r):
+            nr = None if self.mix_sizes else getattr(r.desc, "nr", None)
+            return (nr, getattr(r.desc, "precision", None), _opts_key(r.opts))
+
+        hk = key(head)
         for r in list(queue)[1:self.window]:
             if len(group) >= self.batch_max or (realtime and r.arrival > now):
                 break
-            if (getattr(r.desc, "nr", None), getattr(r.desc, "precision", None), _opts_key(r.opts)) == hk:
+            if key(r) == hk:
                 group.append(r)
         return group
 

@@ -76,13 +76,13 @@ def test_poisson_arrivals_latency_accounting():
     assert p[50] <= p[99]
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_batched_server_results_identical_to_alone(prec):
-    # same-size requests admitted together run as one lockstep batch (one
-    # launch per contraction over all their tiles); results are bitwise those
-    # of the requests solved one at a time
+@pytest.mark.parametrize("prec,mix", [(1, False), (2, False), (1, True)])
+def test_batched_server_results_identical_to_alone(prec, mix):
+    # requests admitted together (of one size, or of any size with mix)
+    # run as one lockstep batch (one launch per contraction over all their
+    # tiles); results are bitwise those of the requests solved one at a time
     alone = serving.Server(1 << 36, max_active=1, reuse=False).run(_requests(prec), realtime=False)
-    srv = serving.Server(1 << 36, max_active=2, batch_max=4)
+    srv = serving.Server(1 << 36, max_active=2, batch_max=4, mix_sizes=mix)
     out = srv.run(_requests(prec), realtime=False)
     assert srv.batches >= 2
     for a, m in zip(alone, out):

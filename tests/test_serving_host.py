@@ -216,3 +216,18 @@ def test_batch_members_respect_the_budget(fake, monkeypatch):
     out = srv.run(reqs, realtime=False)
     assert [r.status for r in out] == [0] * 4
     assert max(len(b.handles) for b in FakeBatch.made) == 2 and srv.peak_used <= 100
+
+
+def test_mixed_size_batches_take_any_size_of_one_precision(fake, monkeypatch):
+    fake({})
+    monkeypatch.setattr(serving.T, "tlr_mdd_workspace_bytes", lambda d: 10)
+    monkeypatch.setattr(serving.T, "Batch", FakeBatch)
+    FakeBatch.made = []
+    reqs = [_sreq(0, 1024, "a"), _sreq(1, 2048, "b"), _sreq(2, 4096, "c"), _sreq(3, 1024, "d", prec=0),
+            _sreq(4, 8192, "e")]
+    srv = serving.Server(1000, max_active=1, stream_factory=object, poll_s=0, batch_max=4, mix_sizes=True)
+    out = srv.run(reqs, realtime=False)
+    assert [r.status for r in out] == [0] * 5
+    # the four tensor-core requests of four sizes in one batch; the FP32 one alone
+    assert [len(b.handles) for b in FakeBatch.made] == [4] and srv.batches == 1
+    srv.close()
