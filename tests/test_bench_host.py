@@ -13,3 +13,26 @@ def test_clock_rules():
     # a clock held far below its maximum with no reason: a leftover lock
     assert "no reason" in bench.clock_problem({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": []})
     assert bench.clock_problem({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}) is None
+
+
+def test_traffic_figures_apply_only_to_the_captured_case():
+    case = bench.GEMM_TRAFFIC_CASE
+    got = bench.gemm_traffic("cgemm_expand", case["nr"], case["tile"], case["ranks"], case["precision"])
+    # the committed sources either hash to the capture (a figure) or not (null)
+    assert got is None or got == bench.GEMM_TRAFFIC_BYTES["cgemm_expand"]
+    assert bench.gemm_traffic("cgemm_expand", case["nr"], case["tile"], case["ranks"][:-1],
+                              case["precision"]) is None
+    assert bench.gemm_traffic("cgemm_expand", case["nr"], 256, case["ranks"], case["precision"]) is None
+    assert bench.gemm_traffic("cgemm_expand", case["nr"], case["tile"], case["ranks"], "fp32") is None
+
+
+def test_rank_schedule_and_step_batches():
+    wl = bench.PRECISION_FORM
+    ranks = wl.ranks(wl.nfreq)
+    assert ranks[0] == wl.rank_lo and ranks[-1] == wl.rank_hi and len(ranks) == 128
+    assert all(b >= a for a, b in zip(ranks, ranks[1:]))
+    from paper_2412_14973_gb300 import sharding
+    steps = sharding.batches(sharding.frequency_plan(wl.nfreq, 0, 1), wl.batch)
+    assert len(steps) == 16 and sorted(f for s in steps for f in s) == list(range(128))
+    # every step spans the rank range (the captured traffic case is the first step)
+    assert [ranks[f] for f in steps[0]] == bench.GEMM_TRAFFIC_CASE["ranks"]
