@@ -1,6 +1,8 @@
 """Multi-process path of the benchmark on CPU (gloo, world size 2): the rank
 logic bench.py runs (frequency plan, steps, max-over-ranks timing, gather of
-the per-frequency results on rank 0) and its own start of N ranks."""
+the per-frequency results on rank 0), its own start of N ranks, and failure
+detection on the host: a rank that leaves between steps or never joins ends
+the others' next collective or rendezvous with an error, not a hang."""
 import os
 import socket
 import sys
@@ -116,3 +118,69 @@ def test_bench_starts_its_own_ranks(monkeypatch):
         assert env["RANK"] == str(r) and env["LOCAL_RANK"] == str(r) and env["WORLD_SIZE"] == "3"
         assert env["MASTER_ADDR"] == "127.0.0.1"
         assert cmd[1].endswith("bench.py") and cmd[2:] == ["--gpus", "3", "--steps", "2"]
+
+
+def _failing_worker(rank, world, port, out):
+    # rank 1 leaves between steps (after joining, before the gather); rank 0
+    # must learn it from its collective (an error or its short timeout), not hang
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)
+    try:
+        gather_results([{"freq": 0}], dist)
+        out[rank] = "no error"
+    except Exception as e:  # a lost peer surfaces as a backend error
+        out[rank] = "error: " + type(e).__name__
+
+
+def test_a_rank_that_leaves_is_detected_by_the_others():
+    import time
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, out)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung after its peer left"
+    assert procs[1].exitcode == 3
+    assert out.get(0, "").startswith("error"), out.get(0)
+    assert time.time() - t0 < 120
+
+
+def _lonely_worker(port, out):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    try:
+        dist.init_process_group("gloo", rank=0, world_size=2, timeout=datetime.timedelta(seconds=5))
+        gather_results([{"freq": 0}], dist)
+        out[0] = "no error"
+    except Exception as e:  # the peer never joined: the rendezvous times out
+        out[0] = "error: " + type(e).__name__
+
+
+def test_a_rank_that_never_joins_ends_the_rendezvous_with_an_error():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    p = ctx.Process(target=_lonely_worker, args=(_free_port(), out))
+    p.start()
+    p.join(120)
+    if p.is_alive():
+        p.kill()
+        pytest.fail("the lone rank hung")
+    assert out.get(0, "").startswith("error"), out.get(0)
