@@ -18,6 +18,12 @@ D, U), so its admission allocates nothing and records nothing.  Idle cached
 handles count against the budget and are destroyed, least recently used
 first, when an admission needs their memory.
 
+A queued request can be withdrawn (``Server.cancel``, from any thread) or
+carry an admission deadline (``SolveRequest.deadline``, seconds after its
+arrival); either ends it before admission with status ``CANCELLED`` or
+``EXPIRED`` (server codes outside the library's TLR_ERR_* range).  An
+admitted solve always runs to its end: its launch sequence is on the GPU.
+
 Only host-side scheduling lives here; every computation is in the CUDA
 library.  Results do not depend on what else is running: the library's
 reductions have a fixed order, so a request gives the same bits alone and in
@@ -27,12 +33,18 @@ from __future__ import annotations
 
 import collections
 import json
+import threading
 import time
 from dataclasses import dataclass, field
 
 import torch
 
 from . import tlr_mdd as T
+
+
+# statuses the server itself gives (the library's codes are -1 .. -8)
+CANCELLED = -101   # withdrawn while queued
+EXPIRED = -102     # not admitted within its deadline
 
 
 @dataclass
@@ -44,6 +56,7 @@ class SolveRequest:
     U: torch.Tensor
     theta0: torch.Tensor        # complex64 start point, on the device
     opts: T.SolveOpts = field(default_factory=T.solve_opts)
+    deadline: float | None = None   # seconds after arrival by which it must be admitted
 
 
 @dataclass
@@ -106,6 +119,37 @@ class Server:
         self.created = 0
         self.reused = 0
         self.evicted = 0
+        self._cancelled = set()   # request ids withdrawn by cancel()
+        self._cancel_lock = threading.Lock()
+
+    def cancel(self, rid) -> None:
+        """Withdraw request ``rid`` of the current or next ``run`` if it is
+        still queued (safe to call from another thread while ``run`` serves;
+        an admitted request finishes, and ``run`` forgets such cancels when
+        it returns)."""
+        with self._cancel_lock:
+            self._cancelled.add(rid)
+
+    def _drop_withdrawn(self, queue, out, now) -> bool:
+        """End the queued requests that were cancelled or whose admission
+        deadline has passed; True if any."""
+        with self._cancel_lock:
+            cancelled = set(self._cancelled)
+        dropped = False
+        for r in list(queue):
+            if r.rid in cancelled:
+                queue.remove(r)
+                with self._cancel_lock:
+                    self._cancelled.discard(r.rid)
+                out.append(SolveResult(r.rid, None, CANCELLED, "cancelled before admission", r.arrival, now, now,
+                                       0.0, 0))
+                dropped = True
+            elif r.deadline is not None and now - r.arrival > r.deadline:
+                queue.remove(r)
+                out.append(SolveResult(r.rid, None, EXPIRED, "admission deadline passed", r.arrival, now, now,
+                                       0.0, 0))
+                dropped = True
+        return dropped
 
     def footprint(self, req: SolveRequest) -> int:
         return T.tlr_mdd_workspace_bytes(req.desc)
@@ -178,7 +222,7 @@ class Server:
         t0 = time.perf_counter()
         while queue or active:
             now = time.perf_counter() - t0
-            progressed = False
+            progressed = self._drop_withdrawn(queue, out, now)
             while queue and free and (not realtime or queue[0].arrival <= now):
                 members = []
                 blocked = False
@@ -229,6 +273,8 @@ class Server:
                     time.sleep(max(0.0, min(queue[0].arrival - (time.perf_counter() - t0), 0.01)))
                 else:
                     time.sleep(self.poll_s)
+        with self._cancel_lock:
+            self._cancelled.clear()   # cancels of requests that were already admitted
         return sorted(out, key=lambda r: r.rid)
 
     def _start(self, members, stream, out, now):

@@ -231,3 +231,41 @@ def test_mixed_size_batches_take_any_size_of_one_precision(fake, monkeypatch):
     # the four tensor-core requests of four sizes in one batch; the FP32 one alone
     assert [len(b.handles) for b in FakeBatch.made] == [4] and srv.batches == 1
     srv.close()
+
+
+def test_cancelled_requests_end_before_admission(fake):
+    f = fake({"a": 60, "b": 60, "c": 60})
+    srv = serving.Server(100, max_active=2, stream_factory=object, poll_s=0)
+    srv.cancel(1)          # withdrawn before the run serves it; "a" holds the memory meanwhile
+    out = srv.run([_req(0, "a"), _req(1, "b"), _req(2, "c")], realtime=False)
+    assert [r.status for r in out] == [0, serving.CANCELLED, 0]
+    assert out[1].theta is None and out[1].message.startswith("cancelled")
+    assert f.order == ["a", "c"]
+    # the cancel was consumed: the same id is served on the next run
+    out2 = srv.run([_req(1, "b")], realtime=False)
+    assert out2[0].status == 0
+    srv.close()
+
+
+def test_cancel_from_another_thread_while_serving(fake):
+    import threading
+    fake({"a": 60, "b": 60}, polls=200)
+    srv = serving.Server(100, max_active=1, stream_factory=object, poll_s=1e-4)
+    t = threading.Timer(0.005, srv.cancel, args=(1,))
+    t.start()
+    out = srv.run([_req(0, "a"), _req(1, "b")], realtime=False)
+    t.join()
+    assert out[0].status == 0 and out[1].status == serving.CANCELLED
+    srv.close()
+
+
+def test_admission_deadline_expires_queued_requests(fake):
+    f = fake({"a": 60, "b": 60, "c": 60}, polls=400)
+    reqs = [_req(0, "a"), _req(1, "b"), _req(2, "c")]
+    reqs[1].deadline = 0.002    # "a" holds the memory for ~40 ms, so "b" expires in the queue
+    reqs[2].deadline = 60.0     # plenty of time
+    srv = serving.Server(100, max_active=2, stream_factory=object, poll_s=1e-4)
+    out = srv.run(reqs, realtime=True)
+    assert [r.status for r in out] == [0, serving.EXPIRED, 0]
+    assert f.order == ["a", "c"]
+    srv.close()
