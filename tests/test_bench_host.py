@@ -36,3 +36,23 @@ def test_rank_schedule_and_step_batches():
     assert len(steps) == 16 and sorted(f for s in steps for f in s) == list(range(128))
     # every step spans the rank range (the captured traffic case is the first step)
     assert [ranks[f] for f in steps[0]] == bench.GEMM_TRAFFIC_CASE["ranks"]
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the oracle as the reference arm: one bounded sample step, on the host
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--oracle-cols", "64"], capture_output=True, text=True, timeout=600,
+                       cwd=root)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "freq-solves/s" and d["unit"] == "freq-solves/s"
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
